@@ -1,0 +1,292 @@
+#!/usr/bin/env python
+"""GoDec-BRP benchmark: iterations/s and HBM roofline on the 10000 x 10000, r = 50,
+q = 2, k = 1e6 float32 workload (synthetic, seeded).
+
+A step is one iteration of Algorithm 1 (all passes of the L-step, the S-step
+and the update of X - S).  The timed region runs K iterations from S = 0 with
+X resident in HBM (X and X - S are 400 MB each, above the 129 MB L2, so no
+flush is needed between iterations).  Multi-GPU runs are independent replicas
+(one problem per rank, no collective on the data path): weak scaling.
+
+--impl reference times the float64 CPU oracle on a bounded row sample of the
+same workload and scales it to the full workload's iterations/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] if os.path.exists(
+    os.path.join(ROOT, "BASELINE.json")) else "GoDec-BRP iterations/s"
+UNIT = "iterations/s"
+M = N = 10000
+R, K_CARD, Q = 50, 1000000, 2
+WORKLOAD = ("plain GoDec-BRP float32, X = U V^T + S + G, m = n = 10000, rank-50 N(0,1) factors, "
+            "1% sparse U[-20,20], noise sigma 1e-2; r = 50, k = 1e6, q = 2, iterations from S = 0")
+SAMPLE_ROWS = 1000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        under_load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(under_load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def pass_traffic():
+    """DRAM bytes per launch of the streaming product from a committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1309_0302_gb300", "csrc", "k_stream.cu")
+    p = os.path.join(ROOT, "profiles", "product_pass_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d.get("dram_bytes_per_launch") if d.get("source_sha") == h else None
+
+
+def oracle_rate(iters: int, seed: int = 1309):
+    """float64 oracle on the first SAMPLE_ROWS rows of the workload (same n, r, q, density);
+    returns full-workload iterations/s (cost scales linearly with m at fixed n, r)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    d = synth.lowrank_sparse(SAMPLE_ROWS, N, R, int(K_CARD * SAMPLE_ROWS / M), -20.0, 20.0, 1e-2, seed, "c2")
+    X, A1 = d["X"].astype(np.float64), d["A1"].astype(np.float64)
+    k = int(K_CARD * SAMPLE_ROWS / M)
+    S_idx, S_val = np.zeros(0, np.int64), np.zeros(0)
+    times = []
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        st = oracle.godec_step(X, A1, S_idx, S_val, k, Q)
+        times.append(time.perf_counter() - t0)
+        S_idx, S_val = st["S_idx"], st["S_val"]
+    per_iter = sum(times) / len(times)
+    return (SAMPLE_ROWS / M) / per_iter, times, os.cpu_count()
+
+
+def emit(line: dict):
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    warm = min(args.warmup, 1)
+    oracle_rate(warm) if warm else None
+    rate, times, cores = oracle_rate(args.steps)
+    emit({"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": warm, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
+          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "m": M, "n": N, "r": R, "k": K_CARD, "q": Q},
+          "cpu_baseline": {"kind": "oracle", "cores": cores, "value": rate, "unit": UNIT,
+                           "sample": f"each step: one float64 oracle iteration on the first {SAMPLE_ROWS} rows "
+                                     f"(n, r, q and density unchanged), time scaled by m/{SAMPLE_ROWS}"},
+          "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+def run_gb300(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    d = synth.lowrank_sparse(M, N, R, K_CARD, -20.0, 20.0, 1e-2, 1309 + rank, "c2")
+    X = torch.from_numpy(d["X"]).cuda()
+    A1 = torch.from_numpy(d["A1"]).cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = G.GoDec(X, A1, R, K_CARD, Q, tol=1e-7, max_iter=args.steps, stream=stream)
+        g.iterate(max(1, args.warmup))          # warm-up iterations; captures the graph
+        g.reset()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rel = g.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        info = g.info()
+        # per-kernel device times of the same iterations (eager launches bracketed by events)
+        g.reset()
+        prof = g.profile(args.steps)
+        g.close()
+    value = ws * args.steps / (ms / 1000.0)
+    npass = prof["launches"]["product"]
+    pass_ms = prof["ms"]["product"] / max(npass, 1)
+    achieved = prof["bytes_product"] / (pass_ms / 1000.0) / 1e9
+    peak, peak_src = peaks()
+    passes_per_iter = npass / args.steps
+    # algorithmic bytes of one iteration: every streaming product reads X - S once, the
+    # S-step pass reads X once (plus one more per extra selection pass), factors and S
+    bytes_iter = 4.0 * M * N * (passes_per_iter + prof["launches"]["residual"] / args.steps) \
+        + 12.0 * K_CARD * 2 + 4.0 * (M + N) * R * passes_per_iter
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "r": R, "k": K_CARD, "q": Q,
+                   "iterations": args.steps, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (X and X - S are 400 MB each); no flush"},
+        "rel_err": rel,
+        "roofline": {"bound": "hbm", "kernel": "streaming product over X - S", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": pass_traffic(),
+                     "peak_source": peak_src, "avg_launch_ms": pass_ms,
+                     "bytes_per_launch": prof["bytes_product"]},
+        "iteration_roofline": {"achieved": bytes_iter * (value / ws) / 1e9, "unit": "GB/s",
+                               "frac": bytes_iter * (value / ws) / 1e9 / peak,
+                               "bytes_per_iter": bytes_iter},
+        "kernel_ms_per_iter": {k: v / args.steps for k, v in prof["ms"].items()},
+        "clocks": ck,
+        "gpu_launches": int(info["launches_per_iter"]) * args.steps,
+    }
+    if not args.no_e2e:
+        line["e2e"] = e2e(args, d)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, times, cores = oracle_rate(5)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"5 float64 oracle iterations from S = 0 on the first {SAMPLE_ROWS} "
+                                          f"rows (n, r, q and density unchanged), time scaled by m/{SAMPLE_ROWS}"}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        emit(line)
+
+
+def e2e(args, d):
+    """Same metric through godec_run_host: pinned host X and A1 in, L factors and S out,
+    all copies and allocations inside the timed call."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    Xh = torch.empty((M, N), dtype=torch.float32).pin_memory()
+    Xh.numpy()[:] = d["X"]
+    Ah = torch.from_numpy(d["A1"]).pin_memory()
+    out = {"U": torch.empty((M, R)).pin_memory().numpy(), "V": torch.empty((N, R)).pin_memory().numpy(),
+           "sigma": np.empty(R, np.float32), "S_idx": torch.empty(K_CARD, dtype=torch.int64).pin_memory().numpy(),
+           "S_val": torch.empty(K_CARD, dtype=torch.float32).pin_memory().numpy()}
+    G.run_host(Xh.numpy(), Ah.numpy(), R, K_CARD, Q, 1, out=out)          # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.run_host(Xh.numpy(), Ah.numpy(), R, K_CARD, Q, args.steps, out=out)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = 4.0 * M * N + 4.0 * N * R
+    d2h = 4.0 * (M + N) * R + 4.0 * R + 12.0 * K_CARD
+    return {"value": args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+            "d2h_bytes_per_step": d2h / args.steps,
+            "note": "one godec_run_host call per measurement: H2D of X and A1, K iterations, D2H of L "
+                    "factors and sorted S; bytes per step = bytes per call / K"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gb300(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

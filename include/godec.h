@@ -1,0 +1,225 @@
+/*
+ * godec.h - C ABI of the GB300 (sm_103a) GoDec-BRP library.
+ *
+ * GoDec (Zhou & Tao, arXiv:1309.0302) splits a dense m x n matrix X into a
+ * rank-r part L, a part S with at most k nonzeros and noise G (Sec. 2, eq.
+ * GoDecMODEL), minimising ||X - L - S||_F^2 (eq. ls_app) by alternating an
+ * L-step and an S-step (eq. raw_ls).  This library runs Algorithm 1 ("GoDec
+ * by BRP"): the L-step is the bilateral random projection with power scheme
+ * (Sec. 3.1, eqs. lr_app and mlr_app), the S-step is the entry-wise hard
+ * threshold keeping the k largest |X - L| (eq. raw_lss).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major.  "Device" pointers are CUDA global memory on the
+ *    device that is current when godec_init is called; "host" pointers are
+ *    ordinary (preferably pinned) host memory.
+ *  - Every call returns a godec_status and never throws.  After an error the
+ *    context stays usable unless the status is GODEC_ERR_STATE or
+ *    GODEC_ERR_CUDA; godec_last_error() gives a one-line reason.
+ *  - Calls on one context are not thread-safe; separate contexts are
+ *    independent.  All GPU work of a context runs on the stream passed to
+ *    godec_init (a cudaStream_t passed as void*; NULL = legacy default).
+ *  - L is never formed densely: it is returned as U diag(sigma) V^T with
+ *    U (m x r_eff) and V (n x r_eff) having orthonormal columns.
+ *  - S is returned as COO: int64 linear indices i*n + j in ascending order
+ *    and float32 values.
+ */
+#ifndef GODEC_H
+#define GODEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum godec_status {
+  GODEC_OK = 0,
+  GODEC_ERR_ARG = 1,         /* invalid argument (sizes, pointers, alignment) */
+  GODEC_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  GODEC_ERR_OOM = 3,         /* device or host allocation failed */
+  GODEC_ERR_NONFINITE = 4,   /* X or an intermediate holds NaN/Inf */
+  GODEC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  GODEC_ERR_STATE = 6,       /* call not valid in the context's state */
+  GODEC_ERR_UNSUPPORTED = 7  /* valid request outside the built limits */
+} godec_status;
+
+/* Arithmetic of the X-streaming products. */
+enum {
+  GODEC_PREC_FP32 = 0,        /* float32 X, float32 accumulation */
+  GODEC_PREC_BF16_REFINE = 1  /* bf16 copy of X - S for the power chain, then
+                                 one float32 correction visit (see below) */
+};
+
+/* Maximum target rank handled by the kernels. */
+#define GODEC_MAX_RANK 64
+
+typedef struct godec_params {
+  int64_t m, n;      /* X is m x n (any m, n >= 1) */
+  int64_t ldx;       /* row stride of X in elements, >= n */
+  int32_t r;         /* target rank, 1 <= r <= min(m, n, GODEC_MAX_RANK) */
+  int32_t q;         /* power-scheme exponent of eq. mlr_app, 0 <= q <= 8 */
+  int64_t k;         /* cardinality bound of S, 0 <= k <= m*n */
+  double tol;        /* epsilon of the stop test ||X-L-S||^2/||X||^2 <= tol */
+  int32_t max_iter;  /* iteration cap of godec_solve, >= 1 */
+  int32_t precision; /* GODEC_PREC_* */
+  double rank_tol;   /* relative singular-value tolerance of the rank test of
+                        Algorithm 1 (line 7); <= 0 selects 1e-4 */
+  int32_t flags;     /* GODEC_FLAG_* */
+  int32_t reserved;  /* must be 0 */
+} godec_params;
+
+/* Record per-iteration factors and supports so godec_backward can run. */
+#define GODEC_FLAG_TAPE 1
+
+typedef struct godec_ctx godec_ctx;
+
+/*
+ * Create a context for Algorithm 1 on X.
+ *   X  : device, m x ldx float32, BORROWED: it must stay valid and unchanged
+ *        until godec_destroy.  ldx*4 must be a multiple of 16 bytes.
+ *   A1 : device, n x r float32 (row-major), the random test matrix of
+ *        Algorithm 1 line 5; copied.  Reading of the paper: A1 is drawn once
+ *        by the caller (e.g. standard Gaussian) and kept for all iterations.
+ *   stream : cudaStream_t (as void*) on which all work of the context runs.
+ * The context owns its workspace (about 4*m*n bytes for the working copy of
+ * X - S, plus O((m+n)*64 + k) bytes).  S starts at 0 and t at 0.
+ * Errors: GODEC_ERR_ARG for invalid params or pointers, GODEC_ERR_OOM,
+ * GODEC_ERR_CUDA.  On error *ctx is set to NULL.
+ */
+godec_status godec_init(godec_ctx** ctx, const godec_params* params,
+                        const float* X, const float* A1, void* stream);
+
+/* Restart from S = 0, t = 0 and the initial rank; X and A1 are kept. */
+godec_status godec_reset(godec_ctx* ctx);
+
+/*
+ * Run exactly n_iter iterations of Algorithm 1 (lines 3-9), ignoring the
+ * stop test.  Each iteration: Z = X - S_{t-1}; L_t from the BRP power chain
+ * with the rank test; S_t = P_Omega(X - L_t) with Omega the nonzero subset of
+ * the k largest |X - L_t| (ties by ascending linear index).
+ * rel_err (host, nullable) receives ||X - L_t - S_t||_F^2 / ||X||_F^2 of the
+ * last iteration.  Synchronises the stream before returning.
+ * Errors: GODEC_ERR_NONFINITE if X - L holds NaN/Inf (state then reset),
+ * GODEC_ERR_CUDA.
+ */
+godec_status godec_iterate(godec_ctx* ctx, int32_t n_iter, double* rel_err);
+
+/*
+ * Algorithm 1 with its stop test: iterate until
+ * ||X - L_t - S_t||^2 / ||X||^2 <= tol or t = max_iter (a do-while: at least
+ * one iteration).  iters and rel_err (host, nullable) receive t and the last
+ * relative error.
+ */
+godec_status godec_solve(godec_ctx* ctx, int32_t* iters, double* rel_err);
+
+/*
+ * Copy the factors of L_t = U diag(sigma) V^T.
+ *   U : device, m x r_eff float32 (row stride r_eff), nullable
+ *   sigma : device, r_eff float32, descending, nullable
+ *   V : device, n x r_eff float32 (row stride r_eff), nullable
+ *   r_eff : host, receives the current rank (< r after a rank drop)
+ * Buffers must hold at least params.r columns.  GODEC_ERR_STATE before the
+ * first iteration.
+ */
+godec_status godec_get_L(godec_ctx* ctx, float* U, float* sigma, float* V, int32_t* r_eff);
+
+/*
+ * Copy S_t as COO sorted by ascending linear index i*n + j.
+ *   idx : device int64[cap], val : device float32[cap] (both nullable when
+ *   cap = 0), nnz : host, receives |Omega| (<= k).
+ * GODEC_ERR_ARG if cap < nnz (nnz is still written).
+ */
+godec_status godec_get_S(godec_ctx* ctx, int64_t* idx, float* val, int64_t cap, int64_t* nnz);
+
+/* State after the last committed iteration t: its objective
+   ||X - L_t - S_t||_F^2 (E_t^2 of Appendix I), |Omega| and bookkeeping. */
+typedef struct godec_info {
+  int32_t iter;
+  int32_t r_eff;
+  double rel_err;
+  double obj;          /* ||X - L_t - S_t||_F^2 */
+  double normX2;       /* ||X||_F^2 */
+  int64_t nnz;
+  int32_t select_passes;   /* residual passes used by the last S-step (1-3) */
+  int32_t rank_drops;      /* times the rank test lowered r */
+  int32_t launches_per_iter;  /* kernels in one captured iteration (0 before the first) */
+  int32_t reserved;
+} godec_info;
+godec_status godec_get_info(godec_ctx* ctx, godec_info* info);
+
+/* Release the context and its workspace (NULL is ignored). */
+void godec_destroy(godec_ctx* ctx);
+
+/* One-line description of the context's last error ("" if none; a static
+   string for ctx == NULL). */
+const char* godec_last_error(const godec_ctx* ctx);
+const char* godec_status_string(godec_status s);
+
+/*
+ * Whole run from HOST buffers: copy X (m x n, row stride n) and A1 (n x r)
+ * to the device, run n_iter iterations of Algorithm 1 (n_iter <= 0 means:
+ * godec_solve with params->tol and params->max_iter), copy the results back
+ * and release everything.
+ *   U (m x r), sigma (r), V (n x r): host, nullable; r_eff host.
+ *   S_idx, S_val: host arrays of S_cap entries (sorted COO), nullable.
+ *   nnz, iters, rel_err: host, nullable.
+ * All device memory is allocated and freed inside the call on `stream`.
+ */
+godec_status godec_run_host(const godec_params* params, const float* X_host,
+                            const float* A1_host, int32_t n_iter, void* stream,
+                            float* U, float* sigma, float* V, int32_t* r_eff,
+                            int64_t* S_idx, float* S_val, int64_t S_cap, int64_t* nnz,
+                            int32_t* iters, double* rel_err);
+
+/*
+ * Streaming tall-skinny products (the "(X - S) A" contractions of Sec. 3.1,
+ * Algorithm 1 lines 5-6), exposed for testing and benchmarking.
+ *   godec_mul_ZB : Y = Z B,    Z m x n (row stride ldz), B n x r, Y m x r
+ *   godec_mul_ZtC: W = Z^T C,  Z m x n (row stride ldz), C m x r, W n x r
+ * All pointers are device float32, row-major with row stride r for B, C, Y,
+ * W.  1 <= r <= GODEC_MAX_RANK, ldz >= n, ldz*4 a multiple of 16 bytes.
+ * The call allocates its split-K scratch on `stream` and frees it before
+ * returning (stream-ordered), and does not synchronise.
+ */
+godec_status godec_mul_ZB(const float* Z, int64_t m, int64_t n, int64_t ldz,
+                          const float* B, int32_t r, float* Y, void* stream);
+godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz,
+                           const float* C, int32_t r, float* W, void* stream);
+
+/*
+ * Kernel-level timing: run n_iter real iterations (they advance the state like
+ * godec_iterate) launching each kernel directly on the context stream with a
+ * CUDA event before and after it, and accumulate per kernel class:
+ *   ms[c]       : total device time in milliseconds (host arrays of
+ *   launches[c] : number of launches               GODEC_PROF_CLASSES entries)
+ * Classes: 0 streaming product, 1 split-K reduce + Gram partials, 2 r x r
+ * Cholesky/rank test, 3 tall x small product, 4 r x r SVD and root,
+ * 5 residual pass (S-step), 6 S-step pass control, 7 radix-select rounds,
+ * 8 S emit, 9 sparse update of X - S.
+ * bytes_product (host, nullable) receives the algorithmic bytes of one
+ * streaming product at the current rank: 4*m*n (X - S) + 4*(m + n)*r.
+ */
+#define GODEC_PROF_CLASSES 10
+godec_status godec_profile(godec_ctx* ctx, int32_t n_iter, double* ms, int64_t* launches,
+                           double* bytes_product);
+
+/*
+ * Entry-wise hard threshold of a dense matrix (eq. raw_lss, Algorithm 1
+ * line 9, with L = 0): the nonzero subset of the k largest |R|, ties by
+ * ascending linear index, runs the same kernels as the S-step.
+ *   R : device, m x ldr float32 (ldr*4 a multiple of 16 bytes, 16-byte aligned)
+ *   idx, val : device int64[cap] / float32[cap], receive the COO sorted by
+ *              linear index; nnz (host) receives min(k, #nonzeros of R).
+ * Scratch is allocated and freed inside the call (stream-ordered); the call
+ * synchronises the stream.  GODEC_ERR_ARG if cap < the result size.
+ */
+godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t ldr, int64_t k,
+                                  int64_t* idx, float* val, int64_t cap, int64_t* nnz,
+                                  void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GODEC_H */

@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) GoDec-BRP: Python binding of the C ABI in include/godec.h.
+
+Every step of Algorithm 1 runs in the CUDA library ``_lib/libgodec.so``; this
+module only marshals arguments.  PyTorch provides device memory and streams.
+There is no CPU fallback: if the library cannot be loaded, calls raise.
+"""
+from ._binding import (  # noqa: F401
+    GoDec, GodecError, library, mul_ZB, mul_ZtC, run_host, hard_threshold, header_symbols,
+    PREC_FP32, PREC_BF16_REFINE, MAX_RANK,
+)

@@ -1,0 +1,286 @@
+"""ctypes binding of libgodec (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(HERE), "include", "godec.h")
+
+PREC_FP32 = 0
+PREC_BF16_REFINE = 1
+MAX_RANK = 64
+
+
+class GodecParams(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ldx", C.c_int64), ("r", C.c_int32),
+                ("q", C.c_int32), ("k", C.c_int64), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("precision", C.c_int32), ("rank_tol", C.c_double), ("flags", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class GodecInfo(C.Structure):
+    _fields_ = [("iter", C.c_int32), ("r_eff", C.c_int32), ("rel_err", C.c_double),
+                ("obj", C.c_double), ("normX2", C.c_double), ("nnz", C.c_int64),
+                ("select_passes", C.c_int32), ("rank_drops", C.c_int32),
+                ("launches_per_iter", C.c_int32), ("reserved", C.c_int32)]
+
+
+class GodecError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+_LIB = None
+_P = C.c_void_p
+
+
+def _declare(lib):
+    i64p, f32p, f64p, i32p = C.POINTER(C.c_int64), C.POINTER(C.c_float), C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    sig = {
+        "godec_init": ([C.POINTER(_P), C.POINTER(GodecParams), _P, _P, _P], C.c_int),
+        "godec_reset": ([_P], C.c_int),
+        "godec_iterate": ([_P, C.c_int32, f64p], C.c_int),
+        "godec_solve": ([_P, i32p, f64p], C.c_int),
+        "godec_get_L": ([_P, _P, _P, _P, i32p], C.c_int),
+        "godec_get_S": ([_P, _P, _P, C.c_int64, i64p], C.c_int),
+        "godec_get_info": ([_P, C.POINTER(GodecInfo)], C.c_int),
+        "godec_destroy": ([_P], None),
+        "godec_last_error": ([_P], C.c_char_p),
+        "godec_status_string": ([C.c_int], C.c_char_p),
+        "godec_run_host": ([C.POINTER(GodecParams), _P, _P, C.c_int32, _P, _P, _P, _P, i32p, _P, _P,
+                            C.c_int64, i64p, i32p, f64p], C.c_int),
+        "godec_profile": ([_P, C.c_int32, f64p, i64p, f64p], C.c_int),
+        "godec_hard_threshold": ([_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, _P, C.c_int64, i64p, _P],
+                                 C.c_int),
+        "godec_mul_ZB": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
+        "godec_mul_ZtC": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+def library(build_if_missing: bool = True):
+    """Load libgodec.so (building it with nvcc first if it is missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        from . import build as _build
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"GoDec CUDA library not found at {path}; run paper_1309_0302_gb300.build")
+        _LIB = _declare(C.CDLL(path))
+    return _LIB
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/godec.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(godec_\w+)\s*\(", txt)))
+
+
+def _check(status: int, where: str, ctx=None):
+    if status != 0:
+        lib = library()
+        msg = lib.godec_last_error(ctx).decode(errors="replace")
+        raise GodecError(status, where, msg)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the GoDec library needs a CUDA device")
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class GoDec:
+    """One GoDec-BRP problem on the GPU (Algorithm 1).
+
+    X: CUDA float32 (m, n), row-major (a padded copy is made if its row stride
+    is not a multiple of 4 elements).  It is borrowed and must stay unchanged.
+    A1: CUDA float32 (n, r) random test matrix.
+    """
+
+    def __init__(self, X, A1, r: int, k: int, q: int, tol: float = 1e-7, max_iter: int = 50,
+                 rank_tol: float = 0.0, precision: int = PREC_FP32, stream=None):
+        torch = _torch()
+        lib = library()
+        if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
+            raise ValueError("X must be a 2-D CUDA float32 tensor")
+        m, n = X.shape
+        if X.stride(1) != 1 or X.stride(0) % 4 or X.stride(0) < n or X.data_ptr() % 16:
+            Xp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+            Xp[:, :n] = X
+            X = Xp
+        self._X = X
+        self._A1 = A1.contiguous().to(torch.float32)
+        self.m, self.n, self.r, self.k, self.q = m, n, int(r), int(k), int(q)
+        self.stream = stream
+        p = GodecParams(m=m, n=n, ldx=X.stride(0), r=int(r), q=int(q), k=int(k), tol=float(tol),
+                        max_iter=int(max_iter), precision=int(precision), rank_tol=float(rank_tol),
+                        flags=0, reserved=0)
+        h = C.c_void_p()
+        st = lib.godec_init(C.byref(h), C.byref(p), _ptr(X), _ptr(self._A1), _stream_ptr(stream))
+        _check(st, "godec_init", None)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().godec_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def reset(self):
+        _check(library().godec_reset(self._h), "godec_reset", self._h)
+
+    def iterate(self, n_iter: int = 1) -> float:
+        e = C.c_double(0.0)
+        _check(library().godec_iterate(self._h, int(n_iter), C.byref(e)), "godec_iterate", self._h)
+        return e.value
+
+    def solve(self):
+        it, e = C.c_int32(0), C.c_double(0.0)
+        _check(library().godec_solve(self._h, C.byref(it), C.byref(e)), "godec_solve", self._h)
+        return it.value, e.value
+
+    def info(self) -> dict:
+        inf = GodecInfo()
+        _check(library().godec_get_info(self._h, C.byref(inf)), "godec_get_info", self._h)
+        return {f: getattr(inf, f) for f, _ in GodecInfo._fields_}
+
+    PROF_CLASSES = ["product", "reduce_gram", "chol", "tall_small", "svd_root", "residual",
+                    "pass_control", "select", "emit", "z_update"]
+
+    def profile(self, n_iter: int):
+        """Run n_iter iterations with per-kernel CUDA events; returns per-class totals."""
+        nc = len(self.PROF_CLASSES)
+        ms = (C.c_double * nc)()
+        cnt = (C.c_int64 * nc)()
+        bp = C.c_double(0.0)
+        _check(library().godec_profile(self._h, int(n_iter), ms, cnt, C.byref(bp)), "godec_profile", self._h)
+        return {"ms": {k: ms[i] for i, k in enumerate(self.PROF_CLASSES)},
+                "launches": {k: cnt[i] for i, k in enumerate(self.PROF_CLASSES)},
+                "bytes_product": bp.value}
+
+    def L(self):
+        """(U (m, r_eff), sigma (r_eff,), V (n, r_eff)) as CUDA float32 tensors."""
+        torch = _torch()
+        dev = self._X.device
+        U = torch.empty((self.m, self.r), dtype=torch.float32, device=dev)
+        V = torch.empty((self.n, self.r), dtype=torch.float32, device=dev)
+        s = torch.empty((self.r,), dtype=torch.float32, device=dev)
+        re = C.c_int32(0)
+        _check(library().godec_get_L(self._h, _ptr(U), _ptr(s), _ptr(V), C.byref(re)), "godec_get_L", self._h)
+        r = re.value
+        return U.view(-1)[: self.m * r].view(self.m, r), s[:r], V.view(-1)[: self.n * r].view(self.n, r)
+
+    def S(self):
+        """(idx int64 ascending linear indices, val float32) of S as CUDA tensors."""
+        torch = _torch()
+        nnz = C.c_int64(0)
+        lib = library()
+        inf = self.info()
+        cnt = int(inf["nnz"])
+        idx = torch.empty((max(cnt, 1),), dtype=torch.int64, device=self._X.device)
+        val = torch.empty((max(cnt, 1),), dtype=torch.float32, device=self._X.device)
+        _check(lib.godec_get_S(self._h, _ptr(idx), _ptr(val), cnt, C.byref(nnz)), "godec_get_S", self._h)
+        return idx[: nnz.value], val[: nnz.value]
+
+
+def _mul(name, Z, B, stream=None):
+    torch = _torch()
+    if Z.dtype != torch.float32 or B.dtype != torch.float32 or not Z.is_cuda:
+        raise ValueError("Z and B must be CUDA float32")
+    m, n = Z.shape
+    if Z.stride(1) != 1 or Z.stride(0) % 4 or Z.data_ptr() % 16:
+        Zp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=Z.device)
+        Zp[:, :n] = Z
+        Z = Zp
+    B = B.contiguous()
+    r = B.shape[1]
+    out = torch.empty(((n if name == "godec_mul_ZtC" else m), r), dtype=torch.float32, device=Z.device)
+    st = getattr(library(), name)(_ptr(Z), m, n, Z.stride(0), _ptr(B), r, _ptr(out), _stream_ptr(stream))
+    _check(st, name)
+    return out
+
+
+def hard_threshold(R, k: int, stream=None):
+    """Entry-wise hard threshold of a CUDA float32 matrix on the GPU (S-step with L = 0).
+
+    Returns (idx int64 ascending, val float32) CUDA tensors.
+    """
+    torch = _torch()
+    m, n = R.shape
+    if R.stride(1) != 1 or R.stride(0) % 4 or R.data_ptr() % 16:
+        Rp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=R.device)
+        Rp[:, :n] = R
+        R = Rp
+    cap = max(1, min(int(k), m * n))
+    idx = torch.empty((cap,), dtype=torch.int64, device=R.device)
+    val = torch.empty((cap,), dtype=torch.float32, device=R.device)
+    nnz = C.c_int64(0)
+    st = library().godec_hard_threshold(_ptr(R), m, n, R.stride(0), int(k), _ptr(idx), _ptr(val), cap,
+                                        C.byref(nnz), _stream_ptr(stream))
+    _check(st, "godec_hard_threshold")
+    return idx[: nnz.value], val[: nnz.value]
+
+
+def mul_ZB(Z, B, stream=None):
+    """Y = Z @ B on the GPU (Z m x n, B n x r)."""
+    return _mul("godec_mul_ZB", Z, B, stream)
+
+
+def mul_ZtC(Z, Cm, stream=None):
+    """W = Z^T @ C on the GPU (Z m x n, C m x r)."""
+    return _mul("godec_mul_ZtC", Z, Cm, stream)
+
+
+def run_host(X: np.ndarray, A1: np.ndarray, r: int, k: int, q: int, n_iter: int, tol: float = 1e-7,
+             max_iter: int = 50, rank_tol: float = 0.0, stream=None, out=None) -> dict:
+    """Whole run from host arrays through godec_run_host (copies inside the call).
+
+    ``out`` may hold preallocated (ideally pinned) host arrays U, sigma, V, S_idx, S_val.
+    """
+    lib = library()
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    A1 = np.ascontiguousarray(A1, dtype=np.float32)
+    m, n = X.shape
+    out = out or {}
+    U = out.get("U", np.empty((m, r), np.float32))
+    V = out.get("V", np.empty((n, r), np.float32))
+    s = out.get("sigma", np.empty((r,), np.float32))
+    Si = out.get("S_idx", np.empty((max(k, 1),), np.int64))
+    Sv = out.get("S_val", np.empty((max(k, 1),), np.float32))
+    p = GodecParams(m=m, n=n, ldx=(n + 3) // 4 * 4, r=r, q=q, k=k, tol=tol, max_iter=max_iter,
+                    precision=0, rank_tol=rank_tol, flags=0, reserved=0)
+    re, nnz, it, e = C.c_int32(0), C.c_int64(0), C.c_int32(0), C.c_double(0.0)
+    st = lib.godec_run_host(C.byref(p), X.ctypes.data_as(C.c_void_p), A1.ctypes.data_as(C.c_void_p),
+                            int(n_iter), _stream_ptr(stream), U.ctypes.data_as(C.c_void_p),
+                            s.ctypes.data_as(C.c_void_p), V.ctypes.data_as(C.c_void_p), C.byref(re),
+                            Si.ctypes.data_as(C.c_void_p), Sv.ctypes.data_as(C.c_void_p), Si.size,
+                            C.byref(nnz), C.byref(it), C.byref(e))
+    _check(st, "godec_run_host")
+    rr, kk = re.value, nnz.value
+    return {"U": U.reshape(-1)[: m * rr].reshape(m, rr), "sigma": s[:rr],
+            "V": V.reshape(-1)[: n * rr].reshape(n, rr), "S_idx": Si[:kk], "S_val": Sv[:kk],
+            "iters": it.value, "rel_err": e.value, "r_eff": rr}

@@ -1,0 +1,209 @@
+// Small helpers: zero fill, padded copies of tall factors, ||X||_F^2 and a
+// stable LSD radix sort of the COO of S by linear index (export order).
+#include <algorithm>
+
+#include "godec_internal.cuh"
+
+namespace godec {
+
+namespace {
+
+__global__ void k_fill_zero(uint4* p, size_t n16) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = make_uint4(0, 0, 0, 0);
+}
+
+__global__ void k_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * RP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / RP;
+    int c = (int)(e % RP);
+    dst[e] = (c < cols) ? src[i * lds + c] : 0.f;
+  }
+}
+
+__global__ void k_unpad_copy(const float* src, int64_t rows, int RP, float* dst, int cols) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e / cols;
+    int c = (int)(e % cols);
+    dst[e] = src[i * RP + c];
+  }
+}
+
+__global__ void k_sumsq(const float* X, int64_t m, int64_t n, int64_t ldx, double* out) {
+  double acc = 0.0;
+  const int64_t total = m * n;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16; base < total;
+       base += (int64_t)gridDim.x * blockDim.x * 16) {
+    float f = 0.f;
+    for (int64_t e = base; e < min(total, base + 16); ++e) {
+      int64_t i = e / n, j = e % n;
+      float v = X[i * ldx + j];
+      f = fmaf(v, v, f);
+    }
+    acc += (double)f;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// ---- LSD radix sort, 4-bit digits, items owned contiguously by threads (stable) ------
+constexpr int SORT_THREADS = 256, SORT_ITEMS = 16, SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+__global__ void k_sort_hist(const long long* keys, long long n, int shift, unsigned* cnt, int nblk) {
+  __shared__ unsigned h[16];
+  if (threadIdx.x < 16) h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * SORT_TILE;
+  for (int j = threadIdx.x; j < SORT_TILE; j += SORT_THREADS) {
+    long long e = base + j;
+    if (e < n) atomicAdd(&h[(keys[e] >> shift) & 15], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) cnt[threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_sort_scan(unsigned* cnt, int total) {
+  // single block exclusive scan of `total` counts (digit-major), 1024 threads
+  __shared__ unsigned carry;
+  __shared__ unsigned ws[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < total; base += 1024) {
+    int i = base + threadIdx.x;
+    unsigned v = i < total ? cnt[i] : 0u;
+    unsigned x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned s = ws[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    unsigned excl = carry + (w ? ws[w - 1] : 0u) + x - v;
+    if (i < total) cnt[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = excl + v;
+    __syncthreads();
+  }
+}
+
+__global__ void k_sort_scatter(const long long* kin, const float* vin, long long* kout, float* vout,
+                               long long n, int shift, const unsigned* off, int nblk) {
+  __shared__ unsigned tab[16][SORT_THREADS + 1];
+  const int t = threadIdx.x;
+  const long long base = (long long)blockIdx.x * SORT_TILE + (long long)t * SORT_ITEMS;
+  unsigned c[16];
+#pragma unroll
+  for (int d = 0; d < 16; ++d) c[d] = 0;
+  long long kk[SORT_ITEMS];
+#pragma unroll
+  for (int j = 0; j < SORT_ITEMS; ++j) {
+    long long e = base + j;
+    kk[j] = e < n ? kin[e] : -1;
+    if (e < n) c[(kk[j] >> shift) & 15]++;
+  }
+#pragma unroll
+  for (int d = 0; d < 16; ++d) tab[d][t] = c[d];
+  __syncthreads();
+  // exclusive scan of each digit row across the 256 threads: warp w scans rows 2w, 2w+1
+  const int lane = t & 31, w = t >> 5;
+  for (int d = 2 * w; d < 2 * w + 2; ++d) {
+    unsigned run = 0;
+    unsigned vals[8];
+    for (int j = 0; j < 8; ++j) { vals[j] = tab[d][lane * 8 + j]; run += vals[j]; }
+    unsigned x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    unsigned e = x - run;
+    for (int j = 0; j < 8; ++j) { tab[d][lane * 8 + j] = e; e += vals[j]; }
+  }
+  __syncthreads();
+  unsigned pos[16];
+#pragma unroll
+  for (int d = 0; d < 16; ++d) pos[d] = off[d * nblk + blockIdx.x] + tab[d][t];
+#pragma unroll
+  for (int j = 0; j < SORT_ITEMS; ++j) {
+    long long e = base + j;
+    if (e < n) {
+      int d = (int)((kk[j] >> shift) & 15);
+      unsigned p = pos[d]++;
+      kout[p] = kk[j];
+      vout[p] = vin[e];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_fill_zero(void* p, size_t bytes, cudaStream_t st) {
+  // bytes must be a multiple of 16 and p 16-byte aligned
+  size_t n16 = bytes / 16;
+  if (!n16) return;
+  unsigned grid = (unsigned)std::min<size_t>((n16 + 255) / 256, 4096);
+  k_fill_zero<<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(p), n16);
+}
+
+void launch_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP,
+                     cudaStream_t st) {
+  int64_t tot = rows * RP;
+  unsigned grid = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+  if (grid) k_pad_copy<<<grid, 256, 0, st>>>(src, rows, cols, lds, dst, RP);
+}
+
+void launch_unpad_copy(const float* src, int64_t rows, int RP, float* dst, int cols, cudaStream_t st) {
+  int64_t tot = rows * cols;
+  unsigned grid = (unsigned)std::min<int64_t>((tot + 255) / 256, 4096);
+  if (grid) k_unpad_copy<<<grid, 256, 0, st>>>(src, rows, RP, dst, cols);
+}
+
+void launch_sumsq(const float* X, int64_t m, int64_t n, int64_t ldx, double* out, int nsm,
+                  cudaStream_t st) {
+  k_sumsq<<<(unsigned)(4 * nsm), 256, 0, st>>>(X, m, n, ldx, out);
+}
+
+size_t sort_coo_scratch(long long nnz) {
+  long long nblk = (nnz + SORT_TILE - 1) / SORT_TILE;
+  return (size_t)nnz * (sizeof(long long) + sizeof(float)) + (size_t)(16 * nblk + 16) * sizeof(unsigned) + 256;
+}
+
+void launch_sort_coo(long long* idx, float* val, long long nnz, void* scratch, size_t scratch_bytes,
+                     int idx_bits, cudaStream_t st) {
+  if (nnz <= 1) return;
+  const int nblk = (int)((nnz + SORT_TILE - 1) / SORT_TILE);
+  char* p = reinterpret_cast<char*>(scratch);
+  long long* k2 = reinterpret_cast<long long*>(p);
+  float* v2 = reinterpret_cast<float*>(p + (size_t)nnz * sizeof(long long));
+  size_t offb = (size_t)nnz * (sizeof(long long) + sizeof(float));
+  offb = (offb + 255) & ~size_t(255);
+  unsigned* cnt = reinterpret_cast<unsigned*>(p + offb);
+  (void)scratch_bytes;
+  long long* ka = idx;
+  float* va = val;
+  long long* kb = k2;
+  float* vb = v2;
+  int passes = (idx_bits + 3) / 4;
+  if (passes & 1) ++passes;                  // even count: result lands back in idx/val
+  for (int ps = 0; ps < passes; ++ps) {
+    const int shift = 4 * ps;
+    k_sort_hist<<<nblk, SORT_THREADS, 0, st>>>(ka, nnz, shift, cnt, nblk);
+    k_sort_scan<<<1, 1024, 0, st>>>(cnt, 16 * nblk);
+    k_sort_scatter<<<nblk, SORT_THREADS, 0, st>>>(ka, va, kb, vb, nnz, shift, cnt, nblk);
+    long long* tk = ka; ka = kb; kb = tk;
+    float* tv = va; va = vb; vb = tv;
+  }
+}
+
+}  // namespace godec

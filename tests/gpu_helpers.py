@@ -1,0 +1,68 @@
+"""Shared helpers of the GPU tests (not a test module)."""
+import numpy as np
+
+
+def to_gpu(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def lfro_rel(Ua, sa, Va, Ub, sb, Vb):
+    """||Ua diag(sa) Va^T - Ub diag(sb) Vb^T||_F / ||Ub diag(sb) Vb^T||_F from the factors."""
+    Aa, Ab = Ua * sa, Ub * sb
+    aa = np.sum((Aa.T @ Aa) * (Va.T @ Va))
+    bb = np.sum((Ab.T @ Ab) * (Vb.T @ Vb))
+    ab = np.sum((Aa.T @ Ab) * (Va.T @ Vb))
+    return float(np.sqrt(max(aa + bb - 2.0 * ab, 0.0)) / np.sqrt(bb))
+
+
+def s_rel(ia, va, ib, vb):
+    """Relative Frobenius distance of two sparse matrices given as COO."""
+    u = np.union1d(ia, ib)
+    A = np.zeros(u.size)
+    B = np.zeros(u.size)
+    A[np.searchsorted(u, ia)] = va
+    B[np.searchsorted(u, ib)] = vb
+    nb = np.linalg.norm(B)
+    return float(np.linalg.norm(A - B) / (nb if nb > 0 else 1.0))
+
+
+def fma32(a, b, c):
+    """float32 fused multiply-add emulated in float64 (the product is exact)."""
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+
+
+def residual_like_kernel(X, U, sigma, V):
+    """The S-step kernel's float32 residual X - (U*sigma) V^T, with its operation order:
+    u*sigma rounded to float32, then a fused multiply-add chain over l = 0..r-1."""
+    X = X.astype(np.float32)
+    Us = (U.astype(np.float32) * sigma.astype(np.float32)[None, :]).astype(np.float32)
+    Vf = V.astype(np.float32)
+    acc = np.zeros(X.shape, dtype=np.float32)
+    for l in range(U.shape[1]):
+        acc = fma32(Us[:, l][:, None], Vf[:, l][None, :], acc)
+    return (X - acc).astype(np.float32)
+
+
+class GpuRun:
+    def __init__(self, d, tol=1e-7, max_iter=50, rank_tol=0.0):
+        import paper_1309_0302_gb300 as G
+        self.d = d
+        self.g = G.GoDec(to_gpu(d["X"]), to_gpu(d["A1"]), d["r"], d["k"], d["q"], tol=tol,
+                         max_iter=max_iter, rank_tol=rank_tol)
+
+    def factors(self):
+        U, s, V = self.g.L()
+        return to_np(U).astype(np.float64), to_np(s).astype(np.float64), to_np(V).astype(np.float64)
+
+    def factors32(self):
+        U, s, V = self.g.L()
+        return to_np(U), to_np(s), to_np(V)
+
+    def sparse(self):
+        i, v = self.g.S()
+        return to_np(i), to_np(v).astype(np.float64)
