@@ -19,6 +19,7 @@ struct godec_ctx {
   int r = 0;          // current rank (drops after a failed rank test)
   int RP = 0;         // padded width of the skinny buffers (from the initial r)
   cudaStream_t st = nullptr;
+  cudaStream_t cap_st = nullptr;   // private stream used only while capturing the graph
   int dev = 0, nsm = 0;
   const float* X = nullptr;
   float* Z = nullptr;
@@ -268,9 +269,18 @@ void enqueue_iteration(godec_ctx* c) {
 godec_status build_graph(godec_ctx* c) {
   free_graph(c);
   cudaGraph_t g = nullptr;
-  CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  enqueue_iteration(c);
-  cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  // The caller's stream may be the legacy default stream, which cannot be captured:
+  // record on a private stream and launch the graph on the caller's stream.
+  if (!c->cap_st) CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+  CK(cudaStreamSynchronize(c->st));
+  cudaStream_t user = c->st;
+  c->st = c->cap_st;
+  cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_iteration(c);
+    e = cudaStreamEndCapture(c->st, &g);
+  }
+  c->st = user;
   if (e != cudaSuccess) return fail(c, GODEC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   size_t nodes = 0;
   cudaGraphGetNodes(g, nullptr, &nodes);
@@ -408,6 +418,7 @@ void godec_destroy(godec_ctx* c) {
                   c->S_val[0], c->S_val[1]};
   for (void* p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   delete c;
 }
 

@@ -68,7 +68,8 @@ struct Ctl {
   int svd_sweeps;
   int converged;                // stop test met (sets abort, not an error)
   int last_passes;              // residual passes used by the last committed S-step
-  int pad2;
+  int chol_shifts;              // Cholesky factorisations that needed a diagonal shift
+  double m_logscale;            // M is stored divided by exp(m_logscale)
   // --- histograms ------------------------------------------------------------
   unsigned hist[kHistBins];     // digit-1 histogram of |R| keys (full pass)
   unsigned sel_hist[kHistBins];

@@ -70,6 +70,23 @@ k_chol(CholArgs a, const double* __restrict__ gram64) {
   }
   __syncthreads();
 
+  // ---- non-finite Gram: X - S holds NaN/Inf ---------------------------------------------
+  {
+    __shared__ int s_nf;
+    if (tid == 0) s_nf = 0;
+    __syncthreads();
+    for (int e = tid; e < npair; e += CHOL_THREADS)
+      if (!isfinite(G[e / RP][e % RP])) s_nf = 1;
+    __syncthreads();
+    if (s_nf) {
+      if (tid == 0) {
+        ctl->nonfinite = 1;
+        ctl->abort = 1;
+      }
+      return;
+    }
+  }
+
   // ---- numerical rank by pivoted Cholesky in float64 ------------------------------------
   if (a.rank_test) {
     if (tid == 0) {
@@ -135,33 +152,58 @@ k_chol(CholArgs a, const double* __restrict__ gram64) {
   }
 
   // ---- Cholesky G = R^T R (float32, right-looking) -------------------------------------
+  // Pivots below 1e-6 of the largest diagonal mean the factor is numerically rank
+  // deficient (noise columns of a power chain whose Z has rank < r); the factorisation
+  // is then redone on G + shift*I (shifted CholeskyQR), which keeps Q bounded until
+  // the rank test of the last chain lowers r.
+  __shared__ float s_d;
+  __shared__ float s_gmax;
+  __shared__ int s_bad;
   for (int e = tid; e < npair; e += CHOL_THREADS) {
     int i = e / RP, j = e % RP;
-    R[i][j] = 0.f;
     if (i >= r || j >= r) G[i][j] = (i == j) ? 1.f : 0.f;   // padded columns: identity
+    Ri[i][j] = G[i][j];                                      // keep a copy for a retry
   }
   __syncthreads();
-  __shared__ float s_d;
-  for (int j = 0; j < RP; ++j) {
-    if (tid == 0) {
-      float d = G[j][j];
-      if (!(d > 0.f) || !isfinite(d)) {
-        if (!isfinite(d)) ctl->nonfinite = 1;
-        ctl->chol_fail = 1;
-        d = 1e-30f;
+  if (tid == 0) {
+    float gm = 0.f;
+    for (int j = 0; j < r; ++j) gm = fmaxf(gm, G[j][j]);
+    s_gmax = gm;
+    if (!isfinite(gm)) ctl->nonfinite = 1;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (attempt == 1) {
+      for (int e = tid; e < npair; e += CHOL_THREADS) {
+        int i = e / RP, j = e % RP;
+        G[i][j] = Ri[i][j] + ((i == j && i < r) ? 1e-5f * s_gmax : 0.f);
       }
-      s_d = sqrtf(d);
-      R[j][j] = s_d;
     }
+    for (int e = tid; e < npair; e += CHOL_THREADS) R[e / RP][e % RP] = 0.f;
+    if (tid == 0) s_bad = 0;
     __syncthreads();
-    const float dj = s_d;
-    for (int c = j + 1 + tid; c < RP; c += CHOL_THREADS) R[j][c] = G[j][c] / dj;
-    __syncthreads();
-    const int w = RP - j - 1;
-    for (int e = tid; e < w * w; e += CHOL_THREADS) {
-      int aa = j + 1 + e / w, cc = j + 1 + e % w;
-      if (cc >= aa) G[aa][cc] -= R[j][aa] * R[j][cc];
+    for (int j = 0; j < RP; ++j) {
+      if (tid == 0) {
+        float d = G[j][j];
+        if (!(d > 1e-6f * s_gmax) && j < r) {
+          s_bad = 1;
+          if (!(d > 0.f)) d = 1e-6f * s_gmax + 1e-30f;
+        }
+        s_d = sqrtf(d);
+        R[j][j] = s_d;
+      }
+      __syncthreads();
+      const float dj = s_d;
+      for (int c = j + 1 + tid; c < RP; c += CHOL_THREADS) R[j][c] = G[j][c] / dj;
+      __syncthreads();
+      const int w = RP - j - 1;
+      for (int e = tid; e < w * w; e += CHOL_THREADS) {
+        int aa = j + 1 + e / w, cc = j + 1 + e % w;
+        if (cc >= aa) G[aa][cc] -= R[j][aa] * R[j][cc];
+      }
+      __syncthreads();
     }
+    if (!s_bad) break;
+    if (tid == 0) ctl->chol_shifts += 1;
     __syncthreads();
   }
 
@@ -189,18 +231,32 @@ k_chol(CholArgs a, const double* __restrict__ gram64) {
   }
 
   // ---- core of the last chain: M := R M ------------------------------------------------
-  if (a.accumulate == 2) {
-    for (int e = tid; e < npair; e += CHOL_THREADS) a.M[e] = R[e / RP][e % RP];
-  } else if (a.accumulate == 1) {
-    // G is free now: hold the old M there.
+  // M grows like sigma^(2q+1); it is kept divided by its scale, with log(scale) in
+  // float64 in the control block, so float32 never overflows.
+  if (a.accumulate) {
+    __shared__ float s_scale;
     __syncthreads();
-    for (int e = tid; e < npair; e += CHOL_THREADS) G[e / RP][e % RP] = a.M[e];
+    if (tid == 0) {
+      float mx = 0.f;
+      for (int i = 0; i < RP; ++i)
+        for (int j = i; j < RP; ++j) mx = fmaxf(mx, fabsf(R[i][j]));
+      s_scale = mx > 0.f ? mx : 1.f;
+      ctl->m_logscale = (a.accumulate == 2 ? 0.0 : ctl->m_logscale) + log((double)s_scale);
+    }
     __syncthreads();
-    for (int e = tid; e < npair; e += CHOL_THREADS) {
-      int i = e / RP, j = e % RP;
-      float s = 0.f;
-      for (int t = i; t < RP; ++t) s = fmaf(R[i][t], G[t][j], s);
-      a.M[e] = s;
+    const float inv = 1.f / s_scale;
+    if (a.accumulate == 2) {
+      for (int e = tid; e < npair; e += CHOL_THREADS) a.M[e] = R[e / RP][e % RP] * inv;
+    } else {
+      // G is free now: hold the old M there.
+      for (int e = tid; e < npair; e += CHOL_THREADS) G[e / RP][e % RP] = a.M[e];
+      __syncthreads();
+      for (int e = tid; e < npair; e += CHOL_THREADS) {
+        int i = e / RP, j = e % RP;
+        float acc = 0.f;
+        for (int t = i; t < RP; ++t) acc = fmaf(R[i][t] * inv, G[t][j], acc);
+        a.M[e] = acc;
+      }
     }
   }
 }
@@ -258,7 +314,7 @@ k_svd_root(SvdArgs a) {
             be += __shfl_xor_sync(0xffffffffu, be, o);
             ga += __shfl_xor_sync(0xffffffffu, ga, o);
           }
-          if (fabsf(ga) > 1e-6f * sqrtf(al * be) && ga != 0.f) {
+          if (fabsf(ga) > 1e-6f * sqrtf(al) * sqrtf(be) && ga != 0.f) {
             float zeta = (be - al) / (2.f * ga);
             float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
             float c = rsqrtf(1.f + t * t);
@@ -298,7 +354,8 @@ k_svd_root(SvdArgs a) {
     ctl->svd_sweeps = sweeps;
   }
   __syncthreads();
-  const float inv_e = 1.f / (float)(2 * a.q + 1);
+  const double inv_e = 1.0 / (double)(2 * a.q + 1);
+  const double lsc = ctl->m_logscale;
   for (int e = tid; e < RP * RP; e += SVD_THREADS) {
     int i = e / RP, j = e % RP;            // output [row i][col j]
     float u = 0.f, v = 0.f;
@@ -315,7 +372,7 @@ k_svd_root(SvdArgs a) {
     float sv = 0.f;
     if (tid < r) {
       float sc = s[order[tid]];
-      sv = (sc > 0.f) ? powf(sc, inv_e) : 0.f;
+      sv = (sc > 0.f) ? (float)exp((log((double)sc) + lsc) * inv_e) : 0.f;
     }
     a.sigma[tid] = sv;
   }
