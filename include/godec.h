@@ -218,6 +218,26 @@ godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t 
                                   int64_t* idx, float* val, int64_t cap, int64_t* nnz,
                                   void* stream);
 
+/*
+ * godec_mul_ZB_noalloc: Y = Z B like godec_mul_ZB, for callers that must not
+ * allocate device memory while they run (an application that reserves all GPU
+ * memory at start-up and forbids later allocations, or a latency-critical loop
+ * that cannot afford an allocation's synchronisation).  The paper has no
+ * counterpart; this is a library convenience.
+ *   Same arguments, layout and results as godec_mul_ZB.
+ *   Scratch: a fixed 32 MiB device array inside the library, reserved on every
+ *   GPU that loads it until the process exits; no allocation or free happens in
+ *   the call.  Problems whose scratch (padded B, split-K partials, padded Y)
+ *   exceeds 32 MiB are rejected with GODEC_ERR_UNSUPPORTED and a message in
+ *   godec_last_error(NULL).  The first call on each device looks up the array's
+ *   device address; make that first call before any stream capture.
+ *   All calls on a device share the array and leave its contents behind:
+ *   calls that overlap on the GPU (different streams, threads or processes
+ *   without ordering) race and corrupt each other's results.
+ */
+godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t n, int64_t ldz,
+                                  const float* B, int32_t r, float* Y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -399,6 +399,13 @@ char g_static_err[256];
 
 }  // namespace
 
+void godec::set_static_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_static_err, sizeof(g_static_err), fmt, ap);
+  va_end(ap);
+}
+
 extern "C" {
 
 const char* godec_status_string(godec_status s) {

@@ -183,6 +183,9 @@ void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);
 // Reset the per-iteration S-step state (after an aborted iteration or at start).
 void launch_reset_iter(Ctl* ctl, cudaStream_t st);
 
+// Error text returned by godec_last_error(NULL) for calls without a context.
+void set_static_error(const char* fmt, ...);
+
 // Kernel attributes (dynamic shared memory limits); call before launching or capturing.
 cudaError_t prepare_small_kernels();
 cudaError_t prepare_select_kernels();

@@ -1,0 +1,113 @@
+// godec_mul_ZB_noalloc: the streaming product Y = Z B with its scratch in a
+// fixed device array instead of memory allocated per call.
+//
+// Some callers cannot allocate device memory while they run: a host
+// application that reserves all GPU memory at start-up and forbids plugins
+// to allocate afterwards, or a latency-critical loop where an allocation may
+// synchronise the device or fragment a pool.  For them this entry point keeps
+// the padded copy of B, the split-K partial products and the padded result in
+// one file-scope array of kNoAllocScratchBytes bytes.  Every GPU that loads
+// this library reserves that array until the process exits.
+#include <mutex>
+
+#include "godec_internal.cuh"
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32u << 20;   // 32 MiB per device
+static __device__ __align__(256) unsigned char g_mul_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mu;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Device address of the array on the current device, looked up once per device
+// (host code cannot use the symbol itself: it names a host-side stand-in).
+godec_status scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    godec::set_static_error("godec_mul_ZB_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    return GODEC_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    godec::set_static_error("godec_mul_ZB_noalloc: device ordinal %d above %d", dev, kMaxDevices - 1);
+    return GODEC_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_mul_scratch);
+    if (e != cudaSuccess || !p) {
+      godec::set_static_error("godec_mul_ZB_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return GODEC_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return GODEC_OK;
+}
+
+}  // namespace
+
+extern "C" godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t n, int64_t ldz,
+                                             const float* B, int32_t r, float* Y, void* stream) {
+  using namespace godec;
+  if (!Z || !B || !Y || m < 1 || n < 1 || ldz < n || (ldz * 4) % 16 || r < 1 || r > GODEC_MAX_RANK ||
+      (reinterpret_cast<uintptr_t>(Z) & 15)) {
+    set_static_error("godec_mul_ZB_noalloc: invalid argument");
+    return GODEC_ERR_ARG;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int RP = (r + 7) / 8 * 8;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    set_static_error("godec_mul_ZB_noalloc: no CUDA device");
+    return GODEC_ERR_CUDA;
+  }
+  int splits;
+  int64_t kchunk;
+  pass_geometry(m, n, nsm, &splits, &kchunk);
+  const size_t bytes_b = align256((size_t)n * RP * sizeof(float));
+  const size_t bytes_p = align256((size_t)splits * m * RP * sizeof(float));
+  const size_t bytes_y = align256((size_t)m * RP * sizeof(float));
+  if (bytes_b + bytes_p + bytes_y > kNoAllocScratchBytes) {
+    set_static_error("godec_mul_ZB_noalloc: m=%lld n=%lld r=%d needs %zu bytes of scratch, above the "
+                     "fixed %zu", (long long)m, (long long)n, r, bytes_b + bytes_p + bytes_y,
+                     kNoAllocScratchBytes);
+    return GODEC_ERR_UNSUPPORTED;
+  }
+  void* base = nullptr;
+  godec_status s = scratch_address(&base);
+  if (s) return s;
+  char* p = reinterpret_cast<char*>(base);
+  float* Bp = reinterpret_cast<float*>(p);
+  float* part = reinterpret_cast<float*>(p + bytes_b);
+  float* Yp = reinterpret_cast<float*>(p + bytes_b + bytes_p);
+  // Every scratch element read below is written first in the same call (all K x RP
+  // of Bp, all splits x m x RP partials, all m x RP of Yp): nothing is cleared.
+  launch_pad_copy(B, n, r, r, Bp, RP, st);
+  PassArgs pa{};
+  pa.Z = Z;
+  pa.m = m;
+  pa.n = n;
+  pa.ldz = ldz;
+  pa.B = Bp;
+  pa.part = part;
+  pa.splits = splits;
+  pa.kchunk = kchunk;
+  pa.trans = 0;
+  pa.RP = RP;
+  launch_pass(pa, st);
+  launch_reduce(part, splits, m, RP, Yp, nullptr, 0, nullptr, st);
+  launch_unpad_copy(Yp, m, RP, Y, r, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_static_error("godec_mul_ZB_noalloc: %s", cudaGetErrorString(e));
+    return GODEC_ERR_CUDA;
+  }
+  return GODEC_OK;
+}
