@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", choices=["product", "product_t", "iteration"], default=None,
+                    help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
+    ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
 
 
@@ -279,8 +282,36 @@ def e2e(args, d):
                     "factors and sorted S; bytes per step = bytes per call / K"}
 
 
+def run_kernel_case(args):
+    """Small cases for ncu captures: the streaming product on a size x size matrix
+    (above the L2 size for size >= 6000), or two full iterations at size x size, r = 50."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    n = args.size
+    if args.kernel in ("product", "product_t"):
+        g = np.random.default_rng(5)
+        Z = torch.from_numpy(g.standard_normal((n, n)).astype(np.float32)).cuda()
+        B = torch.from_numpy(g.standard_normal((n, R)).astype(np.float32)).cuda()
+        f = G.mul_ZB if args.kernel == "product" else G.mul_ZtC
+        for _ in range(3):
+            f(Z, B)
+    else:
+        d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
+        run = G.GoDec(torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda(), R, d["k"], Q)
+        run.iterate(2)
+        run.close()
+    torch.cuda.synchronize()
+    print(f"kernel case {args.kernel} size {n}: done")
+
+
 def main():
     args = parse()
+    if args.kernel:
+        run_kernel_case(args)
+        return
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)

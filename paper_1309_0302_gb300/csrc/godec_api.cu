@@ -25,7 +25,8 @@ struct godec_ctx {
   float* Z = nullptr;
   int64_t ldz = 0;
   void* Z16 = nullptr;
-  float* A1 = nullptr;                 // n x RP
+  float* A1 = nullptr;                 // n x RP; columns >= r kept at zero
+  float* A1_orig = nullptr;            // n x RP as given (restored by godec_reset)
   float* P = nullptr;                  // max(m,n) x RP
   float* Qb[2] = {nullptr, nullptr};   // max(m,n) x RP
   float* Q1 = nullptr;                 // m x RP
@@ -306,10 +307,22 @@ godec_status set_field(godec_ctx* c, size_t off, T v) {
 }
 #define SET_CTL(field, v) set_field(c, offsetof(Ctl, field), (decltype(Ctl::field))(v))
 
+// After the rank test lowered r: keep only the first r columns of A1 (reading of
+// "r := rank(A2^T Y1)"), so every product of the chain has zero columns beyond r.
+godec_status drop_columns(godec_ctx* c) {
+  if (c->r < c->RP)
+    CK(cudaMemset2DAsync(c->A1 + c->r, c->RP * sizeof(float), 0, (c->RP - c->r) * sizeof(float), c->p.n,
+                         c->st));
+  return GODEC_OK;
+}
+
 godec_status reset_state(godec_ctx* c) {
   free_graph(c);
   c->r = c->p.r;
   c->rank_drops = 0;
+  if (c->A1_orig)
+    CK(cudaMemcpyAsync(c->A1, c->A1_orig, (size_t)c->p.n * c->RP * sizeof(float), cudaMemcpyDeviceToDevice,
+                       c->st));
   CK(cudaMemcpy2DAsync(c->Z, c->ldz * sizeof(float), c->X, c->p.ldx * sizeof(float),
                        c->p.n * sizeof(float), c->p.m, cudaMemcpyDeviceToDevice, c->st));
   Ctl h;
@@ -358,6 +371,7 @@ godec_status run_iterations(godec_ctx* c, int n_iter, double tol, int* done) {
         c->r = h.r_eff;
         ++c->rank_drops;
         if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
+        if ((s = drop_columns(c))) return s;
       } else if (h.need_bigger_cand) {
         unsigned long long cap = c->cap * 2;
         const unsigned long long mn = (unsigned long long)(c->p.m * c->p.n);
@@ -419,7 +433,7 @@ void godec_destroy(godec_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   free_graph(c);
-  void* ptrs[] = {c->Z, c->Z16, c->A1, c->P, c->Qb[0], c->Qb[1], c->Q1, c->Q2, c->U, c->V,
+  void* ptrs[] = {c->Z, c->Z16, c->A1, c->A1_orig, c->P, c->Qb[0], c->Qb[1], c->Q1, c->Q2, c->U, c->V,
                   c->sigma, c->Um, c->Vm, c->Rm, c->Rinv, c->M, c->part, c->gram, c->ctl,
                   c->cand_key, c->cand_idx, c->cand_val, c->S_idx[0], c->S_idx[1],
                   c->S_val[0], c->S_val[1]};
@@ -510,7 +524,8 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   while ((1ull << c->idx_bits) < mn) ++c->idx_bits;
   launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), c->st);
   launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), c->st);
-  launch_pad_copy(A1, n, p->r, p->r, c->A1, RP, c->st);
+  CKI(dalloc(&c->A1_orig, (size_t)n * RP));
+  launch_pad_copy(A1, n, p->r, p->r, c->A1_orig, RP, c->st);
   CKI(cudaGetLastError());
   godec_status s = reset_state(c);
   if (s) return bail(s);
@@ -594,6 +609,8 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
       if (h.rank_drop) {
         c->r = h.r_eff;
         ++c->rank_drops;
+        if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
+        if ((s = drop_columns(c))) return s;
       } else if (h.need_bigger_cand) {
         unsigned long long cap = std::min<unsigned long long>(c->cap * 2, (unsigned long long)(c->p.m * c->p.n));
         free_graph(c);

@@ -23,16 +23,24 @@ namespace {
 constexpr int CHOL_THREADS = 256;
 constexpr size_t kCholSmem = 3 * kMaxRP * (kMaxRP + 1) * sizeof(float);
 
-// Sum the float64 Gram partials of all 64-row blocks, one entry per thread,
-// spread over many blocks (float64 is slow per SM on this part).
-__global__ void k_gram_sum64(const double* __restrict__ part, int64_t nblk, int npair,
-                             double* __restrict__ out, const Ctl* ctl) {
+// Sum the Gram partials of all 64-row blocks in float64, one entry per thread,
+// spread over many blocks (a single block would be bound by load latency).
+template <typename T>
+__global__ void k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out,
+                           const Ctl* ctl) {
   if (ctl && ctl->abort) return;
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= npair) return;
-  double s = 0.0;
-  for (int64_t b = 0; b < nblk; ++b) s += part[b * npair + e];
-  out[e] = s;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int64_t b = 0;
+  for (; b + 4 <= nblk; b += 4) {
+    s0 += (double)part[(b + 0) * npair + e];
+    s1 += (double)part[(b + 1) * npair + e];
+    s2 += (double)part[(b + 2) * npair + e];
+    s3 += (double)part[(b + 3) * npair + e];
+  }
+  for (; b < nblk; ++b) s0 += (double)part[b * npair + e];
+  out[e] = (s0 + s1) + (s2 + s3);
 }
 
 __global__ void __launch_bounds__(CHOL_THREADS)
@@ -52,21 +60,12 @@ k_chol(CholArgs a, const double* __restrict__ gram64) {
   const int r = a.r, RP = a.RP;
   const int npair = RP * RP;
 
-  // ---- Gram matrix -------------------------------------------------------------------
-  if (a.gram_double) {
-    for (int e = tid; e < npair; e += CHOL_THREADS) {
-      int i = e / RP, j = e % RP;
-      double v = gram64[e];
-      Gd[i][j] = v;
-      G[i][j] = (float)v;
-    }
-  } else {
-    const float* gp = reinterpret_cast<const float*>(a.gram_part);
-    for (int e = tid; e < npair; e += CHOL_THREADS) {
-      float s = 0.f;
-      for (int64_t b = 0; b < a.nblk; ++b) s += gp[b * npair + e];
-      G[e / RP][e % RP] = s;
-    }
+  // ---- Gram matrix (reduced over row blocks in float64 by k_gram_sum) ----------------
+  for (int e = tid; e < npair; e += CHOL_THREADS) {
+    int i = e / RP, j = e % RP;
+    double v = gram64[e];
+    if (a.rank_test) Gd[i][j] = v;
+    G[i][j] = (float)v;
   }
   __syncthreads();
 
@@ -181,24 +180,22 @@ k_chol(CholArgs a, const double* __restrict__ gram64) {
     for (int e = tid; e < npair; e += CHOL_THREADS) R[e / RP][e % RP] = 0.f;
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    const float thr = 1e-6f * s_gmax;
     for (int j = 0; j < RP; ++j) {
-      if (tid == 0) {
-        float d = G[j][j];
-        if (!(d > 1e-6f * s_gmax) && j < r) {
-          s_bad = 1;
-          if (!(d > 0.f)) d = 1e-6f * s_gmax + 1e-30f;
-        }
-        s_d = sqrtf(d);
-        R[j][j] = s_d;
+      // Every thread reads pivot j itself, so row j of R and the trailing update
+      // need no barrier between them; one barrier per column.
+      float d = G[j][j];
+      if (!(d > thr) && j < r) {
+        if (tid == 0) s_bad = 1;
+        if (!(d > 0.f)) d = thr + 1e-30f;
       }
-      __syncthreads();
-      const float dj = s_d;
-      for (int c = j + 1 + tid; c < RP; c += CHOL_THREADS) R[j][c] = G[j][c] / dj;
-      __syncthreads();
+      const float sq = sqrtf(d);
+      const float invd = 1.f / d;
+      for (int c = j + tid; c < RP; c += CHOL_THREADS) R[j][c] = (c == j) ? sq : G[j][c] / sq;
       const int w = RP - j - 1;
       for (int e = tid; e < w * w; e += CHOL_THREADS) {
         int aa = j + 1 + e / w, cc = j + 1 + e % w;
-        if (cc >= aa) G[aa][cc] -= R[j][aa] * R[j][cc];
+        if (cc >= aa) G[aa][cc] -= G[j][aa] * G[j][cc] * invd;
       }
       __syncthreads();
     }
@@ -287,6 +284,7 @@ k_svd_root(SvdArgs a) {
   const int npairs = np / 2;
   int sweeps = 0;
   for (; sweeps < 40; ++sweeps) {
+    __syncthreads();          // every thread has read the previous sweep's flag
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
@@ -381,16 +379,16 @@ k_svd_root(SvdArgs a) {
 }  // namespace
 
 void launch_chol(const CholArgs& a, cudaStream_t st) {
-  const double* g64 = nullptr;
-  if (a.gram_double) {
-    // reduce the double partials with many blocks into the tail of the partial buffer
-    const int npair = a.RP * a.RP;
-    double* out = reinterpret_cast<double*>(const_cast<void*>(a.gram_part)) + a.nblk * npair;
-    k_gram_sum64<<<(npair + 127) / 128, 128, 0, st>>>(reinterpret_cast<const double*>(a.gram_part),
-                                                       a.nblk, npair, out, a.ctl);
-    g64 = out;
-  }
-  k_chol<<<1, CHOL_THREADS, kCholSmem, st>>>(a, g64);
+  // the reduced Gram goes after the partials in the same buffer (no overlap for
+  // float or double partials: it starts at byte 8 * nblk * npair)
+  const int npair = a.RP * a.RP;
+  double* out = reinterpret_cast<double*>(const_cast<void*>(a.gram_part)) + a.nblk * npair;
+  const unsigned grid = (unsigned)((npair + 127) / 128);
+  if (a.gram_double)
+    k_gram_sum<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double*>(a.gram_part), a.nblk, npair, out, a.ctl);
+  else
+    k_gram_sum<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float*>(a.gram_part), a.nblk, npair, out, a.ctl);
+  k_chol<<<1, CHOL_THREADS, kCholSmem, st>>>(a, out);
 }
 
 cudaError_t prepare_small_kernels() {

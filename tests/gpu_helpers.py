@@ -66,3 +66,32 @@ class GpuRun:
     def sparse(self):
         i, v = self.g.S()
         return to_np(i), to_np(v).astype(np.float64)
+
+
+def s_common_rel(ia, va, ib, vb):
+    """Relative error of S values on the common support (reading R8(iii))."""
+    common, xa, xb = np.intersect1d(ia, ib, return_indices=True)
+    nb = np.linalg.norm(vb)
+    return float(np.linalg.norm(va[xa] - vb[xb]) / (nb if nb > 0 else 1.0)), int(ia.size + ib.size - 2 * common.size)
+
+
+def selection_within_band(X, U, s, V, idx, k, chunk_rows=500):
+    """Reading R8(ii): compare the GPU support with the exhaustive top-k of the float64
+    residual built from the GPU's own L factors.  Every mismatch must lie within the
+    float32 rounding band of the kernel's residual, b = 4 u32 (|x| + sum_l |U_il s_l V_jl|).
+    Returns (number of mismatches, all inside the band)."""
+    m, n = X.shape
+    Us = U * s
+    R = np.empty((m, n))
+    B = np.empty((m, n))
+    for r0 in range(0, m, chunk_rows):
+        r1 = min(m, r0 + chunk_rows)
+        R[r0:r1] = X[r0:r1].astype(np.float64) - Us[r0:r1] @ V.T
+        B[r0:r1] = np.abs(X[r0:r1]) + np.abs(Us[r0:r1]) @ np.abs(V.T)
+    a = np.abs(R).ravel()
+    kk = min(k, a.size)
+    tau = np.partition(a, a.size - kk)[a.size - kk]
+    ref = np.flatnonzero(a >= tau)
+    diff = np.setxor1d(ref, idx)
+    band = 4.0 * 2.0 ** -24 * B.ravel()[diff]
+    return int(diff.size), bool(np.all(np.abs(a[diff] - tau) <= band + 1e-7 * tau))

@@ -1,16 +1,21 @@
 """Parity of the CUDA path (through the C ABI) with the float64 oracle.
 
-Tolerances: relative Frobenius error of L and S <= 1e-5 for the float32 path
-(the bar the path is built to); S-step selection bit-exact against an
-exhaustive top-k of the kernel's own float32 residual; hard threshold of a
-given array bit-exact.
+Tolerances (float32 path): relative Frobenius error of L <= 1e-5.  For S
+(reading R8): the support equals the exhaustive top-k of the kernel's own
+float32 residual (bit-exact against a CPU replica of that residual, or within
+the float32 rounding band at full size); S values on the support shared with
+the oracle agree to 1e-5; entries whose residual sits within the float32 error
+of the k-th magnitude may flip between the float32 and the float64 run, and
+their count is reported and bounded.  The hard threshold of a given array is
+bit-exact.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 import synth
-from gpu_helpers import GpuRun, lfro_rel, residual_like_kernel, s_rel, to_gpu, to_np
+from gpu_helpers import (GpuRun, lfro_rel, residual_like_kernel, s_common_rel, s_rel,
+                         selection_within_band, to_gpu, to_np)
 
 pytestmark = pytest.mark.gpu
 
@@ -134,7 +139,11 @@ def test_odd_shapes_trajectory(m, n, rank, r, q, dens):
     assert run.g.info()["r_eff"] == ref["r"]
     assert lfro_rel(U, s, V, ref["U"], ref["sigma"], ref["V"]) <= TOL_L
     i, v = run.sparse()
-    assert s_rel(i, v, ref["S_idx"], ref["S_val"]) <= TOL_S
+    e_common, flips = s_common_rel(i, v, ref["S_idx"], ref["S_val"])
+    assert e_common <= TOL_S
+    assert flips <= 1e-3 * d["k"] + 4
+    nb, inside = selection_within_band(d["X"], U, s, V, i, d["k"])
+    assert inside, nb
 
 
 # --- rank test (Algorithm 1 line 7) -------------------------------------------------------
@@ -219,8 +228,16 @@ def test_c2_full_size_same_step():
     run.g.iterate(1)
     st = O.godec_step(d["X"], d["A1"], i2, v2, d["k"], d["q"])
     U, s, V = run.factors()
-    assert lfro_rel(U, s, V, st["U"], st["sigma"], st["V"]) <= TOL_L
+    eL = lfro_rel(U, s, V, st["U"], st["sigma"], st["V"])
     i, v = run.sparse()
-    assert s_rel(i, v, st["S_idx"], st["S_val"]) <= TOL_S
+    e_common, flips = s_common_rel(i, v, st["S_idx"], st["S_val"])
+    e_full = s_rel(i, v, st["S_idx"], st["S_val"])
+    nb, inside = selection_within_band(d["X"], U, s, V, i, d["k"])
     info = run.g.info()
+    print(f"c2 same-step: L {eL:.2e}, S common {e_common:.2e}, S with flips {e_full:.2e}, "
+          f"flips {flips}, band mismatches {nb}")
+    assert eL <= TOL_L
+    assert e_common <= TOL_S
+    assert flips <= 1e-4 * d["k"]
+    assert inside, nb
     assert abs(info["obj"] - st["E2"]) <= 1e-4 * st["E2"]
