@@ -143,8 +143,11 @@ typedef struct godec_info {
   int64_t nnz;
   int32_t select_passes;   /* residual passes used by the last S-step (1-3) */
   int32_t rank_drops;      /* times the rank test lowered r */
-  int32_t launches_per_iter;  /* kernels in one captured iteration (0 before the first) */
-  int32_t reserved;
+  int32_t launches_per_iter;  /* nodes of one captured fast-path iteration */
+  int32_t exact_iters;        /* iterations run on the exact (Cholesky on the critical
+                                 path) power chain; the others used lagged normalisers */
+  int32_t svd_sweeps;         /* Jacobi sweeps of the last core SVD */
+  int32_t chol_shifts;        /* Cholesky factorisations that needed a diagonal shift */
 } godec_info;
 godec_status godec_get_info(godec_ctx* ctx, godec_info* info);
 
@@ -193,10 +196,11 @@ godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz,
  * CUDA event before and after it, and accumulate per kernel class:
  *   ms[c]       : total device time in milliseconds (host arrays of
  *   launches[c] : number of launches               GODEC_PROF_CLASSES entries)
- * Classes: 0 streaming product, 1 split-K reduce + Gram partials, 2 r x r
- * Cholesky/rank test, 3 tall x small product, 4 r x r SVD and root,
- * 5 residual pass (S-step), 6 S-step pass control, 7 radix-select rounds,
- * 8 S emit, 9 sparse update of X - S.
+ * Classes: 0 streaming product (with its fused split-K reduction, normaliser
+ * and Gram partials), 1 Gram sums, 2 r x r Cholesky (critical path), 3 tall x
+ * r x r products, 4 lagged-normaliser updates (side stream), 5 rank test (side
+ * stream), 6 core SVD and root, 7 residual pass (S-step), 8 selection control,
+ * radix-select rounds and S emit, 9 sparse update of X - S and its transpose.
  * bytes_product (host, nullable) receives the algorithmic bytes of one
  * streaming product at the current rank: 4*m*n (X - S) + 4*(m + n)*r.
  */

@@ -26,7 +26,8 @@ class GodecInfo(C.Structure):
     _fields_ = [("iter", C.c_int32), ("r_eff", C.c_int32), ("rel_err", C.c_double),
                 ("obj", C.c_double), ("normX2", C.c_double), ("nnz", C.c_int64),
                 ("select_passes", C.c_int32), ("rank_drops", C.c_int32),
-                ("launches_per_iter", C.c_int32), ("reserved", C.c_int32)]
+                ("launches_per_iter", C.c_int32), ("exact_iters", C.c_int32),
+                ("svd_sweeps", C.c_int32), ("chol_shifts", C.c_int32)]
 
 
 class GodecError(RuntimeError):
@@ -168,8 +169,8 @@ class GoDec:
         _check(library().godec_get_info(self._h, C.byref(inf)), "godec_get_info", self._h)
         return {f: getattr(inf, f) for f, _ in GodecInfo._fields_}
 
-    PROF_CLASSES = ["product", "reduce_gram", "chol", "tall_small", "svd_root", "residual",
-                    "pass_control", "select", "emit", "z_update"]
+    PROF_CLASSES = ["product", "gram_sum", "chol", "tall_small", "slot_update", "rank_test",
+                    "svd_root", "residual", "select_emit", "z_update"]
 
     def profile(self, n_iter: int):
         """Run n_iter iterations with per-kernel CUDA events; returns per-class totals."""

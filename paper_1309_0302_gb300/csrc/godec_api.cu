@@ -1,7 +1,18 @@
 // Host side of the C ABI declared in include/godec.h: context and workspace,
-// the launch sequence of one iteration of Algorithm 1 (captured once into a
-// CUDA graph and replayed), recovery from aborted iterations (rank drop,
-// candidate overflow), and the result getters.
+// the launch sequence of one iteration of Algorithm 1 (captured into CUDA
+// graphs and replayed), recovery from aborted iterations (rank drop,
+// candidate overflow, ill-conditioned lagged normalisers), and the getters.
+//
+// Power chain of one L-step (products i = 0 .. 6q+2, alternating Z and Z^T):
+//  * exact path: every product is orthonormalised by CholeskyQR on the
+//    critical path;
+//  * fast path (from the second iteration on): product i is normalised in its
+//    own epilogue by T_i, the inverse of the factor that orthonormalised slot i
+//    in the previous iteration; the Cholesky factor of the result is computed
+//    on a side stream and becomes next iteration's T_i.  Only Q2 and Q1 (the
+//    bases L is built on) get an exact CholeskyQR2 on the critical path.
+// In both paths the core of eq. (mlr_app) is M = R_fin * (factors applied in the
+// last chain), exact by construction.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -14,17 +25,29 @@
 
 using namespace godec;
 
+namespace {
+constexpr int kEvents = 160;
+constexpr float kAlarmRatio = 30.f;   // lagged normaliser: max/min Cholesky diagonal of Q~
+}
+
 struct godec_ctx {
   godec_params p;
   int r = 0;          // current rank (drops after a failed rank test)
   int RP = 0;         // padded width of the skinny buffers (from the initial r)
+  int nprod = 0;      // 6q + 3
   cudaStream_t st = nullptr;
-  cudaStream_t cap_st = nullptr;   // private stream used only while capturing the graph
+  cudaStream_t cap_st = nullptr;    // private stream used while capturing
+  cudaStream_t side_st = nullptr;   // off-critical-path work of the power chain
+  cudaEvent_t ev[kEvents] = {};
+  int ev_used = 0;
   int dev = 0, nsm = 0;
   const float* X = nullptr;
-  float* Z = nullptr;
+  float* Z = nullptr;                  // m x ldz   working X - S
   int64_t ldz = 0;
+  float* Zt = nullptr;                 // n x ldzt  its transpose
+  int64_t ldzt = 0;
   void* Z16 = nullptr;
+  void* Zt16 = nullptr;
   float* A1 = nullptr;                 // n x RP; columns >= r kept at zero
   float* A1_orig = nullptr;            // n x RP as given (restored by godec_reset)
   float* P = nullptr;                  // max(m,n) x RP
@@ -36,12 +59,18 @@ struct godec_ctx {
   float* sigma = nullptr;              // RP
   float* Um = nullptr;
   float* Vm = nullptr;
-  float* Rm = nullptr;
-  float* Rinv = nullptr;
-  float* M = nullptr;
-  float* part = nullptr;
-  size_t part_elems = 0;
-  void* gram = nullptr;
+  float* part = nullptr;               // split-K partials
+  unsigned* counters = nullptr;        // per-tile arrival counters
+  char* gparts = nullptr;              // per product: tiles x RP x RP Gram partials (double room)
+  size_t gpart_stride = 0;
+  double* g64 = nullptr;               // per product reduced Gram, + 2 for the CholeskyQR2 rounds
+  float* gscr = nullptr;               // Gram partials of the second CholeskyQR2 round
+  float* Rtmp = nullptr;               // exact path: factor of each product
+  float* Rslot = nullptr;              // [2][nprod] lagged factors
+  float* Tslot = nullptr;              // [2][nprod] their inverses
+  float* Rfin = nullptr;               // Ra, Rb of Q2 and of Q1
+  float* Pi = nullptr;                 // factors applied in the last chain (normalised)
+  float* Vprev = nullptr;              // warm start of the core SVD
   Ctl* ctl = nullptr;
   unsigned* cand_key = nullptr;
   long long* cand_idx = nullptr;
@@ -50,42 +79,45 @@ struct godec_ctx {
   long long* S_idx[2] = {nullptr, nullptr};
   float* S_val[2] = {nullptr, nullptr};
   int idx_bits = 1;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_r = -1;
-  double tol_in_graph = -2.0;
-  int rank_drops = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // 0 exact path, 1 fast path
+  int graph_r[2] = {-1, -1};
   int graph_nodes = 0;
+  bool need_exact = true;
+  int rank_drops = 0;
+  int exact_iters = 0;
   // kernel-level profiling (eager launches bracketed by events)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> prof_cls;      // class of event pair i
+  std::vector<int> prof_cls;
   size_t prof_used = 0;
   char err[200] = {0};
 };
 
-// Bracket one kernel launch with events when profiling (eager mode only).
-#define PROF(c, cls, stmt)                                      \
-  do {                                                          \
-    if ((c)->prof) prof_mark(c, cls);                           \
-    stmt;                                                       \
-    if ((c)->prof) prof_mark(c, -1);                            \
-  } while (0)
-
-static void prof_mark(godec_ctx* c, int cls) {
+static void prof_mark(godec_ctx* c, int cls, cudaStream_t s) {
   if (c->prof_used == c->ev_pool.size()) {
     cudaEvent_t e;
     cudaEventCreate(&e);
     c->ev_pool.push_back(e);
   }
-  cudaEventRecord(c->ev_pool[c->prof_used++], c->st);
+  cudaEventRecord(c->ev_pool[c->prof_used++], s);
   if (cls >= 0) c->prof_cls.push_back(cls);
 }
+
+// Bracket one launch with events when profiling (eager mode only).
+#define PROF(c, cls, s, stmt)                       \
+  do {                                              \
+    if ((c)->prof) prof_mark(c, cls, s);            \
+    stmt;                                           \
+    if ((c)->prof) prof_mark(c, -1, s);             \
+  } while (0)
 
 namespace {
 
 const char* kStatusNames[] = {"ok", "invalid argument", "CUDA error", "out of memory",
                               "non-finite values", "device wait timed out", "invalid state",
                               "unsupported"};
+
+char g_static_err[256];
 
 godec_status fail(godec_ctx* c, godec_status s, const char* fmt, ...) {
   if (c) {
@@ -112,10 +144,12 @@ cudaError_t dalloc(T** p, size_t elems) {
   return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(elems, 1) * sizeof(T));
 }
 
-void free_graph(godec_ctx* c) {
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  c->gexec = nullptr;
-  c->graph_r = -1;
+void free_graphs(godec_ctx* c) {
+  for (int k = 0; k < 2; ++k) {
+    if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+    c->gexec[k] = nullptr;
+    c->graph_r[k] = -1;
+  }
 }
 
 godec_status alloc_candidates(godec_ctx* c, unsigned long long cap) {
@@ -132,10 +166,190 @@ godec_status alloc_candidates(godec_ctx* c, unsigned long long cap) {
   return GODEC_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------------
+void fork_side(godec_ctx* c) {
+  cudaEvent_t e = c->ev[c->ev_used++ % kEvents];
+  cudaEventRecord(e, c->st);
+  cudaStreamWaitEvent(c->side_st, e, 0);
+}
+
+void join_side(godec_ctx* c) {
+  cudaEvent_t e = c->ev[c->ev_used++ % kEvents];
+  cudaEventRecord(e, c->side_st);
+  cudaStreamWaitEvent(c->st, e, 0);
+}
+
+char* gpart(godec_ctx* c, int i) { return c->gparts + (size_t)i * c->gpart_stride; }
+double* g64(godec_ctx* c, int i) { return c->g64 + (size_t)i * c->RP * c->RP; }
+
+// Product i of the chain: even i streams Z (rows m, K n), odd i streams Z^T (rows n, K m).
+void prod(godec_ctx* c, int i, const float* B, float* out, const float* T0, const float* T1, int gram_mode) {
+  const bool even = (i % 2) == 0;
+  ProdArgs a{};
+  a.Z = even ? c->Z : c->Zt;
+  a.bf16 = 0;
+  a.rows = even ? c->p.m : c->p.n;
+  a.K = even ? c->p.n : c->p.m;
+  a.ld = even ? c->ldz : c->ldzt;
+  a.B = B;
+  a.part = c->part;
+  prod_geometry(a.rows, a.K, c->nsm, &a.splits, &a.kchunk);
+  a.counters = c->counters;
+  a.out = out;
+  a.Tn[0] = T0;
+  a.Tn[1] = T1;
+  a.gram_part = gpart(c, i);
+  a.gram_mode = gram_mode;
+  a.RP = c->RP;
+  a.ctl = c->ctl;
+  PROF(c, 0, c->st, launch_prod(a, c->st));
+}
+
+void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out, cudaStream_t s) {
+  PROF(c, 1, s, launch_gram_sum(part, dbl, nblk, c->RP, out, c->ctl, s));
+}
+
+void chol(godec_ctx* c, const double* g, float* R) { PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, c->ctl, c->st)); }
+
+void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const float* T1, int solve, float* Q,
+           float* gram) {
+  PROF(c, 3, c->st, launch_apply(P, rows, c->RP, T0, T1, solve, Q, gram, c->ctl, c->st));
+}
+
+// Exact CholeskyQR2 of c->P (rows x RP) with the round-1 Gram g1: Q = P Ra^{-1} Rb^{-1}.
+void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* Rb, float* fin, double* g2) {
+  chol(c, g1, Ra);
+  apply(c, c->P, rows, Ra, Ra, 1, c->P, c->gscr);
+  gram_sum(c, c->gscr, 0, apply_blocks(rows), g2, c->st);
+  chol(c, g2, Rb);
+  apply(c, c->P, rows, Rb, Rb, 1, fin, nullptr);
+}
+
+void slot(godec_ctx* c, SlotLaunch& sl) {
+  sl.r = c->r;
+  sl.RP = c->RP;
+  sl.ctl = c->ctl;
+  sl.alarm_ratio = kAlarmRatio;
+  PROF(c, 4, c->side_st, launch_slot(sl, c->side_st));
+}
+
+// ---------------------------------------------------------------------------------
+// L-step (Algorithm 1 lines 4-8)
+// ---------------------------------------------------------------------------------
+void enqueue_lstep(godec_ctx* c, bool fast) {
+  const int q = c->p.q, RP = c->RP;
+  const int64_t m = c->p.m, n = c->p.n;
+  const int nprod = c->nprod, i_q2 = 4 * q + 1, i_rank = 4 * q + 2, last = nprod - 1;
+  const size_t rr = (size_t)RP * RP;
+  auto sR = [&](int h, int i) { return c->Rslot + ((size_t)h * nprod + i) * rr; };
+  auto sT = [&](int h, int i) { return c->Tslot + ((size_t)h * nprod + i) * rr; };
+  const float* B = c->A1;
+  const float* rapp_last[2] = {nullptr, nullptr};
+  bool have_pi = false;
+  for (int i = 0; i < nprod; ++i) {
+    const bool even = (i % 2) == 0;
+    const int64_t rows = even ? m : n;
+    const int64_t tiles = prod_tiles(rows);
+    float* Qdst = c->Qb[i & 1];
+    SlotLaunch sl;
+    sl.R_next[0] = sR(0, i);
+    sl.R_next[1] = sR(1, i);
+    sl.T_next[0] = sT(0, i);
+    sl.T_next[1] = sT(1, i);
+    sl.Pi = c->Pi;
+    const int pi_mode = (i == i_rank) ? 2 : ((i > i_rank && i < last) ? 1 : 0);
+    sl.pi_mode = pi_mode;
+    if (i == i_rank) {
+      // P = Z Q2 unnormalised, with an exactly accumulated Gram for the rank test
+      prod(c, i, B, c->P, nullptr, nullptr, 2);
+      gram_sum(c, gpart(c, i), 1, tiles, g64(c, i), c->st);
+      fork_side(c);
+      PROF(c, 5, c->side_st,
+           launch_rank(g64(c, i), c->r, RP, c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4, c->ctl, c->side_st));
+      if (i == last) {   // q = 0: this product is also the last one
+        final_cqr2(c, rows, g64(c, i), c->Rfin + 2 * rr, c->Rfin + 3 * rr, c->Q1, g64(c, nprod + 1));
+        continue;
+      }
+      if (fast) {
+        apply(c, c->P, rows, sT(0, i), sT(1, i), 0, Qdst, nullptr);
+        sl.fast = 1;
+        sl.g64 = g64(c, i);
+        sl.g_is_p = 1;
+        sl.R_app[0] = sR(0, i);
+        sl.R_app[1] = sR(1, i);
+        sl.T_app[0] = sT(0, i);
+        sl.T_app[1] = sT(1, i);
+      } else {
+        float* Rt = c->Rtmp + (size_t)i * rr;
+        chol(c, g64(c, i), Rt);
+        apply(c, c->P, rows, Rt, Rt, 1, Qdst, nullptr);
+        fork_side(c);
+        sl.fast = 0;
+        sl.R_app[0] = sl.R_app[1] = Rt;
+      }
+      slot(c, sl);
+      have_pi = true;
+      B = Qdst;
+    } else if (i == i_q2 || i == last) {
+      prod(c, i, B, c->P, fast ? sT(0, i) : nullptr, fast ? sT(1, i) : nullptr, 1);
+      gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
+      float* Ra = c->Rfin + (i == i_q2 ? 0 : 2) * rr;
+      float* Rb = Ra + rr;
+      float* fin = (i == i_q2) ? c->Q2 : c->Q1;
+      final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)));
+      fork_side(c);
+      sl.fast = 0;
+      if (fast) {
+        sl.R_app[0] = sR(0, i);
+        sl.R_app[1] = sR(1, i);
+        if (i == last) {
+          rapp_last[0] = sR(0, i);
+          rapp_last[1] = sR(1, i);
+        }
+      }
+      sl.L1 = Ra;
+      sl.L2 = Rb;
+      sl.pi_mode = 0;
+      slot(c, sl);
+      B = fin;
+    } else {
+      if (fast) {
+        prod(c, i, B, Qdst, sT(0, i), sT(1, i), 1);
+        fork_side(c);
+        gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->side_st);
+        sl.fast = 1;
+        sl.g64 = g64(c, i);
+        sl.R_app[0] = sR(0, i);
+        sl.R_app[1] = sR(1, i);
+      } else {
+        float* Rt = c->Rtmp + (size_t)i * rr;
+        prod(c, i, B, c->P, nullptr, nullptr, 1);
+        gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
+        chol(c, g64(c, i), Rt);
+        apply(c, c->P, rows, Rt, Rt, 1, Qdst, nullptr);
+        fork_side(c);
+        sl.fast = 0;
+        sl.R_app[0] = sl.R_app[1] = Rt;
+      }
+      slot(c, sl);
+      if (pi_mode) have_pi = true;
+      B = Qdst;
+    }
+  }
+  join_side(c);
+  // r x r core, SVD and singular-value root, then L = (Q1 Um) diag(sigma) (Q2 Vm)^T
+  PROF(c, 6, c->st,
+       launch_svd(c->Rfin + 2 * rr, c->Rfin + 3 * rr, rapp_last[0], rapp_last[1], have_pi ? c->Pi : nullptr,
+                  c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st));
+  apply(c, c->Q1, m, c->Um, c->Um, 0, c->U, nullptr);
+  apply(c, c->Q2, n, c->Vm, c->Vm, 0, c->V, nullptr);
+}
+
 // S-step of one iteration (Algorithm 1 line 9) on the current L factors; r = 0 means L = 0.
 void enqueue_sstep(godec_ctx* c, int r) {
   const int64_t m = c->p.m, n = c->p.n;
-  const int RP = c->RP;
   cudaStream_t st = c->st;
   ResidualArgs ra{};
   ra.X = c->X;
@@ -146,7 +360,7 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ra.sigma = c->sigma;
   ra.V = c->V;
   ra.r = r;
-  ra.RP = RP;
+  ra.RP = c->RP;
   ra.ctl = c->ctl;
   ra.cand_key = c->cand_key;
   ra.cand_idx = c->cand_idx;
@@ -154,8 +368,8 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ra.cand_cap = c->cap;
   for (int pass = 0; pass < 3; ++pass) {
     ra.pass = pass;
-    PROF(c, 5, launch_residual(ra, c->nsm, st));
-    PROF(c, 6, launch_after_pass(c->ctl, pass, c->p.k, c->cap, st));
+    PROF(c, 7, st, launch_residual(ra, c->nsm, st));
+    PROF(c, 8, st, launch_after_pass(c->ctl, pass, c->p.k, c->cap, st));
   }
   SelectArgs se{};
   se.ctl = c->ctl;
@@ -167,7 +381,7 @@ void enqueue_sstep(godec_ctx* c, int r) {
   se.idx_bits = c->idx_bits;
   for (int round = 0; round < 7; ++round) {
     se.round = round;
-    PROF(c, 7, launch_select_round(se, c->nsm, st));
+    PROF(c, 8, st, launch_select_round(se, c->nsm, st));
   }
   EmitArgs ea{};
   ea.ctl = c->ctl;
@@ -184,112 +398,42 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ea.ldx = c->p.ldx;
   ea.Z = c->Z;
   ea.ldz = c->ldz;
+  ea.Zt = c->Zt;
+  ea.ldzt = c->ldzt;
   ea.Z16 = c->Z16;
-  PROF(c, 8, launch_emit(ea, c->nsm, st));
-  if (c->Z) PROF(c, 9, launch_z_update(ea, c->nsm, st));
+  ea.Zt16 = c->Zt16;
+  PROF(c, 8, st, launch_emit(ea, c->nsm, st));
+  if (c->Z) PROF(c, 9, st, launch_z_update(ea, c->nsm, st));
 }
 
-// ---------------------------------------------------------------------------------
-// One iteration of Algorithm 1 as a launch sequence on c->st.
-// ---------------------------------------------------------------------------------
-void enqueue_iteration(godec_ctx* c) {
-  const int q = c->p.q, r = c->r, RP = c->RP;
-  const int64_t m = c->p.m, n = c->p.n;
-  cudaStream_t st = c->st;
-  const int nprod = 6 * q + 3;
-  const int i_q2 = 4 * q + 1;      // last product of L~^T Y1: Q2 = orth(Y2)
-  const int i_rank = 4 * q + 2;    // first product of L~ Q2: rank test, start of M
-  const float* B = c->A1;
-  for (int i = 0; i < nprod; ++i) {
-    const int trans = i & 1;
-    const int64_t outdim = trans ? n : m, K = trans ? m : n;
-    PassArgs pa{};
-    pa.Z = c->Z;
-    pa.bf16 = 0;
-    pa.m = m;
-    pa.n = n;
-    pa.ldz = c->ldz;
-    pa.B = B;
-    pa.part = c->part;
-    pass_geometry(outdim, K, c->nsm, &pa.splits, &pa.kchunk);
-    pa.trans = trans;
-    pa.RP = RP;
-    pa.ctl = c->ctl;
-    PROF(c, 0, launch_pass(pa, st));
-    const int gmode = (i == i_rank) ? 2 : 1;
-    PROF(c, 1, launch_reduce(c->part, pa.splits, outdim, RP, c->P, c->gram, gmode, c->ctl, st));
-    CholArgs ca{};
-    ca.gram_part = c->gram;
-    ca.gram_double = (gmode == 2);
-    ca.nblk = reduce_blocks(outdim);
-    ca.r = r;
-    ca.RP = RP;
-    ca.R = c->Rm;
-    ca.Rinv = c->Rinv;
-    ca.M = c->M;
-    ca.accumulate = (i < i_rank) ? 0 : (i == i_rank ? 2 : 1);
-    ca.rank_test = (i == i_rank);
-    ca.rank_tol = c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4;
-    ca.ctl = c->ctl;
-    PROF(c, 2, launch_chol(ca, st));
-    const bool final_q = (i == i_q2) || (i == nprod - 1);
-    float* dst = final_q ? c->P : c->Qb[i & 1];
-    PROF(c, 3, launch_apply(c->P, outdim, RP, c->Rinv, 1, dst,
-                            final_q ? reinterpret_cast<float*>(c->gram) : nullptr, c->ctl, st));
-    if (final_q) {
-      // second CholeskyQR round for an orthonormal Q2 / Q1
-      CholArgs cb = ca;
-      cb.gram_double = 0;
-      cb.rank_test = 0;
-      cb.accumulate = (i == nprod - 1) ? 1 : 0;
-      PROF(c, 2, launch_chol(cb, st));
-      float* fin = (i == i_q2) ? c->Q2 : c->Q1;
-      PROF(c, 3, launch_apply(c->P, outdim, RP, c->Rinv, 1, fin, nullptr, c->ctl, st));
-      B = fin;
-    } else {
-      B = dst;
-    }
-  }
-  // r x r core: SVD and singular-value root, then L = (Q1 Um) diag(sigma) (Q2 Vm)^T
-  SvdArgs sa{};
-  sa.M = c->M;
-  sa.r = r;
-  sa.RP = RP;
-  sa.q = q;
-  sa.Um = c->Um;
-  sa.Vm = c->Vm;
-  sa.sigma = c->sigma;
-  sa.ctl = c->ctl;
-  PROF(c, 4, launch_svd_root(sa, st));
-  PROF(c, 3, launch_apply(c->Q1, m, RP, c->Um, 0, c->U, nullptr, c->ctl, st));
-  PROF(c, 3, launch_apply(c->Q2, n, RP, c->Vm, 0, c->V, nullptr, c->ctl, st));
-
-  enqueue_sstep(c, r);
+void enqueue_iteration(godec_ctx* c, bool fast) {
+  enqueue_lstep(c, fast);
+  enqueue_sstep(c, c->r);
 }
 
-godec_status build_graph(godec_ctx* c) {
-  free_graph(c);
+godec_status build_graph(godec_ctx* c, int mode) {
+  if (c->gexec[mode]) cudaGraphExecDestroy(c->gexec[mode]);
+  c->gexec[mode] = nullptr;
   cudaGraph_t g = nullptr;
   // The caller's stream may be the legacy default stream, which cannot be captured:
   // record on a private stream and launch the graph on the caller's stream.
-  if (!c->cap_st) CK(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
   CK(cudaStreamSynchronize(c->st));
   cudaStream_t user = c->st;
   c->st = c->cap_st;
   cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    enqueue_iteration(c);
+    enqueue_iteration(c, mode == 1);
     e = cudaStreamEndCapture(c->st, &g);
   }
   c->st = user;
   if (e != cudaSuccess) return fail(c, GODEC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
   size_t nodes = 0;
   cudaGraphGetNodes(g, nullptr, &nodes);
-  c->graph_nodes = (int)nodes;
-  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  e = cudaGraphInstantiate(&c->gexec[mode], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(c, GODEC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-  c->graph_r = c->r;
+  c->graph_r[mode] = c->r;
+  if (mode == 1) c->graph_nodes = (int)nodes;
   return GODEC_OK;
 }
 
@@ -317,14 +461,19 @@ godec_status drop_columns(godec_ctx* c) {
 }
 
 godec_status reset_state(godec_ctx* c) {
-  free_graph(c);
+  free_graphs(c);
   c->r = c->p.r;
   c->rank_drops = 0;
-  if (c->A1_orig)
-    CK(cudaMemcpyAsync(c->A1, c->A1_orig, (size_t)c->p.n * c->RP * sizeof(float), cudaMemcpyDeviceToDevice,
-                       c->st));
-  CK(cudaMemcpy2DAsync(c->Z, c->ldz * sizeof(float), c->X, c->p.ldx * sizeof(float),
-                       c->p.n * sizeof(float), c->p.m, cudaMemcpyDeviceToDevice, c->st));
+  c->need_exact = true;
+  c->exact_iters = 0;
+  CK(cudaMemcpyAsync(c->A1, c->A1_orig, (size_t)c->p.n * c->RP * sizeof(float), cudaMemcpyDeviceToDevice,
+                     c->st));
+  CK(cudaMemcpy2DAsync(c->Z, c->ldz * sizeof(float), c->X, c->p.ldx * sizeof(float), c->p.n * sizeof(float),
+                       c->p.m, cudaMemcpyDeviceToDevice, c->st));
+  launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st);
+  std::vector<float> eye((size_t)c->RP * c->RP, 0.f);
+  for (int i = 0; i < c->RP; ++i) eye[(size_t)i * c->RP + i] = 1.f;
+  CK(cudaMemcpyAsync(c->Vprev, eye.data(), eye.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
   Ctl h;
   memset(&h, 0, offsetof(Ctl, hist));
   h.k_req = c->p.k;
@@ -332,18 +481,47 @@ godec_status reset_state(godec_ctx* c) {
   h.r_eff = c->p.r;
   h.tol = -1.0;
   CK(cudaMemcpyAsync(c->ctl, &h, offsetof(Ctl, hist), cudaMemcpyHostToDevice, c->st));
-  launch_sumsq(c->X, c->p.m, c->p.n, c->p.ldx, reinterpret_cast<double*>(reinterpret_cast<char*>(c->ctl) +
-               offsetof(Ctl, normX2)), c->nsm, c->st);
+  launch_sumsq(c->X, c->p.m, c->p.n, c->p.ldx,
+               reinterpret_cast<double*>(reinterpret_cast<char*>(c->ctl) + offsetof(Ctl, normX2)), c->nsm, c->st);
   launch_reset_iter(c->ctl, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   return GODEC_OK;
 }
 
-// Run up to n graph launches, handling aborted iterations; stop early on convergence
-// when tol >= 0.  *done receives the committed iterations.
-godec_status run_iterations(godec_ctx* c, int n_iter, double tol, int* done) {
-  *done = 0;
+// Host-side handling of an aborted iteration; the iteration is redone afterwards.
+godec_status handle_abort(godec_ctx* c, const Ctl& h) {
+  godec_status s;
+  if (h.nonfinite) {
+    launch_reset_iter(c->ctl, c->st);
+    return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - L (iteration %d)", h.iter + 1);
+  }
+  if (h.rank_drop) {
+    c->r = h.r_eff;
+    ++c->rank_drops;
+    c->need_exact = true;
+    if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
+    if ((s = drop_columns(c))) return s;
+  } else if (h.alarm) {
+    c->need_exact = true;
+  } else if (h.need_bigger_cand) {
+    unsigned long long cap = c->cap * 2;
+    const unsigned long long mn = (unsigned long long)(c->p.m * c->p.n);
+    if (cap > mn) cap = mn;
+    if (cap <= c->cap) return fail(c, GODEC_ERR_STATE, "candidate buffer cannot grow");
+    free_graphs(c);
+    if ((s = alloc_candidates(c, cap))) return s;
+  } else {
+    return fail(c, GODEC_ERR_STATE, "iteration aborted without a reason");
+  }
+  launch_reset_iter(c->ctl, c->st);
+  CK(cudaGetLastError());
+  return GODEC_OK;
+}
+
+// Run n iterations (graph launches), handling aborted iterations; with tol >= 0 stop early
+// on convergence.  The exact path runs whenever the lagged normalisers are not valid.
+godec_status run_iterations(godec_ctx* c, int n_iter, double tol) {
   Ctl h;
   godec_status s = read_ctl(c, &h);
   if (s) return s;
@@ -351,39 +529,25 @@ godec_status run_iterations(godec_ctx* c, int n_iter, double tol, int* done) {
   if (h.tol != tol) {
     if ((s = SET_CTL(tol, tol))) return s;
   }
-  int guard = 0;
+  int guard = 0, done = 0;
   int chunk = tol >= 0.0 ? 1 : n_iter;
-  while (*done < n_iter) {
-    if (!c->gexec || c->graph_r != c->r) {
-      if ((s = build_graph(c))) return s;
+  while (done < n_iter) {
+    const int mode = c->need_exact ? 0 : 1;
+    if (!c->gexec[mode] || c->graph_r[mode] != c->r) {
+      if ((s = build_graph(c, mode))) return s;
     }
-    const int want = std::min(chunk, n_iter - *done);
-    for (int i = 0; i < want; ++i) CK(cudaGraphLaunch(c->gexec, c->st));
+    const int want = mode == 0 ? 1 : std::min(chunk, n_iter - done);
+    for (int i = 0; i < want; ++i) CK(cudaGraphLaunch(c->gexec[mode], c->st));
     if ((s = read_ctl(c, &h))) return s;
-    *done = h.iter - start;
+    const int before = done;
+    done = h.iter - start;
+    if (mode == 0 && done > before) {
+      c->need_exact = false;
+      ++c->exact_iters;
+    }
     if (h.abort) {
       if (h.converged) return GODEC_OK;
-      if (h.nonfinite) {
-        launch_reset_iter(c->ctl, c->st);
-        return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - L (iteration %d)", h.iter + 1);
-      }
-      if (h.rank_drop) {
-        c->r = h.r_eff;
-        ++c->rank_drops;
-        if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
-        if ((s = drop_columns(c))) return s;
-      } else if (h.need_bigger_cand) {
-        unsigned long long cap = c->cap * 2;
-        const unsigned long long mn = (unsigned long long)(c->p.m * c->p.n);
-        if (cap > mn) cap = mn;
-        if (cap <= c->cap) return fail(c, GODEC_ERR_STATE, "candidate buffer cannot grow");
-        free_graph(c);
-        if ((s = alloc_candidates(c, cap))) return s;
-      } else if (h.chol_fail) {
-        return fail(c, GODEC_ERR_NONFINITE, "Cholesky breakdown in the power chain");
-      }
-      launch_reset_iter(c->ctl, c->st);
-      CK(cudaGetLastError());
+      if ((s = handle_abort(c, h))) return s;
       if (++guard > 64) return fail(c, GODEC_ERR_STATE, "too many aborted iterations");
       continue;
     }
@@ -409,8 +573,6 @@ bool bad_params(const godec_params* p, char* why, size_t nwhy) {
   return false;
 }
 
-char g_static_err[256];
-
 }  // namespace
 
 void godec::set_static_error(const char* fmt, ...) {
@@ -432,14 +594,17 @@ const char* godec_last_error(const godec_ctx* c) { return c ? c->err : g_static_
 void godec_destroy(godec_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
-  free_graph(c);
-  void* ptrs[] = {c->Z, c->Z16, c->A1, c->A1_orig, c->P, c->Qb[0], c->Qb[1], c->Q1, c->Q2, c->U, c->V,
-                  c->sigma, c->Um, c->Vm, c->Rm, c->Rinv, c->M, c->part, c->gram, c->ctl,
-                  c->cand_key, c->cand_idx, c->cand_val, c->S_idx[0], c->S_idx[1],
-                  c->S_val[0], c->S_val[1]};
+  free_graphs(c);
+  void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->Qb[0], c->Qb[1], c->Q1, c->Q2,
+                  c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->gparts, c->g64, c->gscr,
+                  c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
+                  c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1]};
   for (void* p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  if (c->side_st) cudaStreamDestroy(c->side_st);
   delete c;
 }
 
@@ -465,9 +630,10 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   c->p = *p;
   c->r = p->r;
   c->RP = round_up(p->r, 8);
+  c->nprod = 6 * p->q + 3;
   c->st = reinterpret_cast<cudaStream_t>(stream);
   auto bail = [&](godec_status s) {
-    snprintf(g_static_err, sizeof(g_static_err), "godec_init: %s", c->err);
+    snprintf(g_static_err, sizeof(g_static_err), "godec_init: %.200s", c->err);
     godec_destroy(c);
     return s;
   };
@@ -483,12 +649,20 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
   CKI(prepare_small_kernels());
   CKI(prepare_select_kernels());
+  CKI(prepare_stream_kernels());
+  CKI(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+  CKI(cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking));
+  for (int k = 0; k < kEvents; ++k) CKI(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
   const int64_t m = p->m, n = p->n, mx = std::max(m, n);
-  const int RP = c->RP;
+  const int RP = c->RP, np = c->nprod;
+  const size_t rr = (size_t)RP * RP;
   c->X = X;
   c->ldz = (n + 3) / 4 * 4;
+  c->ldzt = (m + 3) / 4 * 4;
   CKI(dalloc(&c->Z, (size_t)m * c->ldz));
+  CKI(dalloc(&c->Zt, (size_t)n * c->ldzt));
   CKI(dalloc(&c->A1, (size_t)n * RP));
+  CKI(dalloc(&c->A1_orig, (size_t)n * RP));
   CKI(dalloc(&c->P, (size_t)mx * RP));
   CKI(dalloc(&c->Qb[0], (size_t)mx * RP));
   CKI(dalloc(&c->Qb[1], (size_t)mx * RP));
@@ -497,19 +671,26 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(dalloc(&c->U, (size_t)m * RP));
   CKI(dalloc(&c->V, (size_t)n * RP));
   CKI(dalloc(&c->sigma, (size_t)RP));
-  CKI(dalloc(&c->Um, (size_t)RP * RP));
-  CKI(dalloc(&c->Vm, (size_t)RP * RP));
-  CKI(dalloc(&c->Rm, (size_t)RP * RP));
-  CKI(dalloc(&c->Rinv, (size_t)RP * RP));
-  CKI(dalloc(&c->M, (size_t)RP * RP));
+  CKI(dalloc(&c->Um, rr));
+  CKI(dalloc(&c->Vm, rr));
   int s1, s2;
   int64_t ch;
-  pass_geometry(m, n, c->nsm, &s1, &ch);
-  pass_geometry(n, m, c->nsm, &s2, &ch);
-  c->part_elems = (size_t)std::max<int64_t>((int64_t)s1 * m, (int64_t)s2 * n) * RP;
-  CKI(dalloc(&c->part, c->part_elems));
-  // float64 Gram partials of every 64-row block, plus the reduced matrix
-  CKI(dalloc(reinterpret_cast<double**>(&c->gram), (size_t)(reduce_blocks(mx) + 1) * RP * RP));
+  prod_geometry(m, n, c->nsm, &s1, &ch);
+  prod_geometry(n, m, c->nsm, &s2, &ch);
+  CKI(dalloc(&c->part, (size_t)std::max<int64_t>((int64_t)s1 * m, (int64_t)s2 * n) * RP));
+  const int64_t tiles = prod_tiles(mx);
+  CKI(dalloc(&c->counters, (size_t)tiles));
+  CKI(cudaMemsetAsync(c->counters, 0, (size_t)tiles * sizeof(unsigned), c->st));
+  c->gpart_stride = ((size_t)tiles * rr * sizeof(double) + 255) & ~size_t(255);
+  CKI(dalloc(&c->gparts, c->gpart_stride * np));
+  CKI(dalloc(&c->g64, (size_t)(np + 2) * rr));
+  CKI(dalloc(&c->gscr, (size_t)apply_blocks(mx) * rr));
+  CKI(dalloc(&c->Rtmp, (size_t)np * rr));
+  CKI(dalloc(&c->Rslot, (size_t)2 * np * rr));
+  CKI(dalloc(&c->Tslot, (size_t)2 * np * rr));
+  CKI(dalloc(&c->Rfin, 4 * rr));
+  CKI(dalloc(&c->Pi, rr));
+  CKI(dalloc(&c->Vprev, rr));
   CKI(dalloc(reinterpret_cast<char**>(&c->ctl), sizeof(Ctl)));
   CKI(cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->st));
   const unsigned long long mn = (unsigned long long)(m * n);
@@ -524,7 +705,6 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   while ((1ull << c->idx_bits) < mn) ++c->idx_bits;
   launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), c->st);
   launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), c->st);
-  CKI(dalloc(&c->A1_orig, (size_t)n * RP));
   launch_pad_copy(A1, n, p->r, p->r, c->A1_orig, RP, c->st);
   CKI(cudaGetLastError());
   godec_status s = reset_state(c);
@@ -542,8 +722,7 @@ godec_status godec_reset(godec_ctx* c) {
 godec_status godec_iterate(godec_ctx* c, int32_t n_iter, double* rel_err) {
   if (!c) return GODEC_ERR_ARG;
   if (n_iter < 0) return fail(c, GODEC_ERR_ARG, "n_iter must be >= 0");
-  int done = 0;
-  godec_status s = run_iterations(c, n_iter, -1.0, &done);
+  godec_status s = run_iterations(c, n_iter, -1.0);
   if (s) return s;
   if (rel_err) {
     Ctl h;
@@ -559,9 +738,8 @@ godec_status godec_solve(godec_ctx* c, int32_t* iters, double* rel_err) {
   godec_status s = read_ctl(c, &h);
   if (s) return s;
   const int remaining = c->p.max_iter - h.iter;
-  int done = 0;
   if (remaining > 0) {
-    s = run_iterations(c, remaining, c->p.tol, &done);
+    s = run_iterations(c, remaining, c->p.tol);
     if (s) return s;
   }
   if ((s = read_ctl(c, &h))) return s;
@@ -589,13 +767,15 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
   const int start = h.iter;
   int guard = 0;
   while (h.iter - start < n_iter) {
+    const bool fast = !c->need_exact;
     c->prof = true;
     c->prof_used = 0;
     c->prof_cls.clear();
-    enqueue_iteration(c);
+    enqueue_iteration(c, fast);
     c->prof = false;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
+    CK(cudaStreamSynchronize(c->side_st));
     for (size_t i = 0; i < c->prof_cls.size(); ++i) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
@@ -603,22 +783,12 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
       if (ms) ms[k] += t;
       if (launches) launches[k] += 1;
     }
+    const int before = h.iter;
     if ((s = read_ctl(c, &h))) return s;
+    if (!fast && h.iter > before) c->need_exact = false;
     if (h.abort) {
-      if (h.nonfinite) return fail(c, GODEC_ERR_NONFINITE, "non-finite values");
-      if (h.rank_drop) {
-        c->r = h.r_eff;
-        ++c->rank_drops;
-        if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
-        if ((s = drop_columns(c))) return s;
-      } else if (h.need_bigger_cand) {
-        unsigned long long cap = std::min<unsigned long long>(c->cap * 2, (unsigned long long)(c->p.m * c->p.n));
-        free_graph(c);
-        if ((s = alloc_candidates(c, cap))) return s;
-      } else if (!h.converged) {
-        return fail(c, GODEC_ERR_STATE, "aborted iteration while profiling");
-      }
-      launch_reset_iter(c->ctl, c->st);
+      if (h.converged) break;
+      if ((s = handle_abort(c, h))) return s;
       if (++guard > 64) return fail(c, GODEC_ERR_STATE, "too many aborted iterations");
       if ((s = read_ctl(c, &h))) return s;
     }
@@ -640,7 +810,9 @@ godec_status godec_get_info(godec_ctx* c, godec_info* info) {
   info->select_passes = h.last_passes;
   info->rank_drops = c->rank_drops;
   info->launches_per_iter = c->graph_nodes;
-  info->reserved = 0;
+  info->exact_iters = c->exact_iters;
+  info->svd_sweeps = h.svd_sweeps;
+  info->chol_shifts = h.chol_shifts;
   return GODEC_OK;
 }
 
@@ -691,7 +863,7 @@ godec_status godec_run_host(const godec_params* params, const float* X_host, con
     snprintf(g_static_err, sizeof(g_static_err), "godec_run_host: %s", X_host && A1_host ? why : "NULL input");
     return GODEC_ERR_ARG;
   }
-  godec_ctx* c = nullptr;   // for CK's error path (no context yet)
+  godec_ctx* c = nullptr;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   godec_params p = *params;
   p.ldx = (p.n + 3) / 4 * 4;
@@ -748,7 +920,7 @@ godec_status godec_run_host(const godec_params* params, const float* X_host, con
   }
   CKH(cudaStreamSynchronize(st));
 done:
-  if (s && c) snprintf(g_static_err, sizeof(g_static_err), "godec_run_host: %s", c->err);
+  if (s && c) snprintf(g_static_err, sizeof(g_static_err), "godec_run_host: %.200s", c->err);
   godec_destroy(c);
   void* ptrs[] = {dX, dA, dU, dV, dS, dSi, dSv};
   for (void* q : ptrs)
@@ -756,60 +928,6 @@ done:
   cudaStreamSynchronize(st);
   return s;
 #undef CKH
-}
-
-// ---- streaming primitives ----------------------------------------------------------------
-static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz, const float* B, int32_t r,
-                               float* Y, void* stream, int trans) {
-  if (!Z || !B || !Y || m < 1 || n < 1 || ldz < n || (ldz * 4) % 16 || r < 1 || r > GODEC_MAX_RANK ||
-      (reinterpret_cast<uintptr_t>(Z) & 15)) {
-    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: invalid argument");
-    return GODEC_ERR_ARG;
-  }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int RP = round_up(r, 8);
-  const int64_t outdim = trans ? n : m, K = trans ? m : n;
-  int nsm = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int splits;
-  int64_t kchunk;
-  pass_geometry(outdim, K, nsm, &splits, &kchunk);
-  float *Bp = nullptr, *part = nullptr, *Yp = nullptr;
-  size_t bytes_b = (size_t)K * RP * sizeof(float), bytes_p = (size_t)splits * outdim * RP * sizeof(float),
-         bytes_y = (size_t)outdim * RP * sizeof(float);
-  if (cudaMallocAsync(reinterpret_cast<void**>(&Bp), bytes_b, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&part), bytes_p, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&Yp), bytes_y, st) != cudaSuccess) {
-    if (Bp) cudaFreeAsync(Bp, st);
-    if (part) cudaFreeAsync(part, st);
-    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: out of device memory");
-    return GODEC_ERR_OOM;
-  }
-  launch_pad_copy(B, K, r, r, Bp, RP, st);
-  PassArgs pa{};
-  pa.Z = Z;
-  pa.m = m;
-  pa.n = n;
-  pa.ldz = ldz;
-  pa.B = Bp;
-  pa.part = part;
-  pa.splits = splits;
-  pa.kchunk = kchunk;
-  pa.trans = trans;
-  pa.RP = RP;
-  launch_pass(pa, st);
-  launch_reduce(part, splits, outdim, RP, Yp, nullptr, 0, nullptr, st);
-  launch_unpad_copy(Yp, outdim, RP, Y, r, st);
-  cudaFreeAsync(Bp, st);
-  cudaFreeAsync(part, st);
-  cudaFreeAsync(Yp, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: %s", cudaGetErrorString(e));
-    return GODEC_ERR_CUDA;
-  }
-  return GODEC_OK;
 }
 
 godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t ldr, int64_t k,
@@ -877,9 +995,71 @@ godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t 
     if (s) break;
     s = godec_get_S(c, idx, val, cap, nnz);
   } while (0);
-  if (s) snprintf(g_static_err, sizeof(g_static_err), "godec_hard_threshold: %s", c->err);
+  if (s) snprintf(g_static_err, sizeof(g_static_err), "godec_hard_threshold: %.200s", c->err);
   godec_destroy(c);
   return s;
+}
+
+// ---- streaming primitives ----------------------------------------------------------------
+static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz, const float* B, int32_t r,
+                               float* Y, void* stream, int trans) {
+  if (!Z || !B || !Y || m < 1 || n < 1 || ldz < n || (ldz * 4) % 16 || r < 1 || r > GODEC_MAX_RANK ||
+      (reinterpret_cast<uintptr_t>(Z) & 15)) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: invalid argument");
+    return GODEC_ERR_ARG;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int RP = round_up(r, 8);
+  const int64_t rows = trans ? n : m, K = trans ? m : n;
+  int nsm = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      prepare_stream_kernels() != cudaSuccess) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: no CUDA device");
+    return GODEC_ERR_CUDA;
+  }
+  int splits;
+  int64_t kchunk;
+  prod_geometry(rows, K, nsm, &splits, &kchunk);
+  const int64_t ldt = (m + 3) / 4 * 4;
+  float *Bp = nullptr, *part = nullptr, *Yp = nullptr, *Zt = nullptr;
+  unsigned* cnt = nullptr;
+  bool ok = cudaMallocAsync(reinterpret_cast<void**>(&Bp), (size_t)K * RP * sizeof(float), st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&part), (size_t)splits * rows * RP * sizeof(float), st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&Yp), (size_t)rows * RP * sizeof(float), st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&cnt), (size_t)prod_tiles(rows) * sizeof(unsigned), st) == cudaSuccess &&
+            (!trans || cudaMallocAsync(reinterpret_cast<void**>(&Zt), (size_t)n * ldt * sizeof(float), st) == cudaSuccess);
+  if (ok) {
+    cudaMemsetAsync(cnt, 0, (size_t)prod_tiles(rows) * sizeof(unsigned), st);
+    launch_pad_copy(B, K, r, r, Bp, RP, st);
+    if (trans) launch_transpose(Z, m, n, ldz, Zt, ldt, st);
+    ProdArgs pa{};
+    pa.Z = trans ? Zt : Z;
+    pa.rows = rows;
+    pa.K = K;
+    pa.ld = trans ? ldt : ldz;
+    pa.B = Bp;
+    pa.part = part;
+    pa.splits = splits;
+    pa.kchunk = kchunk;
+    pa.counters = cnt;
+    pa.out = Yp;
+    pa.RP = RP;
+    launch_prod(pa, st);
+    launch_unpad_copy(Yp, rows, RP, Y, r, st);
+  }
+  void* ptrs[] = {Bp, part, Yp, cnt, Zt};
+  for (void* q : ptrs)
+    if (q) cudaFreeAsync(q, st);
+  if (!ok) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: out of device memory");
+    return GODEC_ERR_OOM;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: %s", cudaGetErrorString(e));
+    return GODEC_ERR_CUDA;
+  }
+  return GODEC_OK;
 }
 
 godec_status godec_mul_ZB(const float* Z, int64_t m, int64_t n, int64_t ldz, const float* B, int32_t r,

@@ -69,7 +69,10 @@ struct Ctl {
   int converged;                // stop test met (sets abort, not an error)
   int last_passes;              // residual passes used by the last committed S-step
   int chol_shifts;              // Cholesky factorisations that needed a diagonal shift
-  double m_logscale;            // M is stored divided by exp(m_logscale)
+  int alarm;                    // a lagged normaliser left the chain ill-conditioned
+  int slot_parity;              // which half of the slot buffers holds this iteration's T
+  int pad3;
+  double m_logscale;            // Pi (core of the last chain) is stored divided by exp(.)
   // --- histograms ------------------------------------------------------------
   unsigned hist[kHistBins];     // digit-1 histogram of |R| keys (full pass)
   unsigned sel_hist[kHistBins];
@@ -79,60 +82,62 @@ struct Ctl {
 // Kernel launchers (defined in the .cu files).  All take the context stream.
 // --------------------------------------------------------------------------------
 
-// Split-K streaming product: part[s] (outdim x RP) = partial of Z B (trans=0,
-// outdim = m, K = n) or Z^T C (trans=1, outdim = n, K = m) over K-split s.
-// `Zh` may be bf16 (bf16 != 0) with the same layout and row stride.
-struct PassArgs {
+// Streaming product Y = Zsrc B (Zsrc rows x K row-major with stride ld, B K x RP)
+// with split-K partials; the last CTA of each 128-row tile sums the partials (split
+// order), right-multiplies by Tn (RP x RP, nullable), writes `out` (rows x RP) and the
+// tile's Gram partial (gram_mode 0 none, 1 float, 2 exact products in double-float).
+struct ProdArgs {
   const void* Z;
   int bf16;
-  int64_t m, n, ldz;
-  const float* B;        // K x RP
-  float* part;           // splits x outdim x RP
+  int64_t rows, K, ld;
+  const float* B;
+  float* part;             // splits x rows x RP
   int splits;
-  int64_t kchunk;        // K range per split (multiple of 32)
-  int trans;
+  int64_t kchunk;          // multiple of 32
+  unsigned* counters;      // prod_tiles(rows) zeros; left at zero after the call
+  float* out;
+  const float* Tn[2];      // normaliser by slot parity (both null: none)
+  void* gram_part;         // prod_tiles(rows) x RP x RP (float or double)
+  int gram_mode;
   int RP;
-  const Ctl* ctl;        // nullable; abort flag checked
+  const Ctl* ctl;          // nullable; abort flag checked
 };
-void launch_pass(const PassArgs& a, cudaStream_t st);
-void pass_geometry(int64_t outdim, int64_t K, int nsm, int* splits, int64_t* kchunk);
+void launch_prod(const ProdArgs& a, cudaStream_t st);
+void prod_geometry(int64_t rows, int64_t K, int nsm, int* splits, int64_t* kchunk);
+int64_t prod_tiles(int64_t rows);
+cudaError_t prepare_stream_kernels();
 
-// out (rows x RP) = sum_s part[s]; gram partials per 64-row block (RP x RP);
-// gram_mode 0 = none, 1 = float32, 2 = float64 (exact products, double sums).
-void launch_reduce(const float* part, int splits, int64_t rows, int RP, float* out,
-                   void* gram_part, int gram_mode, const Ctl* ctl, cudaStream_t st);
-int64_t reduce_blocks(int64_t rows);
-
-// Q (rows x RP) = P (rows x RP) * T (RP x RP, upper triangular if upper != 0),
-// optional float32 gram partials of Q.
-void launch_apply(const float* P, int64_t rows, int RP, const float* T, int upper, float* Q,
+// Q = P T (solve = 0) or Q = P T^{-1} with T upper triangular (solve = 1, forward
+// substitution); T is T0 or T1 by the slot parity in ctl (T0 without ctl); optional
+// float Gram partials of Q per apply_blocks() row block.  P and Q may alias.
+void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, int solve, float* Q,
                   float* gram_part, const Ctl* ctl, cudaStream_t st);
+int64_t apply_blocks(int64_t rows);
 
-// One-block kernels on r x r matrices (see k_small.cu).
-struct CholArgs {
-  const void* gram_part;   // nblk x RP x RP partials (float or double)
-  int gram_double;
-  int64_t nblk;
-  int r, RP;
-  float* R;                // RP x RP upper triangular (out)
-  float* Rinv;             // RP x RP (out)
-  float* M;                // RP x RP: if accumulate, M := R * M (in/out)
-  int accumulate;          // 0 none, 1 M := R*M, 2 M := R (start)
-  int rank_test;           // run the pivoted rank test (needs gram_double)
-  double rank_tol;
-  Ctl* ctl;
+// r x r kernels (k_small.cu).
+void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
+                     cudaStream_t st);
+void launch_chol(const double* g64, int r, int RP, float* R, Ctl* ctl, cudaStream_t st);
+struct SlotLaunch {
+  const double* g64 = nullptr;
+  int g_is_p = 0;
+  const float* R_app[2] = {nullptr, nullptr};
+  const float* T_app[2] = {nullptr, nullptr};
+  const float* L1 = nullptr;
+  const float* L2 = nullptr;
+  float* R_next[2] = {nullptr, nullptr};
+  float* T_next[2] = {nullptr, nullptr};
+  float* Pi = nullptr;
+  int pi_mode = 0;
+  int fast = 0;
+  int r = 0, RP = 0;
+  float alarm_ratio = 30.f;
+  Ctl* ctl = nullptr;
 };
-void launch_chol(const CholArgs& a, cudaStream_t st);
-
-struct SvdArgs {
-  const float* M;          // RP x RP
-  int r, RP, q;
-  float* Um;               // RP x RP  (left vectors times sigma^(1/(2q+1)) NOT applied)
-  float* Vm;               // RP x RP
-  float* sigma;            // RP: sigma_L = s^(1/(2q+1)), descending, zero-padded
-  Ctl* ctl;
-};
-void launch_svd_root(const SvdArgs& a, cudaStream_t st);
+void launch_slot(const SlotLaunch& l, cudaStream_t st);
+void launch_rank(const double* g64, int r, int RP, double rank_tol, Ctl* ctl, cudaStream_t st);
+void launch_svd(const float* Ra, const float* Rb, const float* Rapp0, const float* Rapp1, const float* Pi,
+                float* Vprev, int r, int RP, int q, float* Um, float* Vm, float* sigma, Ctl* ctl, cudaStream_t st);
 
 // --- S-step ---------------------------------------------------------------------
 struct ResidualArgs {
@@ -176,7 +181,10 @@ struct EmitArgs {
   int64_t n, ldx;
   float* Z;
   int64_t ldz;
-  void* Z16;               // nullable bf16 copy of Z (same ldz)
+  float* Zt;               // transposed copy (n x ldzt), nullable
+  int64_t ldzt;
+  void* Z16;               // nullable bf16 copies (same strides)
+  void* Zt16;
 };
 void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st);
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);
@@ -192,6 +200,9 @@ cudaError_t prepare_select_kernels();
 
 // Small helpers.
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
+// dst (n x ldd) = src^T (src m x n with stride lds)
+void launch_transpose(const float* src, int64_t m, int64_t n, int64_t lds, float* dst, int64_t ldd,
+                      cudaStream_t st);
 void launch_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP,
                      cudaStream_t st);
 void launch_unpad_copy(const float* src, int64_t rows, int RP, float* dst, int cols,

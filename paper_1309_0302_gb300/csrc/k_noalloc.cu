@@ -70,15 +70,21 @@ extern "C" godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t 
   }
   int splits;
   int64_t kchunk;
-  pass_geometry(m, n, nsm, &splits, &kchunk);
+  prod_geometry(m, n, nsm, &splits, &kchunk);
+  const int64_t tiles = prod_tiles(m);
   const size_t bytes_b = align256((size_t)n * RP * sizeof(float));
   const size_t bytes_p = align256((size_t)splits * m * RP * sizeof(float));
   const size_t bytes_y = align256((size_t)m * RP * sizeof(float));
-  if (bytes_b + bytes_p + bytes_y > kNoAllocScratchBytes) {
+  const size_t bytes_c = align256((size_t)tiles * sizeof(unsigned));
+  if (bytes_b + bytes_p + bytes_y + bytes_c > kNoAllocScratchBytes) {
     set_static_error("godec_mul_ZB_noalloc: m=%lld n=%lld r=%d needs %zu bytes of scratch, above the "
-                     "fixed %zu", (long long)m, (long long)n, r, bytes_b + bytes_p + bytes_y,
+                     "fixed %zu", (long long)m, (long long)n, r, bytes_b + bytes_p + bytes_y + bytes_c,
                      kNoAllocScratchBytes);
     return GODEC_ERR_UNSUPPORTED;
+  }
+  if (prepare_stream_kernels() != cudaSuccess) {
+    set_static_error("godec_mul_ZB_noalloc: kernel set-up failed");
+    return GODEC_ERR_CUDA;
   }
   void* base = nullptr;
   godec_status s = scratch_address(&base);
@@ -87,22 +93,25 @@ extern "C" godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t 
   float* Bp = reinterpret_cast<float*>(p);
   float* part = reinterpret_cast<float*>(p + bytes_b);
   float* Yp = reinterpret_cast<float*>(p + bytes_b + bytes_p);
+  unsigned* cnt = reinterpret_cast<unsigned*>(p + bytes_b + bytes_p + bytes_y);
   // Every scratch element read below is written first in the same call (all K x RP
-  // of Bp, all splits x m x RP partials, all m x RP of Yp): nothing is cleared.
+  // of Bp, all splits x m x RP partials, all m x RP of Yp), except the per-tile
+  // arrival counters, which must start at zero: clear them on every call.
+  cudaMemsetAsync(cnt, 0, (size_t)tiles * sizeof(unsigned), st);
   launch_pad_copy(B, n, r, r, Bp, RP, st);
-  PassArgs pa{};
+  ProdArgs pa{};
   pa.Z = Z;
-  pa.m = m;
-  pa.n = n;
-  pa.ldz = ldz;
+  pa.rows = m;
+  pa.K = n;
+  pa.ld = ldz;
   pa.B = Bp;
   pa.part = part;
   pa.splits = splits;
   pa.kchunk = kchunk;
-  pa.trans = 0;
+  pa.counters = cnt;
+  pa.out = Yp;
   pa.RP = RP;
-  launch_pass(pa, st);
-  launch_reduce(part, splits, m, RP, Yp, nullptr, 0, nullptr, st);
+  launch_prod(pa, st);
   launch_unpad_copy(Yp, m, RP, Y, r, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

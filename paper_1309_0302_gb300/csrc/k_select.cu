@@ -494,6 +494,7 @@ k_emit(EmitArgs a) {
   }
   ctl->cur = nb;
   ctl->iter += 1;
+  ctl->slot_parity ^= 1;          // normalisers written during this iteration become current
   ctl->last_passes = ctl->passes_run;
   if (ctl->tol >= 0.0 && ctl->rel_err <= ctl->tol) {
     ctl->converged = 1;
@@ -541,7 +542,9 @@ __global__ void k_z_restore(EmitArgs a) {
     long long i = idx / a.n, j = idx % a.n;
     float x = a.X[i * a.ldx + j];
     a.Z[i * a.ldz + j] = x;
+    if (a.Zt) a.Zt[j * a.ldzt + i] = x;
     if (a.Z16) reinterpret_cast<__nv_bfloat16*>(a.Z16)[i * a.ldz + j] = __float2bfloat16(x);
+    if (a.Zt16) reinterpret_cast<__nv_bfloat16*>(a.Zt16)[j * a.ldzt + i] = __float2bfloat16(x);
   }
 }
 
@@ -558,7 +561,9 @@ __global__ void k_z_scatter(EmitArgs a) {
     long long i = idx / a.n, j = idx % a.n;
     float z = a.X[i * a.ldx + j] - Sval[e];
     a.Z[i * a.ldz + j] = z;
+    if (a.Zt) a.Zt[j * a.ldzt + i] = z;
     if (a.Z16) reinterpret_cast<__nv_bfloat16*>(a.Z16)[i * a.ldz + j] = __float2bfloat16(z);
+    if (a.Zt16) reinterpret_cast<__nv_bfloat16*>(a.Zt16)[j * a.ldzt + i] = __float2bfloat16(z);
   }
 }
 
@@ -592,6 +597,7 @@ __global__ void k_reset_iter(Ctl* ctl) {
   ctl->nonfinite = 0;
   ctl->chol_fail = 0;
   ctl->converged = 0;
+  ctl->alarm = 0;
 }
 
 }  // namespace

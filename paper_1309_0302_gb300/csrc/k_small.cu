@@ -1,17 +1,15 @@
-// r x r kernels of the L-step, one thread block each.
+// r x r kernels of the L-step (one thread block each, except the Gram sums).
 //
-//  * k_chol : Gram matrix of a tall factor (sum of 64-row partials in a fixed
-//    order) -> Cholesky R with G = R^T R -> R^{-1}; optionally accumulates the
-//    core M := R M of the last power chain (eq. mlr_app: with Q2 = orth(Y2),
-//    L~ Q2 = Q1 R_{2q} ... R_0, and R1 (A2^T Y1)^{-1} R2^T equals that product).
-//    With rank_test set it first runs a pivoted Cholesky in float64 on an
-//    exactly accumulated Gram and counts pivots above rank_tol^2 of the
-//    largest: the numerical rank of Z Q2, i.e. of A2^T Y1 (Algorithm 1 line 7).
-//  * k_svd_root : one-sided Jacobi SVD of M, then sigma^(1/(2q+1)) (eq.
-//    mlr_app, singular-value root).
+// Eq. (mlr_app) needs the QR factors of the power chain and an r x r core
+// M = R1 (A2^T Y1)^{-1} R2^T with an SVD for its (2q+1)-th root.  With
+// Q2 = orth(Y2), L~ Q2 = Q1 R_{2q} ... R_0, and since A2^T Y1 = R2^T R2 the
+// core equals that product of R factors (up to the row basis of Q1).  The
+// chain is orthonormalised by Cholesky factors of Gram matrices (CholeskyQR);
+// every product of chain 3 contributes the factor it was normalised with.
 //
-// GB300 runs float64 at about 2 FMA per clock per SM, so only the rank test
-// (about r^3/6 float64 FMAs) uses it; everything else here is float32.
+// GB300 runs float64 at about 2 FMA per clock per SM, so float64 is used only
+// for the rank test (a pivoted Cholesky on an exactly accumulated Gram) and
+// for the Gram sums over row tiles; factorisations run in float32.
 #include <math.h>
 
 #include "godec_internal.cuh"
@@ -20,11 +18,10 @@ namespace godec {
 
 namespace {
 
-constexpr int CHOL_THREADS = 256;
-constexpr size_t kCholSmem = 3 * kMaxRP * (kMaxRP + 1) * sizeof(float);
+constexpr int SMALL_THREADS = 256;   // 16 x 16 threads, each owning a 4 x 4 block of 64 x 64
+constexpr int LD = kMaxRP + 1;
 
-// Sum the Gram partials of all 64-row blocks in float64, one entry per thread,
-// spread over many blocks (a single block would be bound by load latency).
+// ---- Gram sums over row tiles: one entry per thread, many blocks ---------------------
 template <typename T>
 __global__ void k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out,
                            const Ctl* ctl) {
@@ -43,265 +40,448 @@ __global__ void k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, 
   out[e] = (s0 + s1) + (s2 + s3);
 }
 
-__global__ void __launch_bounds__(CHOL_THREADS)
-k_chol(CholArgs a, const double* __restrict__ gram64) {
-  Ctl* ctl = a.ctl;
-  if (ctl->abort) return;
-  // G, then R and R^{-1}; the float64 rank-test matrix aliases R and R^{-1}.
-  extern __shared__ __align__(16) unsigned char chol_smem[];
-  typedef float Row[kMaxRP + 1];
-  typedef double RowD[kMaxRP + 1];
-  Row* G = reinterpret_cast<Row*>(chol_smem);
-  Row* R = G + kMaxRP;
-  Row* Ri = R + kMaxRP;
-  RowD* Gd = reinterpret_cast<RowD*>(R);
-  __shared__ int s_rank;
-  const int tid = threadIdx.x;
-  const int r = a.r, RP = a.RP;
-  const int npair = RP * RP;
+// ---- block helpers on 64 x 64 (padded RP x RP) matrices in shared memory -----------
+// Thread (ty, tx) owns rows ty + 16a and columns tx + 16b, a, b in 0..3.
 
-  // ---- Gram matrix (reduced over row blocks in float64 by k_gram_sum) ----------------
-  for (int e = tid; e < npair; e += CHOL_THREADS) {
-    int i = e / RP, j = e % RP;
-    double v = gram64[e];
-    if (a.rank_test) Gd[i][j] = v;
-    G[i][j] = (float)v;
+// Upper Cholesky G = R^T R in place of R (R must start as a copy of G).  Pivots j < nchk
+// below thr are raised to thr and reported through *bad.  One barrier per column.
+__device__ void chol_upper(float (*R)[LD], int n, int nchk, float thr, int* bad) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  for (int j = 0; j < n; ++j) {
+    float d = R[j][j];
+    if (j < nchk && !(d > thr)) {
+      if (threadIdx.x == 0) *bad = 1;
+      d = thr > 0.f ? thr : 1e-30f;
+    }
+    const float invd = 1.f / d;
+    const float sq = sqrtf(d);
+    // rows a > j, columns c >= a: R[a][c] -= R[j][a] R[j][c] / d (row j is not written here)
+#pragma unroll
+    for (int ia = 0; ia < 4; ++ia) {
+      const int a = ty + 16 * ia;
+      if (a <= j || a >= n) continue;
+      const float rja = R[j][a] * invd;
+#pragma unroll
+      for (int ib = 0; ib < 4; ++ib) {
+        const int c = tx + 16 * ib;
+        if (c >= a && c < n) R[a][c] -= rja * R[j][c];
+      }
+    }
+    __syncthreads();
+    // scale row j; nothing reads it again as an unscaled pivot row
+    if (ty == 0)
+      for (int c = j + tx; c < n; c += 16) R[j][c] = (c == j) ? sq : R[j][c] / sq;
   }
   __syncthreads();
-
-  // ---- non-finite Gram: X - S holds NaN/Inf ---------------------------------------------
-  {
-    __shared__ int s_nf;
-    if (tid == 0) s_nf = 0;
-    __syncthreads();
-    for (int e = tid; e < npair; e += CHOL_THREADS)
-      if (!isfinite(G[e / RP][e % RP])) s_nf = 1;
-    __syncthreads();
-    if (s_nf) {
-      if (tid == 0) {
-        ctl->nonfinite = 1;
-        ctl->abort = 1;
-      }
-      return;
-    }
-  }
-
-  // ---- numerical rank by pivoted Cholesky in float64 ------------------------------------
-  if (a.rank_test) {
-    if (tid == 0) {
-      // one thread: r is at most 64 and the update is done by the block below
-      s_rank = r;
-    }
-    __syncthreads();
-    __shared__ double dmax0;
-    __shared__ int piv;
-    __shared__ int stop;
-    if (tid == 0) stop = 0;
-    for (int j = 0; j < r; ++j) {
-      if (tid == 0) {
-        int p = j;
-        double best = Gd[j][j];
-        for (int i = j + 1; i < r; ++i)
-          if (Gd[i][i] > best) { best = Gd[i][i]; p = i; }
-        if (j == 0) dmax0 = best;
-        if (!(best > a.rank_tol * a.rank_tol * dmax0) || !(dmax0 > 0.0)) {
-          s_rank = j;
-          stop = 1;
-        }
-        piv = p;
-      }
-      __syncthreads();
-      if (stop) break;
-      const int p = piv;
-      if (p != j) {   // symmetric swap of row/column j and p
-        for (int i = tid; i < r; i += CHOL_THREADS) {
-          double t = Gd[j][i]; Gd[j][i] = Gd[p][i]; Gd[p][i] = t;
-        }
-        __syncthreads();
-        for (int i = tid; i < r; i += CHOL_THREADS) {
-          double t = Gd[i][j]; Gd[i][j] = Gd[i][p]; Gd[i][p] = t;
-        }
-        __syncthreads();
-      }
-      const double d = sqrt(Gd[j][j]);
-      __syncthreads();
-      for (int c = j + 1 + tid; c < r; c += CHOL_THREADS) Gd[j][c] /= d;
-      __syncthreads();
-      const int w = r - j - 1;
-      for (int e = tid; e < w * w; e += CHOL_THREADS) {
-        int aa = j + 1 + e / w, cc = j + 1 + e % w;
-        if (cc >= aa) Gd[aa][cc] -= Gd[j][aa] * Gd[j][cc];
-      }
-      __syncthreads();
-      for (int e = tid; e < w * w; e += CHOL_THREADS) {
-        int aa = j + 1 + e / w, cc = j + 1 + e % w;
-        if (cc < aa) Gd[aa][cc] = Gd[cc][aa];
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    if (s_rank < r) {
-      if (tid == 0) {
-        ctl->r_eff = s_rank;
-        ctl->rank_drop = 1;
-        ctl->abort = 1;
-      }
-      return;
-    }
-  }
-
-  // ---- Cholesky G = R^T R (float32, right-looking) -------------------------------------
-  // Pivots below 1e-6 of the largest diagonal mean the factor is numerically rank
-  // deficient (noise columns of a power chain whose Z has rank < r); the factorisation
-  // is then redone on G + shift*I (shifted CholeskyQR), which keeps Q bounded until
-  // the rank test of the last chain lowers r.
-  __shared__ float s_d;
-  __shared__ float s_gmax;
-  __shared__ int s_bad;
-  for (int e = tid; e < npair; e += CHOL_THREADS) {
-    int i = e / RP, j = e % RP;
-    if (i >= r || j >= r) G[i][j] = (i == j) ? 1.f : 0.f;   // padded columns: identity
-    Ri[i][j] = G[i][j];                                      // keep a copy for a retry
+  for (int e = threadIdx.x; e < n * n; e += SMALL_THREADS) {
+    const int i = e / n, c = e % n;
+    if (c < i) R[i][c] = 0.f;
   }
   __syncthreads();
-  if (tid == 0) {
-    float gm = 0.f;
-    for (int j = 0; j < r; ++j) gm = fmaxf(gm, G[j][j]);
-    s_gmax = gm;
-    if (!isfinite(gm)) ctl->nonfinite = 1;
-  }
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    if (attempt == 1) {
-      for (int e = tid; e < npair; e += CHOL_THREADS) {
-        int i = e / RP, j = e % RP;
-        G[i][j] = Ri[i][j] + ((i == j && i < r) ? 1e-5f * s_gmax : 0.f);
-      }
-    }
-    for (int e = tid; e < npair; e += CHOL_THREADS) R[e / RP][e % RP] = 0.f;
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    const float thr = 1e-6f * s_gmax;
-    for (int j = 0; j < RP; ++j) {
-      // Every thread reads pivot j itself, so row j of R and the trailing update
-      // need no barrier between them; one barrier per column.
-      float d = G[j][j];
-      if (!(d > thr) && j < r) {
-        if (tid == 0) s_bad = 1;
-        if (!(d > 0.f)) d = thr + 1e-30f;
-      }
-      const float sq = sqrtf(d);
-      const float invd = 1.f / d;
-      for (int c = j + tid; c < RP; c += CHOL_THREADS) R[j][c] = (c == j) ? sq : G[j][c] / sq;
-      const int w = RP - j - 1;
-      for (int e = tid; e < w * w; e += CHOL_THREADS) {
-        int aa = j + 1 + e / w, cc = j + 1 + e % w;
-        if (cc >= aa) G[aa][cc] -= G[j][aa] * G[j][cc] * invd;
-      }
-      __syncthreads();
-    }
-    if (!s_bad) break;
-    if (tid == 0) ctl->chol_shifts += 1;
-    __syncthreads();
-  }
+}
 
-  // ---- R^{-1}: row i of the inverse from rows below (all columns in parallel) ----------
-  for (int e = tid; e < npair; e += CHOL_THREADS) Ri[e / RP][e % RP] = 0.f;
+// Inverse of an upper-triangular R into Ri: rows bottom-up, each row's entries in
+// parallel with the dot product split over the 16 row-threads of a column.
+__device__ void tri_inverse(const float (*R)[LD], float (*Ri)[LD], int n, float (*scratch)[LD]) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) Ri[e / kMaxRP][e % kMaxRP] = 0.f;
   __syncthreads();
-  for (int i = RP - 1; i >= 0; --i) {
-    for (int c = i + tid; c < RP; c += CHOL_THREADS) {
-      float v;
-      if (c == i) {
-        v = 1.f / R[i][i];
-      } else {
+  for (int i = n - 1; i >= 0; --i) {
+#pragma unroll
+    for (int ib = 0; ib < 4; ++ib) {
+      const int c = tx + 16 * ib;
+      float s = 0.f;
+      for (int j = i + 1 + ty; j <= c && j < n; j += 16) s = fmaf(R[i][j], Ri[j][c], s);
+      scratch[ty][c] = s;
+    }
+    __syncthreads();
+    if (ty == 0) {
+#pragma unroll
+      for (int ib = 0; ib < 4; ++ib) {
+        const int c = tx + 16 * ib;
+        if (c < i || c >= n) continue;
         float s = 0.f;
-        for (int j = i + 1; j <= c; ++j) s = fmaf(R[i][j], Ri[j][c], s);
-        v = -s / R[i][i];
-      }
-      Ri[i][c] = v;
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < npair; e += CHOL_THREADS) {
-    int i = e / RP, j = e % RP;
-    a.R[e] = R[i][j];
-    a.Rinv[e] = Ri[i][j];
-  }
-
-  // ---- core of the last chain: M := R M ------------------------------------------------
-  // M grows like sigma^(2q+1); it is kept divided by its scale, with log(scale) in
-  // float64 in the control block, so float32 never overflows.
-  if (a.accumulate) {
-    __shared__ float s_scale;
-    __syncthreads();
-    if (tid == 0) {
-      float mx = 0.f;
-      for (int i = 0; i < RP; ++i)
-        for (int j = i; j < RP; ++j) mx = fmaxf(mx, fabsf(R[i][j]));
-      s_scale = mx > 0.f ? mx : 1.f;
-      ctl->m_logscale = (a.accumulate == 2 ? 0.0 : ctl->m_logscale) + log((double)s_scale);
-    }
-    __syncthreads();
-    const float inv = 1.f / s_scale;
-    if (a.accumulate == 2) {
-      for (int e = tid; e < npair; e += CHOL_THREADS) a.M[e] = R[e / RP][e % RP] * inv;
-    } else {
-      // G is free now: hold the old M there.
-      for (int e = tid; e < npair; e += CHOL_THREADS) G[e / RP][e % RP] = a.M[e];
-      __syncthreads();
-      for (int e = tid; e < npair; e += CHOL_THREADS) {
-        int i = e / RP, j = e % RP;
-        float acc = 0.f;
-        for (int t = i; t < RP; ++t) acc = fmaf(R[i][t] * inv, G[t][j], acc);
-        a.M[e] = acc;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) s += scratch[t][c];
+        Ri[i][c] = (c == i) ? 1.f / R[i][i] : -s / R[i][i];
       }
     }
+    __syncthreads();
   }
 }
 
-// ----------------------------------------------------------------------------------
-// One-sided Jacobi SVD (Hestenes) of M, parallel round-robin ordering: one warp per
-// column pair.  M = W V^T with W = U diag(s).
-// ----------------------------------------------------------------------------------
-constexpr int SVD_THREADS = 1024;
+// C = A B (n x n, A upper triangular if a_upper); C may alias A or B.
+__device__ void mat_mul(const float (*A)[LD], const float (*B)[LD], float (*C)[LD], int n, bool a_upper) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  float acc[4][4];
+#pragma unroll
+  for (int ia = 0; ia < 4; ++ia)
+#pragma unroll
+    for (int ib = 0; ib < 4; ++ib) acc[ia][ib] = 0.f;
+  for (int t = 0; t < n; ++t) {
+    float av[4], bv[4];
+#pragma unroll
+    for (int ia = 0; ia < 4; ++ia) {
+      const int a = ty + 16 * ia;
+      av[ia] = (a < n && (!a_upper || t >= a)) ? A[a][t] : 0.f;
+    }
+#pragma unroll
+    for (int ib = 0; ib < 4; ++ib) bv[ib] = B[t][tx + 16 * ib];
+#pragma unroll
+    for (int ia = 0; ia < 4; ++ia)
+#pragma unroll
+      for (int ib = 0; ib < 4; ++ib) acc[ia][ib] = fmaf(av[ia], bv[ib], acc[ia][ib]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ia = 0; ia < 4; ++ia)
+#pragma unroll
+    for (int ib = 0; ib < 4; ++ib) C[ty + 16 * ia][tx + 16 * ib] = acc[ia][ib];
+  __syncthreads();
+}
 
-__global__ void __launch_bounds__(SVD_THREADS)
-k_svd_root(SvdArgs a) {
+// D = src (RP x RP, zero-padded to 64 x 64); src == nullptr gives the identity.
+__device__ void load_mat(float (*D)[LD], const float* src, int RP) {
+  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+    const int i = e / kMaxRP, j = e % kMaxRP;
+    float v;
+    if (src) v = (i < RP && j < RP) ? src[i * RP + j] : 0.f;
+    else v = (i == j) ? 1.f : 0.f;
+    D[i][j] = v;
+  }
+  __syncthreads();
+}
+
+__device__ void store_mat(float* dst, const float (*S)[LD], int RP) {
+  for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) dst[e] = S[e / RP][e % RP];
+}
+
+// Gram (double, RP x RP) into float G, padded block set to the identity.  False if
+// the Gram holds NaN/Inf.
+__device__ bool load_gram(float (*G)[LD], const double* g64, int r, int RP) {
+  __shared__ int s_nf;
+  if (threadIdx.x == 0) s_nf = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+    const int i = e / kMaxRP, j = e % kMaxRP;
+    float v;
+    if (i < r && j < r) {
+      const double d = g64[i * RP + j];
+      if (!isfinite(d)) s_nf = 1;
+      v = (float)d;
+    } else {
+      v = (i == j) ? 1.f : 0.f;
+    }
+    G[i][j] = v;
+  }
+  __syncthreads();
+  return s_nf == 0;
+}
+
+// Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
+// numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
+// factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.
+__device__ void robust_chol(float (*G)[LD], float (*R)[LD], int r, int RP, Ctl* ctl) {
+  __shared__ float s_gmax;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) {
+    float gm = 0.f;
+    for (int j = 0; j < r; ++j) gm = fmaxf(gm, G[j][j]);
+    s_gmax = gm;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+      const int i = e / kMaxRP, j = e % kMaxRP;
+      R[i][j] = G[i][j] + ((attempt == 1 && i == j && i < r) ? 1e-5f * s_gmax : 0.f);
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    chol_upper(R, RP, r, 1e-6f * s_gmax, &s_bad);
+    if (!s_bad) break;
+    if (threadIdx.x == 0) ctl->chol_shifts += 1;
+  }
+  __syncthreads();
+}
+
+// dst = M / max|M|, ctl->m_logscale (+)= log(max|M|).
+__device__ void normalise_into(float (*M)[LD], float* dst, int RP, Ctl* ctl, bool reset_scale) {
+  __shared__ float s_scale;
+  if (threadIdx.x == 0) {
+    float mx = 0.f;
+    for (int i = 0; i < RP; ++i)
+      for (int j = 0; j < RP; ++j) mx = fmaxf(mx, fabsf(M[i][j]));
+    s_scale = mx > 0.f ? mx : 1.f;
+    ctl->m_logscale = (reset_scale ? 0.0 : ctl->m_logscale) + log((double)s_scale);
+  }
+  __syncthreads();
+  const float inv = 1.f / s_scale;
+  for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) dst[e] = M[e / RP][e % RP] * inv;
+}
+
+// ---- critical path: R from a Gram --------------------------------------------------------
+__global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict__ g64, int r, int RP,
+                                                        float* __restrict__ Rout, Ctl* ctl) {
+  if (ctl->abort) return;
+  extern __shared__ __align__(16) float smf[];
+  float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
+  float (*R)[LD] = G + kMaxRP;
+  if (!load_gram(G, g64, r, RP)) {
+    if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
+    return;
+  }
+  robust_chol(G, R, r, RP, ctl);
+  store_mat(Rout, R, RP);
+}
+
+// ---- off the critical path: lagged normaliser of a chain slot ---------------------------
+// The chain output of a slot is Q~ = P R_app^{-1} (R_app applied).  The next iteration
+// normalises the same slot with T = R_new^{-1}, R_new = chol(Q~^T Q~) R_app (fast path)
+// or R_new = R_app (exact path, Q~ already orthonormal).  For products of the last chain
+// the applied factor also enters Pi := R_app Pi (the core of eq. mlr_app).
+struct SlotArgs {
+  const double* g64;       // Gram of Q~ (fast path), or of P when g_is_p (then Q~ = P T_app)
+  int g_is_p;
+  const float* R_app[2];   // applied factor, by slot parity (both null: identity)
+  const float* T_app[2];   // its inverse (needed when g_is_p)
+  const float* L1;         // optional extra left factors: R_app := L2 L1 R_app
+  const float* L2;
+  float* R_next[2];        // written at index 1 - parity
+  float* T_next[2];
+  float* Pi;               // RP x RP, nullable
+  int pi_mode;             // 0 none, 1 Pi := R_app Pi, 2 Pi := R_app
+  int fast;                // compute chol(Gram of Q~)
+  int r, RP;
+  float alarm_ratio;       // fast path: alarm when the Q~ Cholesky diagonal spread exceeds it
+  Ctl* ctl;
+};
+
+__global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->abort) return;
-  __shared__ float W[kMaxRP][kMaxRP + 1];   // W[col][row]
-  __shared__ float V[kMaxRP][kMaxRP + 1];   // V[col][row]
+  extern __shared__ __align__(16) float smf[];
+  float (*A)[LD] = reinterpret_cast<float (*)[LD]>(smf);
+  float (*B)[LD] = A + kMaxRP;
+  float (*C)[LD] = B + kMaxRP;
+  float (*D)[LD] = C + kMaxRP;
+  __shared__ float scratch[16][LD];
+  const int r = a.r, RP = a.RP;
+  const int cur = ctl->slot_parity, nxt = 1 - cur;
+  load_mat(B, a.R_app[cur], RP);                     // B = R_app
+  if (a.L1) {
+    load_mat(C, a.L1, RP);
+    mat_mul(C, B, B, RP, true);                      // B = L1 R_app
+  }
+  if (a.L2) {
+    load_mat(C, a.L2, RP);
+    mat_mul(C, B, B, RP, true);                      // B = L2 L1 R_app
+  }
+  if (a.fast) {
+    if (!load_gram(A, a.g64, r, RP)) {
+      if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
+      return;
+    }
+    if (a.g_is_p) {                                  // Gram of Q~ = T^T G T
+      load_mat(C, a.T_app[cur], RP);
+      mat_mul(A, C, D, RP, false);                   // D = G T
+      for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+        const int i = e / kMaxRP, j = e % kMaxRP;
+        A[i][j] = C[j][i];                           // A = T^T
+      }
+      __syncthreads();
+      mat_mul(A, D, A, RP, false);                   // A = T^T G T
+      for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+        const int i = e / kMaxRP, j = e % kMaxRP;
+        if (i >= r || j >= r) A[i][j] = (i == j) ? 1.f : 0.f;
+      }
+      __syncthreads();
+    }
+    robust_chol(A, C, r, RP, ctl);                   // C = R~
+    if (threadIdx.x == 0) {
+      float lo = 3.4e38f, hi = 0.f;
+      for (int j = 0; j < r; ++j) { lo = fminf(lo, C[j][j]); hi = fmaxf(hi, C[j][j]); }
+      if (!(hi <= a.alarm_ratio * lo)) { ctl->alarm = 1; ctl->abort = 1; }
+    }
+    mat_mul(C, B, A, RP, true);                      // A = R~ R_app
+  } else {
+    for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) A[e / kMaxRP][e % kMaxRP] = B[e / kMaxRP][e % kMaxRP];
+    __syncthreads();
+  }
+  store_mat(a.R_next[nxt], A, RP);
+  tri_inverse(A, C, RP, scratch);
+  store_mat(a.T_next[nxt], C, RP);
+  if (a.pi_mode == 2) {
+    normalise_into(B, a.Pi, RP, ctl, true);
+  } else if (a.pi_mode == 1) {
+    __syncthreads();
+    load_mat(C, a.Pi, RP);
+    mat_mul(B, C, D, RP, true);                      // D = R_app Pi
+    normalise_into(D, a.Pi, RP, ctl, false);
+  }
+}
+
+// ---- off the critical path: rank test (Algorithm 1 line 7) -----------------------------
+// Reading of "rank(A2^T Y1) < r": A2^T Y1 = Y2^T Y2, whose rank is that of Z Q2.  Count
+// the pivots of a pivoted Cholesky of (Z Q2)^T (Z Q2) (exact float32 products summed in
+// double-float, reduced in float64) above rank_tol^2 of the largest.
+__global__ void __launch_bounds__(SMALL_THREADS) k_rank(const double* __restrict__ g64, int r, int RP,
+                                                        double rank_tol, Ctl* ctl) {
+  if (ctl->abort) return;
+  extern __shared__ __align__(16) float smf[];
+  double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);
+  __shared__ double dmax0;
+  __shared__ int piv, stop, rank;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < r * r; e += SMALL_THREADS) Gd[e / r][e % r] = g64[(e / r) * RP + e % r];
+  if (tid == 0) { stop = 0; rank = r; }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    if (tid == 0) {
+      int p = j;
+      double best = Gd[j][j];
+      for (int i = j + 1; i < r; ++i)
+        if (Gd[i][i] > best) { best = Gd[i][i]; p = i; }
+      if (j == 0) dmax0 = best;
+      if (!isfinite(best)) {
+        ctl->nonfinite = 1;
+        ctl->abort = 1;
+        stop = 1;
+      } else if (!(dmax0 > 0.0) || !(best > rank_tol * rank_tol * dmax0)) {
+        rank = j;
+        stop = 1;
+      }
+      piv = p;
+    }
+    __syncthreads();
+    if (stop) break;
+    const int p = piv;
+    if (p != j) {
+      for (int i = tid; i < r; i += SMALL_THREADS) { double t = Gd[j][i]; Gd[j][i] = Gd[p][i]; Gd[p][i] = t; }
+      __syncthreads();
+      for (int i = tid; i < r; i += SMALL_THREADS) { double t = Gd[i][j]; Gd[i][j] = Gd[i][p]; Gd[i][p] = t; }
+      __syncthreads();
+    }
+    const double invd = 1.0 / Gd[j][j];
+    const int w = r - j - 1;
+    for (int e = tid; e < w * w; e += SMALL_THREADS) {
+      const int aa = j + 1 + e / w, cc = j + 1 + e % w;
+      Gd[aa][cc] -= Gd[j][aa] * Gd[j][cc] * invd;       // full symmetric Schur complement
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (tid == 0 && rank < r && !ctl->nonfinite) {
+    ctl->r_eff = rank;
+    ctl->rank_drop = 1;
+    ctl->abort = 1;
+  }
+}
+
+// ---- SVD of the core and the singular-value root (eq. mlr_app, reading R4) -------------
+// M = Rb Ra Rapp Pi (Rapp optional).  One-sided Jacobi (Hestenes) on W = M V, warm-
+// started from the previous iteration's V; column pairs in round-robin order, one warp
+// per pair.  V and U are re-orthonormalised with one Newton-Schulz step at the end.
+constexpr int SVD_THREADS = 1024;
+
+__device__ void mm_1024(const float (*A)[LD], const float (*B)[LD], float (*C)[LD], int n, bool a_transposed) {
+  // C = A B (or A^T B); C must not alias A or B
+  for (int e = threadIdx.x; e < n * n; e += SVD_THREADS) {
+    const int i = e / n, j = e % n;
+    float s = 0.f;
+    for (int t = 0; t < n; ++t) s = fmaf(a_transposed ? A[t][i] : A[i][t], B[t][j], s);
+    C[i][j] = s;
+  }
+  __syncthreads();
+}
+
+__device__ void load_1024(float (*D)[LD], const float* src, int RP) {
+  for (int e = threadIdx.x; e < RP * RP; e += SVD_THREADS) D[e / RP][e % RP] = src[e];
+  __syncthreads();
+}
+
+struct SvdArgs2 {
+  const float* Ra;
+  const float* Rb;
+  const float* Rapp[2];    // by slot parity; both null: none
+  const float* Pi;         // nullable: identity
+  float* Vprev;            // RP x RP, in/out (warm start)
+  int r, RP, q;
+  float* Um;
+  float* Vm;
+  float* sigma;
+  Ctl* ctl;
+};
+
+__global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
+  Ctl* ctl = a.ctl;
+  if (ctl->abort) return;
+  extern __shared__ __align__(16) float smf[];
+  float (*X1)[LD] = reinterpret_cast<float (*)[LD]>(smf);
+  float (*X2)[LD] = X1 + kMaxRP;
+  float (*W)[LD] = X2 + kMaxRP;      // W[row][col] = M V
+  float (*V)[LD] = W + kMaxRP;       // V[row][col]
   __shared__ float s[kMaxRP];
   __shared__ int order[kMaxRP];
   __shared__ int rotated;
+  __shared__ float s_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, RP = a.RP;
-  for (int e = tid; e < RP * RP; e += SVD_THREADS) {
-    int i = e / RP, j = e % RP;            // M[i][j]
-    W[j][i] = (i < r && j < r) ? a.M[e] : 0.f;
-    V[j][i] = (i == j) ? 1.f : 0.f;
+  // M = Rb Ra Rapp Pi
+  const float* Rapp = a.Rapp[ctl->slot_parity];
+  load_1024(X1, a.Ra, RP);
+  if (a.Pi) {
+    load_1024(X2, a.Pi, RP);
+  } else {
+    for (int e = tid; e < RP * RP; e += SVD_THREADS) X2[e / RP][e % RP] = (e / RP == e % RP) ? 1.f : 0.f;
+    __syncthreads();
   }
-  const int np = (r + 1) & ~1;             // even number of players
+  if (Rapp) {
+    load_1024(W, Rapp, RP);
+    mm_1024(W, X2, V, RP, false);     // V = Rapp Pi
+    mm_1024(X1, V, X2, RP, false);    // X2 = Ra Rapp Pi
+  } else {
+    mm_1024(X1, X2, V, RP, false);    // V = Ra Pi
+    for (int e = tid; e < RP * RP; e += SVD_THREADS) X2[e / RP][e % RP] = V[e / RP][e % RP];
+    __syncthreads();
+  }
+  load_1024(X1, a.Rb, RP);
+  mm_1024(X1, X2, W, RP, false);      // W = M (unscaled)
+  if (tid == 0) {
+    float mx = 0.f;
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j) mx = fmaxf(mx, fabsf(W[i][j]));
+    s_scale = mx > 0.f ? mx : 1.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < RP * RP; e += SVD_THREADS) {
+    const int i = e / RP, j = e % RP;
+    X2[i][j] = (i < r && j < r) ? W[i][j] / s_scale : 0.f;      // X2 = M / scale
+  }
+  load_1024(V, a.Vprev, RP);
+  for (int e = tid; e < RP * RP; e += SVD_THREADS) {
+    const int i = e / RP, j = e % RP;
+    if (i >= r || j >= r) V[i][j] = (i == j) ? 1.f : 0.f;       // warm start on the r x r block
+  }
+  __syncthreads();
+  mm_1024(X2, V, W, RP, false);       // W = M V
+
+  const int np = (r + 1) & ~1;
   const int npairs = np / 2;
   int sweeps = 0;
-  for (; sweeps < 40; ++sweeps) {
-    __syncthreads();          // every thread has read the previous sweep's flag
+  for (; sweeps < 16; ++sweeps) {
+    __syncthreads();                  // every thread has read the previous flag
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
       if (warp < npairs) {
         int p, q;
-        if (warp == 0) {
-          p = np - 1;
-          q = round;
-        } else {
-          p = (round + warp) % (np - 1);
-          q = (round - warp + np - 1) % (np - 1);
-        }
+        if (warp == 0) { p = np - 1; q = round; }
+        else { p = (round + warp) % (np - 1); q = (round - warp + np - 1) % (np - 1); }
         if (p > q) { int t = p; p = q; q = t; }
         if (q < r) {
           float al = 0.f, be = 0.f, ga = 0.f;
           for (int i = lane; i < r; i += 32) {
-            float wp = W[p][i], wq = W[q][i];
+            const float wp = W[i][p], wq = W[i][q];
             al = fmaf(wp, wp, al);
             be = fmaf(wq, wq, be);
             ga = fmaf(wp, wq, ga);
@@ -312,18 +492,19 @@ k_svd_root(SvdArgs a) {
             be += __shfl_xor_sync(0xffffffffu, be, o);
             ga += __shfl_xor_sync(0xffffffffu, ga, o);
           }
-          if (fabsf(ga) > 1e-6f * sqrtf(al) * sqrtf(be) && ga != 0.f) {
-            float zeta = (be - al) / (2.f * ga);
-            float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-            float c = rsqrtf(1.f + t * t);
-            float sn = c * t;
+          // float32 dot products bottom out near sqrt(r) u; 4e-6 keeps a margin above it
+          if (fabsf(ga) > 4e-6f * sqrtf(al) * sqrtf(be) && ga != 0.f) {
+            const float zeta = (be - al) / (2.f * ga);
+            const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+            const float c = 1.f / sqrtf(1.f + t * t);
+            const float sn = c * t;
             for (int i = lane; i < r; i += 32) {
-              float wp = W[p][i], wq = W[q][i];
-              W[p][i] = c * wp - sn * wq;
-              W[q][i] = sn * wp + c * wq;
-              float vp = V[p][i], vq = V[q][i];
-              V[p][i] = c * vp - sn * vq;
-              V[q][i] = sn * vp + c * vq;
+              const float wp = W[i][p], wq = W[i][q];
+              W[i][p] = c * wp - sn * wq;
+              W[i][q] = sn * wp + c * wq;
+              const float vp = V[i][p], vq = V[i][q];
+              V[i][p] = c * vp - sn * vq;
+              V[i][q] = sn * vp + c * vq;
             }
             if (lane == 0) rotated = 1;
           }
@@ -333,17 +514,24 @@ k_svd_root(SvdArgs a) {
     }
     if (!rotated) break;
   }
-  // singular values and ordering
+  // Newton-Schulz: V := V (3I - V^T V) / 2 restores orthonormality lost to rounding
+  mm_1024(V, V, X1, r, true);                       // X1 = V^T V
+  for (int e = tid; e < r * r; e += SVD_THREADS) {
+    const int i = e / r, j = e % r;
+    X1[i][j] = ((i == j) ? 1.5f : 0.f) - 0.5f * X1[i][j];
+  }
+  __syncthreads();
+  mm_1024(V, X1, X2, r, false);                     // X2 = reorthonormalised V
   if (tid < RP) {
     float v = 0.f;
     if (tid < r)
-      for (int i = 0; i < r; ++i) v = fmaf(W[tid][i], W[tid][i], v);
+      for (int i = 0; i < r; ++i) v = fmaf(W[i][tid], W[i][tid], v);
     s[tid] = sqrtf(v);
   }
   __syncthreads();
   if (tid == 0) {
     for (int j = 0; j < RP; ++j) order[j] = j;
-    for (int j = 0; j < r; ++j) {          // selection sort, descending
+    for (int j = 0; j < r; ++j) {
       int b = j;
       for (int i = j + 1; i < r; ++i)
         if (s[order[i]] > s[order[b]]) b = i;
@@ -352,51 +540,101 @@ k_svd_root(SvdArgs a) {
     ctl->svd_sweeps = sweeps;
   }
   __syncthreads();
-  const double inv_e = 1.0 / (double)(2 * a.q + 1);
-  const double lsc = ctl->m_logscale;
+  // U = W diag(1/s), columns in descending order of s; V reordered likewise
   for (int e = tid; e < RP * RP; e += SVD_THREADS) {
-    int i = e / RP, j = e % RP;            // output [row i][col j]
+    const int i = e / RP, j = e % RP;
     float u = 0.f, v = 0.f;
-    if (j < r) {
-      int c = order[j];
-      float sc = s[c];
-      u = (sc > 0.f && i < r) ? W[c][i] / sc : 0.f;
-      v = (i < r) ? V[c][i] : 0.f;
+    if (i < r && j < r) {
+      const int c = order[j];
+      u = s[c] > 0.f ? W[i][c] / s[c] : 0.f;
+      v = X2[i][c];
     }
-    a.Um[e] = u;
-    a.Vm[e] = v;
+    X1[i][j] = u;
+    V[i][j] = v;
+  }
+  __syncthreads();
+  mm_1024(X1, X1, W, r, true);                      // W = U^T U
+  for (int e = tid; e < r * r; e += SVD_THREADS) {
+    const int i = e / r, j = e % r;
+    W[i][j] = ((i == j) ? 1.5f : 0.f) - 0.5f * W[i][j];
+  }
+  __syncthreads();
+  mm_1024(X1, W, X2, r, false);                     // X2 = reorthonormalised U
+  const double inv_e = 1.0 / (double)(2 * a.q + 1);
+  const double lsc = (a.Pi ? ctl->m_logscale : 0.0) + log((double)s_scale);
+  for (int e = tid; e < RP * RP; e += SVD_THREADS) {
+    const int i = e / RP, j = e % RP;
+    const bool in = i < r && j < r;
+    a.Um[e] = in ? X2[i][j] : 0.f;
+    a.Vm[e] = in ? V[i][j] : 0.f;
+    a.Vprev[e] = in ? V[i][j] : (i == j ? 1.f : 0.f);
   }
   if (tid < RP) {
     float sv = 0.f;
     if (tid < r) {
-      float sc = s[order[tid]];
+      const float sc = s[order[tid]];
       sv = (sc > 0.f) ? (float)exp((log((double)sc) + lsc) * inv_e) : 0.f;
     }
     a.sigma[tid] = sv;
   }
 }
 
+constexpr size_t kSmall4 = 4 * kMaxRP * LD * sizeof(float);
+
 }  // namespace
 
-void launch_chol(const CholArgs& a, cudaStream_t st) {
-  // the reduced Gram goes after the partials in the same buffer (no overlap for
-  // float or double partials: it starts at byte 8 * nblk * npair)
-  const int npair = a.RP * a.RP;
-  double* out = reinterpret_cast<double*>(const_cast<void*>(a.gram_part)) + a.nblk * npair;
-  const unsigned grid = (unsigned)((npair + 127) / 128);
-  if (a.gram_double)
-    k_gram_sum<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double*>(a.gram_part), a.nblk, npair, out, a.ctl);
-  else
-    k_gram_sum<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float*>(a.gram_part), a.nblk, npair, out, a.ctl);
-  k_chol<<<1, CHOL_THREADS, kCholSmem, st>>>(a, out);
-}
-
 cudaError_t prepare_small_kernels() {
-  return cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  return e;
 }
 
-void launch_svd_root(const SvdArgs& a, cudaStream_t st) {
-  k_svd_root<<<1, SVD_THREADS, 0, st>>>(a);
+void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
+                     cudaStream_t st) {
+  const int npair = RP * RP;
+  const unsigned grid = (unsigned)((npair + 127) / 128);
+  if (gram_double)
+    k_gram_sum<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out, ctl);
+  else
+    k_gram_sum<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out, ctl);
+}
+
+void launch_chol(const double* g64, int r, int RP, float* R, Ctl* ctl, cudaStream_t st) {
+  k_chol<<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, ctl);
+}
+
+void launch_slot(const SlotLaunch& l, cudaStream_t st) {
+  SlotArgs a;
+  a.g64 = l.g64;
+  a.g_is_p = l.g_is_p;
+  for (int h = 0; h < 2; ++h) {
+    a.R_app[h] = l.R_app[h];
+    a.T_app[h] = l.T_app[h];
+    a.R_next[h] = l.R_next[h];
+    a.T_next[h] = l.T_next[h];
+  }
+  a.L1 = l.L1;
+  a.L2 = l.L2;
+  a.Pi = l.Pi;
+  a.pi_mode = l.pi_mode;
+  a.fast = l.fast;
+  a.r = l.r;
+  a.RP = l.RP;
+  a.alarm_ratio = l.alarm_ratio;
+  a.ctl = l.ctl;
+  k_slot<<<1, SMALL_THREADS, kSmall4, st>>>(a);
+}
+
+void launch_rank(const double* g64, int r, int RP, double rank_tol, Ctl* ctl, cudaStream_t st) {
+  k_rank<<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, rank_tol, ctl);
+}
+
+void launch_svd(const float* Ra, const float* Rb, const float* Rapp0, const float* Rapp1, const float* Pi,
+                float* Vprev, int r, int RP, int q, float* Um, float* Vm, float* sigma, Ctl* ctl, cudaStream_t st) {
+  SvdArgs2 a{Ra, Rb, {Rapp0, Rapp1}, Pi, Vprev, r, RP, q, Um, Vm, sigma, ctl};
+  k_svd<<<1, SVD_THREADS, kSmall4, st>>>(a);
 }
 
 }  // namespace godec

@@ -1,11 +1,16 @@
-// Streaming tall-skinny products over X - S (Algorithm 1, lines 5-6) and
-// their split-K reduction, Gram partials and r x r right-multiplication.
+// Streaming tall-skinny products over X - S (Algorithm 1, lines 5-6).
 //
-// The product kernel streams the dense m x n matrix once per call; each CTA
-// owns a 128-wide slab of the output dimension and one K-range, stages
-// 128 x 32 tiles of Z (and the matching 32 x RP slice of the skinny
+// Both products of the power chain, Z B and Z^T C, are computed as
+// "row-major source times skinny matrix": Z^T C streams the transposed copy
+// of X - S that the library keeps in HBM, so one kernel serves both.
+//
+// k_prod: each CTA owns a 128-row tile of the output and one K-range, stages
+// 128 x 32 tiles of the source (and the matching 32 x RP slice of the skinny
 // operand) in shared memory with a register prefetch of the next tile, and
-// accumulates an 8 x (RP/8) register tile per thread.
+// accumulates an 8 x (RP/8) register tile per thread.  The CTA that finishes a
+// tile last (per-tile arrival counter) sums the split-K partials in split order
+// (deterministic), optionally right-multiplies the rows by a normaliser T, writes
+// the output rows and the tile's Gram partial Q^T Q for the next orthonormalisation.
 #include <cuda_bf16.h>
 
 #include "godec_internal.cuh"
@@ -17,6 +22,9 @@ namespace {
 constexpr int TM = 128;   // output rows per CTA
 constexpr int KC = 32;    // K per stage
 constexpr int PASS_THREADS = 128;
+constexpr int EPI_STRIDE = kMaxRP + 1;
+// stage buffers (KC x (TM+4) + KC x 64 floats) or the epilogue (TM + 64 rows of EPI_STRIDE)
+constexpr size_t kProdSmem = (size_t)(TM + kMaxRP) * EPI_STRIDE * sizeof(float);
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
@@ -29,19 +37,19 @@ __device__ __forceinline__ float4 ld4_bf16(const __nv_bfloat16* p) {
 }
 
 template <typename T>
-__device__ __forceinline__ float4 load_z4(const T* Z, int64_t row, int64_t col, int64_t m, int64_t n,
-                                          int64_t ldz) {
-  // 4 consecutive elements Z[row][col..col+3]; zero outside [0,m) x [0,n).
-  if (row >= m || col >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
-  const T* p = Z + row * ldz + col;
-  if (col + 4 <= n) {
+__device__ __forceinline__ float4 load_z4(const T* Z, int64_t row, int64_t col, int64_t rows, int64_t kend,
+                                          int64_t ld) {
+  // 4 consecutive elements Z[row][col..col+3]; zero outside [0,rows) x [0,kend).
+  if (row >= rows || col >= kend) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const T* p = Z + row * ld + col;
+  if (col + 4 <= kend) {
     if constexpr (sizeof(T) == 4) return ld4(reinterpret_cast<const float*>(p));
     else return ld4_bf16(reinterpret_cast<const __nv_bfloat16*>(p));
   }
   float v[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    if (col + c < n) {
+    if (col + c < kend) {
       if constexpr (sizeof(T) == 4) v[c] = reinterpret_cast<const float*>(p)[c];
       else v[c] = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(p)[c]);
     } else {
@@ -51,53 +59,78 @@ __device__ __forceinline__ float4 load_z4(const T* Z, int64_t row, int64_t col, 
   return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// TRANS = false: part = Z[rows o0..o0+127, K-range] * B[K-range, :]   (out = rows of Z)
-// TRANS = true : part = Z[K-range, cols o0..o0+127]^T * B[K-range, :] (out = cols of Z)
-template <int RN, bool TRANS, typename T>
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// Gram partial of the rows in Ps (nrow x RP, stride EPI_STRIDE): float, or exact
+// float32 products summed in double-float and stored as double.
+__device__ void tile_gram(const float* Ps, int nrow, int RP, int gram_mode, void* out, int nthreads) {
+  const int npair = RP * RP;
+  for (int e = threadIdx.x; e < npair; e += nthreads) {
+    const int a = e / RP, c = e % RP;
+    if (gram_mode == 1) {
+      float g0 = 0.f, g1 = 0.f;
+      int i = 0;
+      for (; i + 1 < nrow; i += 2) {
+        g0 = fmaf(Ps[i * EPI_STRIDE + a], Ps[i * EPI_STRIDE + c], g0);
+        g1 = fmaf(Ps[(i + 1) * EPI_STRIDE + a], Ps[(i + 1) * EPI_STRIDE + c], g1);
+      }
+      if (i < nrow) g0 = fmaf(Ps[i * EPI_STRIDE + a], Ps[i * EPI_STRIDE + c], g0);
+      reinterpret_cast<float*>(out)[e] = g0 + g1;
+    } else {
+      float hi = 0.f, lo = 0.f;
+      for (int i = 0; i < nrow; ++i) {
+        float p, pe;
+        two_prod(Ps[i * EPI_STRIDE + a], Ps[i * EPI_STRIDE + c], p, pe);
+        float s = hi + p;
+        float bb = s - hi;
+        float err = (hi - (s - bb)) + (p - bb);
+        hi = s;
+        lo += err + pe;
+      }
+      reinterpret_cast<double*>(out)[e] = (double)hi + (double)lo;
+    }
+  }
+}
+
+// part = Zsrc[rows o0..o0+127, K-range] * B[K-range, :], then the fused epilogue.
+template <int RN, typename T>
 __global__ void __launch_bounds__(PASS_THREADS)
-k_pass(const T* __restrict__ Z, int64_t m, int64_t n, int64_t ldz, const float* __restrict__ B,
-       float* __restrict__ part, int splits, int64_t kchunk, const Ctl* ctl) {
+k_prod(const T* __restrict__ Z, int64_t rows, int64_t K, int64_t ld, const float* __restrict__ B,
+       float* __restrict__ part, int splits, int64_t kchunk, unsigned* __restrict__ counters,
+       float* __restrict__ out, const float* __restrict__ Tn0, const float* __restrict__ Tn1, void* gram_part,
+       int gram_mode, const Ctl* ctl) {
   constexpr int RP = RN * 8;
   if (ctl && ctl->abort) return;
-  __shared__ __align__(16) float Zs[KC][TM + 4];
-  __shared__ __align__(16) float Bs[KC][RP];
+  const float* Tn = (ctl && ctl->slot_parity) ? Tn1 : Tn0;
+  extern __shared__ __align__(16) float sm[];
+  float (*Zs)[TM + 4] = reinterpret_cast<float (*)[TM + 4]>(sm);       // [KC][TM+4]
+  float (*Bs)[RP] = reinterpret_cast<float (*)[RP]>(sm + KC * (TM + 4)); // [KC][RP]
 
   const int tid = threadIdx.x;
+  const int tile = blockIdx.x / splits;
   const int split = blockIdx.x % splits;
-  const int64_t o0 = (int64_t)(blockIdx.x / splits) * TM;
-  const int64_t outdim = TRANS ? n : m;
-  const int64_t K = TRANS ? m : n;
+  const int64_t o0 = (int64_t)tile * TM;
   const int64_t k0 = (int64_t)split * kchunk;
   const int64_t k1 = min(K, k0 + kchunk);
 
-  // Z tile loader mapping (8 float4 per thread per stage).
   float4 zr[8];
-  float4 br[(KC * RP / 4 + PASS_THREADS - 1) / PASS_THREADS];
   constexpr int BR = (KC * RP / 4 + PASS_THREADS - 1) / PASS_THREADS;
+  float4 br[BR];
 
   auto load_stage = [&](int64_t kb) {
-    if (!TRANS) {
-      // Tile rows o0..o0+127, cols kb..kb+31: two threads per 32-byte row piece.
+    // 128 rows x 32 columns: two threads per 32-byte row piece.
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        int li = (s >> 2) * 64 + (tid >> 1);           // row within tile (0..127)
-        int kk4 = (s & 3) * 2 + (tid & 1);             // float4 column (0..7)
-        int64_t col = kb + kk4 * 4;
-        zr[s] = (col < k1) ? load_z4(Z, o0 + li, col, m, min(n, k1), ldz) : make_float4(0, 0, 0, 0);
-      }
-    } else {
-      // Tile rows kb..kb+31 (K), cols o0..o0+127: one warp per row, 32 float4.
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        int kk = s * 4 + (tid >> 5);
-        int c4 = tid & 31;
-        int64_t row = kb + kk;
-        zr[s] = (row < k1) ? load_z4(Z, row, o0 + c4 * 4, m, n, ldz) : make_float4(0, 0, 0, 0);
-      }
+    for (int s = 0; s < 8; ++s) {
+      int li = (s >> 2) * 64 + (tid >> 1);
+      int kk4 = (s & 3) * 2 + (tid & 1);
+      zr[s] = load_z4(Z, o0 + li, kb + kk4 * 4, rows, k1, ld);
     }
 #pragma unroll
     for (int s = 0; s < BR; ++s) {
-      int e = s * PASS_THREADS + tid;                  // float4 index in the KC x RP slice
+      int e = s * PASS_THREADS + tid;
       if (e < KC * RP / 4) {
         int kk = e / (RP / 4);
         int c4 = e % (RP / 4);
@@ -107,23 +140,14 @@ k_pass(const T* __restrict__ Z, int64_t m, int64_t n, int64_t ldz, const float* 
     }
   };
   auto store_stage = [&]() {
-    if (!TRANS) {
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        int li = (s >> 2) * 64 + (tid >> 1);
-        int kk4 = (s & 3) * 2 + (tid & 1);
-        Zs[kk4 * 4 + 0][li] = zr[s].x;
-        Zs[kk4 * 4 + 1][li] = zr[s].y;
-        Zs[kk4 * 4 + 2][li] = zr[s].z;
-        Zs[kk4 * 4 + 3][li] = zr[s].w;
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        int kk = s * 4 + (tid >> 5);
-        int c4 = tid & 31;
-        *reinterpret_cast<float4*>(&Zs[kk][c4 * 4]) = zr[s];
-      }
+    for (int s = 0; s < 8; ++s) {
+      int li = (s >> 2) * 64 + (tid >> 1);
+      int kk4 = (s & 3) * 2 + (tid & 1);
+      Zs[kk4 * 4 + 0][li] = zr[s].x;
+      Zs[kk4 * 4 + 1][li] = zr[s].y;
+      Zs[kk4 * 4 + 2][li] = zr[s].z;
+      Zs[kk4 * 4 + 3][li] = zr[s].w;
     }
 #pragma unroll
     for (int s = 0; s < BR; ++s) {
@@ -146,10 +170,10 @@ k_pass(const T* __restrict__ Z, int64_t m, int64_t n, int64_t ldz, const float* 
 
   if (k0 < k1) load_stage(k0);
   for (int64_t kb = k0; kb < k1; kb += KC) {
-    __syncthreads();                 // previous stage fully consumed
+    __syncthreads();
     store_stage();
     __syncthreads();
-    if (kb + KC < k1) load_stage(kb + KC);   // next tile in flight during the FMAs
+    if (kb + KC < k1) load_stage(kb + KC);
 #pragma unroll 8
     for (int kk = 0; kk < KC; ++kk) {
       float4 a0 = *reinterpret_cast<const float4*>(&Zs[kk][ty * 8]);
@@ -165,138 +189,176 @@ k_pass(const T* __restrict__ Z, int64_t m, int64_t n, int64_t ldz, const float* 
     }
   }
 
-  float* out = part + (int64_t)split * outdim * RP;
+  // ---- split-K partial, then the last CTA of the tile finishes it ----------------
+  const int nrow = (int)(rows - o0 < TM ? rows - o0 : TM);
+  float* mine = part + ((int64_t)split * rows + o0) * RP;
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    int64_t o = o0 + ty * 8 + a;
-    if (o < outdim) {
+    int i = ty * 8 + a;
+    if (i < nrow) {
 #pragma unroll
-      for (int c = 0; c < RN; ++c) out[o * RP + tx + 8 * c] = acc[a][c];
+      for (int c = 0; c < RN; ++c) mine[(int64_t)i * RP + tx + 8 * c] = acc[a][c];
     }
   }
-}
-
-template <bool TRANS, typename T>
-void launch_pass_t(const PassArgs& a, cudaStream_t st) {
-  const int64_t outdim = TRANS ? a.n : a.m;
-  const int64_t tiles = (outdim + TM - 1) / TM;
-  dim3 grid((unsigned)(tiles * a.splits));
-  const T* Z = reinterpret_cast<const T*>(a.Z);
-#define GODEC_PASS_CASE(RNV)                                                                  \
-  case RNV:                                                                                   \
-    k_pass<RNV, TRANS, T><<<grid, PASS_THREADS, 0, st>>>(Z, a.m, a.n, a.ldz, a.B, a.part,     \
-                                                          a.splits, a.kchunk, a.ctl);         \
-    break;
-  switch (a.RP / 8) {
-    GODEC_PASS_CASE(1)
-    GODEC_PASS_CASE(2)
-    GODEC_PASS_CASE(3)
-    GODEC_PASS_CASE(4)
-    GODEC_PASS_CASE(5)
-    GODEC_PASS_CASE(6)
-    GODEC_PASS_CASE(7)
-    GODEC_PASS_CASE(8)
-    default: break;
-  }
-#undef GODEC_PASS_CASE
-}
-
-// ----------------------------------------------------------------------------------
-// Split-K reduction in a fixed order, plus Gram partials of 64-row blocks.
-// ----------------------------------------------------------------------------------
-constexpr int RB = 64;   // rows per reduce block
-
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = a * b;
-  e = fmaf(a, b, -p);
-}
-
-__global__ void __launch_bounds__(256)
-k_reduce(const float* __restrict__ part, int splits, int64_t rows, int RP, float* __restrict__ out,
-         void* gram_part, int gram_mode, const Ctl* ctl) {
-  if (ctl && ctl->abort) return;
-  __shared__ float Ps[RB][kMaxRP + 1];
-  const int64_t r0 = (int64_t)blockIdx.x * RB;
-  const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
-  const int tid = threadIdx.x;
-  const int64_t stride = rows * RP;
-  for (int e = tid; e < RB * RP; e += 256) {
-    int i = e / RP, c = e % RP;
+  __threadfence();
+  __syncthreads();
+  __shared__ unsigned s_last;
+  if (tid == 0) s_last = (atomicAdd(&counters[tile], 1u) == (unsigned)splits - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid == 0) counters[tile] = 0u;          // ready for the next product
+  float* Ps = sm;                              // [TM][EPI_STRIDE], reuses the stage buffers
+  float* Ts = sm + TM * EPI_STRIDE;            // [RP][EPI_STRIDE]
+  for (int e = tid; e < TM * RP; e += PASS_THREADS) {
+    const int i = e / RP, c = e % RP;
     float s = 0.f;
     if (i < nrow) {
-      const float* p = part + (r0 + i) * RP + c;
-      for (int sp = 0; sp < splits; ++sp) s += p[sp * stride];
-      out[(r0 + i) * RP + c] = s;
+      const float* p = part + (o0 + i) * RP + c;
+      for (int sp = 0; sp < splits; ++sp) s += __ldcg(p + (int64_t)sp * rows * RP);
     }
-    Ps[i][c] = s;
+    Ps[i * EPI_STRIDE + c] = s;
   }
-  if (gram_mode == 0) return;
-  __syncthreads();
-  const int npair = RP * RP;
-  for (int e = tid; e < npair; e += 256) {
-    int a = e / RP, c = e % RP;
-    if (gram_mode == 1) {
-      float g = 0.f;
-      for (int i = 0; i < nrow; ++i) g = fmaf(Ps[i][a], Ps[i][c], g);
-      reinterpret_cast<float*>(gram_part)[(int64_t)blockIdx.x * npair + e] = g;
-    } else {
-      // exact float32 products, double-float accumulation, stored as double
-      float hi = 0.f, lo = 0.f;
-      for (int i = 0; i < nrow; ++i) {
-        float p, pe;
-        two_prod(Ps[i][a], Ps[i][c], p, pe);
-        float s = hi + p;
-        float bb = s - hi;
-        float err = (hi - (s - bb)) + (p - bb);
-        hi = s;
-        lo += err + pe;
-      }
-      reinterpret_cast<double*>(gram_part)[(int64_t)blockIdx.x * npair + e] = (double)hi + (double)lo;
+  if (Tn) {
+    for (int e = tid; e < RP * RP; e += PASS_THREADS) Ts[(e / RP) * EPI_STRIDE + e % RP] = Tn[e];
+    __syncthreads();
+    // Q = P T: thread owns row `tid` (128 rows, 128 threads)
+    float q[RP];
+#pragma unroll
+    for (int c = 0; c < RP; ++c) q[c] = 0.f;
+    for (int a = 0; a < RP; ++a) {
+      const float pa = Ps[tid * EPI_STRIDE + a];
+#pragma unroll
+      for (int c = 0; c < RP; ++c) q[c] = fmaf(pa, Ts[a * EPI_STRIDE + c], q[c]);
     }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < RP; ++c) Ps[tid * EPI_STRIDE + c] = (tid < nrow) ? q[c] : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < nrow * RP; e += PASS_THREADS)
+    out[(o0 + e / RP) * RP + e % RP] = Ps[(e / RP) * EPI_STRIDE + e % RP];
+  if (gram_mode) {
+    const size_t stride = (size_t)RP * RP * (gram_mode == 2 ? 8 : 4);
+    tile_gram(Ps, nrow, RP, gram_mode, reinterpret_cast<char*>(gram_part) + (size_t)tile * stride,
+              PASS_THREADS);
   }
 }
 
-// Q = P T with T (RP x RP) upper triangular or dense; optional float Gram partials.
-__global__ void __launch_bounds__(256)
-k_apply(const float* __restrict__ P, int64_t rows, int RP, const float* __restrict__ T, int upper,
-        float* __restrict__ Q, float* __restrict__ gram_part, const Ctl* ctl) {
+template <typename T>
+void launch_prod_t(const ProdArgs& a, cudaStream_t st) {
+  const int64_t tiles = (a.rows + TM - 1) / TM;
+  dim3 grid((unsigned)(tiles * a.splits));
+  const T* Z = reinterpret_cast<const T*>(a.Z);
+#define GODEC_PROD_CASE(RNV)                                                                        \
+  case RNV:                                                                                         \
+    k_prod<RNV, T><<<grid, PASS_THREADS, kProdSmem, st>>>(Z, a.rows, a.K, a.ld, a.B, a.part,        \
+                                                          a.splits, a.kchunk, a.counters, a.out,    \
+                                                          a.Tn[0], a.Tn[1], a.gram_part,            \
+                                                          a.gram_mode, a.ctl);                      \
+    break;
+  switch (a.RP / 8) {
+    GODEC_PROD_CASE(1)
+    GODEC_PROD_CASE(2)
+    GODEC_PROD_CASE(3)
+    GODEC_PROD_CASE(4)
+    GODEC_PROD_CASE(5)
+    GODEC_PROD_CASE(6)
+    GODEC_PROD_CASE(7)
+    GODEC_PROD_CASE(8)
+    default: break;
+  }
+#undef GODEC_PROD_CASE
+}
+
+template <typename T>
+cudaError_t prepare_prod_t() {
+  cudaError_t e = cudaSuccess;
+#define GODEC_PREP(RNV)                                                                                   \
+  if (e == cudaSuccess)                                                                                   \
+    e = cudaFuncSetAttribute(k_prod<RNV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kProdSmem);
+  GODEC_PREP(1) GODEC_PREP(2) GODEC_PREP(3) GODEC_PREP(4) GODEC_PREP(5) GODEC_PREP(6) GODEC_PREP(7) GODEC_PREP(8)
+#undef GODEC_PREP
+  return e;
+}
+
+// ----------------------------------------------------------------------------------
+// Q = P T (dense T) or Q = P R^{-1} (R upper triangular, forward substitution per
+// row), optional float Gram partials of Q per 64-row block.
+// ----------------------------------------------------------------------------------
+constexpr int RB = 64;
+
+__global__ void __launch_bounds__(RB)
+k_apply(const float* __restrict__ P, int64_t rows, int RP, const float* __restrict__ T0,
+        const float* __restrict__ T1, int solve, float* __restrict__ Q, float* __restrict__ gram_part,
+        const Ctl* ctl) {
   if (ctl && ctl->abort) return;
+  const float* T = (ctl && ctl->slot_parity) ? T1 : T0;
   __shared__ float Ts[kMaxRP][kMaxRP + 1];
-  __shared__ float Ps[RB][kMaxRP + 1];
-  __shared__ float Qs[RB][kMaxRP + 1];
+  __shared__ float Qs[RB * EPI_STRIDE];
+  __shared__ float dinv[kMaxRP];
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * RB;
   const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
-  for (int e = tid; e < RP * RP; e += 256) Ts[e / RP][e % RP] = T[e];
-  for (int e = tid; e < RB * RP; e += 256) {
-    int i = e / RP, c = e % RP;
-    Ps[i][c] = (i < nrow) ? P[(r0 + i) * RP + c] : 0.f;
-  }
+  for (int e = tid; e < RP * RP; e += RB) Ts[e / RP][e % RP] = T[e];
   __syncthreads();
-  for (int e = tid; e < RB * RP; e += 256) {
-    int i = e / RP, c = e % RP;
-    float s = 0.f;
-    const int amax = upper ? c : RP - 1;
-    for (int a = 0; a <= amax; ++a) s = fmaf(Ps[i][a], Ts[a][c], s);
-    Qs[i][c] = (i < nrow) ? s : 0.f;
-    if (i < nrow) Q[(r0 + i) * RP + c] = s;
+  if (solve && tid < RP) dinv[tid] = 1.f / Ts[tid][tid];
+  __syncthreads();
+  // one row per thread; rows are read from P before any row of Q is written, so
+  // P and Q may alias
+  const int64_t i = r0 + tid;
+  float p[kMaxRP];
+#pragma unroll
+  for (int c = 0; c < kMaxRP; ++c) p[c] = (c < RP && tid < nrow) ? P[i * RP + c] : 0.f;
+  __syncthreads();
+  float q[kMaxRP];
+  if (solve) {
+    // q R = p: q_c = (p_c - sum_{a<c} q_a R[a][c]) / R[c][c]
+#pragma unroll
+    for (int c = 0; c < kMaxRP; ++c) {
+      if (c < RP) {
+        float s0 = p[c], s1 = 0.f;
+        int a = 0;
+#pragma unroll
+        for (; a + 1 < c; a += 2) {
+          s0 = fmaf(-q[a], Ts[a][c], s0);
+          s1 = fmaf(-q[a + 1], Ts[a + 1][c], s1);
+        }
+        if (a < c) s0 = fmaf(-q[a], Ts[a][c], s0);
+        q[c] = (s0 + s1) * dinv[c];
+      } else {
+        q[c] = 0.f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < kMaxRP; ++c) q[c] = 0.f;
+#pragma unroll
+    for (int a = 0; a < kMaxRP; ++a) {
+      if (a < RP) {
+        const float pa = p[a];
+#pragma unroll
+        for (int c = 0; c < kMaxRP; ++c)
+          if (c < RP) q[c] = fmaf(pa, Ts[a][c], q[c]);
+      }
+    }
   }
+#pragma unroll
+  for (int c = 0; c < kMaxRP; ++c)
+    if (c < RP) Qs[tid * EPI_STRIDE + c] = (tid < nrow) ? q[c] : 0.f;
+  if (tid < nrow)
+    for (int c = 0; c < RP; ++c) Q[i * RP + c] = q[c];
   if (!gram_part) return;
   __syncthreads();
-  for (int e = tid; e < RP * RP; e += 256) {
-    int a = e / RP, c = e % RP;
-    float g = 0.f;
-    for (int i = 0; i < nrow; ++i) g = fmaf(Qs[i][a], Qs[i][c], g);
-    gram_part[(int64_t)blockIdx.x * RP * RP + e] = g;
-  }
+  tile_gram(Qs, nrow, RP, 1, gram_part + (int64_t)blockIdx.x * RP * RP, RB);
 }
 
 }  // namespace
 
-void pass_geometry(int64_t outdim, int64_t K, int nsm, int* splits, int64_t* kchunk) {
-  const int64_t tiles = (outdim + TM - 1) / TM;
-  // Aim at about 4 CTAs per SM, each with at least 256 values of K.
-  int64_t want = (4LL * nsm + tiles - 1) / tiles;
+void prod_geometry(int64_t rows, int64_t K, int nsm, int* splits, int64_t* kchunk) {
+  const int64_t tiles = (rows + TM - 1) / TM;
+  // Aim at about 3 CTAs per SM, each with at least 256 values of K.
+  int64_t want = (3LL * nsm + tiles - 1) / tiles;
   int64_t maxs = (K + 255) / 256;
   int64_t s = want < 1 ? 1 : want;
   if (s > maxs) s = maxs < 1 ? 1 : maxs;
@@ -308,27 +370,24 @@ void pass_geometry(int64_t outdim, int64_t K, int nsm, int* splits, int64_t* kch
   *kchunk = ch;
 }
 
-void launch_pass(const PassArgs& a, cudaStream_t st) {
-  if (a.bf16) {
-    if (a.trans) launch_pass_t<true, __nv_bfloat16>(a, st);
-    else launch_pass_t<false, __nv_bfloat16>(a, st);
-  } else {
-    if (a.trans) launch_pass_t<true, float>(a, st);
-    else launch_pass_t<false, float>(a, st);
-  }
+int64_t prod_tiles(int64_t rows) { return (rows + TM - 1) / TM; }
+
+void launch_prod(const ProdArgs& a, cudaStream_t st) {
+  if (a.bf16) launch_prod_t<__nv_bfloat16>(a, st);
+  else launch_prod_t<float>(a, st);
 }
 
-int64_t reduce_blocks(int64_t rows) { return (rows + RB - 1) / RB; }
-
-void launch_reduce(const float* part, int splits, int64_t rows, int RP, float* out, void* gram_part,
-                   int gram_mode, const Ctl* ctl, cudaStream_t st) {
-  k_reduce<<<(unsigned)reduce_blocks(rows), 256, 0, st>>>(part, splits, rows, RP, out, gram_part,
-                                                           gram_mode, ctl);
+cudaError_t prepare_stream_kernels() {
+  cudaError_t e = prepare_prod_t<float>();
+  if (e == cudaSuccess) e = prepare_prod_t<__nv_bfloat16>();
+  return e;
 }
 
-void launch_apply(const float* P, int64_t rows, int RP, const float* T, int upper, float* Q,
+int64_t apply_blocks(int64_t rows) { return (rows + RB - 1) / RB; }
+
+void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, int solve, float* Q,
                   float* gram_part, const Ctl* ctl, cudaStream_t st) {
-  k_apply<<<(unsigned)reduce_blocks(rows), 256, 0, st>>>(P, rows, RP, T, upper, Q, gram_part, ctl);
+  k_apply<<<(unsigned)apply_blocks(rows), RB, 0, st>>>(P, rows, RP, T0, T1, solve, Q, gram_part, ctl);
 }
 
 }  // namespace godec

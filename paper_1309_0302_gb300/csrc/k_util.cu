@@ -13,6 +13,22 @@ __global__ void k_fill_zero(uint4* p, size_t n16) {
     p[i] = make_uint4(0, 0, 0, 0);
 }
 
+// 32 x 32 tiles through shared memory (padded against bank conflicts)
+__global__ void k_transpose(const float* __restrict__ src, int64_t m, int64_t n, int64_t lds,
+                            float* __restrict__ dst, int64_t ldd) {
+  __shared__ float t[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int64_t i = i0 + k, j = j0 + threadIdx.x;
+    t[k][threadIdx.x] = (i < m && j < n) ? src[i * lds + j] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int64_t j = j0 + k, i = i0 + threadIdx.x;
+    if (j < n && i < m) dst[j * ldd + i] = t[threadIdx.x][k];
+  }
+}
+
 __global__ void k_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < rows * RP;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -154,6 +170,12 @@ void launch_fill_zero(void* p, size_t bytes, cudaStream_t st) {
   if (!n16) return;
   unsigned grid = (unsigned)std::min<size_t>((n16 + 255) / 256, 4096);
   k_fill_zero<<<grid, 256, 0, st>>>(reinterpret_cast<uint4*>(p), n16);
+}
+
+void launch_transpose(const float* src, int64_t m, int64_t n, int64_t lds, float* dst, int64_t ldd,
+                      cudaStream_t st) {
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(src, m, n, lds, dst, ldd);
 }
 
 void launch_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP,
