@@ -51,7 +51,6 @@ struct godec_ctx {
   float* A1 = nullptr;                 // n x RP; columns >= r kept at zero
   float* A1_orig = nullptr;            // n x RP as given (restored by godec_reset)
   float* P = nullptr;                  // max(m,n) x RP
-  float* Qb[2] = {nullptr, nullptr};   // max(m,n) x RP
   float* Q1 = nullptr;                 // m x RP
   float* Q2 = nullptr;                 // n x RP
   float* U = nullptr;                  // m x RP
@@ -59,8 +58,19 @@ struct godec_ctx {
   float* sigma = nullptr;              // RP
   float* Um = nullptr;
   float* Vm = nullptr;
-  float* part = nullptr;               // split-K partials
+  // Operands of the tensor-core products in float16 split transposed form, each
+  // 2 RP x ldb halves.  bt2[0] is written by even products (read by odd ones, K = m),
+  // bt2[1] by odd products (read by even ones, K = n), bt2[2] holds A1 (read by product 0).
+  void* bt2 = nullptr;
+  int64_t ldb = 0;
+  int RPp = 0;
+  float* cs = nullptr;                 // [2][RP] output factors: A1's column scales, 1 / kSkinnyScale
+  float* rescale_tmp = nullptr;        // 2 floats: factor applied by rescale_z
+  alignas(64) unsigned char tmap[5][128];   // tensor maps: Z, Z^T, bt2[0], bt2[1], bt2[2]
+  TcGeom tg[2];                        // work split of even (Z) and odd (Z^T) products
+  float* part = nullptr;               // stream-K partial slots
   unsigned* counters = nullptr;        // per-tile arrival counters
+  int64_t ncounters = 0;
   char* gparts = nullptr;              // per product: tiles x RP x RP Gram partials (double room)
   size_t gpart_stride = 0;
   double* g64 = nullptr;               // per product reduced Gram, + 2 for the CholeskyQR2 rounds
@@ -85,6 +95,7 @@ struct godec_ctx {
   bool need_exact = true;
   int rank_drops = 0;
   int exact_iters = 0;
+  int rescales = 0;
   // kernel-level profiling (eager launches bracketed by events)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -182,29 +193,35 @@ void join_side(godec_ctx* c) {
 }
 
 char* gpart(godec_ctx* c, int i) { return c->gparts + (size_t)i * c->gpart_stride; }
+void* bt2(godec_ctx* c, int b) { return static_cast<char*>(c->bt2) + (size_t)b * 2 * c->RP * c->ldb * 2; }
 double* g64(godec_ctx* c, int i) { return c->g64 + (size_t)i * c->RP * c->RP; }
 
 // Product i of the chain: even i streams Z (rows m, K n), odd i streams Z^T (rows n, K m).
-void prod(godec_ctx* c, int i, const float* B, float* out, const float* T0, const float* T1, int gram_mode) {
+// Its skinny operand is the split transposed output of product i-1 (A1 for i = 0); the
+// rows go to `out` (nullable) and, with want_bt2, to the operand of product i+1.
+void prod(godec_ctx* c, int i, float* out, bool want_bt2, const float* T0, const float* T1, int gram_mode) {
   const bool even = (i % 2) == 0;
-  ProdArgs a{};
-  a.Z = even ? c->Z : c->Zt;
-  a.bf16 = 0;
-  a.rows = even ? c->p.m : c->p.n;
-  a.K = even ? c->p.n : c->p.m;
-  a.ld = even ? c->ldz : c->ldzt;
-  a.B = B;
-  a.part = c->part;
-  prod_geometry(a.rows, a.K, c->nsm, &a.splits, &a.kchunk);
-  a.counters = c->counters;
-  a.out = out;
-  a.Tn[0] = T0;
-  a.Tn[1] = T1;
-  a.gram_part = gpart(c, i);
-  a.gram_mode = gram_mode;
-  a.RP = c->RP;
-  a.ctl = c->ctl;
-  PROF(c, 0, c->st, launch_prod(a, c->st));
+  TcLaunch l{};
+  l.mapA = c->tmap[even ? 0 : 1];
+  l.mapB = c->tmap[i == 0 ? 4 : 2 + ((i - 1) & 1)];
+  l.rows = even ? c->p.m : c->p.n;
+  l.K = even ? c->p.n : c->p.m;
+  l.RP = c->RP;
+  l.geom = c->tg[even ? 0 : 1];
+  l.part = c->part;
+  l.counters = c->counters;
+  l.out = out;
+  l.bt2 = want_bt2 ? bt2(c, i & 1) : nullptr;
+  l.ldb = c->ldb;
+  l.Tn[0] = T0;
+  l.Tn[1] = T1;
+  l.cscale = c->cs + (i == 0 ? 0 : c->RP);
+  l.zscale = c->ctl->zscale;
+  l.prescaled = 1;   // Z and Z^T are stored as (X - S) s_Z
+  l.gram_part = gpart(c, i);
+  l.gram_mode = gram_mode;
+  l.ctl = c->ctl;
+  PROF(c, 0, c->st, launch_prod_tc(l, c->st));
 }
 
 void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out, cudaStream_t s) {
@@ -214,17 +231,19 @@ void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out
 void chol(godec_ctx* c, const double* g, float* R) { PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, c->ctl, c->st)); }
 
 void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const float* T1, int solve, float* Q,
-           float* gram) {
-  PROF(c, 3, c->st, launch_apply(P, rows, c->RP, T0, T1, solve, Q, gram, c->ctl, c->st));
+           float* gram, void* bt2out = nullptr) {
+  PROF(c, 3, c->st, launch_apply(P, rows, c->RP, T0, T1, solve, Q, gram, c->ctl, c->st, bt2out, c->ldb, c->RPp));
 }
 
-// Exact CholeskyQR2 of c->P (rows x RP) with the round-1 Gram g1: Q = P Ra^{-1} Rb^{-1}.
-void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* Rb, float* fin, double* g2) {
+// Exact CholeskyQR2 of c->P (rows x RP) with the round-1 Gram g1: Q = P Ra^{-1} Rb^{-1},
+// written to fin and, if bt2out is set, as the next product's operand.
+void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* Rb, float* fin, double* g2,
+                void* bt2out) {
   chol(c, g1, Ra);
   apply(c, c->P, rows, Ra, Ra, 1, c->P, c->gscr);
   gram_sum(c, c->gscr, 0, apply_blocks(rows), g2, c->st);
   chol(c, g2, Rb);
-  apply(c, c->P, rows, Rb, Rb, 1, fin, nullptr);
+  apply(c, c->P, rows, Rb, Rb, 1, fin, nullptr, bt2out);
 }
 
 void slot(godec_ctx* c, SlotLaunch& sl) {
@@ -245,14 +264,13 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
   const size_t rr = (size_t)RP * RP;
   auto sR = [&](int h, int i) { return c->Rslot + ((size_t)h * nprod + i) * rr; };
   auto sT = [&](int h, int i) { return c->Tslot + ((size_t)h * nprod + i) * rr; };
-  const float* B = c->A1;
   const float* rapp_last[2] = {nullptr, nullptr};
   bool have_pi = false;
   for (int i = 0; i < nprod; ++i) {
     const bool even = (i % 2) == 0;
     const int64_t rows = even ? m : n;
     const int64_t tiles = prod_tiles(rows);
-    float* Qdst = c->Qb[i & 1];
+    void* nextB = bt2(c, i & 1);
     SlotLaunch sl;
     sl.R_next[0] = sR(0, i);
     sl.R_next[1] = sR(1, i);
@@ -263,17 +281,17 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
     sl.pi_mode = pi_mode;
     if (i == i_rank) {
       // P = Z Q2 unnormalised, with an exactly accumulated Gram for the rank test
-      prod(c, i, B, c->P, nullptr, nullptr, 2);
+      prod(c, i, c->P, false, nullptr, nullptr, 2);
       gram_sum(c, gpart(c, i), 1, tiles, g64(c, i), c->st);
       fork_side(c);
       PROF(c, 5, c->side_st,
            launch_rank(g64(c, i), c->r, RP, c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4, c->ctl, c->side_st));
       if (i == last) {   // q = 0: this product is also the last one
-        final_cqr2(c, rows, g64(c, i), c->Rfin + 2 * rr, c->Rfin + 3 * rr, c->Q1, g64(c, nprod + 1));
+        final_cqr2(c, rows, g64(c, i), c->Rfin + 2 * rr, c->Rfin + 3 * rr, c->Q1, g64(c, nprod + 1), nullptr);
         continue;
       }
       if (fast) {
-        apply(c, c->P, rows, sT(0, i), sT(1, i), 0, Qdst, nullptr);
+        apply(c, c->P, rows, sT(0, i), sT(1, i), 0, nullptr, nullptr, nextB);
         sl.fast = 1;
         sl.g64 = g64(c, i);
         sl.g_is_p = 1;
@@ -284,21 +302,20 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       } else {
         float* Rt = c->Rtmp + (size_t)i * rr;
         chol(c, g64(c, i), Rt);
-        apply(c, c->P, rows, Rt, Rt, 1, Qdst, nullptr);
+        apply(c, c->P, rows, Rt, Rt, 1, nullptr, nullptr, nextB);
         fork_side(c);
         sl.fast = 0;
         sl.R_app[0] = sl.R_app[1] = Rt;
       }
       slot(c, sl);
       have_pi = true;
-      B = Qdst;
     } else if (i == i_q2 || i == last) {
-      prod(c, i, B, c->P, fast ? sT(0, i) : nullptr, fast ? sT(1, i) : nullptr, 1);
+      prod(c, i, c->P, false, fast ? sT(0, i) : nullptr, fast ? sT(1, i) : nullptr, 1);
       gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
       float* Ra = c->Rfin + (i == i_q2 ? 0 : 2) * rr;
       float* Rb = Ra + rr;
       float* fin = (i == i_q2) ? c->Q2 : c->Q1;
-      final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)));
+      final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)), i == i_q2 ? nextB : nullptr);
       fork_side(c);
       sl.fast = 0;
       if (fast) {
@@ -313,10 +330,9 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       sl.L2 = Rb;
       sl.pi_mode = 0;
       slot(c, sl);
-      B = fin;
     } else {
       if (fast) {
-        prod(c, i, B, Qdst, sT(0, i), sT(1, i), 1);
+        prod(c, i, nullptr, true, sT(0, i), sT(1, i), 1);
         fork_side(c);
         gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->side_st);
         sl.fast = 1;
@@ -325,17 +341,16 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
         sl.R_app[1] = sR(1, i);
       } else {
         float* Rt = c->Rtmp + (size_t)i * rr;
-        prod(c, i, B, c->P, nullptr, nullptr, 1);
+        prod(c, i, c->P, false, nullptr, nullptr, 1);
         gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
         chol(c, g64(c, i), Rt);
-        apply(c, c->P, rows, Rt, Rt, 1, Qdst, nullptr);
+        apply(c, c->P, rows, Rt, Rt, 1, nullptr, nullptr, nextB);
         fork_side(c);
         sl.fast = 0;
         sl.R_app[0] = sl.R_app[1] = Rt;
       }
       slot(c, sl);
       if (pi_mode) have_pi = true;
-      B = Qdst;
     }
   }
   join_side(c);
@@ -402,6 +417,7 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ea.ldzt = c->ldzt;
   ea.Z16 = c->Z16;
   ea.Zt16 = c->Zt16;
+  ea.zscale = c->ctl->zscale;
   PROF(c, 8, st, launch_emit(ea, c->nsm, st));
   if (c->Z) PROF(c, 9, st, launch_z_update(ea, c->nsm, st));
 }
@@ -457,6 +473,13 @@ godec_status drop_columns(godec_ctx* c) {
   if (c->r < c->RP)
     CK(cudaMemset2DAsync(c->A1 + c->r, c->RP * sizeof(float), 0, (c->RP - c->r) * sizeof(float), c->p.n,
                          c->st));
+  launch_split_t(c->A1, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
+  return GODEC_OK;
+}
+
+// A product that saw the abort flag part-way leaves tile counters behind.
+godec_status clear_counters(godec_ctx* c) {
+  CK(cudaMemsetAsync(c->counters, 0, (size_t)c->ncounters * sizeof(unsigned), c->st));
   return GODEC_OK;
 }
 
@@ -468,9 +491,8 @@ godec_status reset_state(godec_ctx* c) {
   c->exact_iters = 0;
   CK(cudaMemcpyAsync(c->A1, c->A1_orig, (size_t)c->p.n * c->RP * sizeof(float), cudaMemcpyDeviceToDevice,
                      c->st));
-  CK(cudaMemcpy2DAsync(c->Z, c->ldz * sizeof(float), c->X, c->p.ldx * sizeof(float), c->p.n * sizeof(float),
-                       c->p.m, cudaMemcpyDeviceToDevice, c->st));
-  launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st);
+  launch_split_t(c->A1, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
+  if (godec_status s = clear_counters(c)) return s;
   std::vector<float> eye((size_t)c->RP * c->RP, 0.f);
   for (int i = 0; i < c->RP; ++i) eye[(size_t)i * c->RP + i] = 1.f;
   CK(cudaMemcpyAsync(c->Vprev, eye.data(), eye.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
@@ -483,15 +505,46 @@ godec_status reset_state(godec_ctx* c) {
   CK(cudaMemcpyAsync(c->ctl, &h, offsetof(Ctl, hist), cudaMemcpyHostToDevice, c->st));
   launch_sumsq(c->X, c->p.m, c->p.n, c->p.ldx,
                reinterpret_cast<double*>(reinterpret_cast<char*>(c->ctl) + offsetof(Ctl, normX2)), c->nsm, c->st);
+  // working copies Z = X s_Z and Z^T, with s_Z from max |X|
+  launch_zscale(c->X, c->p.m, c->p.n, c->p.ldx, &c->ctl->zmax_bits, c->ctl->zscale, c->nsm, c->st);
+  launch_scale_copy(c->X, c->p.m, c->p.n, c->p.ldx, c->Z, c->ldz, c->ctl->zscale, c->nsm, c->st);
+  launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st, c->ctl->zscale);
   launch_reset_iter(c->ctl, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   return GODEC_OK;
 }
 
+// The S-step wrote an entry of Z beyond the float16 split's range: bring max |Z| back
+// into [2^12, 2^13) by a power of two, exactly, in Z, Z^T and the stored scale.
+godec_status rescale_z(godec_ctx* c) {
+  float* f = c->rescale_tmp;
+  launch_zscale(c->Z, c->p.m, c->p.n, c->ldz, &c->ctl->zmax_bits, f, c->nsm, c->st);
+  launch_scale_copy(c->Z, c->p.m, c->p.n, c->ldz, c->Z, c->ldz, f, c->nsm, c->st);
+  launch_scale_copy(c->Zt, c->p.n, c->p.m, c->ldzt, c->Zt, c->ldzt, f, c->nsm, c->st);
+  launch_scale_update(c->ctl->zscale, f, c->st);
+  CK(cudaGetLastError());
+  ++c->rescales;
+  return GODEC_OK;
+}
+
 // Host-side handling of an aborted iteration; the iteration is redone afterwards.
 godec_status handle_abort(godec_ctx* c, const Ctl& h) {
   godec_status s;
+  if ((s = clear_counters(c))) return s;
+  if (h.timeout) {
+    launch_reset_iter(c->ctl, c->st);
+    return fail(c, GODEC_ERR_TIMEOUT, "a device-side wait of the tensor-core product timed out (iteration %d)",
+                h.iter + 1);
+  }
+  if (h.range_err && !h.nonfinite) {
+    // Z outgrew its scale in the last S-step; the iteration after it was skipped.
+    if ((s = rescale_z(c))) return s;
+    if ((s = SET_CTL(range_err, 0))) return s;
+    launch_reset_iter(c->ctl, c->st);
+    CK(cudaGetLastError());
+    return GODEC_OK;
+  }
   if (h.nonfinite) {
     launch_reset_iter(c->ctl, c->st);
     return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - L (iteration %d)", h.iter + 1);
@@ -595,7 +648,7 @@ void godec_destroy(godec_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   free_graphs(c);
-  void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->Qb[0], c->Qb[1], c->Q1, c->Q2,
+  void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->bt2, c->cs, c->rescale_tmp, c->Q1, c->Q2,
                   c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->gparts, c->g64, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
                   c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1]};
@@ -650,6 +703,7 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(prepare_small_kernels());
   CKI(prepare_select_kernels());
   CKI(prepare_stream_kernels());
+  CKI(prepare_tc_kernels());
   CKI(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
   CKI(cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking));
   for (int k = 0; k < kEvents; ++k) CKI(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
@@ -664,8 +718,6 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(dalloc(&c->A1, (size_t)n * RP));
   CKI(dalloc(&c->A1_orig, (size_t)n * RP));
   CKI(dalloc(&c->P, (size_t)mx * RP));
-  CKI(dalloc(&c->Qb[0], (size_t)mx * RP));
-  CKI(dalloc(&c->Qb[1], (size_t)mx * RP));
   CKI(dalloc(&c->Q1, (size_t)m * RP));
   CKI(dalloc(&c->Q2, (size_t)n * RP));
   CKI(dalloc(&c->U, (size_t)m * RP));
@@ -673,14 +725,36 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(dalloc(&c->sigma, (size_t)RP));
   CKI(dalloc(&c->Um, rr));
   CKI(dalloc(&c->Vm, rr));
-  int s1, s2;
-  int64_t ch;
-  prod_geometry(m, n, c->nsm, &s1, &ch);
-  prod_geometry(n, m, c->nsm, &s2, &ch);
-  CKI(dalloc(&c->part, (size_t)std::max<int64_t>((int64_t)s1 * m, (int64_t)s2 * n) * RP));
+  c->RPp = tc_rpp(RP);
+  c->ldb = (mx + 7) / 8 * 8;
+  CKI(dalloc(reinterpret_cast<unsigned short**>(&c->bt2), (size_t)3 * 2 * RP * c->ldb));
+  CKI(cudaMemsetAsync(c->bt2, 0, (size_t)3 * 2 * RP * c->ldb * 2, c->st));
+  CKI(dalloc(&c->cs, (size_t)2 * RP));
+  CKI(dalloc(&c->rescale_tmp, 2));
+  {
+    std::vector<float> cs(2 * (size_t)RP, 1.f / kSkinnyScale);
+    CKI(cudaMemcpy(c->cs, cs.data(), cs.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  c->tg[0] = tc_geometry(m, n, c->nsm);
+  c->tg[1] = tc_geometry(n, m, c->nsm);
+  size_t npart = 0;
+  for (const TcGeom& g : c->tg) npart = std::max(npart, (size_t)g.tiles * g.maxseg * 128 * RP);
+  CKI(dalloc(&c->part, npart));
   const int64_t tiles = prod_tiles(mx);
+  c->ncounters = tiles;
   CKI(dalloc(&c->counters, (size_t)tiles));
   CKI(cudaMemsetAsync(c->counters, 0, (size_t)tiles * sizeof(unsigned), c->st));
+  {
+    const bool ok = make_tmap_f32(c->tmap[0], c->Z, m, n, c->ldz, 128) &&
+                    make_tmap_f32(c->tmap[1], c->Zt, n, m, c->ldzt, 128) &&
+                    make_tmap_f16(c->tmap[2], bt2(c, 0), 2 * RP, m, c->ldb, 2 * RP) &&
+                    make_tmap_f16(c->tmap[3], bt2(c, 1), 2 * RP, n, c->ldb, 2 * RP) &&
+                    make_tmap_f16(c->tmap[4], bt2(c, 2), 2 * RP, n, c->ldb, 2 * RP);
+    if (!ok) {
+      fail(c, GODEC_ERR_CUDA, "tensor map encoding failed");
+      return bail(GODEC_ERR_CUDA);
+    }
+  }
   c->gpart_stride = ((size_t)tiles * rr * sizeof(double) + 255) & ~size_t(255);
   CKI(dalloc(&c->gparts, c->gpart_stride * np));
   CKI(dalloc(&c->g64, (size_t)(np + 2) * rr));
@@ -1013,46 +1087,61 @@ static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz
   const int64_t rows = trans ? n : m, K = trans ? m : n;
   int nsm = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      prepare_stream_kernels() != cudaSuccess) {
+      prepare_tc_kernels() != cudaSuccess) {
     snprintf(g_static_err, sizeof(g_static_err), "godec_mul: no CUDA device");
     return GODEC_ERR_CUDA;
   }
-  int splits;
-  int64_t kchunk;
-  prod_geometry(rows, K, nsm, &splits, &kchunk);
-  const int64_t ldt = (m + 3) / 4 * 4;
-  float *Bp = nullptr, *part = nullptr, *Yp = nullptr, *Zt = nullptr;
+  const TcGeom geom = tc_geometry(rows, K, nsm);
+  const int64_t ldt = (m + 3) / 4 * 4, ldb = (K + 7) / 8 * 8;
+  float *Bp = nullptr, *part = nullptr, *Yp = nullptr, *Zt = nullptr, *aux = nullptr;
+  void* Bs = nullptr;
   unsigned* cnt = nullptr;
   bool ok = cudaMallocAsync(reinterpret_cast<void**>(&Bp), (size_t)K * RP * sizeof(float), st) == cudaSuccess &&
-            cudaMallocAsync(reinterpret_cast<void**>(&part), (size_t)splits * rows * RP * sizeof(float), st) == cudaSuccess &&
+            cudaMallocAsync(&Bs, (size_t)2 * RP * ldb * 2, st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&aux), (size_t)(4 + RP) * sizeof(float), st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&part), (size_t)geom.tiles * geom.maxseg * 128 * RP * sizeof(float),
+                            st) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&Yp), (size_t)rows * RP * sizeof(float), st) == cudaSuccess &&
-            cudaMallocAsync(reinterpret_cast<void**>(&cnt), (size_t)prod_tiles(rows) * sizeof(unsigned), st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&cnt), (size_t)geom.tiles * sizeof(unsigned), st) == cudaSuccess &&
             (!trans || cudaMallocAsync(reinterpret_cast<void**>(&Zt), (size_t)n * ldt * sizeof(float), st) == cudaSuccess);
+  bool mapped = false;
   if (ok) {
-    cudaMemsetAsync(cnt, 0, (size_t)prod_tiles(rows) * sizeof(unsigned), st);
-    launch_pad_copy(B, K, r, r, Bp, RP, st);
-    if (trans) launch_transpose(Z, m, n, ldz, Zt, ldt, st);
-    ProdArgs pa{};
-    pa.Z = trans ? Zt : Z;
-    pa.rows = rows;
-    pa.K = K;
-    pa.ld = trans ? ldt : ldz;
-    pa.B = Bp;
-    pa.part = part;
-    pa.splits = splits;
-    pa.kchunk = kchunk;
-    pa.counters = cnt;
-    pa.out = Yp;
-    pa.RP = RP;
-    launch_prod(pa, st);
-    launch_unpad_copy(Yp, rows, RP, Y, r, st);
+    alignas(64) unsigned char mapA[128], mapB[128];
+    mapped = make_tmap_f32(mapA, trans ? Zt : Z, rows, K, trans ? ldt : ldz, 128) &&
+             make_tmap_f16(mapB, Bs, 2 * RP, K, ldb, 2 * RP);
+    if (mapped) {
+      cudaMemsetAsync(cnt, 0, (size_t)geom.tiles * sizeof(unsigned), st);
+      // aux: {s_Z, 1/s_Z}, max-|Z| scratch, pad, then RP column factors of B
+      launch_zscale(Z, m, n, ldz, reinterpret_cast<unsigned*>(aux + 2), aux, nsm, st);
+      launch_pad_copy(B, K, r, r, Bp, RP, st);
+      launch_split_t(Bp, K, RP, Bs, ldb, aux + 4, st);
+      if (trans) launch_transpose(Z, m, n, ldz, Zt, ldt, st);
+      TcLaunch l{};
+      l.mapA = mapA;
+      l.mapB = mapB;
+      l.rows = rows;
+      l.K = K;
+      l.RP = RP;
+      l.geom = geom;
+      l.part = part;
+      l.counters = cnt;
+      l.out = Yp;
+      l.cscale = aux + 4;
+      l.zscale = aux;
+      launch_prod_tc(l, st);
+      launch_unpad_copy(Yp, rows, RP, Y, r, st);
+    }
   }
-  void* ptrs[] = {Bp, part, Yp, cnt, Zt};
+  void* ptrs[] = {Bp, Bs, aux, part, Yp, cnt, Zt};
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, st);
   if (!ok) {
     snprintf(g_static_err, sizeof(g_static_err), "godec_mul: out of device memory");
     return GODEC_ERR_OOM;
+  }
+  if (!mapped) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mul: tensor map encoding failed");
+    return GODEC_ERR_CUDA;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

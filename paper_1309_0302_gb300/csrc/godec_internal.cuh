@@ -17,6 +17,16 @@
 namespace godec {
 
 constexpr int kMaxRP = 64;          // maximum padded rank
+// Scale of the orthonormalised skinny operands in their float16 split form.  Entries
+// of a unit column are at most 1, and a lagged normaliser can leave a column far from
+// unit norm before the alarm catches it, so no scale-up: float16 then holds columns of
+// norm up to ~6e4, and the split keeps 22 bits down to magnitudes of 2^-14 (below that
+// the error is an absolute 2^-35, negligible against a unit column).
+constexpr float kSkinnyScale = 1.f;
+// The working copy Z = (X - S) s_Z is kept below this magnitude (float16 holds 65504):
+// s_Z puts max |X| in [2^12, 2^13), and an S-step that writes a larger entry flags
+// range_err so Z is rescaled before the next product.
+constexpr float kZRange = 32768.f;
 constexpr int kHistBins = 4096;     // first radix digit: key bits 30..19
 constexpr int kD1Shift = 19;
 constexpr int kNumSelRounds = 7;    // 3 key digits + 4 index digits
@@ -71,8 +81,11 @@ struct Ctl {
   int chol_shifts;              // Cholesky factorisations that needed a diagonal shift
   int alarm;                    // a lagged normaliser left the chain ill-conditioned
   int slot_parity;              // which half of the slot buffers holds this iteration's T
-  int pad3;
+  int timeout;                  // a bounded device-side wait gave up
   double m_logscale;            // Pi (core of the last chain) is stored divided by exp(.)
+  float zscale[2];              // power-of-two scale s_Z of the stored Z = (X - S) s_Z, and 1 / s_Z
+  unsigned zmax_bits;           // scratch: max |Z| as float bits
+  int range_err;                // the S-step wrote an entry of Z above kZRange (rescale Z before reuse)
   // --- histograms ------------------------------------------------------------
   unsigned hist[kHistBins];     // digit-1 histogram of |R| keys (full pass)
   unsigned sel_hist[kHistBins];
@@ -109,9 +122,57 @@ cudaError_t prepare_stream_kernels();
 
 // Q = P T (solve = 0) or Q = P T^{-1} with T upper triangular (solve = 1, forward
 // substitution); T is T0 or T1 by the slot parity in ctl (T0 without ctl); optional
-// float Gram partials of Q per apply_blocks() row block.  P and Q may alias.
+// float Gram partials of Q per apply_blocks() row block.  P and Q may alias; Q may be
+// null.  With bt2 set, also writes the float16 split transposed operand of the
+// tensor-core product, [c1^T; c2^T] (2 RP x ldb halves) with
+// Q kSkinnyScale = c1 + 2^-11 c2.
 void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, int solve, float* Q,
-                  float* gram_part, const Ctl* ctl, cudaStream_t st);
+                  float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2 = nullptr, int64_t ldb = 0,
+                  int RPp = 0);
+
+// Tensor-core streaming product (k_tc.cu).
+struct TcGeom {
+  int64_t tiles = 0, ks = 0, S = 0;
+  int G = 0, maxseg = 0;
+};
+TcGeom tc_geometry(int64_t rows, int64_t K, int nsm);
+int tc_rpp(int RP);
+// Float16 split transposed operand of a row-major rows x RP matrix B (2 RP x ldb
+// halves), each column scaled by a power of two; cscale (RP) receives the factors that
+// undo the scaling.
+void launch_split_t(const float* B, int64_t rows, int RP, void* bt2, int64_t ldb, float* cscale, cudaStream_t st);
+// zscale = {s, 1/s}: the power of two with max |Z| s in [2^12, 2^13) (1 if Z is zero or
+// not finite); zmax is scratch.
+void launch_zscale(const float* Z, int64_t rows, int64_t cols, int64_t ld, unsigned* zmax, float* zscale, int nsm,
+                   cudaStream_t st);
+// dst = src * scale[0] (rows x cols, strides lds / ldd); dst may equal src.
+void launch_scale_copy(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
+                       const float* scale, int nsm, cudaStream_t st);
+// zscale[0..1] *= f[0..1] (one thread).
+void launch_scale_update(float* zscale, const float* f, cudaStream_t st);
+bool make_tmap_f32(void* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+bool make_tmap_f16(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+cudaError_t prepare_tc_kernels();
+struct TcLaunch {
+  const void* mapA;        // CUtensorMap over Zsrc (rows x K), box 32 x 128
+  const void* mapB;        // CUtensorMap over the float16 split operand (2 RP x K), box 64 x 2 RP
+  int64_t rows, K;
+  int RP;
+  TcGeom geom;
+  float* part;             // tiles x maxseg x 128 x RP
+  unsigned* counters;      // tiles, zero
+  float* out;              // rows x RP (nullable)
+  void* bt2;               // 2 RP x ldb halves (nullable)
+  int64_t ldb;
+  const float* Tn[2];
+  const float* cscale;     // per-column output factor (nullable)
+  const float* zscale;     // {s_Z, 1/s_Z} on the device (nullable)
+  int prescaled;           // Zsrc already holds x s_Z
+  void* gram_part;
+  int gram_mode;
+  Ctl* ctl;
+};
+void launch_prod_tc(const TcLaunch& l, cudaStream_t st);
 int64_t apply_blocks(int64_t rows);
 
 // r x r kernels (k_small.cu).
@@ -185,6 +246,7 @@ struct EmitArgs {
   int64_t ldzt;
   void* Z16;               // nullable bf16 copies (same strides)
   void* Zt16;
+  const float* zscale;     // Z and Zt are stored scaled by zscale[0]
 };
 void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st);
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);
@@ -201,8 +263,9 @@ cudaError_t prepare_select_kernels();
 // Small helpers.
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
 // dst (n x ldd) = src^T (src m x n with stride lds)
+// dst = src^T, optionally times scale[0]
 void launch_transpose(const float* src, int64_t m, int64_t n, int64_t lds, float* dst, int64_t ldd,
-                      cudaStream_t st);
+                      cudaStream_t st, const float* scale = nullptr);
 void launch_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP,
                      cudaStream_t st);
 void launch_unpad_copy(const float* src, int64_t rows, int RP, float* dst, int cols,

@@ -530,22 +530,38 @@ k_emit(EmitArgs a) {
 }
 
 // Z := X on the entries of S_{t-1}, then Z := X - S_t on the entries of S_t.
+// Z and Zt hold (X - S) zscale[0].  An entry whose scaled magnitude reaches kZRange
+// flags range_err; the next product sees the flag, abandons that iteration before
+// reading Z, and the caller rescales Z (setting abort here would cut this update short
+// in blocks that have not started yet).
+__device__ __forceinline__ void z_write(const EmitArgs& a, long long i, long long j, float z, float zs, bool& bad) {
+  const float v = z * zs;
+  bad |= fabsf(v) >= kZRange && isfinite(v);
+  a.Z[i * a.ldz + j] = v;
+  if (a.Zt) a.Zt[j * a.ldzt + i] = v;
+  if (a.Z16) reinterpret_cast<__nv_bfloat16*>(a.Z16)[i * a.ldz + j] = __float2bfloat16(z);
+  if (a.Zt16) reinterpret_cast<__nv_bfloat16*>(a.Zt16)[j * a.ldzt + i] = __float2bfloat16(z);
+}
+
+__device__ __forceinline__ void z_flag(Ctl* ctl, bool bad) {
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) ctl->range_err = 1;
+}
+
 __global__ void k_z_restore(EmitArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->abort) return;
   const int ob = ctl->cur ^ 1;
   const long long nnz = ctl->nnz_prev;
   const long long* Sidx = a.S_idx[ob];
+  const float zs = a.zscale ? a.zscale[0] : 1.f;
+  bool bad = false;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
        e += (long long)gridDim.x * blockDim.x) {
     long long idx = Sidx[e];
     long long i = idx / a.n, j = idx % a.n;
-    float x = a.X[i * a.ldx + j];
-    a.Z[i * a.ldz + j] = x;
-    if (a.Zt) a.Zt[j * a.ldzt + i] = x;
-    if (a.Z16) reinterpret_cast<__nv_bfloat16*>(a.Z16)[i * a.ldz + j] = __float2bfloat16(x);
-    if (a.Zt16) reinterpret_cast<__nv_bfloat16*>(a.Zt16)[j * a.ldzt + i] = __float2bfloat16(x);
+    z_write(a, i, j, a.X[i * a.ldx + j], zs, bad);
   }
+  z_flag(ctl, bad);
 }
 
 __global__ void k_z_scatter(EmitArgs a) {
@@ -555,16 +571,15 @@ __global__ void k_z_scatter(EmitArgs a) {
   const long long nnz = ctl->nnz_cur;
   const long long* Sidx = a.S_idx[cb];
   const float* Sval = a.S_val[cb];
+  const float zs = a.zscale ? a.zscale[0] : 1.f;
+  bool bad = false;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
        e += (long long)gridDim.x * blockDim.x) {
     long long idx = Sidx[e];
     long long i = idx / a.n, j = idx % a.n;
-    float z = a.X[i * a.ldx + j] - Sval[e];
-    a.Z[i * a.ldz + j] = z;
-    if (a.Zt) a.Zt[j * a.ldzt + i] = z;
-    if (a.Z16) reinterpret_cast<__nv_bfloat16*>(a.Z16)[i * a.ldz + j] = __float2bfloat16(z);
-    if (a.Zt16) reinterpret_cast<__nv_bfloat16*>(a.Zt16)[j * a.ldzt + i] = __float2bfloat16(z);
+    z_write(a, i, j, a.X[i * a.ldx + j] - Sval[e], zs, bad);
   }
+  z_flag(ctl, bad);
 }
 
 // Per-iteration S-step state back to "start of an iteration" (one thread).
@@ -598,6 +613,7 @@ __global__ void k_reset_iter(Ctl* ctl) {
   ctl->chol_fail = 0;
   ctl->converged = 0;
   ctl->alarm = 0;
+  ctl->timeout = 0;
 }
 
 }  // namespace

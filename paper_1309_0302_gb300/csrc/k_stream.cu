@@ -13,6 +13,8 @@
 // the output rows and the tile's Gram partial Q^T Q for the next orthonormalisation.
 #include <cuda_bf16.h>
 
+#include <cuda_fp16.h>
+
 #include "godec_internal.cuh"
 
 namespace godec {
@@ -291,7 +293,7 @@ constexpr int RB = 64;
 __global__ void __launch_bounds__(RB)
 k_apply(const float* __restrict__ P, int64_t rows, int RP, const float* __restrict__ T0,
         const float* __restrict__ T1, int solve, float* __restrict__ Q, float* __restrict__ gram_part,
-        const Ctl* ctl) {
+        const Ctl* ctl, void* __restrict__ bt2, int64_t ldb, int RPp) {
   if (ctl && ctl->abort) return;
   const float* T = (ctl && ctl->slot_parity) ? T1 : T0;
   __shared__ float Ts[kMaxRP][kMaxRP + 1];
@@ -346,8 +348,20 @@ k_apply(const float* __restrict__ P, int64_t rows, int RP, const float* __restri
 #pragma unroll
   for (int c = 0; c < kMaxRP; ++c)
     if (c < RP) Qs[tid * EPI_STRIDE + c] = (tid < nrow) ? q[c] : 0.f;
-  if (tid < nrow)
+  if (Q && tid < nrow)
     for (int c = 0; c < RP; ++c) Q[i * RP + c] = q[c];
+  if (bt2 && tid < nrow) {
+    __half* b2 = reinterpret_cast<__half*>(bt2);
+#pragma unroll
+    for (int c = 0; c < kMaxRP; ++c) {
+      if (c < RP) {
+        const float v = q[c] * kSkinnyScale;
+        const __half c1 = __float2half_rn(v);
+        b2[(int64_t)c * ldb + i] = c1;
+        b2[(int64_t)(RP + c) * ldb + i] = __float2half_rn((v - __half2float(c1)) * 2048.f);
+      }
+    }
+  }
   if (!gram_part) return;
   __syncthreads();
   tile_gram(Qs, nrow, RP, 1, gram_part + (int64_t)blockIdx.x * RP * RP, RB);
@@ -386,8 +400,9 @@ cudaError_t prepare_stream_kernels() {
 int64_t apply_blocks(int64_t rows) { return (rows + RB - 1) / RB; }
 
 void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, int solve, float* Q,
-                  float* gram_part, const Ctl* ctl, cudaStream_t st) {
-  k_apply<<<(unsigned)apply_blocks(rows), RB, 0, st>>>(P, rows, RP, T0, T1, solve, Q, gram_part, ctl);
+                  float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2, int64_t ldb, int RPp) {
+  k_apply<<<(unsigned)apply_blocks(rows), RB, 0, st>>>(P, rows, RP, T0, T1, solve, Q, gram_part, ctl, bt2, ldb,
+                                                        RPp);
 }
 
 }  // namespace godec

@@ -1,0 +1,658 @@
+// Streaming product on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   part/out = Zsrc (rows x K, float32, row-major) * B (K x RP)   to float32 accuracy
+//
+// Two-term float16 split ("2xFP16"): with a power-of-two scale s_Z, each element is
+// written x s_Z = h1 + 2^-11 h2, h1 = x s_Z cut to 11 significant bits (exact in
+// float16), h2 = fp16((x s_Z - h1) 2^11) rounded to nearest; the
+// skinny operand likewise, b s_B = c1 + 2^-11 c2, arrives already split and transposed
+// as [c1^T; c2^T] (2 RP x K float16) from the step that produced it.  Then
+//   x b s_Z s_B = h1 c1 + 2^-11 (h1 c2 + h2 c1) + O(2^-22),
+// the dropped h2 c2 term being the only truncation.  Per 16-wide K step:
+//   D[:, 0:2RP] += h1 [c1; c2]^T   and   D[:, RP:RP+RPl] += h2 (rows 0..RPl-1 of [c1; c2])^T,
+// RPl = RP rounded up to 16 (the MMA's N granularity): columns RP..2RP-1 receive h2 c1,
+// columns beyond 2RP collect a product nobody reads.  The result is
+// (D[:, :RP] + 2^-11 D[:, RP:2RP]) / (s_Z s_B).  float16 MMAs run at twice the TF32
+// rate with twice the K per instruction.
+//
+// Converter warps move each 128 x 64 tile of Zsrc from shared memory into tensor memory
+// as the two packed float16 column blocks (h1, h2) and free the shared-memory slot at
+// once, so the TMA ring only has to cover the DRAM latency.  Zsrc is either stored
+// already scaled (the working copy of X - S, whose writers keep it inside the float16
+// range) or scaled here (a caller's matrix, scale from its exact maximum).
+//
+// Work split: the (128-row tile, 64-wide K stage) iteration space is cut into equal
+// contiguous ranges, one per persistent CTA ("stream-K"), so every SM streams the same
+// number of bytes whatever the tile count.  The tensor core accumulates a chunk of
+// kChunk stages in TMEM (double-buffered); the 4 epilogue warps drain each chunk into
+// float32 registers, so the tensor core's own accumulation never runs over more than
+// kChunk * 64 terms (its additions are not round-to-nearest, and over thousands of
+// terms of one sign the bias would show).  At a tile boundary the running sum goes to
+// a partial slot.  The last segment of a tile to arrive adds the slots in order
+// (deterministic), unscales, applies the normaliser T, and writes the rows, the next
+// product's split transposed operand and the tile's Gram partial.
+//
+// Warps: 0 TMA producer of Zsrc tiles, 1 MMA issuer (and TMEM owner), 2-9 converters
+// (two per TMEM lane quarter, one per 32-column half of the tile), 10-13 epilogue,
+// 14 TMA producer of the skinny operand.
+// TMEM (512 columns): 0-255 two accumulators of 128 columns, 256-447 three A slots of
+// 64 columns (32 of packed h1, 32 of packed h2).
+// Synchronisation per stage: TMA -> afull -> converters -> aempty (slot refilled);
+// converters -> tfull (after the skinny tile's bfull too) -> MMA -> sfree -> both the
+// converters' TMEM slot and the skinny TMA slot.  The MMA issuer, the one serial role,
+// waits once and commits once per stage.
+// Every wait is bounded; a timeout sets ctl->timeout and the CTA drains and exits.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include "godec_internal.cuh"
+#include "tc_util.cuh"
+
+namespace godec {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128, BK = 64;   // rows per tile, K per stage (4 MMA steps of 16)
+constexpr int NA = 4;              // shared-memory slots for Zsrc tiles (TMA ring)
+constexpr int NS = 3;              // stage slots: skinny-operand tile in shared memory + converted
+                                   // Zsrc tile in TMEM, freed together by one MMA commit
+constexpr int kThreads = 480;
+constexpr int kConvWarps = 8;
+constexpr uint32_t kTmemCols = 512, kTA0 = 256, kTASlot = 64;
+constexpr int EPI_LD = kMaxRP + 1;
+constexpr size_t kBoxA = (size_t)BM * 32 * 4;               // one 32-column float32 box, 16 KB
+constexpr size_t kStageA = 2 * kBoxA;                       // 32 KB
+constexpr size_t kStageB = (size_t)2 * kMaxRP * BK * 2;     // 16 KB (room for 2 x 64 rows of 64 halves)
+constexpr size_t kOffA = 0;
+constexpr size_t kOffB = kOffA + NA * kStageA;
+constexpr size_t kOffEpi = kOffB + NS * kStageB;
+constexpr size_t kEpiBytes = (size_t)BM * EPI_LD * 4 + (size_t)kMaxRP * kMaxRP * 4;
+constexpr size_t kTcSmem = kOffEpi + kEpiBytes + 1024;       // + alignment slack
+constexpr uint32_t kWaitLimit = 1u << 20;
+constexpr float kLoScale = 2048.f, kLoInv = 1.f / 2048.f;
+#ifndef GODEC_TC_CHUNK
+#define GODEC_TC_CHUNK 2
+#endif
+constexpr int kChunk = GODEC_TC_CHUNK;   // K stages accumulated in TMEM before a drain
+static_assert(kTcSmem <= 232448 - 1024, "shared memory of the tensor-core product");
+
+struct TcArgs {
+  int64_t rows, K;
+  int RP;                   // columns kept (multiple of 8)
+  int64_t ks, S;            // K stages per tile, total stages
+  int G;                    // CTAs
+  int maxseg;
+  float* part;              // tiles x maxseg x BM x RP
+  unsigned* counters;       // tiles
+  float* out;               // rows x RP (nullable)
+  __half* bt2;              // 2 RP x ldb split transposed output (nullable)
+  int64_t ldb;
+  const float* Tn0;
+  const float* Tn1;
+  const float* cscale;      // per-column output factor 1 / s_B (nullable: 1)
+  const float* zscale;      // {s_Z, 1 / s_Z} (nullable: 1)
+  int prescaled;            // Zsrc holds x s_Z already (s_Z then only undone in the epilogue)
+  void* gram_part;
+  int gram_mode;
+  Ctl* ctl;
+};
+
+__device__ __forceinline__ int64_t cta_of(int64_t g, int64_t S, int G) { return ((g + 1) * (int64_t)G - 1) / S; }
+
+__device__ __forceinline__ void note_timeout(Ctl* ctl, volatile int* s_err) {
+  *s_err = 1;
+  if (ctl) {
+    ctl->timeout = 1;
+    ctl->abort = 1;
+  }
+}
+
+// cvt.rn.f16x2: first source goes to the upper half, so element k sits in bits 0-15.
+__device__ __forceinline__ uint32_t pack_h2(float even, float odd) {
+  uint32_t d;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(odd), "f"(even));
+  return d;
+}
+
+// Completion of tile t by its last segment: Ps is BM x EPI_LD, Ts is RPp x RPp.
+template <int RPp>
+__device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int et, float* Ps, float* Ts) {
+  const int RP = a.RP;
+  const int64_t o0 = t * BM;
+  const int nrow = (int)(a.rows - o0 < BM ? a.rows - o0 : BM);
+  __threadfence();
+  if (et == 0) a.counters[t] = 0u;
+  float y[RPp];
+#pragma unroll
+  for (int l = 0; l < RPp; ++l) y[l] = 0.f;
+  for (int sl = 0; sl < nseg; ++sl) {
+    const float4* p = reinterpret_cast<const float4*>(a.part + ((t * a.maxseg + sl) * BM + et) * (int64_t)RP);
+#pragma unroll
+    for (int l = 0; l < RPp; l += 4)
+      if (l < RP) {
+        const float4 v = __ldcg(p + l / 4);
+        y[l] += v.x;
+        y[l + 1] += v.y;
+        y[l + 2] += v.z;
+        y[l + 3] += v.w;
+      }
+  }
+  {
+    const float zi = a.zscale ? a.zscale[1] : 1.f;
+#pragma unroll
+    for (int l = 0; l < RPp; ++l)
+      if (l < RP) y[l] *= (a.cscale ? a.cscale[l] : 1.f) * zi;
+  }
+  const float* Tn = (a.ctl && a.ctl->slot_parity) ? a.Tn1 : a.Tn0;
+  if (Tn) {
+    // y <- y T, with y staged through this thread's row of Ps (keeps one row in registers)
+    for (int e = et; e < RP * RP; e += BM) Ts[(e / RP) * RPp + e % RP] = Tn[e];
+#pragma unroll
+    for (int l = 0; l < RPp; ++l)
+      if (l < RP) Ps[et * EPI_LD + l] = y[l];
+    named_sync(1, BM);
+#pragma unroll
+    for (int l = 0; l < RPp; ++l) y[l] = 0.f;
+    for (int c = 0; c < RP; ++c) {
+      const float yc = Ps[et * EPI_LD + c];
+      const float4* tr = reinterpret_cast<const float4*>(Ts + c * RPp);
+#pragma unroll
+      for (int l = 0; l < RPp; l += 4)
+        if (l < RP) {
+          const float4 tv = tr[l / 4];
+          y[l] = fmaf(yc, tv.x, y[l]);
+          y[l + 1] = fmaf(yc, tv.y, y[l + 1]);
+          y[l + 2] = fmaf(yc, tv.z, y[l + 2]);
+          y[l + 3] = fmaf(yc, tv.w, y[l + 3]);
+        }
+    }
+  }
+  if (et >= nrow) {
+#pragma unroll
+    for (int l = 0; l < RPp; ++l) y[l] = 0.f;
+  }
+  if (a.out && et < nrow) {
+    float* o = a.out + (o0 + et) * (int64_t)RP;
+#pragma unroll
+    for (int l = 0; l < RPp; l += 4)
+      if (l < RP) *reinterpret_cast<float4*>(o + l) = make_float4(y[l], y[l + 1], y[l + 2], y[l + 3]);
+  }
+  if (a.bt2 && et < nrow) {
+#pragma unroll
+    for (int l = 0; l < RPp; ++l) {
+      const float v = (l < RP) ? y[l] * kSkinnyScale : 0.f;
+      const __half c1 = __float2half_rn(v);
+      if (l < RP) {
+        a.bt2[(int64_t)l * a.ldb + o0 + et] = c1;
+        a.bt2[(int64_t)(RP + l) * a.ldb + o0 + et] = __float2half_rn((v - __half2float(c1)) * kLoScale);
+      }
+    }
+  }
+  if (a.gram_mode) {
+#pragma unroll
+    for (int l = 0; l < RPp; ++l)
+      if (l < RP) Ps[et * EPI_LD + l] = y[l];
+    named_sync(1, BM);
+    const int npair = RP * RP;
+    for (int e = et; e < npair; e += BM) {
+      const int i = e / RP, c = e % RP;
+      if (a.gram_mode == 1) {
+        float g0 = 0.f, g1 = 0.f;
+        int r = 0;
+        for (; r + 1 < nrow; r += 2) {
+          g0 = fmaf(Ps[r * EPI_LD + i], Ps[r * EPI_LD + c], g0);
+          g1 = fmaf(Ps[(r + 1) * EPI_LD + i], Ps[(r + 1) * EPI_LD + c], g1);
+        }
+        if (r < nrow) g0 = fmaf(Ps[r * EPI_LD + i], Ps[r * EPI_LD + c], g0);
+        reinterpret_cast<float*>(a.gram_part)[t * npair + e] = g0 + g1;
+      } else {
+        float hi = 0.f, lo = 0.f;
+        for (int r = 0; r < nrow; ++r) {
+          const float x = Ps[r * EPI_LD + i], z = Ps[r * EPI_LD + c];
+          const float p = x * z, pe = fmaf(x, z, -p);
+          const float s = hi + p, bb = s - hi;
+          lo += ((hi - (s - bb)) + (p - bb)) + pe;
+          hi = s;
+        }
+        reinterpret_cast<double*>(a.gram_part)[t * npair + e] = (double)hi + (double)lo;
+      }
+    }
+  }
+  named_sync(1, BM);
+}
+
+// One TMA producer loop over this CTA's stages [g0, g1).  Zsrc stages are two
+// 32-column float32 boxes (the second is skipped when it starts at or beyond K);
+// skinny-operand stages are one 64-column float16 box.
+template <bool IS_A>
+__device__ void produce(const CUtensorMap* map, unsigned char* ring, int nslot, size_t slot_bytes, uint32_t box_bytes,
+                        uint64_t* fullb, uint64_t* emptyb, int64_t g0, int64_t g1, int64_t ks, int64_t K, Ctl* ctl,
+                        volatile int* s_err) {
+  int64_t t = g0 / ks, kst = g0 % ks;
+  int s = 0;
+  uint32_t ph = 0;
+  int64_t issued = 0;
+  for (int64_t g = g0; g < g1 && !*s_err; ++g) {
+    if (!mbar_wait(&emptyb[s], ph ^ 1u, kWaitLimit)) { note_timeout(ctl, s_err); break; }
+    unsigned char* dst = ring + (size_t)s * slot_bytes;
+    if (IS_A) {
+      const bool two = kst * BK + 32 < K;
+      mbar_expect_tx(&fullb[s], two ? 2 * box_bytes : box_bytes);
+      tma_load_2d(dst, map, &fullb[s], (int)(kst * BK), (int)(t * BM));
+      if (two) tma_load_2d(dst + box_bytes, map, &fullb[s], (int)(kst * BK + 32), (int)(t * BM));
+    } else {
+      mbar_expect_tx(&fullb[s], box_bytes);
+      tma_load_2d(dst, map, &fullb[s], (int)(kst * BK), 0);
+    }
+    ++issued;
+    if (++kst == ks) { kst = 0; ++t; }
+    if (++s == nslot) { s = 0; ph ^= 1u; }
+  }
+  // Every copy issued has landed before the CTA may exit (immediate in the normal case).
+  for (int64_t j = (issued > nslot ? issued - nslot : 0); j < issued; ++j)
+    if (!mbar_wait(&fullb[(int)(j % nslot)], (uint32_t)((j / nslot) & 1), kWaitLimit)) note_timeout(ctl, s_err);
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the warp follows (__syncwarp orders the
+// other lanes' later accesses after lane 0's acquire).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait(bar, parity, kWaitLimit) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+template <int RPp, bool PRESCALED>
+__global__ void __launch_bounds__(kThreads, 1)
+k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  Ctl* ctl = a.ctl;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm + kOffA;
+  unsigned char* sB = sm + kOffB;
+  float* Ps = reinterpret_cast<float*>(sm + kOffEpi);
+  float* Ts = Ps + BM * EPI_LD;
+  __shared__ uint64_t afull[NA], aempty[NA], bfull[NS], tfull[NS], sfree[NS];
+  __shared__ uint64_t accfull[2], accempty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_err;   // set by any role that gives up; every loop polls it
+  __shared__ int s_stop, s_last;   // epilogue-wide decisions, written between two named barriers
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x;
+  const int64_t S = a.S, ks = a.ks, K = a.K;
+  const int G = a.G;
+  const int64_t g0 = (int64_t)c * S / G, g1 = (int64_t)(c + 1) * S / G;
+  if (tid == 0) {
+    for (int s = 0; s < NA; ++s) {
+      mbar_init(&afull[s], 1);
+      mbar_init(&aempty[s], kConvWarps);
+    }
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&bfull[s], 1);
+      mbar_init(&tfull[s], kConvWarps);
+      mbar_init(&sfree[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 4);
+    }
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+    // Iteration already abandoned, or Z outgrew its scale in the last S-step (the caller
+    // rescales it): do nothing, and make the rest of the iteration skip too.
+    s_err = (ctl && (ctl->abort || ctl->range_err)) ? 2 : 0;
+    if (ctl && ctl->range_err) ctl->abort = 1;
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: Zsrc tiles ----------------
+    if (lane == 0)
+      produce<true>(&mapA, sA, NA, kStageA, (uint32_t)kBoxA, afull, aempty, g0, g1, ks, K, ctl, &s_err);
+  } else if (warp == 14) {
+    // ---------------- TMA producer: skinny-operand tiles ----------------
+    if (lane == 0)
+      produce<false>(&mapB, sB, NS, kStageB, (uint32_t)(2 * a.RP * BK * 2), bfull, sfree, g0, g1, ks, K, ctl,
+                     &s_err);
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const int RP = a.RP;
+      const uint32_t id_hi = idesc_f16(BM, 2 * RP), id_lo = idesc_f16(BM, RPp);   // RPp: RP rounded up to 16
+      int ch = 0;   // chunks issued by this CTA
+      int st = 0;
+      uint32_t ph = 0;
+      int64_t kst = g0 % ks;
+      int64_t g = g0;
+      while (g < g1 && !s_err) {
+        // this chunk: up to kChunk stages, not past the end of the tile or of the range
+        int64_t n = ks - kst;
+        if (n > kChunk) n = kChunk;
+        if (n > g1 - g) n = g1 - g;
+        const int b = ch & 1;
+        if (!mbar_wait(&accempty[b], (uint32_t)(((ch >> 1) & 1) ^ 1), kWaitLimit)) { note_timeout(ctl, &s_err); break; }
+        tc_fence_after();
+        const uint32_t dcol = tbase + (uint32_t)(b * 128);
+        uint32_t acc = 0;
+        for (int64_t e = 0; e < n; ++e) {
+          if (!mbar_wait(&tfull[st], ph, kWaitLimit)) { note_timeout(ctl, &s_err); break; }
+          tc_fence_after();
+          const uint64_t db = sdesc_k128(sB + (size_t)st * kStageB);
+          const uint32_t ah = tbase + kTA0 + (uint32_t)st * kTASlot, al = ah + 32;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 16 * 2) >> 4);   // 32 bytes per 16-wide K step
+            mma_f16_ta(dcol, ah + kk * 8, db + off, id_hi, acc);
+            mma_f16_ta(dcol + RP, al + kk * 8, db + off, id_lo, 1u);
+            acc = 1u;
+          }
+          mma_commit(&sfree[st]);
+          if (++st == NS) { st = 0; ph ^= 1u; }
+        }
+        if (s_err) break;
+        mma_commit(&accfull[b]);
+        ++ch;
+        g += n;
+        kst += n;
+        if (kst == ks) kst = 0;
+      }
+      mma_commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0, kWaitLimit)) note_timeout(ctl, &s_err);
+    }
+  } else if (warp < 2 + kConvWarps) {
+    // ---------------- converters: Zsrc tile -> TMEM as packed (h1, h2) ----------------
+    const int q = (warp - 2) >> 2;              // 32-column half of the tile handled by this warp
+    const int row = (warp & 3) * 32 + lane;     // this warp may only touch its TMEM lane quarter
+    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+    const float zs = (!PRESCALED && a.zscale) ? a.zscale[0] : 1.f;
+    int sa = 0, st = 0;
+    uint32_t pha = 0, ph = 0;
+    int64_t kst = g0 % ks;
+    for (int64_t g = g0; g < g1; ++g) {
+      if (__any_sync(0xffffffffu, s_err != 0)) break;
+      if (!warp_wait(&afull[sa], pha, lane)) {
+        if (lane == 0) note_timeout(ctl, &s_err);
+        break;
+      }
+      const bool present = q == 0 || kst * BK + 32 < K;   // the second box is not loaded past K
+      // row `row` of a 32-column box: 8 chunks of 16 bytes, chunk u stored at u ^ (row & 7)
+      const float4* src = reinterpret_cast<const float4*>(sA + (size_t)sa * kStageA + q * kBoxA + row * 128);
+      float4 xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = present ? src[u ^ (row & 7)] : make_float4(0.f, 0.f, 0.f, 0.f);
+      uint32_t h[16], l2[16];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 x = xv[u];
+        float xs[4] = {x.x, x.y, x.z, x.w}, hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (!PRESCALED) xs[e] *= zs;
+          hi[e] = __uint_as_float(__float_as_uint(xs[e]) & 0xFFFFE000u);
+          lo[e] = (xs[e] - hi[e]) * kLoScale;
+        }
+        h[2 * u] = pack_h2(hi[0], hi[1]);
+        h[2 * u + 1] = pack_h2(hi[2], hi[3]);
+        l2[2 * u] = pack_h2(lo[0], lo[1]);
+        l2[2 * u + 1] = pack_h2(lo[2], lo[3]);
+      }
+      // every lane has consumed its loads (the packed words depend on them): the slot
+      // may be refilled
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&aempty[sa]);
+      if (++sa == NA) { sa = 0; pha ^= 1u; }
+      if (!warp_wait(&sfree[st], ph ^ 1u, lane)) {
+        if (lane == 0) note_timeout(ctl, &s_err);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ta = tbase + kTA0 + (uint32_t)st * kTASlot + tlane + (uint32_t)(q * 16);
+      tmem_st16(ta, h);
+      tmem_st16(ta + 32, l2);
+      tmem_wait_st();
+      tc_fence_before();
+      // the skinny tile of this stage has landed too: the MMA issuer waits on tfull alone
+      if (!warp_wait(&bfull[st], ph, lane)) {
+        if (lane == 0) note_timeout(ctl, &s_err);
+        break;
+      }
+      if (lane == 0) mbar_arrive(&tfull[st]);
+      if (++st == NS) { st = 0; ph ^= 1u; }
+      if (++kst == ks) kst = 0;
+    }
+  } else {
+    // ---------------- epilogue: TMEM -> running sums -> partial slot, tile completion ----------------
+    // The four warps take every decision together (flag written between two named
+    // barriers), so no warp can leave while the others wait at a barrier.
+    const int et = tid - 32 * (2 + kConvWarps);
+    const int q4 = warp & 3;                 // TMEM lane quarter this warp may access
+    const int row = q4 * 32 + lane;          // tile row held by this thread
+    const uint32_t tlane = (uint32_t)(q4 * 32) << 16;
+    int ch = 0;
+    int64_t g = g0;
+    for (;;) {
+      named_sync(1, BM);
+      if (et == 0) s_stop = (g >= g1) || s_err;
+      named_sync(1, BM);
+      if (s_stop) break;
+      const int64_t t = g / ks;
+      const int64_t tend = ((t + 1) * ks < g1) ? (t + 1) * ks : g1;
+      float y[RPp];
+#pragma unroll
+      for (int l = 0; l < RPp; ++l) y[l] = 0.f;
+      bool failed = false;
+      for (; g < tend; g = (g + kChunk < tend) ? g + kChunk : tend, ++ch) {
+        if (failed) continue;                // keep the loop count; nothing more to read
+        const int b = ch & 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&accfull[b], (uint32_t)((ch >> 1) & 1), kWaitLimit))) {
+          if (lane == 0) note_timeout(ctl, &s_err);
+          failed = true;
+          continue;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tbase + (uint32_t)(b * 128) + tlane;
+#pragma unroll
+        for (int c0 = 0; c0 < RPp; c0 += 8) {
+          if (c0 < a.RP) {
+            float vh[8], vl[8];
+            tmem_ld8(taddr + c0, vh);
+            tmem_ld8(taddr + a.RP + c0, vl);
+#pragma unroll
+            for (int l = 0; l < 8; ++l) y[c0 + l] += fmaf(vl[l], kLoInv, vh[l]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accempty[b]);
+      }
+      named_sync(1, BM);
+      if (et == 0) s_stop = s_err;
+      named_sync(1, BM);
+      if (s_stop) break;
+      const int64_t c_first = cta_of(t * ks, S, G);
+      const int nseg = (int)(cta_of((t + 1) * ks - 1, S, G) - c_first + 1);
+      const int slot = (int)(c - c_first);
+      float* p = a.part + ((t * a.maxseg + slot) * BM + row) * (int64_t)a.RP;
+#pragma unroll
+      for (int l = 0; l < RPp; l += 4)
+        if (l < a.RP) *reinterpret_cast<float4*>(p + l) = make_float4(y[l], y[l + 1], y[l + 2], y[l + 3]);
+      __threadfence();
+      named_sync(1, BM);
+      if (et == 0) s_last = (atomicAdd(&a.counters[t], 1u) == (unsigned)(nseg - 1));
+      named_sync(1, BM);
+      if (s_last) tile_finish<RPp>(a, t, nseg, et, Ps, Ts);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, kTmemCols);
+  }
+}
+
+// Column c of a row-major rows x RP operand B -> rows c and RP + c of the split
+// transposed float16 operand, scaled by the power of two 2^e_c that brings the column's
+// largest magnitude into [2^9, 2^10); cscale[c] = 2^-e_c undoes it.  One block per column.
+__global__ void k_split_t(const float* __restrict__ B, int64_t rows, int RP, __half* __restrict__ bt2, int64_t ldb,
+                          float* __restrict__ cscale) {
+  const int col = blockIdx.x;
+  __shared__ float red[32];
+  __shared__ float s_scale;
+  float m = 0.f;
+  if (col < RP)
+    for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) m = fmaxf(m, fabsf(B[i * RP + col]));
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float mm = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, red[w]);
+    int e = 0;
+    if (mm > 0.f && isfinite(mm)) {
+      int ex;
+      frexpf(mm, &ex);   // mm in [2^(ex-1), 2^ex)
+      e = 10 - ex;
+      e = e < -120 ? -120 : (e > 120 ? 120 : e);
+    }
+    s_scale = ldexpf(1.f, e);
+    if (col < RP) cscale[col] = ldexpf(1.f, -e);
+  }
+  __syncthreads();
+  const float sc = s_scale;
+  for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+    const float v = (col < RP) ? B[i * RP + col] * sc : 0.f;
+    const __half c1 = __float2half_rn(v);
+    bt2[(int64_t)col * ldb + i] = c1;
+    bt2[(int64_t)(RP + col) * ldb + i] = __float2half_rn((v - __half2float(c1)) * kLoScale);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+// A tensor map over a row-major matrix (rows x cols, row stride ld elements) read in
+// boxes of 128 bytes of columns (32 float32 or 64 float16) x box_rows rows with the
+// 128-byte swizzle.
+static bool make_tmap(void* map, CUtensorMapDataType dt, int esize, const void* base, int64_t rows, int64_t cols,
+                      int64_t ld, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), dt, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+bool make_tmap_f32(void* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  return make_tmap(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rows, cols, ld, box_rows);
+}
+bool make_tmap_f16(void* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  return make_tmap(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, rows, cols, ld, box_rows);
+}
+
+int tc_rpp(int RP) { return (RP + 15) / 16 * 16; }
+
+void launch_split_t(const float* B, int64_t rows, int RP, void* bt2, int64_t ldb, float* cscale, cudaStream_t st) {
+  k_split_t<<<RP, 256, 0, st>>>(B, rows, RP, reinterpret_cast<__half*>(bt2), ldb, cscale);
+}
+
+TcGeom tc_geometry(int64_t rows, int64_t K, int nsm) {
+  TcGeom g;
+  g.tiles = (rows + BM - 1) / BM;
+  g.ks = (K + BK - 1) / BK;
+  g.S = g.tiles * g.ks;
+  g.G = (int)(g.S < nsm ? g.S : nsm);
+  int maxseg = 1;
+  for (int64_t t = 0; t < g.tiles; ++t) {
+    const int64_t cf = ((t * g.ks + 1) * g.G - 1) / g.S;
+    const int64_t cl = (((t + 1) * g.ks) * g.G - 1) / g.S;
+    if (cl - cf + 1 > maxseg) maxseg = (int)(cl - cf + 1);
+  }
+  g.maxseg = maxseg;
+  return g;
+}
+
+template <int RPp, bool PS>
+static cudaError_t prep_one() {
+  return cudaFuncSetAttribute(k_prod_tc<RPp, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+}
+
+cudaError_t prepare_tc_kernels() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = prep_one<16, false>();
+  if (e == cudaSuccess) e = prep_one<32, false>();
+  if (e == cudaSuccess) e = prep_one<48, false>();
+  if (e == cudaSuccess) e = prep_one<64, false>();
+  if (e == cudaSuccess) e = prep_one<16, true>();
+  if (e == cudaSuccess) e = prep_one<32, true>();
+  if (e == cudaSuccess) e = prep_one<48, true>();
+  if (e == cudaSuccess) e = prep_one<64, true>();
+  return e;
+}
+
+void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
+  TcArgs a;
+  a.rows = l.rows;
+  a.K = l.K;
+  a.RP = l.RP;
+  a.ks = l.geom.ks;
+  a.S = l.geom.S;
+  a.G = l.geom.G;
+  a.maxseg = l.geom.maxseg;
+  a.part = l.part;
+  a.counters = l.counters;
+  a.out = l.out;
+  a.bt2 = reinterpret_cast<__half*>(l.bt2);
+  a.ldb = l.ldb;
+  a.Tn0 = l.Tn[0];
+  a.Tn1 = l.Tn[1];
+  a.cscale = l.cscale;
+  a.zscale = l.zscale;
+  a.gram_part = l.gram_part;
+  a.gram_mode = l.gram_mode;
+  a.ctl = l.ctl;
+  const CUtensorMap& A = *reinterpret_cast<const CUtensorMap*>(l.mapA);
+  const CUtensorMap& B = *reinterpret_cast<const CUtensorMap*>(l.mapB);
+  a.prescaled = l.prescaled;
+  const int rpp = tc_rpp(l.RP);
+  if (l.prescaled) {
+    switch (rpp) {
+      case 16: k_prod_tc<16, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      case 32: k_prod_tc<32, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      case 48: k_prod_tc<48, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      default: k_prod_tc<64, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+    }
+  } else {
+    switch (rpp) {
+      case 16: k_prod_tc<16, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      case 32: k_prod_tc<32, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      case 48: k_prod_tc<48, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      default: k_prod_tc<64, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+    }
+  }
+}
+
+}  // namespace godec

@@ -15,12 +15,13 @@ __global__ void k_fill_zero(uint4* p, size_t n16) {
 
 // 32 x 32 tiles through shared memory (padded against bank conflicts)
 __global__ void k_transpose(const float* __restrict__ src, int64_t m, int64_t n, int64_t lds,
-                            float* __restrict__ dst, int64_t ldd) {
+                            float* __restrict__ dst, int64_t ldd, const float* __restrict__ scale) {
   __shared__ float t[32][33];
   const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const float sc = scale ? scale[0] : 1.f;
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int64_t i = i0 + k, j = j0 + threadIdx.x;
-    t[k][threadIdx.x] = (i < m && j < n) ? src[i * lds + j] : 0.f;
+    t[k][threadIdx.x] = (i < m && j < n) ? src[i * lds + j] * sc : 0.f;
   }
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += 8) {
@@ -66,6 +67,40 @@ __global__ void k_sumsq(const float* X, int64_t m, int64_t n, int64_t ldx, doubl
 
 // ---- LSD radix sort, 4-bit digits, items owned contiguously by threads (stable) ------
 constexpr int SORT_THREADS = 256, SORT_ITEMS = 16, SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+__global__ void k_scale_copy(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
+                             const float* scale) {
+  const float sc = scale[0];
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) dst[r * ldd + c] = src[r * lds + c] * sc;
+}
+
+__global__ void k_scale_update(float* zscale, const float* f) {
+  zscale[0] *= f[0];
+  zscale[1] *= f[1];
+}
+
+// max |Z| over the matrix (non-negative floats order like their bit patterns).
+__global__ void k_maxabs(const float* Z, int64_t rows, int64_t cols, int64_t ld, unsigned* out) {
+  float m = 0.f;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) m = fmaxf(m, fabsf(Z[r * ld + c]));
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+__global__ void k_make_zscale(const unsigned* mx, float* zscale) {
+  const float m = __uint_as_float(*mx);
+  int e = 0;
+  if (m > 0.f && isfinite(m)) {
+    int ex;
+    frexpf(m, &ex);   // m in [2^(ex-1), 2^ex)
+    e = 13 - ex;
+    e = e < -120 ? -120 : (e > 120 ? 120 : e);
+  }
+  zscale[0] = ldexpf(1.f, e);
+  zscale[1] = ldexpf(1.f, -e);
+}
 
 __global__ void k_sort_hist(const long long* keys, long long n, int shift, unsigned* cnt, int nblk) {
   __shared__ unsigned h[16];
@@ -173,9 +208,9 @@ void launch_fill_zero(void* p, size_t bytes, cudaStream_t st) {
 }
 
 void launch_transpose(const float* src, int64_t m, int64_t n, int64_t lds, float* dst, int64_t ldd,
-                      cudaStream_t st) {
+                      cudaStream_t st, const float* scale) {
   dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
-  k_transpose<<<grid, dim3(32, 8), 0, st>>>(src, m, n, lds, dst, ldd);
+  k_transpose<<<grid, dim3(32, 8), 0, st>>>(src, m, n, lds, dst, ldd, scale);
 }
 
 void launch_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, float* dst, int RP,
@@ -200,6 +235,24 @@ size_t sort_coo_scratch(long long nnz) {
   long long nblk = (nnz + SORT_TILE - 1) / SORT_TILE;
   return (size_t)nnz * (sizeof(long long) + sizeof(float)) + (size_t)(16 * nblk + 16) * sizeof(unsigned) + 256;
 }
+
+void launch_zscale(const float* Z, int64_t rows, int64_t cols, int64_t ld, unsigned* zmax, float* zscale, int nsm,
+                   cudaStream_t st) {
+  cudaMemsetAsync(zmax, 0, sizeof(unsigned), st);
+  int64_t grid = 4LL * nsm;
+  if (grid > rows) grid = rows;
+  k_maxabs<<<(unsigned)grid, 256, 0, st>>>(Z, rows, cols, ld, zmax);
+  k_make_zscale<<<1, 1, 0, st>>>(zmax, zscale);
+}
+
+void launch_scale_copy(const float* src, int64_t rows, int64_t cols, int64_t lds, float* dst, int64_t ldd,
+                       const float* scale, int nsm, cudaStream_t st) {
+  int64_t grid = 4LL * nsm;
+  if (grid > rows) grid = rows;
+  k_scale_copy<<<(unsigned)grid, 256, 0, st>>>(src, rows, cols, lds, dst, ldd, scale);
+}
+
+void launch_scale_update(float* zscale, const float* f, cudaStream_t st) { k_scale_update<<<1, 1, 0, st>>>(zscale, f); }
 
 void launch_sort_coo(long long* idx, float* val, long long nnz, void* scratch, size_t scratch_bytes,
                      int idx_bits, cudaStream_t st) {
