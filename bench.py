@@ -117,16 +117,17 @@ def peaks():
 
 
 def pass_traffic():
-    """DRAM bytes per launch of the streaming product from a committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+    """DRAM bytes per launch of the streaming product (dram__bytes_read.sum +
+    dram__bytes_write.sum of one ncu capture, scaled to the benchmark's size) from the
+    committed summary, if it was taken on the current kernel source; else None."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1309_0302_gb300", "csrc", "k_stream.cu")
-    p = os.path.join(ROOT, "profiles", "product_pass_traffic.json")
+    src = os.path.join(ROOT, "paper_1309_0302_gb300", "csrc", "k_tc.cu")
+    p = os.path.join(ROOT, "profiles", "k_prod_tc_traffic.txt")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
+    kv = dict(line.strip().split("=", 1) for line in open(p) if "=" in line and not line.startswith("#"))
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return d.get("dram_bytes_per_launch") if d.get("source_sha") == h else None
+    return float(kv["dram_bytes_per_launch"]) if kv.get("source_sha") == h else None
 
 
 def oracle_rate(iters: int, seed: int = 1309):

@@ -181,9 +181,12 @@ godec_status godec_run_host(const godec_params* params, const float* X_host,
  *   godec_mul_ZB : Y = Z B,    Z m x n (row stride ldz), B n x r, Y m x r
  *   godec_mul_ZtC: W = Z^T C,  Z m x n (row stride ldz), C m x r, W n x r
  * All pointers are device float32, row-major with row stride r for B, C, Y,
- * W.  1 <= r <= GODEC_MAX_RANK, ldz >= n, ldz*4 a multiple of 16 bytes.
- * The call allocates its split-K scratch on `stream` and frees it before
- * returning (stream-ordered), and does not synchronise.
+ * W.  1 <= r <= GODEC_MAX_RANK, ldz >= n, ldz*4 a multiple of 16 bytes, Z
+ * 16-byte aligned.  Computed on the tensor cores with the two-term float16
+ * split of both operands (float32-level accuracy, about 1e-7 relative); one
+ * extra read of Z finds the power-of-two scale that keeps it in float16 range.
+ * The call allocates its scratch on `stream` and frees it before returning
+ * (stream-ordered), and does not synchronise.
  */
 godec_status godec_mul_ZB(const float* Z, int64_t m, int64_t n, int64_t ldz,
                           const float* B, int32_t r, float* Y, void* stream);
@@ -228,7 +231,8 @@ godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t 
  * memory at start-up and forbids later allocations, or a latency-critical loop
  * that cannot afford an allocation's synchronisation).  The paper has no
  * counterpart; this is a library convenience.
- *   Same arguments, layout and results as godec_mul_ZB.
+ *   Same arguments and layout as godec_mul_ZB; computed with float32 FMAs on
+ *   the CUDA cores (results agree with godec_mul_ZB to float32 rounding).
  *   Scratch: a fixed 32 MiB device array inside the library, reserved on every
  *   GPU that loads it until the process exits; no allocation or free happens in
  *   the call.  Problems whose scratch (padded B, split-K partials, padded Y)
