@@ -242,6 +242,7 @@ def run_gb300(args, ws, rank, local):
         "kernel_ms_per_iter": {k: v / args.steps for k, v in prof["ms"].items()},
         "clocks": ck,
         "gpu_launches": int(info["launches_per_iter"]) * args.steps,
+        "path": {k: info[k] for k in ("svd_sweeps", "select_passes", "exact_iters", "rank_drops", "chol_shifts")},
     }
     if not args.no_e2e:
         line["e2e"] = e2e(args, d)

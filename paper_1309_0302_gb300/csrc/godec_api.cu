@@ -28,6 +28,10 @@ using namespace godec;
 namespace {
 constexpr int kEvents = 160;
 constexpr float kAlarmRatio = 30.f;   // lagged normaliser: max/min Cholesky diagonal of Q~
+// Fast path, Q2 and Q1: one CholeskyQR pass on the lagged-normalised product; a
+// diagonal spread of its factor above this ratio (condition number of the product)
+// sends the iteration to the exact path instead of a second pass.
+constexpr float kCqr1Ratio = 1.5f;
 }
 
 struct godec_ctx {
@@ -75,10 +79,10 @@ struct godec_ctx {
   size_t gpart_stride = 0;
   double* g64 = nullptr;               // per product reduced Gram, + 2 for the CholeskyQR2 rounds
   float* gscr = nullptr;               // Gram partials of the second CholeskyQR2 round
-  float* Rtmp = nullptr;               // exact path: factor of each product
+  float* Rtmp = nullptr;               // exact path: factor of each product and its inverse (2 rr each)
   float* Rslot = nullptr;              // [2][nprod] lagged factors
   float* Tslot = nullptr;              // [2][nprod] their inverses
-  float* Rfin = nullptr;               // Ra, Rb of Q2 and of Q1
+  float* Rfin = nullptr;               // Ra, Rb of Q2 and of Q1, each followed by its inverse (2 rr each)
   float* Pi = nullptr;                 // factors applied in the last chain (normalised)
   float* Vprev = nullptr;              // warm start of the core SVD
   Ctl* ctl = nullptr;
@@ -228,11 +232,15 @@ void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out
   PROF(c, 1, s, launch_gram_sum(part, dbl, nblk, c->RP, out, c->ctl, s));
 }
 
-void chol(godec_ctx* c, const double* g, float* R) { PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, c->ctl, c->st)); }
+// R with Rᵀ R = Gram, and T = R^{-1} stored right after R.
+void chol(godec_ctx* c, const double* g, float* R, float alarm_ratio = 0.f) {
+  PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, R + (size_t)c->RP * c->RP, c->ctl, c->st, alarm_ratio));
+}
+const float* inv_of(godec_ctx* c, const float* R) { return R + (size_t)c->RP * c->RP; }
 
-void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const float* T1, int solve, float* Q,
-           float* gram, void* bt2out = nullptr) {
-  PROF(c, 3, c->st, launch_apply(P, rows, c->RP, T0, T1, solve, Q, gram, c->ctl, c->st, bt2out, c->ldb, c->RPp));
+void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const float* T1, float* Q, float* gram,
+           void* bt2out = nullptr) {
+  PROF(c, 3, c->st, launch_apply(P, rows, c->RP, T0, T1, Q, gram, c->ctl, c->st, bt2out, c->ldb));
 }
 
 // Exact CholeskyQR2 of c->P (rows x RP) with the round-1 Gram g1: Q = P Ra^{-1} Rb^{-1},
@@ -240,10 +248,10 @@ void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const fl
 void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* Rb, float* fin, double* g2,
                 void* bt2out) {
   chol(c, g1, Ra);
-  apply(c, c->P, rows, Ra, Ra, 1, c->P, c->gscr);
+  apply(c, c->P, rows, inv_of(c, Ra), inv_of(c, Ra), c->P, c->gscr);
   gram_sum(c, c->gscr, 0, apply_blocks(rows), g2, c->st);
   chol(c, g2, Rb);
-  apply(c, c->P, rows, Rb, Rb, 1, fin, nullptr, bt2out);
+  apply(c, c->P, rows, inv_of(c, Rb), inv_of(c, Rb), fin, nullptr, bt2out);
 }
 
 void slot(godec_ctx* c, SlotLaunch& sl) {
@@ -287,11 +295,11 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       PROF(c, 5, c->side_st,
            launch_rank(g64(c, i), c->r, RP, c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4, c->ctl, c->side_st));
       if (i == last) {   // q = 0: this product is also the last one
-        final_cqr2(c, rows, g64(c, i), c->Rfin + 2 * rr, c->Rfin + 3 * rr, c->Q1, g64(c, nprod + 1), nullptr);
+        final_cqr2(c, rows, g64(c, i), c->Rfin + 4 * rr, c->Rfin + 6 * rr, c->Q1, g64(c, nprod + 1), nullptr);
         continue;
       }
       if (fast) {
-        apply(c, c->P, rows, sT(0, i), sT(1, i), 0, nullptr, nullptr, nextB);
+        apply(c, c->P, rows, sT(0, i), sT(1, i), nullptr, nullptr, nextB);
         sl.fast = 1;
         sl.g64 = g64(c, i);
         sl.g_is_p = 1;
@@ -300,9 +308,9 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
         sl.T_app[0] = sT(0, i);
         sl.T_app[1] = sT(1, i);
       } else {
-        float* Rt = c->Rtmp + (size_t)i * rr;
+        float* Rt = c->Rtmp + (size_t)i * 2 * rr;
         chol(c, g64(c, i), Rt);
-        apply(c, c->P, rows, Rt, Rt, 1, nullptr, nullptr, nextB);
+        apply(c, c->P, rows, inv_of(c, Rt), inv_of(c, Rt), nullptr, nullptr, nextB);
         fork_side(c);
         sl.fast = 0;
         sl.R_app[0] = sl.R_app[1] = Rt;
@@ -312,10 +320,18 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
     } else if (i == i_q2 || i == last) {
       prod(c, i, c->P, false, fast ? sT(0, i) : nullptr, fast ? sT(1, i) : nullptr, 1);
       gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
-      float* Ra = c->Rfin + (i == i_q2 ? 0 : 2) * rr;
-      float* Rb = Ra + rr;
+      float* Ra = c->Rfin + (i == i_q2 ? 0 : 4) * rr;
+      float* Rb = Ra + 2 * rr;
       float* fin = (i == i_q2) ? c->Q2 : c->Q1;
-      final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)), i == i_q2 ? nextB : nullptr);
+      if (fast) {
+        // the lagged normaliser left P almost orthonormal: one CholeskyQR pass
+        chol(c, g64(c, i), Ra, kCqr1Ratio);
+        apply(c, c->P, rows, inv_of(c, Ra), inv_of(c, Ra), fin, nullptr, i == i_q2 ? nextB : nullptr);
+        Rb = nullptr;
+      } else {
+        final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)),
+                   i == i_q2 ? nextB : nullptr);
+      }
       fork_side(c);
       sl.fast = 0;
       if (fast) {
@@ -327,7 +343,7 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
         }
       }
       sl.L1 = Ra;
-      sl.L2 = Rb;
+      sl.L2 = Rb;   // null after a single pass
       sl.pi_mode = 0;
       slot(c, sl);
     } else {
@@ -340,11 +356,11 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
         sl.R_app[0] = sR(0, i);
         sl.R_app[1] = sR(1, i);
       } else {
-        float* Rt = c->Rtmp + (size_t)i * rr;
+        float* Rt = c->Rtmp + (size_t)i * 2 * rr;
         prod(c, i, c->P, false, nullptr, nullptr, 1);
         gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
         chol(c, g64(c, i), Rt);
-        apply(c, c->P, rows, Rt, Rt, 1, nullptr, nullptr, nextB);
+        apply(c, c->P, rows, inv_of(c, Rt), inv_of(c, Rt), nullptr, nullptr, nextB);
         fork_side(c);
         sl.fast = 0;
         sl.R_app[0] = sl.R_app[1] = Rt;
@@ -356,10 +372,10 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
   join_side(c);
   // r x r core, SVD and singular-value root, then L = (Q1 Um) diag(sigma) (Q2 Vm)^T
   PROF(c, 6, c->st,
-       launch_svd(c->Rfin + 2 * rr, c->Rfin + 3 * rr, rapp_last[0], rapp_last[1], have_pi ? c->Pi : nullptr,
+       launch_svd(c->Rfin + 4 * rr, (fast && last != i_rank) ? nullptr : c->Rfin + 6 * rr, rapp_last[0], rapp_last[1], have_pi ? c->Pi : nullptr,
                   c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st));
-  apply(c, c->Q1, m, c->Um, c->Um, 0, c->U, nullptr);
-  apply(c, c->Q2, n, c->Vm, c->Vm, 0, c->V, nullptr);
+  apply(c, c->Q1, m, c->Um, c->Um, c->U, nullptr);
+  apply(c, c->Q2, n, c->Vm, c->Vm, c->V, nullptr);
 }
 
 // S-step of one iteration (Algorithm 1 line 9) on the current L factors; r = 0 means L = 0.
@@ -759,10 +775,10 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(dalloc(&c->gparts, c->gpart_stride * np));
   CKI(dalloc(&c->g64, (size_t)(np + 2) * rr));
   CKI(dalloc(&c->gscr, (size_t)apply_blocks(mx) * rr));
-  CKI(dalloc(&c->Rtmp, (size_t)np * rr));
+  CKI(dalloc(&c->Rtmp, (size_t)np * 2 * rr));
   CKI(dalloc(&c->Rslot, (size_t)2 * np * rr));
   CKI(dalloc(&c->Tslot, (size_t)2 * np * rr));
-  CKI(dalloc(&c->Rfin, 4 * rr));
+  CKI(dalloc(&c->Rfin, 8 * rr));
   CKI(dalloc(&c->Pi, rr));
   CKI(dalloc(&c->Vprev, rr));
   CKI(dalloc(reinterpret_cast<char**>(&c->ctl), sizeof(Ctl)));

@@ -120,15 +120,13 @@ void prod_geometry(int64_t rows, int64_t K, int nsm, int* splits, int64_t* kchun
 int64_t prod_tiles(int64_t rows);
 cudaError_t prepare_stream_kernels();
 
-// Q = P T (solve = 0) or Q = P T^{-1} with T upper triangular (solve = 1, forward
-// substitution); T is T0 or T1 by the slot parity in ctl (T0 without ctl); optional
-// float Gram partials of Q per apply_blocks() row block.  P and Q may alias; Q may be
-// null.  With bt2 set, also writes the float16 split transposed operand of the
-// tensor-core product, [c1^T; c2^T] (2 RP x ldb halves) with
-// Q kSkinnyScale = c1 + 2^-11 c2.
-void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, int solve, float* Q,
-                  float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2 = nullptr, int64_t ldb = 0,
-                  int RPp = 0);
+// Q = P T with T dense RP x RP (T0 or T1 by the slot parity in ctl; T0 without ctl),
+// optional float Gram partials of Q per apply_blocks() row block.  P and Q may alias;
+// Q may be null.  With bt2 set, also writes the float16 split transposed operand of the
+// tensor-core product, [c1^T; c2^T] (2 RP x ldb halves) with Q kSkinnyScale =
+// c1 + 2^-11 c2.
+void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, float* Q,
+                  float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2 = nullptr, int64_t ldb = 0);
 
 // Tensor-core streaming product (k_tc.cu).
 struct TcGeom {
@@ -178,7 +176,9 @@ int64_t apply_blocks(int64_t rows);
 // r x r kernels (k_small.cu).
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
                      cudaStream_t st);
-void launch_chol(const double* g64, int r, int RP, float* R, Ctl* ctl, cudaStream_t st);
+// R (upper, Rᵀ R = Gram) and T = R^{-1}, both RP x RP.
+void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
+                 float alarm_ratio = 0.f);
 struct SlotLaunch {
   const double* g64 = nullptr;
   int g_is_p = 0;

@@ -21,23 +21,34 @@ namespace {
 constexpr int SMALL_THREADS = 256;   // 16 x 16 threads, each owning a 4 x 4 block of 64 x 64
 constexpr int LD = kMaxRP + 1;
 
-// ---- Gram sums over row tiles: one entry per thread, many blocks ---------------------
+// ---- Gram sums over row tiles --------------------------------------------------------
+// Block = 32 entries x 8 tile strides: each thread sums every 8th partial of one entry
+// (independent loads in flight), the 8 partial sums are added in a fixed order.
+constexpr int GS_ENT = 32, GS_SPLIT = 8;
 template <typename T>
-__global__ void k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out,
-                           const Ctl* ctl) {
+__global__ void __launch_bounds__(GS_ENT * GS_SPLIT)
+k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out, const Ctl* ctl) {
   if (ctl && ctl->abort) return;
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= npair) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int64_t b = 0;
-  for (; b + 4 <= nblk; b += 4) {
-    s0 += (double)part[(b + 0) * npair + e];
-    s1 += (double)part[(b + 1) * npair + e];
-    s2 += (double)part[(b + 2) * npair + e];
-    s3 += (double)part[(b + 3) * npair + e];
+  __shared__ double red[GS_SPLIT][GS_ENT];
+  const int lane = threadIdx.x % GS_ENT, sp = threadIdx.x / GS_ENT;
+  const int e = blockIdx.x * GS_ENT + lane;
+  double s0 = 0.0, s1 = 0.0;
+  if (e < npair) {
+    int64_t b = sp;
+    for (; b + GS_SPLIT < nblk; b += 2 * GS_SPLIT) {
+      s0 += (double)part[b * npair + e];
+      s1 += (double)part[(b + GS_SPLIT) * npair + e];
+    }
+    if (b < nblk) s0 += (double)part[b * npair + e];
   }
-  for (; b < nblk; ++b) s0 += (double)part[b * npair + e];
-  out[e] = (s0 + s1) + (s2 + s3);
+  red[sp][lane] = s0 + s1;
+  __syncthreads();
+  if (sp == 0 && e < npair) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < GS_SPLIT; ++k) t += red[k][lane];
+    out[e] = t;
+  }
 }
 
 // ---- block helpers on 64 x 64 (padded RP x RP) matrices in shared memory -----------
@@ -80,34 +91,26 @@ __device__ void chol_upper(float (*R)[LD], int n, int nchk, float thr, int* bad)
   __syncthreads();
 }
 
-// Inverse of an upper-triangular R into Ri: rows bottom-up, each row's entries in
-// parallel with the dot product split over the 16 row-threads of a column.
-__device__ void tri_inverse(const float (*R)[LD], float (*Ri)[LD], int n, float (*scratch)[LD]) {
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) Ri[e / kMaxRP][e % kMaxRP] = 0.f;
+// Inverse of an upper-triangular R into Ri.  Columns are independent back
+// substitutions R x = e_c; four threads of one warp share a column (the dot product
+// over j is split four ways and reduced with shuffles), so no block barrier is needed.
+// Requires 256 threads; R must be visible to all threads on entry.
+__device__ void tri_inverse(const float (*R)[LD], float (*Ri)[LD], int n, float* dinv) {
+  const int col = threadIdx.x >> 2, part = threadIdx.x & 3;
+  for (int e = threadIdx.x; e < kMaxRP; e += SMALL_THREADS) dinv[e] = (e < n) ? 1.f / R[e][e] : 0.f;
   __syncthreads();
+  for (int i = part; i < kMaxRP; i += 4) Ri[i][col] = 0.f;
+  __syncwarp();
   for (int i = n - 1; i >= 0; --i) {
-#pragma unroll
-    for (int ib = 0; ib < 4; ++ib) {
-      const int c = tx + 16 * ib;
-      float s = 0.f;
-      for (int j = i + 1 + ty; j <= c && j < n; j += 16) s = fmaf(R[i][j], Ri[j][c], s);
-      scratch[ty][c] = s;
-    }
-    __syncthreads();
-    if (ty == 0) {
-#pragma unroll
-      for (int ib = 0; ib < 4; ++ib) {
-        const int c = tx + 16 * ib;
-        if (c < i || c >= n) continue;
-        float s = 0.f;
-#pragma unroll
-        for (int t = 0; t < 16; ++t) s += scratch[t][c];
-        Ri[i][c] = (c == i) ? 1.f / R[i][i] : -s / R[i][i];
-      }
-    }
-    __syncthreads();
+    float s = 0.f;
+    if (col < n && i <= col)
+      for (int j = i + 1 + part; j <= col; j += 4) s = fmaf(R[i][j], Ri[j][col], s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0 && col < n && i <= col) Ri[i][col] = ((i == col ? 1.f : 0.f) - s) * dinv[i];
+    __syncwarp();
   }
+  __syncthreads();
 }
 
 // C = A B (n x n, A upper triangular if a_upper); C may alias A or B.
@@ -178,6 +181,21 @@ __device__ bool load_gram(float (*G)[LD], const double* g64, int r, int RP) {
   return s_nf == 0;
 }
 
+// Largest |M[i][j]| over the n x n block (all threads get it).
+__device__ float block_absmax(const float (*M)[LD], int n) {
+  __shared__ float red[SMALL_THREADS / 32];
+  float m = 0.f;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) m = fmaxf(m, fabsf(M[e / n][e % n]));
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
 // Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
 // numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
 // factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.
@@ -206,32 +224,44 @@ __device__ void robust_chol(float (*G)[LD], float (*R)[LD], int r, int RP, Ctl* 
 
 // dst = M / max|M|, ctl->m_logscale (+)= log(max|M|).
 __device__ void normalise_into(float (*M)[LD], float* dst, int RP, Ctl* ctl, bool reset_scale) {
-  __shared__ float s_scale;
-  if (threadIdx.x == 0) {
-    float mx = 0.f;
-    for (int i = 0; i < RP; ++i)
-      for (int j = 0; j < RP; ++j) mx = fmaxf(mx, fabsf(M[i][j]));
-    s_scale = mx > 0.f ? mx : 1.f;
-    ctl->m_logscale = (reset_scale ? 0.0 : ctl->m_logscale) + log((double)s_scale);
-  }
-  __syncthreads();
-  const float inv = 1.f / s_scale;
+  const float mx = block_absmax(M, RP);
+  const float scale = mx > 0.f ? mx : 1.f;
+  if (threadIdx.x == 0) ctl->m_logscale = (reset_scale ? 0.0 : ctl->m_logscale) + log((double)scale);
+  const float inv = 1.f / scale;
   for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) dst[e] = M[e / RP][e % RP] * inv;
 }
 
 // ---- critical path: R from a Gram --------------------------------------------------------
+// R (upper) with Rᵀ R = G and its inverse T = R^{-1}.  With alarm_ratio > 0 the
+// factor of an almost orthonormal input is checked: a diagonal spread above the ratio
+// means one CholeskyQR pass would not restore orthonormality, and the iteration is
+// sent back to the exact path (alarm).
 __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict__ g64, int r, int RP,
-                                                        float* __restrict__ Rout, Ctl* ctl) {
+                                                        float* __restrict__ Rout, float* __restrict__ Tout,
+                                                        float alarm_ratio, Ctl* ctl) {
   if (ctl->abort) return;
   extern __shared__ __align__(16) float smf[];
   float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
   float (*R)[LD] = G + kMaxRP;
+  float (*Ri)[LD] = R + kMaxRP;
+  __shared__ float dinv[kMaxRP];
   if (!load_gram(G, g64, r, RP)) {
     if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
     return;
   }
   robust_chol(G, R, r, RP, ctl);
+  if (alarm_ratio > 0.f && threadIdx.x < 32) {
+    float lo = 3.4e38f, hi = 0.f;
+    for (int j = threadIdx.x; j < r; j += 32) { lo = fminf(lo, R[j][j]); hi = fmaxf(hi, R[j][j]); }
+    for (int o = 16; o; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (threadIdx.x == 0 && !(hi <= alarm_ratio * lo)) { ctl->alarm = 1; ctl->abort = 1; }
+  }
   store_mat(Rout, R, RP);
+  tri_inverse(R, Ri, RP, dinv);
+  store_mat(Tout, Ri, RP);
 }
 
 // ---- off the critical path: lagged normaliser of a chain slot ---------------------------
@@ -264,7 +294,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
   float (*B)[LD] = A + kMaxRP;
   float (*C)[LD] = B + kMaxRP;
   float (*D)[LD] = C + kMaxRP;
-  __shared__ float scratch[16][LD];
+  __shared__ float dinv[kMaxRP];
   const int r = a.r, RP = a.RP;
   const int cur = ctl->slot_parity, nxt = 1 - cur;
   load_mat(B, a.R_app[cur], RP);                     // B = R_app
@@ -308,7 +338,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
     __syncthreads();
   }
   store_mat(a.R_next[nxt], A, RP);
-  tri_inverse(A, C, RP, scratch);
+  tri_inverse(A, C, RP, dinv);
   store_mat(a.T_next[nxt], C, RP);
   if (a.pi_mode == 2) {
     normalise_into(B, a.Pi, RP, ctl, true);
@@ -336,21 +366,29 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_rank(const double* __restrict
   if (tid == 0) { stop = 0; rank = r; }
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
+    if (tid < 32) {
+      // pivot: largest remaining diagonal (first index on ties), found by warp 0
       int p = j;
       double best = Gd[j][j];
-      for (int i = j + 1; i < r; ++i)
-        if (Gd[i][i] > best) { best = Gd[i][i]; p = i; }
-      if (j == 0) dmax0 = best;
-      if (!isfinite(best)) {
-        ctl->nonfinite = 1;
-        ctl->abort = 1;
-        stop = 1;
-      } else if (!(dmax0 > 0.0) || !(best > rank_tol * rank_tol * dmax0)) {
-        rank = j;
-        stop = 1;
+      for (int i = j + tid; i < r; i += 32)
+        if (Gd[i][i] > best || (Gd[i][i] == best && i < p)) { best = Gd[i][i]; p = i; }
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
       }
-      piv = p;
+      if (tid == 0) {
+        if (j == 0) dmax0 = best;
+        if (!isfinite(best)) {
+          ctl->nonfinite = 1;
+          ctl->abort = 1;
+          stop = 1;
+        } else if (!(dmax0 > 0.0) || !(best > rank_tol * rank_tol * dmax0)) {
+          rank = j;
+          stop = 1;
+        }
+        piv = p;
+      }
     }
     __syncthreads();
     if (stop) break;
@@ -444,13 +482,16 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
     for (int e = tid; e < RP * RP; e += SVD_THREADS) X2[e / RP][e % RP] = V[e / RP][e % RP];
     __syncthreads();
   }
-  load_1024(X1, a.Rb, RP);
-  mm_1024(X1, X2, W, RP, false);      // W = M (unscaled)
-  if (tid == 0) {
-    float mx = 0.f;
-    for (int i = 0; i < r; ++i)
-      for (int j = 0; j < r; ++j) mx = fmaxf(mx, fabsf(W[i][j]));
-    s_scale = mx > 0.f ? mx : 1.f;
+  if (a.Rb) {
+    load_1024(X1, a.Rb, RP);
+    mm_1024(X1, X2, W, RP, false);    // W = M (unscaled)
+  } else {
+    for (int e = tid; e < RP * RP; e += SVD_THREADS) W[e / RP][e % RP] = X2[e / RP][e % RP];
+    __syncthreads();
+  }
+  {
+    const float mx = block_absmax(W, r);
+    if (tid == 0) s_scale = mx > 0.f ? mx : 1.f;
   }
   __syncthreads();
   for (int e = tid; e < RP * RP; e += SVD_THREADS) {
@@ -529,16 +570,16 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
     s[tid] = sqrtf(v);
   }
   __syncthreads();
-  if (tid == 0) {
-    for (int j = 0; j < RP; ++j) order[j] = j;
-    for (int j = 0; j < r; ++j) {
-      int b = j;
-      for (int i = j + 1; i < r; ++i)
-        if (s[order[i]] > s[order[b]]) b = i;
-      int t = order[j]; order[j] = order[b]; order[b] = t;
+  // descending order of s (ties by column index): column j goes to its rank
+  if (tid < RP) {
+    int rk = tid;
+    if (tid < r) {
+      rk = 0;
+      for (int i = 0; i < r; ++i) rk += (s[i] > s[tid]) || (s[i] == s[tid] && i < tid);
     }
-    ctl->svd_sweeps = sweeps;
+    order[rk] = tid;
   }
+  if (tid == 0) ctl->svd_sweeps = sweeps;
   __syncthreads();
   // U = W diag(1/s), columns in descending order of s; V reordered likewise
   for (int e = tid; e < RP * RP; e += SVD_THREADS) {
@@ -594,15 +635,18 @@ cudaError_t prepare_small_kernels() {
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
                      cudaStream_t st) {
   const int npair = RP * RP;
-  const unsigned grid = (unsigned)((npair + 127) / 128);
+  const unsigned grid = (unsigned)((npair + GS_ENT - 1) / GS_ENT);
   if (gram_double)
-    k_gram_sum<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out, ctl);
+    k_gram_sum<double><<<grid, GS_ENT * GS_SPLIT, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out,
+                                                            ctl);
   else
-    k_gram_sum<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out, ctl);
+    k_gram_sum<float><<<grid, GS_ENT * GS_SPLIT, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out,
+                                                           ctl);
 }
 
-void launch_chol(const double* g64, int r, int RP, float* R, Ctl* ctl, cudaStream_t st) {
-  k_chol<<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, ctl);
+void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
+                 float alarm_ratio) {
+  k_chol<<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, T, alarm_ratio, ctl);
 }
 
 void launch_slot(const SlotLaunch& l, cudaStream_t st) {

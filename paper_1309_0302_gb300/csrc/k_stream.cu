@@ -285,86 +285,99 @@ cudaError_t prepare_prod_t() {
 }
 
 // ----------------------------------------------------------------------------------
-// Q = P T (dense T) or Q = P R^{-1} (R upper triangular, forward substitution per
-// row), optional float Gram partials of Q per 64-row block.
+// Q = P T (T dense RP x RP; a triangular inverse is passed as a dense matrix), for
+// rows x RP row-major P.  64 rows per block, four threads per row (16 output columns
+// each); the block's rows are staged in shared memory before any output is written,
+// so P and Q may alias.  Optional outputs: Q itself, the float16 split transposed
+// copy for the tensor-core product, and the block's float Gram partial QᵀQ.
 // ----------------------------------------------------------------------------------
-constexpr int RB = 64;
+constexpr int RB = 64;              // rows per block
+constexpr int AP_THREADS = 256;
+constexpr int AP_LD = kMaxRP + 1;   // odd stride: rows of a warp fall in different banks
 
-__global__ void __launch_bounds__(RB)
-k_apply(const float* __restrict__ P, int64_t rows, int RP, const float* __restrict__ T0,
-        const float* __restrict__ T1, int solve, float* __restrict__ Q, float* __restrict__ gram_part,
-        const Ctl* ctl, void* __restrict__ bt2, int64_t ldb, int RPp) {
+__global__ void __launch_bounds__(AP_THREADS)
+k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, const float* __restrict__ T1, float* Q,
+        float* __restrict__ gram_part, const Ctl* ctl, void* __restrict__ bt2, int64_t ldb) {
   if (ctl && ctl->abort) return;
   const float* T = (ctl && ctl->slot_parity) ? T1 : T0;
-  __shared__ float Ts[kMaxRP][kMaxRP + 1];
-  __shared__ float Qs[RB * EPI_STRIDE];
-  __shared__ float dinv[kMaxRP];
+  __shared__ __align__(16) float Ts[kMaxRP][kMaxRP];
+  __shared__ float Ps[RB][AP_LD];
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * RB;
   const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
-  for (int e = tid; e < RP * RP; e += RB) Ts[e / RP][e % RP] = T[e];
+  for (int e = tid; e < kMaxRP * kMaxRP; e += AP_THREADS) {
+    const int a = e / kMaxRP, c = e % kMaxRP;
+    Ts[a][c] = (a < RP && c < RP) ? T[a * RP + c] : 0.f;
+  }
+  for (int e = tid; e < RB * RP; e += AP_THREADS) {
+    const int i = e / RP, c = e % RP;
+    Ps[i][c] = (i < nrow) ? P[(r0 + i) * RP + c] : 0.f;
+  }
   __syncthreads();
-  if (solve && tid < RP) dinv[tid] = 1.f / Ts[tid][tid];
-  __syncthreads();
-  // one row per thread; rows are read from P before any row of Q is written, so
-  // P and Q may alias
-  const int64_t i = r0 + tid;
-  float p[kMaxRP];
+  const int row = tid >> 2, cg = (tid & 3) * 16;   // this thread: row, columns cg .. cg+15
+  float q[16];
 #pragma unroll
-  for (int c = 0; c < kMaxRP; ++c) p[c] = (c < RP && tid < nrow) ? P[i * RP + c] : 0.f;
-  __syncthreads();
-  float q[kMaxRP];
-  if (solve) {
-    // q R = p: q_c = (p_c - sum_{a<c} q_a R[a][c]) / R[c][c]
+  for (int l = 0; l < 16; ++l) q[l] = 0.f;
+  if (cg < RP) {
+    for (int a = 0; a < RP; ++a) {
+      const float pa = Ps[row][a];
+      const float4* tr = reinterpret_cast<const float4*>(&Ts[a][cg]);
 #pragma unroll
-    for (int c = 0; c < kMaxRP; ++c) {
-      if (c < RP) {
-        float s0 = p[c], s1 = 0.f;
-        int a = 0;
-#pragma unroll
-        for (; a + 1 < c; a += 2) {
-          s0 = fmaf(-q[a], Ts[a][c], s0);
-          s1 = fmaf(-q[a + 1], Ts[a + 1][c], s1);
-        }
-        if (a < c) s0 = fmaf(-q[a], Ts[a][c], s0);
-        q[c] = (s0 + s1) * dinv[c];
-      } else {
-        q[c] = 0.f;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < kMaxRP; ++c) q[c] = 0.f;
-#pragma unroll
-    for (int a = 0; a < kMaxRP; ++a) {
-      if (a < RP) {
-        const float pa = p[a];
-#pragma unroll
-        for (int c = 0; c < kMaxRP; ++c)
-          if (c < RP) q[c] = fmaf(pa, Ts[a][c], q[c]);
+      for (int v = 0; v < 4; ++v) {
+        const float4 t = tr[v];
+        q[4 * v] = fmaf(pa, t.x, q[4 * v]);
+        q[4 * v + 1] = fmaf(pa, t.y, q[4 * v + 1]);
+        q[4 * v + 2] = fmaf(pa, t.z, q[4 * v + 2]);
+        q[4 * v + 3] = fmaf(pa, t.w, q[4 * v + 3]);
       }
     }
   }
+  __syncthreads();   // every thread has read its P row: Ps now holds Q
 #pragma unroll
-  for (int c = 0; c < kMaxRP; ++c)
-    if (c < RP) Qs[tid * EPI_STRIDE + c] = (tid < nrow) ? q[c] : 0.f;
-  if (Q && tid < nrow)
-    for (int c = 0; c < RP; ++c) Q[i * RP + c] = q[c];
-  if (bt2 && tid < nrow) {
+  for (int l = 0; l < 16; ++l)
+    if (cg + l < RP) Ps[row][cg + l] = (row < nrow) ? q[l] : 0.f;
+  __syncthreads();
+  if (Q)
+    for (int e = tid; e < nrow * RP; e += AP_THREADS) Q[(r0 + e / RP) * RP + e % RP] = Ps[e / RP][e % RP];
+  if (bt2) {
     __half* b2 = reinterpret_cast<__half*>(bt2);
-#pragma unroll
-    for (int c = 0; c < kMaxRP; ++c) {
-      if (c < RP) {
-        const float v = q[c] * kSkinnyScale;
+    for (int e = tid; e < RP * RB; e += AP_THREADS) {
+      const int c = e / RB, i = e % RB;   // consecutive threads: consecutive rows of one column
+      if (i < nrow) {
+        const float v = Ps[i][c] * kSkinnyScale;
         const __half c1 = __float2half_rn(v);
-        b2[(int64_t)c * ldb + i] = c1;
-        b2[(int64_t)(RP + c) * ldb + i] = __float2half_rn((v - __half2float(c1)) * 2048.f);
+        b2[(int64_t)c * ldb + r0 + i] = c1;
+        b2[(int64_t)(RP + c) * ldb + r0 + i] = __float2half_rn((v - __half2float(c1)) * 2048.f);
       }
     }
   }
   if (!gram_part) return;
-  __syncthreads();
-  tile_gram(Qs, nrow, RP, 1, gram_part + (int64_t)blockIdx.x * RP * RP, RB);
+  // Gram partial: thread (bi, bj) accumulates the 4 x 4 block rows 4bi.., columns 4bj..
+  const int bi = tid >> 4, bj = tid & 15;
+  float g[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) g[u][v] = 0.f;
+  if (4 * bi < RP && 4 * bj < RP) {
+    for (int i = 0; i < nrow; ++i) {
+      float x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x[u] = Ps[i][4 * bi + u];
+        y[u] = Ps[i][4 * bj + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) g[u][v] = fmaf(x[u], y[v], g[u][v]);
+    }
+    float* out = gram_part + (int64_t)blockIdx.x * RP * RP;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[(4 * bi + u) * RP + 4 * bj + v] = g[u][v];
+  }
 }
 
 }  // namespace
@@ -399,10 +412,9 @@ cudaError_t prepare_stream_kernels() {
 
 int64_t apply_blocks(int64_t rows) { return (rows + RB - 1) / RB; }
 
-void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, int solve, float* Q,
-                  float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2, int64_t ldb, int RPp) {
-  k_apply<<<(unsigned)apply_blocks(rows), RB, 0, st>>>(P, rows, RP, T0, T1, solve, Q, gram_part, ctl, bt2, ldb,
-                                                        RPp);
+void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, float* Q,
+                  float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2, int64_t ldb) {
+  k_apply<<<(unsigned)apply_blocks(rows), AP_THREADS, 0, st>>>(P, rows, RP, T0, T1, Q, gram_part, ctl, bt2, ldb);
 }
 
 }  // namespace godec

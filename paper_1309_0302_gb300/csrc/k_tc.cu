@@ -584,7 +584,11 @@ TcGeom tc_geometry(int64_t rows, int64_t K, int nsm) {
   g.tiles = (rows + BM - 1) / BM;
   g.ks = (K + BK - 1) / BK;
   g.S = g.tiles * g.ks;
-  g.G = (int)(g.S < nsm ? g.S : nsm);
+  // Leave a few SMs without a product CTA: the r x r kernels of the side stream run
+  // there instead of holding an SM that a persistent CTA (which needs the whole shared
+  // memory) would otherwise wait for.
+  const int ncta = nsm > 16 ? nsm - 4 : nsm;
+  g.G = (int)(g.S < ncta ? g.S : ncta);
   int maxseg = 1;
   for (int64_t t = 0; t < g.tiles; ++t) {
     const int64_t cf = ((t * g.ks + 1) * g.G - 1) / g.S;
