@@ -132,6 +132,15 @@ godec_status godec_get_L(godec_ctx* ctx, float* U, float* sigma, float* V, int32
  */
 godec_status godec_get_S(godec_ctx* ctx, int64_t* idx, float* val, int64_t cap, int64_t* nnz);
 
+/*
+ * Dense residual R = X - L_t of the current state (the matrix the S-step of
+ * Algorithm 1, line 9, thresholds), computed by the same tensor-core kernel and
+ * arithmetic as the S-step's residual pass.
+ *   R : device, m x ldr float32, ldr >= n.
+ * GODEC_ERR_STATE before the first iteration.  Synchronises the stream.
+ */
+godec_status godec_residual(godec_ctx* ctx, float* R, int64_t ldr);
+
 /* State after the last committed iteration t: its objective
    ||X - L_t - S_t||_F^2 (E_t^2 of Appendix I), |Omega| and bookkeeping. */
 typedef struct godec_info {
@@ -210,6 +219,16 @@ godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz,
 #define GODEC_PROF_CLASSES 10
 godec_status godec_profile(godec_ctx* ctx, int32_t n_iter, double* ms, int64_t* launches,
                            double* bytes_product);
+
+/*
+ * The launches of the last iteration that godec_profile ran, in enqueue order:
+ * for each (up to cap) its class, whether it ran on the side stream, and its
+ * start and end events in milliseconds after the iteration's first event
+ * (host arrays of cap entries, each nullable).  count (host) receives the
+ * number of launches recorded; 0 before any godec_profile call.
+ */
+godec_status godec_profile_trace(godec_ctx* ctx, int32_t cap, int32_t* cls, int32_t* side, float* t0, float* t1,
+                                 int32_t* count);
 
 /*
  * Entry-wise hard threshold of a dense matrix (eq. raw_lss, Algorithm 1

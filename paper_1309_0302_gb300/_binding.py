@@ -49,6 +49,7 @@ def _declare(lib):
         "godec_solve": ([_P, i32p, f64p], C.c_int),
         "godec_get_L": ([_P, _P, _P, _P, i32p], C.c_int),
         "godec_get_S": ([_P, _P, _P, C.c_int64, i64p], C.c_int),
+        "godec_residual": ([_P, _P, C.c_int64], C.c_int),
         "godec_get_info": ([_P, C.POINTER(GodecInfo)], C.c_int),
         "godec_destroy": ([_P], None),
         "godec_last_error": ([_P], C.c_char_p),
@@ -56,6 +57,7 @@ def _declare(lib):
         "godec_run_host": ([C.POINTER(GodecParams), _P, _P, C.c_int32, _P, _P, _P, _P, i32p, _P, _P,
                             C.c_int64, i64p, i32p, f64p], C.c_int),
         "godec_profile": ([_P, C.c_int32, f64p, i64p, f64p], C.c_int),
+        "godec_profile_trace": ([_P, C.c_int32, i32p, i32p, f32p, f32p, i32p], C.c_int),
         "godec_hard_threshold": ([_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, _P, C.c_int64, i64p, _P],
                                  C.c_int),
         "godec_mul_ZB": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
@@ -183,6 +185,17 @@ class GoDec:
                 "launches": {k: cnt[i] for i, k in enumerate(self.PROF_CLASSES)},
                 "bytes_product": bp.value}
 
+    def profile_trace(self):
+        """Launches of the last profiled iteration: list of (class, side, t0_ms, t1_ms)."""
+        cnt = C.c_int32(0)
+        lib = library()
+        _check(lib.godec_profile_trace(self._h, 0, None, None, None, None, C.byref(cnt)), "godec_profile_trace", self._h)
+        n = cnt.value
+        cls, side = (C.c_int32 * max(n, 1))(), (C.c_int32 * max(n, 1))()
+        t0, t1 = (C.c_float * max(n, 1))(), (C.c_float * max(n, 1))()
+        _check(lib.godec_profile_trace(self._h, n, cls, side, t0, t1, C.byref(cnt)), "godec_profile_trace", self._h)
+        return [(self.PROF_CLASSES[cls[i]], side[i], t0[i], t1[i]) for i in range(n)]
+
     def L(self):
         """(U (m, r_eff), sigma (r_eff,), V (n, r_eff)) as CUDA float32 tensors."""
         torch = _torch()
@@ -206,6 +219,14 @@ class GoDec:
         val = torch.empty((max(cnt, 1),), dtype=torch.float32, device=self._X.device)
         _check(lib.godec_get_S(self._h, _ptr(idx), _ptr(val), cnt, C.byref(nnz)), "godec_get_S", self._h)
         return idx[: nnz.value], val[: nnz.value]
+
+    def residual(self):
+        """Dense R = X - L_t (m, n) as a CUDA float32 tensor, from the S-step's kernel."""
+        torch = _torch()
+        m, n = self._X.shape
+        R = torch.empty((m, n), dtype=torch.float32, device=self._X.device)
+        _check(library().godec_residual(self._h, _ptr(R), n), "godec_residual", self._h)
+        return R
 
 
 def _mul(name, Z, B, stream=None):

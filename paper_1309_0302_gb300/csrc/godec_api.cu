@@ -70,7 +70,9 @@ struct godec_ctx {
   int RPp = 0;
   float* cs = nullptr;                 // [2][RP] output factors: A1's column scales, 1 / kSkinnyScale
   float* rescale_tmp = nullptr;        // 2 floats: factor applied by rescale_z
-  alignas(64) unsigned char tmap[5][128];   // tensor maps: Z, Z^T, bt2[0], bt2[1], bt2[2]
+  alignas(64) unsigned char tmap[8][128];   // tensor maps: Z, Z^T, bt2[0], bt2[1], bt2[2], X, Lsplit A, B
+  void* LA = nullptr;                  // m x 128 halves: float16 split of U diag(sqrt(sigma s_Z))
+  void* LB = nullptr;                  // n x 128 halves: float16 split of V diag(sqrt(sigma s_Z))
   TcGeom tg[2];                        // work split of even (Z) and odd (Z^T) products
   float* part = nullptr;               // stream-K partial slots
   unsigned* counters = nullptr;        // per-tile arrival counters
@@ -104,6 +106,7 @@ struct godec_ctx {
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> prof_cls;
+  std::vector<int> prof_side;   // launch on the side stream
   size_t prof_used = 0;
   char err[200] = {0};
 };
@@ -115,7 +118,10 @@ static void prof_mark(godec_ctx* c, int cls, cudaStream_t s) {
     c->ev_pool.push_back(e);
   }
   cudaEventRecord(c->ev_pool[c->prof_used++], s);
-  if (cls >= 0) c->prof_cls.push_back(cls);
+  if (cls >= 0) {
+    c->prof_cls.push_back(cls);
+    c->prof_side.push_back(s == c->side_st ? 1 : 0);
+  }
 }
 
 // Bracket one launch with events when profiling (eager mode only).
@@ -376,6 +382,8 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
                   c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st));
   apply(c, c->Q1, m, c->Um, c->Um, c->U, nullptr);
   apply(c, c->Q2, n, c->Vm, c->Vm, c->V, nullptr);
+  // operands of the tensor-core residual pass
+  PROF(c, 3, c->st, launch_lsplit(c->U, c->V, c->sigma, m, n, RP, c->r, c->ctl->zscale, c->LA, c->LB, c->st));
 }
 
 // S-step of one iteration (Algorithm 1 line 9) on the current L factors; r = 0 means L = 0.
@@ -399,7 +407,18 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ra.cand_cap = c->cap;
   for (int pass = 0; pass < 3; ++pass) {
     ra.pass = pass;
-    PROF(c, 7, st, launch_residual(ra, c->nsm, st));
+    if (c->LA && r > 0) {
+      ResidTcLaunch rl{};
+      rl.ra = ra;
+      rl.mapX = c->tmap[5];
+      rl.mapA = c->tmap[6];
+      rl.mapB = c->tmap[7];
+      rl.zscale = c->ctl->zscale;
+      rl.nsm = c->nsm;
+      PROF(c, 7, st, launch_resid_tc(rl, st));
+    } else {
+      PROF(c, 7, st, launch_residual(ra, c->nsm, st));
+    }
     PROF(c, 8, st, launch_after_pass(c->ctl, pass, c->p.k, c->cap, st));
   }
   SelectArgs se{};
@@ -664,7 +683,7 @@ void godec_destroy(godec_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   free_graphs(c);
-  void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->bt2, c->cs, c->rescale_tmp, c->Q1, c->Q2,
+  void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->bt2, c->cs, c->rescale_tmp, c->LA, c->LB, c->Q1, c->Q2,
                   c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->gparts, c->g64, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
                   c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1]};
@@ -720,6 +739,7 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(prepare_select_kernels());
   CKI(prepare_stream_kernels());
   CKI(prepare_tc_kernels());
+  CKI(prepare_resid_kernels());
   CKI(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
   CKI(cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking));
   for (int k = 0; k < kEvents; ++k) CKI(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
@@ -760,8 +780,13 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   c->ncounters = tiles;
   CKI(dalloc(&c->counters, (size_t)tiles));
   CKI(cudaMemsetAsync(c->counters, 0, (size_t)tiles * sizeof(unsigned), c->st));
+  CKI(dalloc(reinterpret_cast<unsigned short**>(&c->LA), (size_t)m * 128));
+  CKI(dalloc(reinterpret_cast<unsigned short**>(&c->LB), (size_t)n * 128));
   {
-    const bool ok = make_tmap_f32(c->tmap[0], c->Z, m, n, c->ldz, 128) &&
+    const bool ok = make_tmap_f32(c->tmap[5], X, m, n, p->ldx, 128) &&
+                    make_tmap_f16(c->tmap[6], c->LA, m, 128, 128, 128) &&
+                    make_tmap_f16(c->tmap[7], c->LB, n, 128, 128, 64) &&
+                    make_tmap_f32(c->tmap[0], c->Z, m, n, c->ldz, 128) &&
                     make_tmap_f32(c->tmap[1], c->Zt, n, m, c->ldzt, 128) &&
                     make_tmap_f16(c->tmap[2], bt2(c, 0), 2 * RP, m, c->ldb, 2 * RP) &&
                     make_tmap_f16(c->tmap[3], bt2(c, 1), 2 * RP, n, c->ldb, 2 * RP) &&
@@ -861,6 +886,7 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
     c->prof = true;
     c->prof_used = 0;
     c->prof_cls.clear();
+    c->prof_side.clear();
     enqueue_iteration(c, fast);
     c->prof = false;
     CK(cudaGetLastError());
@@ -882,6 +908,24 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
       if (++guard > 64) return fail(c, GODEC_ERR_STATE, "too many aborted iterations");
       if ((s = read_ctl(c, &h))) return s;
     }
+  }
+  return GODEC_OK;
+}
+
+godec_status godec_profile_trace(godec_ctx* c, int32_t cap, int32_t* cls, int32_t* side, float* t0, float* t1,
+                                 int32_t* count) {
+  if (!c || cap < 0 || !count) return GODEC_ERR_ARG;
+  const size_t nl = c->prof_cls.size();
+  *count = (int32_t)nl;
+  if (nl == 0 || 2 * nl > c->prof_used) return GODEC_OK;
+  for (size_t i = 0; i < nl && i < (size_t)cap; ++i) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, c->ev_pool[0], c->ev_pool[2 * i]));
+    CK(cudaEventElapsedTime(&b, c->ev_pool[0], c->ev_pool[2 * i + 1]));
+    if (cls) cls[i] = c->prof_cls[i];
+    if (side) side[i] = c->prof_side[i];
+    if (t0) t0[i] = a;
+    if (t1) t1[i] = b;
   }
   return GODEC_OK;
 }
@@ -916,6 +960,34 @@ godec_status godec_get_L(godec_ctx* c, float* U, float* sigma, float* V, int32_t
   if (U) launch_unpad_copy(c->U, c->p.m, c->RP, U, c->r, c->st);
   if (V) launch_unpad_copy(c->V, c->p.n, c->RP, V, c->r, c->st);
   if (sigma) CK(cudaMemcpyAsync(sigma, c->sigma, c->r * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  return GODEC_OK;
+}
+
+godec_status godec_residual(godec_ctx* c, float* R, int64_t ldr) {
+  if (!c || !R || ldr < c->p.n) {
+    if (c) fail(c, GODEC_ERR_ARG, "godec_residual: R must be non-NULL with ldr >= n");
+    return GODEC_ERR_ARG;
+  }
+  Ctl h;
+  godec_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (h.iter < 1) return fail(c, GODEC_ERR_STATE, "no iteration has run yet");
+  launch_lsplit(c->U, c->V, c->sigma, c->p.m, c->p.n, c->RP, c->r, c->ctl->zscale, c->LA, c->LB, c->st);
+  ResidTcLaunch rl{};
+  rl.ra.X = c->X;
+  rl.ra.m = c->p.m;
+  rl.ra.n = c->p.n;
+  rl.ra.ctl = c->ctl;
+  rl.mapX = c->tmap[5];
+  rl.mapA = c->tmap[6];
+  rl.mapB = c->tmap[7];
+  rl.zscale = c->ctl->zscale;
+  rl.dump = R;
+  rl.ldd = ldr;
+  rl.nsm = c->nsm;
+  launch_resid_tc(rl, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   return GODEC_OK;

@@ -32,7 +32,7 @@ constexpr int kD1Shift = 19;
 constexpr int kNumSelRounds = 7;    // 3 key digits + 4 index digits
 
 // Pass modes of the residual (S-step) kernel.
-enum PassMode : int { PASS_NONE = 0, PASS_FULL = 1, PASS_CAND = 2 };
+enum PassMode : int { PASS_NONE = 0, PASS_FULL = 1, PASS_CAND = 2, PASS_DUMP = 3 };
 
 // Device-resident control block shared by the kernels of one context.  Scalars come
 // first so the host can read them with one small copy; histograms follow.
@@ -216,6 +216,24 @@ struct ResidualArgs {
   unsigned long long cand_cap;
 };
 void launch_residual(const ResidualArgs& a, int nsm, cudaStream_t st);
+
+// Tensor-core residual pass (k_resid.cu).  A and B hold the float16 split of
+// U diag(sqrt(sigma s_Z)) and V diag(sqrt(sigma s_Z)), rows of 128 halves (64 high,
+// 64 low; K padded to 64), written by launch_lsplit after each L-step.
+void launch_lsplit(const float* U, const float* V, const float* sigma, int64_t m, int64_t n, int RP, int r,
+                   const float* zscale, void* A, void* B, cudaStream_t st);
+struct ResidTcLaunch {
+  ResidualArgs ra;         // X, m, n, pass, ctl and the candidate buffers are used
+  const void* mapX;        // CUtensorMap over X (m x n float32), box 32 x 128
+  const void* mapA;        // over A (m x 128 halves), box 64 x 128
+  const void* mapB;        // over B (n x 128 halves), box 64 x 64
+  const float* zscale;     // {s_Z, 1/s_Z}
+  float* dump;             // non-null: write R densely (row stride ldd) instead of selecting
+  int64_t ldd;
+  int nsm;
+};
+void launch_resid_tc(const ResidTcLaunch& l, cudaStream_t st);
+cudaError_t prepare_resid_kernels();
 void launch_after_pass(Ctl* ctl, int pass, long long k, unsigned long long cap, cudaStream_t st);
 
 struct SelectArgs {

@@ -14,7 +14,7 @@ import pytest
 
 import oracle as O
 import synth
-from gpu_helpers import (GpuRun, lfro_rel, residual_like_kernel, s_common_rel, s_rel,
+from gpu_helpers import (GpuRun, lfro_rel, s_common_rel, s_rel,
                          selection_within_band, to_gpu, to_np)
 
 pytestmark = pytest.mark.gpu
@@ -97,12 +97,13 @@ def test_c1_trajectory(c1):
 
 
 def test_c1_selection_is_exact_topk_of_kernel_residual(c1):
+    """Reading R8(i): the GPU's Omega is exactly the top-k (ties by linear index) of the
+    GPU's own float32 residual, read back densely from the same kernel."""
     d, _ = c1
     run = GpuRun(d)
     for t in range(3):
         run.g.iterate(1)
-        U, s, V = run.factors32()
-        R = residual_like_kernel(d["X"], U, s, V)
+        R = to_np(run.g.residual())
         ri, rv = O.hard_threshold(R.astype(np.float64), d["k"])
         i, v = run.sparse()
         assert np.array_equal(i, ri), t
