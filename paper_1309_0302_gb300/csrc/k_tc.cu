@@ -62,7 +62,8 @@ constexpr int NS = 3;              // stage slots: skinny-operand tile in shared
 constexpr int kThreads = 480;
 constexpr int kConvWarps = 8;
 constexpr uint32_t kTmemCols = 512, kTA0 = 256, kTASlot = 64;
-constexpr int EPI_LD = kMaxRP + 1;
+constexpr int EPI_LD = kMaxRP + 1;   // odd stride: row-wise and column-wise accesses are conflict-free
+constexpr int kMaxPend = 8;          // tile completions deferred to the end of the kernel
 constexpr size_t kBoxA = (size_t)BM * 32 * 4;               // one 32-column float32 box, 16 KB
 constexpr size_t kStageA = 2 * kBoxA;                       // 32 KB
 constexpr size_t kStageB = (size_t)2 * kMaxRP * BK * 2;     // 16 KB (room for 2 x 64 rows of 64 halves)
@@ -117,111 +118,199 @@ __device__ __forceinline__ uint32_t pack_h2(float even, float odd) {
   return d;
 }
 
-// Completion of tile t by its last segment: Ps is BM x EPI_LD, Ts is RPp x RPp.
+// Completion of tile t by its last segment, run by nthr threads (u = 0..nthr-1, a
+// multiple of 32) that synchronise on named barrier `bar`: the partial slots are added
+// in slot order (deterministic whoever finishes) and unscaled, the normaliser T applied,
+// the rows and the next product's split transposed operand written, and the tile's Gram
+// partial formed.  Ps (BM x EPI_LD) holds the tile's rows between the phases, Ts (RPp x
+// RPp) a copy of T; csc = per-column output factors 1 / s_B, zi = 1 / s_Z.
 template <int RPp>
-__device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int et, float* Ps, float* Ts) {
-  const int RP = a.RP;
+__device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nthr, int bar, float* Ps, float* Ts,
+                            const float* csc, float zi) {
+  const int RP = a.RP, RP4 = RP / 4;
   const int64_t o0 = t * BM;
   const int nrow = (int)(a.rows - o0 < BM ? a.rows - o0 : BM);
-  __threadfence();
-  if (et == 0) a.counters[t] = 0u;
-  float y[RPp];
-#pragma unroll
-  for (int l = 0; l < RPp; ++l) y[l] = 0.f;
-  for (int sl = 0; sl < nseg; ++sl) {
-    const float4* p = reinterpret_cast<const float4*>(a.part + ((t * a.maxseg + sl) * BM + et) * (int64_t)RP);
-#pragma unroll
-    for (int l = 0; l < RPp; l += 4)
-      if (l < RP) {
-        const float4 v = __ldcg(p + l / 4);
-        y[l] += v.x;
-        y[l + 1] += v.y;
-        y[l + 2] += v.z;
-        y[l + 3] += v.w;
-      }
-  }
-  {
-    const float zi = a.zscale ? a.zscale[1] : 1.f;
-#pragma unroll
-    for (int l = 0; l < RPp; ++l)
-      if (l < RP) y[l] *= (a.cscale ? a.cscale[l] : 1.f) * zi;
-  }
+  __threadfence();   // the other segments' slots: written before their counter increments
+  if (u == 0) a.counters[t] = 0u;
   const float* Tn = (a.ctl && a.ctl->slot_parity) ? a.Tn1 : a.Tn0;
+  // (1) rows of the tile into Ps: sum of the slots, unscaled.  Consecutive threads take
+  // consecutive float4s of a slot (coalesced); up to four slots are in flight at once.
+  const float4* part = reinterpret_cast<const float4*>(a.part + t * a.maxseg * (int64_t)BM * RP);
+  const int64_t slot4 = (int64_t)BM * RP4;
+  for (int it = u; it < BM * RP4; it += nthr) {
+    const int row = it / RP4, c = (it % RP4) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s0 = 0; s0 < nseg; s0 += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        v[k] = (s0 + k < nseg) ? __ldcg(part + (s0 + k) * slot4 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc.x += v[k].x;
+        acc.y += v[k].y;
+        acc.z += v[k].z;
+        acc.w += v[k].w;
+      }
+    }
+    float* pr = Ps + row * EPI_LD + c;
+    const bool live = row < nrow;
+    pr[0] = live ? acc.x * (csc[c] * zi) : 0.f;
+    pr[1] = live ? acc.y * (csc[c + 1] * zi) : 0.f;
+    pr[2] = live ? acc.z * (csc[c + 2] * zi) : 0.f;
+    pr[3] = live ? acc.w * (csc[c + 3] * zi) : 0.f;
+  }
+  if (Tn)
+    for (int e = u; e < RP * RP4; e += nthr)
+      *reinterpret_cast<float4*>(Ts + (e / RP4) * RPp + (e % RP4) * 4) = __ldg(reinterpret_cast<const float4*>(Tn) + e);
+  named_sync(bar, nthr);
+  // (2) Y <- Y T in place: a warp takes a slab of 16 rows (all of their columns, so only
+  // its own reads precede its own writes), each lane a 4 x 8 block of it
   if (Tn) {
-    // y <- y T, with y staged through this thread's row of Ps (keeps one row in registers)
-    for (int e = et; e < RP * RP; e += BM) Ts[(e / RP) * RPp + e % RP] = Tn[e];
+    const int lane = u & 31, rg = lane >> 3, l0 = (lane & 7) * 8;
+    const bool colok = l0 < RP;
+    for (int slab = u >> 5; slab < BM / 16; slab += nthr >> 5) {
+      const int r0 = slab * 16 + rg * 4;
+      float acc[4][8];
 #pragma unroll
-    for (int l = 0; l < RPp; ++l)
-      if (l < RP) Ps[et * EPI_LD + l] = y[l];
-    named_sync(1, BM);
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int l = 0; l < RPp; ++l) y[l] = 0.f;
-    for (int c = 0; c < RP; ++c) {
-      const float yc = Ps[et * EPI_LD + c];
-      const float4* tr = reinterpret_cast<const float4*>(Ts + c * RPp);
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+      if (colok)
+#pragma unroll 2
+        for (int c = 0; c < RP; ++c) {
+          float yv[4];
 #pragma unroll
-      for (int l = 0; l < RPp; l += 4)
-        if (l < RP) {
-          const float4 tv = tr[l / 4];
-          y[l] = fmaf(yc, tv.x, y[l]);
-          y[l + 1] = fmaf(yc, tv.y, y[l + 1]);
-          y[l + 2] = fmaf(yc, tv.z, y[l + 2]);
-          y[l + 3] = fmaf(yc, tv.w, y[l + 3]);
+          for (int i = 0; i < 4; ++i) yv[i] = Ps[(r0 + i) * EPI_LD + c];
+          const float4 t0 = *reinterpret_cast<const float4*>(Ts + c * RPp + l0);
+          const float4 t1 = *reinterpret_cast<const float4*>(Ts + c * RPp + l0 + 4);
+          const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(yv[i], tv[j], acc[i][j]);
         }
+      __syncwarp();
+      if (colok)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) Ps[(r0 + i) * EPI_LD + l0 + j] = acc[i][j];
+      __syncwarp();
     }
+    named_sync(bar, nthr);
   }
-  if (et >= nrow) {
-#pragma unroll
-    for (int l = 0; l < RPp; ++l) y[l] = 0.f;
-  }
-  if (a.out && et < nrow) {
-    float* o = a.out + (o0 + et) * (int64_t)RP;
-#pragma unroll
-    for (int l = 0; l < RPp; l += 4)
-      if (l < RP) *reinterpret_cast<float4*>(o + l) = make_float4(y[l], y[l + 1], y[l + 2], y[l + 3]);
-  }
-  if (a.bt2 && et < nrow) {
-#pragma unroll
-    for (int l = 0; l < RPp; ++l) {
-      const float v = (l < RP) ? y[l] * kSkinnyScale : 0.f;
-      const __half c1 = __float2half_rn(v);
-      if (l < RP) {
-        a.bt2[(int64_t)l * a.ldb + o0 + et] = c1;
-        a.bt2[(int64_t)(RP + l) * a.ldb + o0 + et] = __float2half_rn((v - __half2float(c1)) * kLoScale);
+  // (3) outputs: rows (float4 per thread), and the split transposed operand (one column
+  // l at a time, consecutive threads on consecutive rows)
+  if (a.out)
+    for (int it = u; it < nrow * RP4; it += nthr) {
+      const int row = it / RP4, c = (it % RP4) * 4;
+      const float* pr = Ps + row * EPI_LD + c;
+      *reinterpret_cast<float4*>(a.out + (o0 + row) * (int64_t)RP + c) = make_float4(pr[0], pr[1], pr[2], pr[3]);
+    }
+  if (a.bt2)
+    for (int it = u; it < RP * BM; it += nthr) {
+      const int l = it / BM, row = it % BM;
+      if (row < nrow) {
+        const float v = Ps[row * EPI_LD + l] * kSkinnyScale;
+        const __half c1 = __float2half_rn(v);
+        a.bt2[(int64_t)l * a.ldb + o0 + row] = c1;
+        a.bt2[(int64_t)(RP + l) * a.ldb + o0 + row] = __float2half_rn((v - __half2float(c1)) * kLoScale);
       }
     }
-  }
+  // (4) Gram partial Y^T Y (rows past nrow are zero): the upper triangle in 4 x 4 blocks,
+  // each block's rows split over four adjacent lanes (row r to lane r mod 4), reduced by
+  // shuffles and mirrored on writing
   if (a.gram_mode) {
-#pragma unroll
-    for (int l = 0; l < RPp; ++l)
-      if (l < RP) Ps[et * EPI_LD + l] = y[l];
-    named_sync(1, BM);
-    const int npair = RP * RP;
-    for (int e = et; e < npair; e += BM) {
-      const int i = e / RP, c = e % RP;
+    const int nb = RP / 4, nblk = nb * (nb + 1) / 2, npair = RP * RP, nit = nblk * 4;
+    const int lane = u & 31;
+    for (int base = u - lane; base < nit; base += nthr) {
+      const int it = base + lane;
+      const bool act = it < nit;
+      const int blk = act ? it >> 2 : 0, sp = it & 3;
+      int bi = 0, rem = blk;
+      while (rem >= nb - bi) {
+        rem -= nb - bi;
+        ++bi;
+      }
+      const int bj = bi + rem;
+      const float* pi = Ps + 4 * bi;
+      const float* pj = Ps + 4 * bj;
+      const bool wr = act && sp == 0;
       if (a.gram_mode == 1) {
-        float g0 = 0.f, g1 = 0.f;
-        int r = 0;
-        for (; r + 1 < nrow; r += 2) {
-          g0 = fmaf(Ps[r * EPI_LD + i], Ps[r * EPI_LD + c], g0);
-          g1 = fmaf(Ps[(r + 1) * EPI_LD + i], Ps[(r + 1) * EPI_LD + c], g1);
+        float acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+        if (act)
+#pragma unroll 4
+          for (int r = sp; r < BM; r += 4) {
+            const float* pr = pi + r * EPI_LD;
+            const float* qr = pj + r * EPI_LD;
+            const float uu[4] = {pr[0], pr[1], pr[2], pr[3]}, vv[4] = {qr[0], qr[1], qr[2], qr[3]};
+#pragma unroll
+            for (int i4 = 0; i4 < 4; ++i4)
+#pragma unroll
+              for (int j4 = 0; j4 < 4; ++j4) acc[i4 * 4 + j4] = fmaf(uu[i4], vv[j4], acc[i4 * 4 + j4]);
+          }
+        float* gp = reinterpret_cast<float*>(a.gram_part) + t * npair;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          float v = acc[e];
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          if (wr) {
+            const int i = 4 * bi + e / 4, j = 4 * bj + e % 4;
+            gp[i * RP + j] = v;
+            gp[j * RP + i] = v;
+          }
         }
-        if (r < nrow) g0 = fmaf(Ps[r * EPI_LD + i], Ps[r * EPI_LD + c], g0);
-        reinterpret_cast<float*>(a.gram_part)[t * npair + e] = g0 + g1;
       } else {
-        float hi = 0.f, lo = 0.f;
-        for (int r = 0; r < nrow; ++r) {
-          const float x = Ps[r * EPI_LD + i], z = Ps[r * EPI_LD + c];
-          const float p = x * z, pe = fmaf(x, z, -p);
-          const float s = hi + p, bb = s - hi;
-          lo += ((hi - (s - bb)) + (p - bb)) + pe;
-          hi = s;
+        // double-float accumulation: exact products (fma residual), two-sum of the running total
+        float hi[16], lo[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
+        if (act)
+#pragma unroll 1
+          for (int r = sp; r < BM; r += 4) {
+            const float* pr = pi + r * EPI_LD;
+            const float* qr = pj + r * EPI_LD;
+            const float uu[4] = {pr[0], pr[1], pr[2], pr[3]}, vv[4] = {qr[0], qr[1], qr[2], qr[3]};
+#pragma unroll
+            for (int i4 = 0; i4 < 4; ++i4)
+#pragma unroll
+              for (int j4 = 0; j4 < 4; ++j4) {
+                const int e = i4 * 4 + j4;
+                const float x = uu[i4], z = vv[j4];
+                const float p = x * z, pe = fmaf(x, z, -p);
+                const float sum = hi[e] + p, bb = sum - hi[e];
+                lo[e] += ((hi[e] - (sum - bb)) + (p - bb)) + pe;
+                hi[e] = sum;
+              }
+          }
+        double* gp = reinterpret_cast<double*>(a.gram_part) + t * npair;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          double d = (double)hi[e] + (double)lo[e];
+          d += __shfl_xor_sync(0xffffffffu, d, 1);
+          d += __shfl_xor_sync(0xffffffffu, d, 2);
+          if (wr) {
+            const int i = 4 * bi + e / 4, j = 4 * bj + e % 4;
+            gp[i * RP + j] = d;
+            gp[j * RP + i] = d;
+          }
         }
-        reinterpret_cast<double*>(a.gram_part)[t * npair + e] = (double)hi + (double)lo;
       }
     }
   }
-  named_sync(1, BM);
+  named_sync(bar, nthr);   // Ps and Ts free again
+}
+
+// Out-of-line entry for the epilogue warps (rare: more completions than the deferred
+// list holds), so the finish's register blocks do not weigh on the streaming loop.
+template <int RPp>
+__device__ __noinline__ void tile_finish_epi(const TcArgs& a, int64_t t, int nseg, int et, float* Ps, float* Ts,
+                                             const float* csc, float zi) {
+  tile_finish<RPp>(a, t, nseg, et, BM, 1, Ps, Ts, csc, zi);
 }
 
 // One TMA producer loop over this CTA's stages [g0, g1).  Zsrc stages are two
@@ -281,6 +370,12 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_err;   // set by any role that gives up; every loop polls it
   __shared__ int s_stop, s_last;   // epilogue-wide decisions, written between two named barriers
+  // tiles this CTA completes, deferred to the end of the kernel where all warps share the work
+  __shared__ long long s_pend_t[kMaxPend];
+  __shared__ int s_pend_nseg[kMaxPend];
+  __shared__ int s_npend;
+  __shared__ float s_csc[kMaxRP];
+  __shared__ float s_zi;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x;
   const int64_t S = a.S, ks = a.ks, K = a.K;
@@ -306,7 +401,10 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     // rescales it): do nothing, and make the rest of the iteration skip too.
     s_err = (ctl && (ctl->abort || ctl->range_err)) ? 2 : 0;
     if (ctl && ctl->range_err) ctl->abort = 1;
+    s_npend = 0;
+    s_zi = a.zscale ? a.zscale[1] : 1.f;
   }
+  if (tid < kMaxRP) s_csc[tid] = (tid < a.RP && a.cscale) ? a.cscale[tid] : 1.f;
   if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
   __syncthreads();
   tc_fence_after();
@@ -435,7 +533,7 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     const int q4 = warp & 3;                 // TMEM lane quarter this warp may access
     const int row = q4 * 32 + lane;          // tile row held by this thread
     const uint32_t tlane = (uint32_t)(q4 * 32) << 16;
-    int ch = 0;
+    int ch = 0, npend = 0;
     int64_t g = g0;
     for (;;) {
       named_sync(1, BM);
@@ -487,8 +585,19 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       named_sync(1, BM);
       if (et == 0) s_last = (atomicAdd(&a.counters[t], 1u) == (unsigned)(nseg - 1));
       named_sync(1, BM);
-      if (s_last) tile_finish<RPp>(a, t, nseg, et, Ps, Ts);
+      if (s_last) {
+        if (npend < kMaxPend) {
+          if (et == 0) {
+            s_pend_t[npend] = t;
+            s_pend_nseg[npend] = nseg;
+          }
+          ++npend;
+        } else {
+          tile_finish_epi<RPp>(a, t, nseg, et, Ps, Ts, s_csc, s_zi);
+        }
+      }
     }
+    if (et == 0) s_npend = npend;
   }
 
   tc_fence_before();
@@ -497,6 +606,9 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     tc_fence_after();
     tmem_dealloc(tbase, kTmemCols);
   }
+  if (!s_err)
+    for (int k = 0; k < s_npend; ++k)
+      tile_finish<RPp>(a, s_pend_t[k], s_pend_nseg[k], tid, kThreads, 0, Ps, Ts, s_csc, s_zi);
 }
 
 // Column c of a row-major rows x RP operand B -> rows c and RP + c of the split
