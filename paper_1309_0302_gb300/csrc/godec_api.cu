@@ -76,6 +76,7 @@ struct godec_ctx {
   TcGeom tg[2];                        // work split of even (Z) and odd (Z^T) products
   float* part = nullptr;               // stream-K partial slots
   unsigned* counters = nullptr;        // per-tile arrival counters
+  int* pend = nullptr;                 // per-CTA lists of deferred tile completions
   int64_t ncounters = 0;
   char* gparts = nullptr;              // per product: tiles x RP x RP Gram partials (double room)
   size_t gpart_stride = 0;
@@ -230,6 +231,8 @@ void prod(godec_ctx* c, int i, float* out, bool want_bt2, const float* T0, const
   l.prescaled = 1;   // Z and Z^T are stored as (X - S) s_Z
   l.gram_part = gpart(c, i);
   l.gram_mode = gram_mode;
+  l.t_upper = 1;     // slot normalisers are inverses of upper-triangular factors
+  l.pend = c->pend;
   l.ctl = c->ctl;
   PROF(c, 0, c->st, launch_prod_tc(l, c->st));
 }
@@ -453,6 +456,7 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ea.Z16 = c->Z16;
   ea.Zt16 = c->Zt16;
   ea.zscale = c->ctl->zscale;
+  ea.max_nnz = c->p.k;
   PROF(c, 8, st, launch_emit(ea, c->nsm, st));
   if (c->Z) PROF(c, 9, st, launch_z_update(ea, c->nsm, st));
 }
@@ -684,7 +688,7 @@ void godec_destroy(godec_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   free_graphs(c);
   void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->bt2, c->cs, c->rescale_tmp, c->LA, c->LB, c->Q1, c->Q2,
-                  c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->gparts, c->g64, c->gscr,
+                  c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->pend, c->gparts, c->g64, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
                   c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1]};
   for (void* p : ptrs) cudaFree(p);
@@ -747,8 +751,10 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   const int RP = c->RP, np = c->nprod;
   const size_t rr = (size_t)RP * RP;
   c->X = X;
-  c->ldz = (n + 3) / 4 * 4;
-  c->ldzt = (m + 3) / 4 * 4;
+  // rows of the working copies start on 256-byte boundaries: every 128-byte TMA box row
+  // is then one whole cache line (a 40000-byte pitch, say, splits every other one)
+  c->ldz = (n + 63) / 64 * 64;
+  c->ldzt = (m + 63) / 64 * 64;
   CKI(dalloc(&c->Z, (size_t)m * c->ldz));
   CKI(dalloc(&c->Zt, (size_t)n * c->ldzt));
   CKI(dalloc(&c->A1, (size_t)n * RP));
@@ -776,6 +782,11 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   size_t npart = 0;
   for (const TcGeom& g : c->tg) npart = std::max(npart, (size_t)g.tiles * g.maxseg * 128 * RP);
   CKI(dalloc(&c->part, npart));
+  {
+    size_t npend = 0;
+    for (const TcGeom& g : c->tg) npend = std::max(npend, (size_t)g.G * g.maxpend);
+    CKI(dalloc(&c->pend, npend));
+  }
   const int64_t tiles = prod_tiles(mx);
   c->ncounters = tiles;
   CKI(dalloc(&c->counters, (size_t)tiles));
@@ -1184,6 +1195,7 @@ static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz
   float *Bp = nullptr, *part = nullptr, *Yp = nullptr, *Zt = nullptr, *aux = nullptr;
   void* Bs = nullptr;
   unsigned* cnt = nullptr;
+  int* pend = nullptr;
   bool ok = cudaMallocAsync(reinterpret_cast<void**>(&Bp), (size_t)K * RP * sizeof(float), st) == cudaSuccess &&
             cudaMallocAsync(&Bs, (size_t)2 * RP * ldb * 2, st) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&aux), (size_t)(4 + RP) * sizeof(float), st) == cudaSuccess &&
@@ -1191,6 +1203,8 @@ static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz
                             st) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&Yp), (size_t)rows * RP * sizeof(float), st) == cudaSuccess &&
             cudaMallocAsync(reinterpret_cast<void**>(&cnt), (size_t)geom.tiles * sizeof(unsigned), st) == cudaSuccess &&
+            cudaMallocAsync(reinterpret_cast<void**>(&pend), (size_t)geom.G * geom.maxpend * sizeof(int), st) ==
+                cudaSuccess &&
             (!trans || cudaMallocAsync(reinterpret_cast<void**>(&Zt), (size_t)n * ldt * sizeof(float), st) == cudaSuccess);
   bool mapped = false;
   if (ok) {
@@ -1216,11 +1230,12 @@ static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz
       l.out = Yp;
       l.cscale = aux + 4;
       l.zscale = aux;
+      l.pend = pend;
       launch_prod_tc(l, st);
       launch_unpad_copy(Yp, rows, RP, Y, r, st);
     }
   }
-  void* ptrs[] = {Bp, Bs, aux, part, Yp, cnt, Zt};
+  void* ptrs[] = {Bp, Bs, aux, part, Yp, cnt, pend, Zt};
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, st);
   if (!ok) {

@@ -132,6 +132,7 @@ void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const f
 struct TcGeom {
   int64_t tiles = 0, ks = 0, S = 0;
   int G = 0, maxseg = 0;
+  int maxpend = 0;           // completions one CTA may owe (list entries per CTA)
 };
 TcGeom tc_geometry(int64_t rows, int64_t K, int nsm);
 int tc_rpp(int RP);
@@ -168,6 +169,8 @@ struct TcLaunch {
   int prescaled;           // Zsrc already holds x s_Z
   void* gram_part;
   int gram_mode;
+  int t_upper;             // Tn upper triangular (inverse of an upper-triangular factor)
+  int* pend;               // G x geom.maxpend ints of scratch
   Ctl* ctl;
 };
 void launch_prod_tc(const TcLaunch& l, cudaStream_t st);
@@ -265,6 +268,7 @@ struct EmitArgs {
   void* Z16;               // nullable bf16 copies (same strides)
   void* Zt16;
   const float* zscale;     // Z and Zt are stored scaled by zscale[0]
+  long long max_nnz;       // bound on the support of S (k): the z-update grid
 };
 void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st);
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);

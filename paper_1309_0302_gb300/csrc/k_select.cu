@@ -547,18 +547,37 @@ __device__ __forceinline__ void z_flag(Ctl* ctl, bool bad) {
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) ctl->range_err = 1;
 }
 
+// Row and column of a linear index (idx = i n + j): a float estimate of the quotient,
+// refined once from the remainder and then corrected exactly in integers (no 64-bit
+// division; the estimate is off by at most a couple of units for any size).
+__device__ __forceinline__ void split_idx(long long idx, long long n, float ninv, long long& i, long long& j) {
+  long long q = (long long)((float)idx * ninv);
+  long long r = idx - q * n;
+  q += (long long)((float)r * ninv);
+  r = idx - q * n;
+  while (r < 0) {
+    --q;
+    r += n;
+  }
+  while (r >= n) {
+    ++q;
+    r -= n;
+  }
+  i = q;
+  j = r;
+}
+
+// One entry per thread (the grid covers the largest possible support, k).
 __global__ void k_z_restore(EmitArgs a) {
   Ctl* ctl = a.ctl;
-  if (ctl->abort) return;
-  const int ob = ctl->cur ^ 1;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctl->abort || (long long)blockIdx.x * blockDim.x >= ctl->nnz_prev) return;
   const long long nnz = ctl->nnz_prev;
-  const long long* Sidx = a.S_idx[ob];
   const float zs = a.zscale ? a.zscale[0] : 1.f;
   bool bad = false;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long idx = Sidx[e];
-    long long i = idx / a.n, j = idx % a.n;
+  if (e < nnz) {
+    long long i, j;
+    split_idx(a.S_idx[ctl->cur ^ 1][e], a.n, 1.f / (float)a.n, i, j);
     z_write(a, i, j, a.X[i * a.ldx + j], zs, bad);
   }
   z_flag(ctl, bad);
@@ -566,18 +585,16 @@ __global__ void k_z_restore(EmitArgs a) {
 
 __global__ void k_z_scatter(EmitArgs a) {
   Ctl* ctl = a.ctl;
-  if (ctl->abort) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctl->abort || (long long)blockIdx.x * blockDim.x >= ctl->nnz_cur) return;
   const int cb = ctl->cur;
   const long long nnz = ctl->nnz_cur;
-  const long long* Sidx = a.S_idx[cb];
-  const float* Sval = a.S_val[cb];
   const float zs = a.zscale ? a.zscale[0] : 1.f;
   bool bad = false;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long idx = Sidx[e];
-    long long i = idx / a.n, j = idx % a.n;
-    z_write(a, i, j, a.X[i * a.ldx + j] - Sval[e], zs, bad);
+  if (e < nnz) {
+    long long i, j;
+    split_idx(a.S_idx[cb][e], a.n, 1.f / (float)a.n, i, j);
+    z_write(a, i, j, a.X[i * a.ldx + j] - a.S_val[cb][e], zs, bad);
   }
   z_flag(ctl, bad);
 }
@@ -644,8 +661,11 @@ void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st) {
 }
 
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st) {
-  k_z_restore<<<(unsigned)(2 * nsm), 256, 0, st>>>(a);
-  k_z_scatter<<<(unsigned)(2 * nsm), 256, 0, st>>>(a);
+  (void)nsm;
+  const long long nb = (a.max_nnz + 255) / 256;
+  const unsigned grid = (unsigned)(nb > 0 ? nb : 1);
+  k_z_restore<<<grid, 256, 0, st>>>(a);
+  k_z_scatter<<<grid, 256, 0, st>>>(a);
 }
 
 }  // namespace godec

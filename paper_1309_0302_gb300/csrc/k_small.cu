@@ -54,63 +54,139 @@ k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restri
 // ---- block helpers on 64 x 64 (padded RP x RP) matrices in shared memory -----------
 // Thread (ty, tx) owns rows ty + 16a and columns tx + 16b, a, b in 0..3.
 
-// Upper Cholesky G = R^T R in place of R (R must start as a copy of G).  Pivots j < nchk
-// below thr are raised to thr and reported through *bad.  One barrier per column.
-__device__ void chol_upper(float (*R)[LD], int n, int nchk, float thr, int* bad) {
-  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  for (int j = 0; j < n; ++j) {
-    float d = R[j][j];
-    if (j < nchk && !(d > thr)) {
-      if (threadIdx.x == 0) *bad = 1;
-      d = thr > 0.f ? thr : 1e-30f;
+// Inverse of the 8 x 8 upper-triangular block at (k0, k0) of R into Ui (lane c < 8
+// back-substitutes column c; rd[i] = 1 / R[k0+i][k0+i]).
+__device__ __forceinline__ void block_inverse8(const float (*R)[LD], int k0, const float* rd, float (*Ui)[LD],
+                                               int ui0, int lane) {
+  if (lane < 8) {
+    float x[8];
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+      float sacc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int j = i + 1; j < 8; ++j) sacc = fmaf(-R[k0 + i][k0 + j], x[j], sacc);
+      x[i] = (i <= lane) ? sacc * rd[i] : 0.f;
     }
-    const float invd = 1.f / d;
-    const float sq = sqrtf(d);
-    // rows a > j, columns c >= a: R[a][c] -= R[j][a] R[j][c] / d (row j is not written here)
 #pragma unroll
-    for (int ia = 0; ia < 4; ++ia) {
-      const int a = ty + 16 * ia;
-      if (a <= j || a >= n) continue;
-      const float rja = R[j][a] * invd;
+    for (int i = 0; i < 8; ++i) Ui[ui0 + i][ui0 + lane] = x[i];
+  }
+}
+
+// Upper Cholesky G = R^T R in place of R (R must start as a copy of G; n a multiple
+// of 8).  Right-looking in 8 x 8 blocks: warp 0 factors the diagonal block (and inverts
+// its factor), all threads solve the block row and update the trailing upper triangle;
+// four barriers per block step instead of one per column.  Pivots j < nchk below thr
+// are raised to thr and reported through *bad.
+constexpr int CB = 8;
+__device__ void chol_upper(float (*R)[LD], int n, int nchk, float thr, int* bad) {
+  __shared__ float Ui[CB][LD];   // inverse of the current diagonal factor
+  __shared__ float rs[CB];       // 1 / diagonal of the current factor
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k0 = 0; k0 < n; k0 += CB) {
+    if (tid < 32) {
+      // (1) diagonal block: column-by-column Cholesky inside one warp (two entries a lane)
+      for (int j = 0; j < CB; ++j) {
+        float d = R[k0 + j][k0 + j];
+        if (k0 + j < nchk && !(d > thr)) {
+          if (lane == 0) *bad = 1;
+          d = thr > 0.f ? thr : 1e-30f;
+        }
+        const float rsq = rsqrtf(d), sq = d * rsq, invd = rsq * rsq;
 #pragma unroll
-      for (int ib = 0; ib < 4; ++ib) {
-        const int c = tx + 16 * ib;
-        if (c >= a && c < n) R[a][c] -= rja * R[j][c];
+        for (int h = 0; h < 2; ++h) {
+          const int e = lane + 32 * h, a = e / CB, c = e % CB;
+          if (a > j && c >= a) R[k0 + a][k0 + c] -= R[k0 + j][k0 + a] * R[k0 + j][k0 + c] * invd;
+        }
+        __syncwarp();
+        if (lane >= j && lane < CB) R[k0 + j][k0 + lane] = (lane == j) ? sq : R[k0 + j][k0 + lane] * rsq;
+        if (lane == 0) rs[j] = rsq;
+        __syncwarp();
+      }
+      block_inverse8(R, k0, rs, Ui, 0, lane);
+    }
+    __syncthreads();
+    // (2) block row: R[k0+i][j] = sum_{t <= i} Ui[t][i] A[k0+t][j] for j beyond the block
+    const int j0 = k0 + CB, w = n - j0;
+    float pv[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + SMALL_THREADS * h;
+      if (e < CB * w) {
+        const int i = e / w, j = j0 + e % w;
+        float sacc = 0.f;
+#pragma unroll
+        for (int t = 0; t < CB; ++t)
+          if (t <= i) sacc = fmaf(Ui[t][i], R[k0 + t][j], sacc);
+        pv[h] = sacc;
       }
     }
     __syncthreads();
-    // scale row j; nothing reads it again as an unscaled pivot row
-    if (ty == 0)
-      for (int c = j + tx; c < n; c += 16) R[j][c] = (c == j) ? sq : R[j][c] / sq;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + SMALL_THREADS * h;
+      if (e < CB * w) R[k0 + e / w][j0 + e % w] = pv[h];
+    }
+    __syncthreads();
+    // (3) trailing upper triangle: A[a][c] -= sum_t R[k0+t][a] R[k0+t][c], c >= a
+    for (int e = tid; e < w * w; e += SMALL_THREADS) {
+      const int a = j0 + e / w, c = j0 + e % w;
+      if (c >= a) {
+        float sacc = R[a][c];
+#pragma unroll
+        for (int t = 0; t < CB; ++t) sacc = fmaf(-R[k0 + t][a], R[k0 + t][c], sacc);
+        R[a][c] = sacc;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += SMALL_THREADS) {
+  for (int e = tid; e < n * n; e += SMALL_THREADS) {
     const int i = e / n, c = e % n;
     if (c < i) R[i][c] = 0.f;
   }
   __syncthreads();
 }
 
-// Inverse of an upper-triangular R into Ri.  Columns are independent back
-// substitutions R x = e_c; four threads of one warp share a column (the dot product
-// over j is split four ways and reduced with shuffles), so no block barrier is needed.
-// Requires 256 threads; R must be visible to all threads on entry.
-__device__ void tri_inverse(const float (*R)[LD], float (*Ri)[LD], int n, float* dinv) {
-  const int col = threadIdx.x >> 2, part = threadIdx.x & 3;
-  for (int e = threadIdx.x; e < kMaxRP; e += SMALL_THREADS) dinv[e] = (e < n) ? 1.f / R[e][e] : 0.f;
+// Inverse Ri of an upper-triangular R (n a multiple of 8), in 8 x 8 blocks: warps
+// invert the diagonal blocks in parallel, then block diagonals d = 1, 2, ... follow from
+// T_ij = -T_ii sum_{k=i+1..j} R_ik T_kj.  One thread per output entry: the 8 threads of
+// a column (adjacent lanes) each form one entry of S = sum R_ik T_kj and exchange them
+// by shuffles for the product with T_ii.  R must be visible to all threads on entry;
+// Ri must not alias R.
+__device__ void tri_inverse(const float (*R)[LD], float (*Ri)[LD], int n, float*) {
+  __shared__ float rdg[kMaxRP];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nb = n / CB;
+  for (int e = tid; e < kMaxRP * kMaxRP; e += SMALL_THREADS) Ri[e / kMaxRP][e % kMaxRP] = 0.f;
+  if (tid < n) rdg[tid] = 1.f / R[tid][tid];
   __syncthreads();
-  for (int i = part; i < kMaxRP; i += 4) Ri[i][col] = 0.f;
-  __syncwarp();
-  for (int i = n - 1; i >= 0; --i) {
-    float s = 0.f;
-    if (col < n && i <= col)
-      for (int j = i + 1 + part; j <= col; j += 4) s = fmaf(R[i][j], Ri[j][col], s);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (part == 0 && col < n && i <= col) Ri[i][col] = ((i == col ? 1.f : 0.f) - s) * dinv[i];
-    __syncwarp();
+  for (int b = warp; b < nb; b += SMALL_THREADS / 32) block_inverse8(R, b * CB, rdg + b * CB, Ri, b * CB, lane);
+  __syncthreads();
+  for (int d = 1; d < nb; ++d) {
+    const int nitem = (nb - d) * CB * CB;   // (block i, column of block i + d, row a)
+    for (int base = tid - lane; base < nitem; base += SMALL_THREADS) {
+      const int it = base + lane;
+      const bool act = it < nitem;
+      const int a = it & 7, cc = (it >> 3) & 7, bi = it >> 6;
+      const int i0 = bi * CB, col = (bi + d) * CB + cc;
+      float s0 = 0.f, s1 = 0.f;
+      if (act) {
+        int k = i0 + CB;
+        for (; k + 1 <= col; k += 2) {
+          s0 = fmaf(R[i0 + a][k], Ri[k][col], s0);
+          s1 = fmaf(R[i0 + a][k + 1], Ri[k + 1][col], s1);
+        }
+        if (k <= col) s0 = fmaf(R[i0 + a][k], Ri[k][col], s0);
+      }
+      const float sv = s0 + s1;
+      float tacc = 0.f;
+#pragma unroll
+      for (int u = 0; u < CB; ++u) {
+        const float su = __shfl_sync(0xffffffffu, sv, u, 8);
+        if (act) tacc = fmaf(Ri[i0 + a][i0 + u], su, tacc);
+      }
+      if (act) Ri[i0 + a][col] = -tacc;
+    }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // C = A B (n x n, A upper triangular if a_upper); C may alias A or B.
@@ -143,16 +219,42 @@ __device__ void mat_mul(const float (*A)[LD], const float (*B)[LD], float (*C)[L
   __syncthreads();
 }
 
-// D = src (RP x RP, zero-padded to 64 x 64); src == nullptr gives the identity.
-__device__ void load_mat(float (*D)[LD], const float* src, int RP) {
-  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
-    const int i = e / kMaxRP, j = e % kMaxRP;
-    float v;
-    if (src) v = (i < RP && j < RP) ? src[i * RP + j] : 0.f;
-    else v = (i == j) ? 1.f : 0.f;
-    D[i][j] = v;
+// D = src (RP x RP, zero-padded to 64 x 64; src == nullptr gives the identity), with no
+// closing barrier: several loads in flight, then one barrier.
+// (256 threads: all sixteen loads of a thread are issued before the first store)
+constexpr int kPerThread = kMaxRP * kMaxRP / SMALL_THREADS;
+__device__ void load_mat_nb(float (*D)[LD], const float* src, int RP) {
+  float v[kPerThread];
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int e = threadIdx.x + k * SMALL_THREADS, i = e / kMaxRP, j = e % kMaxRP;
+    if (src) v[k] = (i < RP && j < RP) ? __ldcg(src + i * RP + j) : 0.f;
+    else v[k] = (i == j) ? 1.f : 0.f;
   }
-  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int e = threadIdx.x + k * SMALL_THREADS;
+    D[e / kMaxRP][e % kMaxRP] = v[k];
+  }
+}
+
+// Gram (double, RP x RP) into float G, padded block set to the identity, no closing
+// barrier; *nf is set if the Gram holds NaN/Inf.
+__device__ void load_gram_nb(float (*G)[LD], const double* g64, int r, int RP, int* nf) {
+  double v[kPerThread];
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int e = threadIdx.x + k * SMALL_THREADS, i = e / kMaxRP, j = e % kMaxRP;
+    v[k] = (i < r && j < r) ? __ldcg(g64 + i * RP + j) : (i == j ? 1.0 : 0.0);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int e = threadIdx.x + k * SMALL_THREADS;
+    bad |= !isfinite(v[k]);
+    G[e / kMaxRP][e % kMaxRP] = (float)v[k];
+  }
+  if (bad) *nf = 1;
 }
 
 __device__ void store_mat(float* dst, const float (*S)[LD], int RP) {
@@ -162,23 +264,9 @@ __device__ void store_mat(float* dst, const float (*S)[LD], int RP) {
 // Gram (double, RP x RP) into float G, padded block set to the identity.  False if
 // the Gram holds NaN/Inf.
 __device__ bool load_gram(float (*G)[LD], const double* g64, int r, int RP) {
-  __shared__ int s_nf;
-  if (threadIdx.x == 0) s_nf = 0;
-  __syncthreads();
-  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
-    const int i = e / kMaxRP, j = e % kMaxRP;
-    float v;
-    if (i < r && j < r) {
-      const double d = g64[i * RP + j];
-      if (!isfinite(d)) s_nf = 1;
-      v = (float)d;
-    } else {
-      v = (i == j) ? 1.f : 0.f;
-    }
-    G[i][j] = v;
-  }
-  __syncthreads();
-  return s_nf == 0;
+  int nf = 0;
+  load_gram_nb(G, g64, r, RP, &nf);
+  return __syncthreads_or(nf) == 0;
 }
 
 // Largest |M[i][j]| over the n x n block (all threads get it).
@@ -244,7 +332,6 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
   float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
   float (*R)[LD] = G + kMaxRP;
   float (*Ri)[LD] = R + kMaxRP;
-  __shared__ float dinv[kMaxRP];
   if (!load_gram(G, g64, r, RP)) {
     if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
     return;
@@ -260,7 +347,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
     if (threadIdx.x == 0 && !(hi <= alarm_ratio * lo)) { ctl->alarm = 1; ctl->abort = 1; }
   }
   store_mat(Rout, R, RP);
-  tri_inverse(R, Ri, RP, dinv);
+  tri_inverse(R, Ri, RP, nullptr);
   store_mat(Tout, Ri, RP);
 }
 
@@ -294,29 +381,34 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
   float (*B)[LD] = A + kMaxRP;
   float (*C)[LD] = B + kMaxRP;
   float (*D)[LD] = C + kMaxRP;
-  __shared__ float dinv[kMaxRP];
+  float (*E1)[LD] = D + kMaxRP;    // L1
+  float (*E2)[LD] = E1 + kMaxRP;   // L2
+  float (*TA)[LD] = E2 + kMaxRP;   // T_app
+  float (*PI)[LD] = TA + kMaxRP;   // Pi
   const int r = a.r, RP = a.RP;
   const int cur = ctl->slot_parity, nxt = 1 - cur;
-  load_mat(B, a.R_app[cur], RP);                     // B = R_app
-  if (a.L1) {
-    load_mat(C, a.L1, RP);
-    mat_mul(C, B, B, RP, true);                      // B = L1 R_app
-  }
-  if (a.L2) {
-    load_mat(C, a.L2, RP);
-    mat_mul(C, B, B, RP, true);                      // B = L2 L1 R_app
-  }
+  // every input in one phase: the kernel runs beside a product that saturates the
+  // memory system, where each dependent round trip costs microseconds
+  int nf = 0;
+  load_mat_nb(B, a.R_app[cur], RP);                  // B = R_app
+  if (a.L1) load_mat_nb(E1, a.L1, RP);
+  if (a.L2) load_mat_nb(E2, a.L2, RP);
+  if (a.fast && a.g_is_p) load_mat_nb(TA, a.T_app[cur], RP);
+  if (a.pi_mode == 1) load_mat_nb(PI, a.Pi, RP);
+  if (a.fast) load_gram_nb(A, a.g64, r, RP, &nf);
+  const int any_nf = __syncthreads_or(nf);
+  if (a.L1) mat_mul(E1, B, B, RP, true);             // B = L1 R_app
+  if (a.L2) mat_mul(E2, B, B, RP, true);             // B = L2 L1 R_app
   if (a.fast) {
-    if (!load_gram(A, a.g64, r, RP)) {
+    if (any_nf) {
       if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
       return;
     }
     if (a.g_is_p) {                                  // Gram of Q~ = T^T G T
-      load_mat(C, a.T_app[cur], RP);
-      mat_mul(A, C, D, RP, false);                   // D = G T
+      mat_mul(A, TA, D, RP, false);                  // D = G T
       for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
         const int i = e / kMaxRP, j = e % kMaxRP;
-        A[i][j] = C[j][i];                           // A = T^T
+        A[i][j] = TA[j][i];                          // A = T^T
       }
       __syncthreads();
       mat_mul(A, D, A, RP, false);                   // A = T^T G T
@@ -338,14 +430,12 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
     __syncthreads();
   }
   store_mat(a.R_next[nxt], A, RP);
-  tri_inverse(A, C, RP, dinv);
+  tri_inverse(A, C, RP, nullptr);
   store_mat(a.T_next[nxt], C, RP);
   if (a.pi_mode == 2) {
     normalise_into(B, a.Pi, RP, ctl, true);
   } else if (a.pi_mode == 1) {
-    __syncthreads();
-    load_mat(C, a.Pi, RP);
-    mat_mul(B, C, D, RP, true);                      // D = R_app Pi
+    mat_mul(B, PI, D, RP, true);                     // D = R_app Pi
     normalise_into(D, a.Pi, RP, ctl, false);
   }
 }
@@ -621,12 +711,13 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
 }
 
 constexpr size_t kSmall4 = 4 * kMaxRP * LD * sizeof(float);
+constexpr size_t kSmall8 = 8 * kMaxRP * LD * sizeof(float);
 
 }  // namespace
 
 cudaError_t prepare_small_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall8);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
   return e;
@@ -668,7 +759,7 @@ void launch_slot(const SlotLaunch& l, cudaStream_t st) {
   a.RP = l.RP;
   a.alarm_ratio = l.alarm_ratio;
   a.ctl = l.ctl;
-  k_slot<<<1, SMALL_THREADS, kSmall4, st>>>(a);
+  k_slot<<<1, SMALL_THREADS, kSmall8, st>>>(a);
 }
 
 void launch_rank(const double* g64, int r, int RP, double rank_tol, Ctl* ctl, cudaStream_t st) {

@@ -56,22 +56,22 @@ namespace {
 using namespace tc;
 
 constexpr int BM = 128, BK = 64;   // rows per tile, K per stage (4 MMA steps of 16)
-constexpr int NA = 4;              // shared-memory slots for Zsrc tiles (TMA ring)
+constexpr int NA = 5;              // shared-memory slots for Zsrc tiles (TMA ring)
 constexpr int NS = 3;              // stage slots: skinny-operand tile in shared memory + converted
                                    // Zsrc tile in TMEM, freed together by one MMA commit
 constexpr int kThreads = 480;
 constexpr int kConvWarps = 8;
 constexpr uint32_t kTmemCols = 512, kTA0 = 256, kTASlot = 64;
 constexpr int EPI_LD = kMaxRP + 1;   // odd stride: row-wise and column-wise accesses are conflict-free
-constexpr int kMaxPend = 8;          // tile completions deferred to the end of the kernel
 constexpr size_t kBoxA = (size_t)BM * 32 * 4;               // one 32-column float32 box, 16 KB
 constexpr size_t kStageA = 2 * kBoxA;                       // 32 KB
 constexpr size_t kStageB = (size_t)2 * kMaxRP * BK * 2;     // 16 KB (room for 2 x 64 rows of 64 halves)
 constexpr size_t kOffA = 0;
 constexpr size_t kOffB = kOffA + NA * kStageA;
-constexpr size_t kOffEpi = kOffB + NS * kStageB;
+// tile completion runs after the stream, in the then idle Zsrc ring
 constexpr size_t kEpiBytes = (size_t)BM * EPI_LD * 4 + (size_t)kMaxRP * kMaxRP * 4;
-constexpr size_t kTcSmem = kOffEpi + kEpiBytes + 1024;       // + alignment slack
+constexpr size_t kTcSmem = kOffB + NS * kStageB + 1024;     // + alignment slack
+static_assert(kEpiBytes <= NA * kStageA, "completion staging fits the Zsrc ring");
 constexpr uint32_t kWaitLimit = 1u << 20;
 constexpr float kLoScale = 2048.f, kLoInv = 1.f / 2048.f;
 #ifndef GODEC_TC_CHUNK
@@ -98,6 +98,9 @@ struct TcArgs {
   int prescaled;            // Zsrc holds x s_Z already (s_Z then only undone in the epilogue)
   void* gram_part;
   int gram_mode;
+  int t_upper;              // the normaliser is upper triangular
+  int* pend;                // G x maxpend: tiles each CTA completes, deferred to its end
+  int maxpend;
   Ctl* ctl;
 };
 
@@ -134,70 +137,96 @@ __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nth
   if (u == 0) a.counters[t] = 0u;
   const float* Tn = (a.ctl && a.ctl->slot_parity) ? a.Tn1 : a.Tn0;
   // (1) rows of the tile into Ps: sum of the slots, unscaled.  Consecutive threads take
-  // consecutive float4s of a slot (coalesced); up to four slots are in flight at once.
+  // consecutive float4s of a slot (coalesced); four items per thread and up to four slots
+  // each are in flight at once.
   const float4* part = reinterpret_cast<const float4*>(a.part + t * a.maxseg * (int64_t)BM * RP);
   const int64_t slot4 = (int64_t)BM * RP4;
-  for (int it = u; it < BM * RP4; it += nthr) {
-    const int row = it / RP4, c = (it % RP4) * 4;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int nitem = BM * RP4;
+  for (int it0 = u; it0 < nitem; it0 += 4 * nthr) {
+    float4 acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int s0 = 0; s0 < nseg; s0 += 4) {
-      float4 v[4];
+      float4 v[4][4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        v[k] = (s0 + k < nseg) ? __ldcg(part + (s0 + k) * slot4 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        acc.x += v[k].x;
-        acc.y += v[k].y;
-        acc.z += v[k].z;
-        acc.w += v[k].w;
+        for (int k = 0; k < 4; ++k) {
+          const int it = it0 + q * nthr;
+          v[q][k] = (s0 + k < nseg && it < nitem) ? __ldcg(part + (s0 + k) * slot4 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[q].x += v[q][k].x;
+          acc[q].y += v[q][k].y;
+          acc[q].z += v[q][k].z;
+          acc[q].w += v[q][k].w;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int it = it0 + q * nthr;
+      if (it < nitem) {
+        const int row = it / RP4, c = (it % RP4) * 4;
+        float* pr = Ps + row * EPI_LD + c;
+        const bool live = row < nrow;
+        pr[0] = live ? acc[q].x * (csc[c] * zi) : 0.f;
+        pr[1] = live ? acc[q].y * (csc[c + 1] * zi) : 0.f;
+        pr[2] = live ? acc[q].z * (csc[c + 2] * zi) : 0.f;
+        pr[3] = live ? acc[q].w * (csc[c + 3] * zi) : 0.f;
       }
     }
-    float* pr = Ps + row * EPI_LD + c;
-    const bool live = row < nrow;
-    pr[0] = live ? acc.x * (csc[c] * zi) : 0.f;
-    pr[1] = live ? acc.y * (csc[c + 1] * zi) : 0.f;
-    pr[2] = live ? acc.z * (csc[c + 2] * zi) : 0.f;
-    pr[3] = live ? acc.w * (csc[c + 3] * zi) : 0.f;
   }
   if (Tn)
     for (int e = u; e < RP * RP4; e += nthr)
       *reinterpret_cast<float4*>(Ts + (e / RP4) * RPp + (e % RP4) * 4) = __ldg(reinterpret_cast<const float4*>(Tn) + e);
   named_sync(bar, nthr);
-  // (2) Y <- Y T in place: a warp takes a slab of 16 rows (all of their columns, so only
-  // its own reads precede its own writes), each lane a 4 x 8 block of it
+  // (2) Y <- Y T.  A warp takes an 8-column group of the output for one half of the rows
+  // (lane: rows lane and lane + 32 of the half), so T is read at warp-uniform addresses;
+  // with T upper triangular the group needs rows c <= its last column only.  Results stay
+  // in registers until every warp has read Y (at most two items per warp for nthr >= 256).
   if (Tn) {
-    const int lane = u & 31, rg = lane >> 3, l0 = (lane & 7) * 8;
-    const bool colok = l0 < RP;
-    for (int slab = u >> 5; slab < BM / 16; slab += nthr >> 5) {
-      const int r0 = slab * 16 + rg * 4;
-      float acc[4][8];
+    const int lane = u & 31, nw = nthr >> 5, CB = RP / 8, nit = 2 * CB;
+    float acc[2][2][8];
+    int item[2] = {-1, -1};
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+    for (int k = 0; k < 2; ++k) {
+      const int itm = (u >> 5) + k * nw;
+      if (itm < nit) {
+        item[k] = itm;
+        const int cg = itm >> 1, r0 = (itm & 1) * 64 + lane, l0 = cg * 8;
+        const int cend = a.t_upper ? l0 + 8 : RP;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-      if (colok)
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[k][i][j] = 0.f;
 #pragma unroll 2
-        for (int c = 0; c < RP; ++c) {
-          float yv[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) yv[i] = Ps[(r0 + i) * EPI_LD + c];
+        for (int c = 0; c < cend; ++c) {
+          const float y0 = Ps[r0 * EPI_LD + c], y1 = Ps[(r0 + 32) * EPI_LD + c];
           const float4 t0 = *reinterpret_cast<const float4*>(Ts + c * RPp + l0);
           const float4 t1 = *reinterpret_cast<const float4*>(Ts + c * RPp + l0 + 4);
           const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(yv[i], tv[j], acc[i][j]);
+          for (int j = 0; j < 8; ++j) {
+            acc[k][0][j] = fmaf(y0, tv[j], acc[k][0][j]);
+            acc[k][1][j] = fmaf(y1, tv[j], acc[k][1][j]);
+          }
         }
-      __syncwarp();
-      if (colok)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) Ps[(r0 + i) * EPI_LD + l0 + j] = acc[i][j];
-      __syncwarp();
+      }
     }
+    named_sync(bar, nthr);   // every read of Y done before it is overwritten
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (item[k] >= 0) {
+        const int cg = item[k] >> 1, r0 = (item[k] & 1) * 64 + lane, l0 = cg * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          Ps[r0 * EPI_LD + l0 + j] = acc[k][0][j];
+          Ps[(r0 + 32) * EPI_LD + l0 + j] = acc[k][1][j];
+        }
+      }
     named_sync(bar, nthr);
   }
   // (3) outputs: rows (float4 per thread), and the split transposed operand (one column
@@ -305,14 +334,6 @@ __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nth
   named_sync(bar, nthr);   // Ps and Ts free again
 }
 
-// Out-of-line entry for the epilogue warps (rare: more completions than the deferred
-// list holds), so the finish's register blocks do not weigh on the streaming loop.
-template <int RPp>
-__device__ __noinline__ void tile_finish_epi(const TcArgs& a, int64_t t, int nseg, int et, float* Ps, float* Ts,
-                                             const float* csc, float zi) {
-  tile_finish<RPp>(a, t, nseg, et, BM, 1, Ps, Ts, csc, zi);
-}
-
 // One TMA producer loop over this CTA's stages [g0, g1).  Zsrc stages are two
 // 32-column float32 boxes (the second is skipped when it starts at or beyond K);
 // skinny-operand stages are one 64-column float16 box.
@@ -363,17 +384,14 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm + kOffA;
   unsigned char* sB = sm + kOffB;
-  float* Ps = reinterpret_cast<float*>(sm + kOffEpi);
+  float* Ps = reinterpret_cast<float*>(sm + kOffA);   // completion staging: the ring, once idle
   float* Ts = Ps + BM * EPI_LD;
   __shared__ uint64_t afull[NA], aempty[NA], bfull[NS], tfull[NS], sfree[NS];
   __shared__ uint64_t accfull[2], accempty[2], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_err;   // set by any role that gives up; every loop polls it
   __shared__ int s_stop, s_last;   // epilogue-wide decisions, written between two named barriers
-  // tiles this CTA completes, deferred to the end of the kernel where all warps share the work
-  __shared__ long long s_pend_t[kMaxPend];
-  __shared__ int s_pend_nseg[kMaxPend];
-  __shared__ int s_npend;
+  __shared__ int s_npend;   // tiles this CTA completes (listed in a.pend), done at its end
   __shared__ float s_csc[kMaxRP];
   __shared__ float s_zi;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -586,15 +604,11 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       if (et == 0) s_last = (atomicAdd(&a.counters[t], 1u) == (unsigned)(nseg - 1));
       named_sync(1, BM);
       if (s_last) {
-        if (npend < kMaxPend) {
-          if (et == 0) {
-            s_pend_t[npend] = t;
-            s_pend_nseg[npend] = nseg;
-          }
-          ++npend;
-        } else {
-          tile_finish_epi<RPp>(a, t, nseg, et, Ps, Ts, s_csc, s_zi);
+        if (et == 0) {
+          if (npend < a.maxpend) a.pend[(int64_t)c * a.maxpend + npend] = (int)t;
+          else if (ctl) ctl->abort = 1;   // cannot happen with the host's bound; never skip silently
         }
+        ++npend;
       }
     }
     if (et == 0) s_npend = npend;
@@ -606,9 +620,14 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     tc_fence_after();
     tmem_dealloc(tbase, kTmemCols);
   }
-  if (!s_err)
-    for (int k = 0; k < s_npend; ++k)
-      tile_finish<RPp>(a, s_pend_t[k], s_pend_nseg[k], tid, kThreads, 0, Ps, Ts, s_csc, s_zi);
+  // completions: the whole CTA on each tile whose last segment was this CTA's
+  const int np = s_err ? 0 : (s_npend < a.maxpend ? s_npend : a.maxpend);
+  for (int k = 0; k < np; ++k) {
+    const int64_t t = a.pend[(int64_t)c * a.maxpend + k];
+    const int64_t c_first = cta_of(t * ks, S, G);
+    const int nseg = (int)(cta_of((t + 1) * ks - 1, S, G) - c_first + 1);
+    tile_finish<RPp>(a, t, nseg, tid, kThreads, 0, Ps, Ts, s_csc, s_zi);
+  }
 }
 
 // Column c of a row-major rows x RP operand B -> rows c and RP + c of the split
@@ -708,6 +727,9 @@ TcGeom tc_geometry(int64_t rows, int64_t K, int nsm) {
     if (cl - cf + 1 > maxseg) maxseg = (int)(cl - cf + 1);
   }
   g.maxseg = maxseg;
+  // tiles meeting one CTA's range (its completions are listed for the end of the kernel)
+  const int64_t span = (g.S + g.G - 1) / g.G;
+  g.maxpend = (int)((span + g.ks - 1) / g.ks + 1);
   return g;
 }
 
@@ -749,6 +771,9 @@ void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   a.zscale = l.zscale;
   a.gram_part = l.gram_part;
   a.gram_mode = l.gram_mode;
+  a.t_upper = l.t_upper;
+  a.pend = l.pend;
+  a.maxpend = l.geom.maxpend;
   a.ctl = l.ctl;
   const CUtensorMap& A = *reinterpret_cast<const CUtensorMap*>(l.mapA);
   const CUtensorMap& B = *reinterpret_cast<const CUtensorMap*>(l.mapB);
