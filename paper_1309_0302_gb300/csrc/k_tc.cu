@@ -15,11 +15,13 @@
 // (D[:, :RP] + 2^-11 D[:, RP:2RP]) / (s_Z s_B).  float16 MMAs run at twice the TF32
 // rate with twice the K per instruction.
 //
-// Converter warps move each 128 x 64 tile of Zsrc from shared memory into tensor memory
-// as the two packed float16 column blocks (h1, h2) and free the shared-memory slot at
-// once, so the TMA ring only has to cover the DRAM latency.  Zsrc is either stored
-// already scaled (the working copy of X - S, whose writers keep it inside the float16
-// range) or scaled here (a caller's matrix, scale from its exact maximum).
+// A copier thread moves each landed 128 x 64 float32 tile of Zsrc from shared memory into
+// tensor memory (tcgen05.cp) and frees the shared-memory slot when the copy completes;
+// converter warps then turn the tile into the two packed float16 blocks (h1, h2) in place
+// with TMEM loads and stores.  The working warps thus leave the shared-memory load path
+// to the TMA stream.  Zsrc is either stored already scaled (the working copy of X - S,
+// whose writers keep it inside the float16 range) or scaled here (a caller's matrix,
+// scale from its exact maximum).
 //
 // Work split: the (128-row tile, 64-wide K stage) iteration space is cut into equal
 // contiguous ranges, one per persistent CTA ("stream-K"), so every SM streams the same
@@ -34,13 +36,14 @@
 //
 // Warps: 0 TMA producer of Zsrc tiles, 1 MMA issuer (and TMEM owner), 2-9 converters
 // (two per TMEM lane quarter, one per 32-column half of the tile), 10-13 epilogue,
-// 14 TMA producer of the skinny operand.
-// TMEM (512 columns): 0-255 two accumulators of 128 columns, 256-447 three A slots of
-// 64 columns (32 of packed h1, 32 of packed h2).
-// Synchronisation per stage: TMA -> afull -> converters -> aempty (slot refilled);
-// converters -> tfull (after the skinny tile's bfull too) -> MMA -> sfree -> both the
-// converters' TMEM slot and the skinny TMA slot.  The MMA issuer, the one serial role,
-// waits once and commits once per stage.
+// 14 TMA producer of the skinny operand, 15 copier.
+// TMEM (512 columns): 0-255 two accumulators of 128 columns, 256-447 three stage slots of
+// 64 columns (the float32 tile, then per 32-column half 16 columns of packed h1 and 16
+// of packed h2).
+// Synchronisation per stage: TMA -> afull -> copier (after sfree) -> aempty (slot
+// refilled) and cpdone -> converters -> tfull (after the skinny tile's bfull too) -> MMA
+// -> sfree -> the stage slot and the skinny TMA slot.  The MMA issuer waits once and
+// commits once per stage.
 // Every wait is bounded; a timeout sets ctl->timeout and the CTA drains and exits.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -59,7 +62,7 @@ constexpr int BM = 128, BK = 64;   // rows per tile, K per stage (4 MMA steps of
 constexpr int NA = 5;              // shared-memory slots for Zsrc tiles (TMA ring)
 constexpr int NS = 3;              // stage slots: skinny-operand tile in shared memory + converted
                                    // Zsrc tile in TMEM, freed together by one MMA commit
-constexpr int kThreads = 480;
+constexpr int kThreads = 512;
 constexpr int kConvWarps = 8;
 constexpr uint32_t kTmemCols = 512, kTA0 = 256, kTASlot = 64;
 constexpr int EPI_LD = kMaxRP + 1;   // odd stride: row-wise and column-wise accesses are conflict-free
@@ -349,10 +352,10 @@ __device__ void produce(const CUtensorMap* map, unsigned char* ring, int nslot, 
     if (!mbar_wait(&emptyb[s], ph ^ 1u, kWaitLimit)) { note_timeout(ctl, s_err); break; }
     unsigned char* dst = ring + (size_t)s * slot_bytes;
     if (IS_A) {
-      const bool two = kst * BK + 32 < K;
-      mbar_expect_tx(&fullb[s], two ? 2 * box_bytes : box_bytes);
+      // both boxes always: columns at and past K are zero-filled
+      mbar_expect_tx(&fullb[s], 2 * box_bytes);
       tma_load_2d(dst, map, &fullb[s], (int)(kst * BK), (int)(t * BM));
-      if (two) tma_load_2d(dst + box_bytes, map, &fullb[s], (int)(kst * BK + 32), (int)(t * BM));
+      tma_load_2d(dst + box_bytes, map, &fullb[s], (int)(kst * BK + 32), (int)(t * BM));
     } else {
       mbar_expect_tx(&fullb[s], box_bytes);
       tma_load_2d(dst, map, &fullb[s], (int)(kst * BK), 0);
@@ -386,7 +389,7 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   unsigned char* sB = sm + kOffB;
   float* Ps = reinterpret_cast<float*>(sm + kOffA);   // completion staging: the ring, once idle
   float* Ts = Ps + BM * EPI_LD;
-  __shared__ uint64_t afull[NA], aempty[NA], bfull[NS], tfull[NS], sfree[NS];
+  __shared__ uint64_t afull[NA], aempty[NA], bfull[NS], tfull[NS], sfree[NS], cpdone[NS];
   __shared__ uint64_t accfull[2], accempty[2], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_err;   // set by any role that gives up; every loop polls it
@@ -402,12 +405,13 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   if (tid == 0) {
     for (int s = 0; s < NA; ++s) {
       mbar_init(&afull[s], 1);
-      mbar_init(&aempty[s], kConvWarps);
+      mbar_init(&aempty[s], 1);   // the copier's commit
     }
     for (int s = 0; s < NS; ++s) {
       mbar_init(&bfull[s], 1);
       mbar_init(&tfull[s], kConvWarps);
       mbar_init(&sfree[s], 1);
+      mbar_init(&cpdone[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accfull[b], 1);
@@ -461,12 +465,14 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
           if (!mbar_wait(&tfull[st], ph, kWaitLimit)) { note_timeout(ctl, &s_err); break; }
           tc_fence_after();
           const uint64_t db = sdesc_k128(sB + (size_t)st * kStageB);
-          const uint32_t ah = tbase + kTA0 + (uint32_t)st * kTASlot, al = ah + 32;
+          // slot columns: [h of K 0..31 | l of K 0..31 | h of K 32..63 | l of K 32..63], 16 each
+          const uint32_t aslot = tbase + kTA0 + (uint32_t)st * kTASlot;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t off = (uint64_t)((kk * 16 * 2) >> 4);   // 32 bytes per 16-wide K step
-            mma_f16_ta(dcol, ah + kk * 8, db + off, id_hi, acc);
-            mma_f16_ta(dcol + RP, al + kk * 8, db + off, id_lo, 1u);
+            const uint32_t ah = aslot + (uint32_t)((kk >> 1) * 32 + (kk & 1) * 8);
+            mma_f16_ta(dcol, ah, db + off, id_hi, acc);
+            mma_f16_ta(dcol + RP, ah + 16, db + off, id_lo, 1u);
             acc = 1u;
           }
           mma_commit(&sfree[st]);
@@ -482,56 +488,67 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       mma_commit(&mma_done);
       if (!mbar_wait(&mma_done, 0, kWaitLimit)) note_timeout(ctl, &s_err);
     }
+  } else if (warp == 15) {
+    // ---------------- copier: landed Zsrc stage -> its TMEM stage slot ----------------
+    if (lane == 0) {
+      int sa = 0, st = 0;
+      uint32_t pha = 0, ph = 0;
+      int64_t n = 0;
+      for (int64_t g = g0; g < g1 && !s_err; ++g) {
+        if (!mbar_wait(&afull[sa], pha, kWaitLimit) || !mbar_wait(&sfree[st], ph ^ 1u, kWaitLimit)) {
+          note_timeout(ctl, &s_err);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dst = tbase + kTA0 + (uint32_t)st * kTASlot;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const uint64_t d = sdesc_k128(sA + (size_t)sa * kStageA + b * kBoxA);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) tmem_cp_128x256b(dst + (uint32_t)(b * 32 + k * 8), d + (uint64_t)(2 * k));
+        }
+        mma_commit(&cpdone[st]);   // the converters may read the slot
+        mma_commit(&aempty[sa]);   // the shared-memory slot may be refilled
+        ++n;
+        if (++sa == NA) { sa = 0; pha ^= 1u; }
+        if (++st == NS) { st = 0; ph ^= 1u; }
+      }
+      // the last copies have finished reading shared memory and writing TMEM
+      for (int64_t j = (n > NS ? n - NS : 0); j < n; ++j)
+        if (!mbar_wait(&cpdone[(int)(j % NS)], (uint32_t)((j / NS) & 1), kWaitLimit)) note_timeout(ctl, &s_err);
+    }
   } else if (warp < 2 + kConvWarps) {
-    // ---------------- converters: Zsrc tile -> TMEM as packed (h1, h2) ----------------
+    // ---------------- converters: float32 stage in TMEM -> packed (h1, h2) in place ----------------
     const int q = (warp - 2) >> 2;              // 32-column half of the tile handled by this warp
-    const int row = (warp & 3) * 32 + lane;     // this warp may only touch its TMEM lane quarter
-    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;   // this warp's TMEM lane quarter
     const float zs = (!PRESCALED && a.zscale) ? a.zscale[0] : 1.f;
-    int sa = 0, st = 0;
-    uint32_t pha = 0, ph = 0;
-    int64_t kst = g0 % ks;
+    int st = 0;
+    uint32_t ph = 0;
     for (int64_t g = g0; g < g1; ++g) {
       if (__any_sync(0xffffffffu, s_err != 0)) break;
-      if (!warp_wait(&afull[sa], pha, lane)) {
-        if (lane == 0) note_timeout(ctl, &s_err);
-        break;
-      }
-      const bool present = q == 0 || kst * BK + 32 < K;   // the second box is not loaded past K
-      // row `row` of a 32-column box: 8 chunks of 16 bytes, chunk u stored at u ^ (row & 7)
-      const float4* src = reinterpret_cast<const float4*>(sA + (size_t)sa * kStageA + q * kBoxA + row * 128);
-      float4 xv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) xv[u] = present ? src[u ^ (row & 7)] : make_float4(0.f, 0.f, 0.f, 0.f);
-      uint32_t h[16], l2[16];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 x = xv[u];
-        float xs[4] = {x.x, x.y, x.z, x.w}, hi[4], lo[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (!PRESCALED) xs[e] *= zs;
-          hi[e] = __uint_as_float(__float_as_uint(xs[e]) & 0xFFFFE000u);
-          lo[e] = (xs[e] - hi[e]) * kLoScale;
-        }
-        h[2 * u] = pack_h2(hi[0], hi[1]);
-        h[2 * u + 1] = pack_h2(hi[2], hi[3]);
-        l2[2 * u] = pack_h2(lo[0], lo[1]);
-        l2[2 * u + 1] = pack_h2(lo[2], lo[3]);
-      }
-      // every lane has consumed its loads (the packed words depend on them): the slot
-      // may be refilled
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&aempty[sa]);
-      if (++sa == NA) { sa = 0; pha ^= 1u; }
-      if (!warp_wait(&sfree[st], ph ^ 1u, lane)) {
+      if (!warp_wait(&cpdone[st], ph, lane)) {
         if (lane == 0) note_timeout(ctl, &s_err);
         break;
       }
       tc_fence_after();
-      const uint32_t ta = tbase + kTA0 + (uint32_t)st * kTASlot + tlane + (uint32_t)(q * 16);
+      const uint32_t ta = tbase + kTA0 + (uint32_t)st * kTASlot + tlane + (uint32_t)(q * 32);
+      float xs[32];
+      tmem_ld32(ta, xs);
+      uint32_t h[16], l2[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        float x0 = xs[2 * k], x1 = xs[2 * k + 1];
+        if (!PRESCALED) {
+          x0 *= zs;
+          x1 *= zs;
+        }
+        const float h0 = __uint_as_float(__float_as_uint(x0) & 0xFFFFE000u);
+        const float h1 = __uint_as_float(__float_as_uint(x1) & 0xFFFFE000u);
+        h[k] = pack_h2(h0, h1);
+        l2[k] = pack_h2((x0 - h0) * kLoScale, (x1 - h1) * kLoScale);
+      }
       tmem_st16(ta, h);
-      tmem_st16(ta + 32, l2);
+      tmem_st16(ta + 16, l2);
       tmem_wait_st();
       tc_fence_before();
       // the skinny tile of this stage has landed too: the MMA issuer waits on tfull alone
@@ -541,7 +558,6 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       }
       if (lane == 0) mbar_arrive(&tfull[st]);
       if (++st == NS) { st = 0; ph ^= 1u; }
-      if (++kst == ks) kst = 0;
     }
   } else {
     // ---------------- epilogue: TMEM -> running sums -> partial slot, tile completion ----------------

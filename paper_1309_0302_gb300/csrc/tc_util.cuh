@@ -26,15 +26,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Wait for the phase with the given parity to complete; gives up after `limit` polls
-// (each poll may suspend the thread for a short hardware-defined time).
+// Wait for the phase with the given parity to complete; gives up after `limit` polls.
+// Each poll suspends the thread until the phase completes or kPollNs nanoseconds pass,
+// so a waiting warp issues almost nothing (busy polling floods the memory-instruction
+// pipe that the loads, barriers and TMEM accesses of the working warps go through);
+// the longest wait is about limit * kPollNs.
+constexpr uint32_t kPollNs = 2000;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kPollNs)
         : "memory");
     if (done) return true;
   }
@@ -105,6 +109,12 @@ __device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uin
 }
 
 // Arrive on `bar` once every MMA issued so far by this thread has completed.
+// Shared memory -> TMEM copy of a 128-row x 32-byte slice described by a shared-memory
+// matrix descriptor (lane = row, 8 consecutive 32-bit columns), issued by one thread.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t desc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(desc) : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
