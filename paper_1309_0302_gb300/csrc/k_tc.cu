@@ -60,7 +60,7 @@ using namespace tc;
 
 constexpr int BM = 128, BK = 64;   // rows per tile, K per stage (4 MMA steps of 16)
 constexpr int NA = 5;              // shared-memory slots for Zsrc tiles (TMA ring)
-constexpr int NS = 3;              // stage slots: skinny-operand tile in shared memory + converted
+constexpr int NS = 4;              // stage slots: skinny-operand tile in shared memory + converted
                                    // Zsrc tile in TMEM, freed together by one MMA commit
 constexpr int kThreads = 512;
 constexpr int kConvWarps = 8;
