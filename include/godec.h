@@ -231,6 +231,33 @@ godec_status godec_profile_trace(godec_ctx* ctx, int32_t cap, int32_t* cls, int3
                                  int32_t* count);
 
 /*
+ * Differentiated form (q = 0): the gradient with respect to X of a loss of L_T after T
+ * unrolled iterations of Algorithm 1 at q = 0 (L_t = Y1 (A2^T Y1)^{-1} Y2^T, eq. lr_app;
+ * S_t = P_Omega_t(X - L_t), eq. raw_lss) with the supports Omega_1 .. Omega_{T-1} held
+ * fixed (the selection is piecewise constant in X), starting from S_0 = 0.
+ *   X        : device, m x ldx float32 (ldx*4 a multiple of 16 bytes)
+ *   A1       : device, n x r float32 row-major (the same A1 as the forward run), r <= 64
+ *   T        : number of iterations, >= 1
+ *   supports : host array of T-1 device pointers; supports[t-1] holds the int64 linear
+ *              indices (i*n + j, no duplicates, any order) of Omega_t
+ *   support_nnz : host array of the T-1 sizes
+ *   dLoss/dL_T, one of: gU (device m x g) and gV (device n x g) row-major, g <= 64,
+ *              meaning gU gV^T; or gL (device, m x ldg float32, ldg*4 a multiple of
+ *              16 bytes).  The unused pointers are null.
+ *   dX       : device, m x lddx float32, overwritten with the gradient
+ * The per-iteration factors are recomputed in a forward sweep (checkpointed for the
+ * backward sweep), so only the supports are needed from the forward run.  Scratch is
+ * allocated and freed on `stream` (stream-ordered); the call does not synchronise.
+ * Float32 arithmetic with the float32-accurate tensor-core products; the sparse products
+ * accumulate with float atomics (results may differ in the last bits between runs).
+ * GODEC_ERR_ARG on invalid arguments, GODEC_ERR_OOM when scratch cannot be allocated.
+ */
+godec_status godec_backward(const float* X, int64_t m, int64_t n, int64_t ldx, const float* A1, int32_t r,
+                            int32_t T, const int64_t* const* supports, const int64_t* support_nnz,
+                            const float* gU, const float* gV, int32_t g_rank, const float* gL, int64_t ldg,
+                            float* dX, int64_t lddx, void* stream);
+
+/*
  * Entry-wise hard threshold of a dense matrix (eq. raw_lss, Algorithm 1
  * line 9, with L = 0): the nonzero subset of the k largest |R|, ties by
  * ascending linear index, runs the same kernels as the S-step.

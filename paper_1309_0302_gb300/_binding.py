@@ -61,6 +61,8 @@ def _declare(lib):
         "godec_hard_threshold": ([_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, _P, C.c_int64, i64p, _P],
                                  C.c_int),
         "godec_mul_ZB": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
+        "godec_backward": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, C.c_int32, C.POINTER(_P), i64p,
+                            _P, _P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
         "godec_mul_ZtC": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -275,6 +277,47 @@ def mul_ZB(Z, B, stream=None):
 def mul_ZtC(Z, Cm, stream=None):
     """W = Z^T @ C on the GPU (Z m x n, C m x r)."""
     return _mul("godec_mul_ZtC", Z, Cm, stream)
+
+
+def backward(X, A1, T: int, supports, gU=None, gV=None, gL=None, stream=None):
+    """dLoss/dX of T unrolled q = 0 iterations with frozen supports (godec_backward).
+
+    X (m, n) and A1 (n, r) CUDA float32; ``supports`` the T-1 int64 CUDA tensors of
+    linear indices of Omega_1 .. Omega_{T-1}; dLoss/dL_T as gU (m, g) and gV (n, g)
+    (meaning gU gV^T) or dense gL (m, n).  Returns dX (m, n).
+    """
+    torch = _torch()
+    m, n = X.shape
+    r = A1.shape[1]
+    X = _pad_rows(X)
+    A1 = A1.contiguous()
+    if len(supports) != T - 1:
+        raise ValueError("need T - 1 supports")
+    sup = [s.contiguous() for s in supports]
+    ptrs = (_P * max(T - 1, 1))(*[_ptr(s) for s in sup]) if T > 1 else None
+    nnz = (C.c_int64 * max(T - 1, 1))(*[int(s.numel()) for s in sup]) if T > 1 else None
+    dXp = torch.empty((m, (n + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+    if gL is not None:
+        gL = _pad_rows(gL)
+        args = (None, None, 0, _ptr(gL), gL.stride(0))
+    else:
+        gU, gV = gU.contiguous(), gV.contiguous()
+        args = (_ptr(gU), _ptr(gV), gU.shape[1], None, 0)
+    st = library().godec_backward(_ptr(X), m, n, X.stride(0), _ptr(A1), r, int(T), ptrs, nnz, *args,
+                                  _ptr(dXp), dXp.stride(0), _stream_ptr(stream))
+    _check(st, "godec_backward")
+    return dXp[:, :n]
+
+
+def _pad_rows(A):
+    """A with unit column stride, a 16-byte multiple row stride and 16-byte alignment."""
+    torch = _torch()
+    m, n = A.shape
+    if A.stride(1) != 1 or A.stride(0) % 4 or A.data_ptr() % 16:
+        Ap = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=A.device)
+        Ap[:, :n] = A
+        return Ap
+    return A
 
 
 def run_host(X: np.ndarray, A1: np.ndarray, r: int, k: int, q: int, n_iter: int, tol: float = 1e-7,

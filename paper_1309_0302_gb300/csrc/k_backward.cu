@@ -1,0 +1,236 @@
+// Kernels of the differentiated form (q = 0, supports frozen): tall x small products,
+// cross Grams A^T B of tall matrices, sparse (COO) times tall products, low-rank values
+// at COO positions, and the dense accumulation of low-rank terms into dX.  The streaming
+// products with the iterate Z_t run on the tensor-core kernel of the forward pass.
+#include "godec_internal.cuh"
+
+namespace godec {
+
+namespace {
+
+constexpr int BW_THREADS = 256;
+
+// C = A^T B over a fixed row partition: block g adds rows [g R / G, (g+1) R / G) into
+// part[g] (a x b, float64); a, b <= 64.  Each thread owns entries tid + 256 k of a x b.
+__global__ void __launch_bounds__(BW_THREADS)
+k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __restrict__ B, int64_t ldb, int b,
+             int64_t rows, double* __restrict__ part) {
+  constexpr int CH = 32;
+  __shared__ float sA[CH][kMaxRP + 1], sB[CH][kMaxRP + 1];
+  const int tid = threadIdx.x, G = gridDim.x, g = blockIdx.x;
+  const int64_t r0 = (int64_t)g * rows / G, r1 = (int64_t)(g + 1) * rows / G;
+  const int ne = a * b;
+  double acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+  for (int64_t c0 = r0; c0 < r1; c0 += CH) {
+    const int nr = (int)(r1 - c0 < CH ? r1 - c0 : CH);
+    __syncthreads();
+    for (int e = tid; e < CH * kMaxRP; e += BW_THREADS) {
+      const int rr = e / kMaxRP, cc = e % kMaxRP;
+      sA[rr][cc] = (rr < nr && cc < a) ? A[(c0 + rr) * lda + cc] : 0.f;
+      sB[rr][cc] = (rr < nr && cc < b) ? B[(c0 + rr) * ldb + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int e = tid + k * BW_THREADS;
+      if (e < ne) {
+        const int i = e / b, j = e % b;
+        float s = 0.f;
+#pragma unroll 8
+        for (int rr = 0; rr < CH; ++rr) s = fmaf(sA[rr][i], sB[rr][j], s);
+        acc[k] += (double)s;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int e = tid + k * BW_THREADS;
+    if (e < ne) part[(int64_t)g * ne + e] = acc[k];
+  }
+}
+
+// out[e] = sum over the partition partials in partition order (deterministic); with a
+// row stride ldo for the a x b result (ldo >= b).
+__global__ void k_cross_sum(const double* __restrict__ part, int G, int a, int b, double* __restrict__ out, int ldo) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x, ne = a * b;
+  if (e >= ne) return;
+  double t = 0.0;
+  for (int g = 0; g < G; ++g) t += part[(int64_t)g * ne + e];
+  out[(e / b) * ldo + e % b] = t;
+}
+
+// C[i][c] = beta C[i][c] + alpha sum_l A[i][l] Bm[l][c] (Bm small, a x c, row stride ldbm;
+// transposed: Bm[c][l]).  One thread per output entry; Bm staged in shared memory.
+template <typename TB>
+__global__ void __launch_bounds__(BW_THREADS)
+k_tall_small(const float* __restrict__ A, int64_t lda, int a, const TB* __restrict__ Bm, int ldbm, int trans, int c,
+             int64_t rows, float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+  __shared__ float sB[kMaxRP][kMaxRP + 1];   // a, c <= 64
+  for (int e = threadIdx.x; e < a * c; e += BW_THREADS) {
+    const int l = e / c, cc = e % c;
+    sB[l][cc] = (float)(trans ? Bm[cc * ldbm + l] : Bm[l * ldbm + cc]);
+  }
+  __syncthreads();
+  const int64_t o = (int64_t)blockIdx.x * BW_THREADS + threadIdx.x;
+  if (o >= rows * c) return;
+  const int64_t i = o / c;
+  const int cc = (int)(o % c);
+  const float* ar = A + i * lda;
+  float s = 0.f;
+  for (int l = 0; l < a; ++l) s = fmaf(ar[l], sB[l][cc], s);
+  float* cp = C + i * ldc + cc;
+  *cp = (beta != 0.f ? beta * *cp : 0.f) + alpha * s;
+}
+
+// out[row][c] += v_e B[col][c] (or, transposed, out[col][c] += v_e B[row][c]) for the COO
+// entries e (linear index row * n + col); float atomics.
+__global__ void k_spmm(const int64_t* __restrict__ idx, const float* __restrict__ val, int64_t nnz, int64_t n,
+                       const float* __restrict__ B, int64_t ldb, int c, int trans, float* __restrict__ out,
+                       int64_t ldo) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnz * c) return;
+  const int64_t e = t / c;
+  const int cc = (int)(t % c);
+  const int64_t row = idx[e] / n, col = idx[e] % n;
+  const float v = val[e];
+  if (trans) atomicAdd(out + col * ldo + cc, v * B[row * ldb + cc]);
+  else atomicAdd(out + row * ldo + cc, v * B[col * ldb + cc]);
+}
+
+// vals[e] = sum_c U[row][c] V[col][c] at the COO positions; with sub, also
+// D[row][col] -= vals[e].
+__global__ void k_eval_lr(const int64_t* __restrict__ idx, int64_t nnz, int64_t n, const float* __restrict__ U,
+                          int64_t ldu, const float* __restrict__ V, int64_t ldv, int K, float* __restrict__ vals,
+                          float* __restrict__ D, int64_t ldd) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const int64_t row = idx[e] / n, col = idx[e] % n;
+  const float* u = U + row * ldu;
+  const float* v = V + col * ldv;
+  float s = 0.f;
+  for (int c = 0; c < K; ++c) s = fmaf(u[c], v[c], s);
+  if (vals) vals[e] = s;
+  if (D) D[row * ldd + col] -= s;
+}
+
+// Z[row][col] = vals[e] at the COO positions (Z holds a copy of X elsewhere).
+__global__ void k_scatter_set(const int64_t* __restrict__ idx, const float* __restrict__ vals, int64_t nnz, int64_t n,
+                              float* __restrict__ Z, int64_t ldz) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const int64_t row = idx[e] / n, col = idx[e] % n;
+  Z[row * ldz + col] = vals[e];
+}
+
+// D (m x n) = beta D + U V^T, U m x K (ldu), V n x K (ldv), K <= 192: 64 x 64 output
+// tiles, 256 threads each owning a 4 x 4 block, K in chunks of 32 through shared memory.
+__global__ void __launch_bounds__(BW_THREADS)
+k_outer_acc(const float* __restrict__ U, int64_t ldu, const float* __restrict__ V, int64_t ldv, int K, int64_t m,
+            int64_t n, float beta, float* __restrict__ D, int64_t ldd) {
+  constexpr int TM = 64, KC = 32;
+  __shared__ float sU[KC][TM + 1], sV[KC][TM + 1];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TM;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    __syncthreads();
+    for (int e = tid; e < KC * TM; e += BW_THREADS) {
+      const int rr = e / KC, kk = e % KC;   // consecutive threads along k: rows of U / V are contiguous
+      const int64_t gi = i0 + rr, gj = j0 + rr;
+      sU[kk][rr] = (gi < m && k0 + kk < K) ? U[gi * ldu + k0 + kk] : 0.f;
+      sV[kk][rr] = (gj < n && k0 + kk < K) ? V[gj * ldv + k0 + kk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      float u[4], v[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) u[a] = sU[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) v[b] = sV[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(u[a], v[b], acc[a][b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t gi = i0 + ty + 16 * a;
+    if (gi >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t gj = j0 + tx + 16 * b;
+      if (gj < n) {
+        float* d = D + gi * ldd + gj;
+        *d = (beta != 0.f ? beta * *d : 0.f) + acc[a][b];
+      }
+    }
+  }
+}
+
+// y += alpha x
+__global__ void k_axpy(const float* __restrict__ x, float* __restrict__ y, int64_t count, float alpha) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) y[i] = fmaf(alpha, x[i], y[i]);
+}
+
+unsigned blocks_for(int64_t n) { return (unsigned)((n + BW_THREADS - 1) / BW_THREADS); }
+
+}  // namespace
+
+void launch_cross_gram(const float* A, int64_t lda, int a, const float* B, int64_t ldb, int b, int64_t rows,
+                       double* part, int G, double* out, int ldo, cudaStream_t st) {
+  k_cross_part<<<G, BW_THREADS, 0, st>>>(A, lda, a, B, ldb, b, rows, part);
+  k_cross_sum<<<blocks_for((int64_t)a * b), BW_THREADS, 0, st>>>(part, G, a, b, out, ldo);
+}
+
+void launch_tall_small_f(const float* A, int64_t lda, int a, const float* Bm, int ldbm, int trans, int c, int64_t rows,
+                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st) {
+  if (rows * c == 0) return;
+  k_tall_small<float><<<blocks_for(rows * c), BW_THREADS, 0, st>>>(A, lda, a, Bm, ldbm, trans, c, rows, alpha, beta,
+                                                                   C, ldc);
+}
+
+void launch_tall_small_d(const float* A, int64_t lda, int a, const double* Bm, int ldbm, int trans, int c,
+                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st) {
+  if (rows * c == 0) return;
+  k_tall_small<double><<<blocks_for(rows * c), BW_THREADS, 0, st>>>(A, lda, a, Bm, ldbm, trans, c, rows, alpha, beta,
+                                                                    C, ldc);
+}
+
+void launch_spmm(const int64_t* idx, const float* val, int64_t nnz, int64_t n, const float* B, int64_t ldb, int c,
+                 int trans, float* out, int64_t ldo, cudaStream_t st) {
+  if (nnz * c == 0) return;
+  k_spmm<<<blocks_for(nnz * c), BW_THREADS, 0, st>>>(idx, val, nnz, n, B, ldb, c, trans, out, ldo);
+}
+
+void launch_eval_lr(const int64_t* idx, int64_t nnz, int64_t n, const float* U, int64_t ldu, const float* V,
+                    int64_t ldv, int K, float* vals, float* D, int64_t ldd, cudaStream_t st) {
+  if (nnz == 0) return;
+  k_eval_lr<<<blocks_for(nnz), BW_THREADS, 0, st>>>(idx, nnz, n, U, ldu, V, ldv, K, vals, D, ldd);
+}
+
+void launch_scatter_set(const int64_t* idx, const float* vals, int64_t nnz, int64_t n, float* Z, int64_t ldz,
+                        cudaStream_t st) {
+  if (nnz == 0) return;
+  k_scatter_set<<<blocks_for(nnz), BW_THREADS, 0, st>>>(idx, vals, nnz, n, Z, ldz);
+}
+
+void launch_axpy(const float* x, float* y, int64_t count, float alpha, cudaStream_t st) {
+  if (count > 0) k_axpy<<<blocks_for(count), BW_THREADS, 0, st>>>(x, y, count, alpha);
+}
+
+void launch_outer_acc(const float* U, int64_t ldu, const float* V, int64_t ldv, int K, int64_t m, int64_t n,
+                      float beta, float* D, int64_t ldd, cudaStream_t st) {
+  dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 63) / 64));
+  k_outer_acc<<<grid, BW_THREADS, 0, st>>>(U, ldu, V, ldv, K, m, n, beta, D, ldd);
+}
+
+}  // namespace godec
