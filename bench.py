@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kernel", choices=["product", "product_t", "iteration"], default=None,
+    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
@@ -300,6 +300,33 @@ def run_kernel_case(args):
         f = G.mul_ZB if args.kernel == "product" else G.mul_ZtC
         for _ in range(3):
             f(Z, B)
+    elif args.kernel == "backward":
+        # differentiated form at C5 (4096 x 4096, r = 20, q = 0, T = 10): forward iterations and
+        # godec_backward, each timed with CUDA events after one warm-up
+        d = synth.config_c5()
+        r, k, T = d["r"], d["k"], d["T"]
+        X = torch.from_numpy(d["X"]).cuda()
+        A1 = torch.from_numpy(d["A1"]).cuda()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep in range(2):
+            ev[0].record()
+            g = G.GoDec(X, A1, r, k, 0, tol=0.0, max_iter=T)
+            sup = []
+            for t in range(T):
+                g.iterate(1)
+                if t < T - 1:
+                    sup.append(g.S()[0].clone())
+            U, s, V = g.L()
+            g.close()
+            ev[1].record()
+            gU = torch.cat([2.0 * U * s, -2.0 * torch.from_numpy(d["Ustar"]).float().cuda()], 1).contiguous()
+            gV = torch.cat([V, torch.from_numpy(d["Vstar"]).float().cuda()], 1).contiguous()
+            ev[2].record()
+            G.backward(X, A1, T, sup, gU=gU, gV=gV)
+            ev[3].record()
+            torch.cuda.synchronize()
+        print(f"C5 forward {T} iterations (incl. context setup): {ev[0].elapsed_time(ev[1]):.2f} ms, "
+              f"backward: {ev[2].elapsed_time(ev[3]):.2f} ms")
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
         run = G.GoDec(torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda(), R, d["k"], Q)

@@ -289,6 +289,11 @@ def backward(X, A1, T: int, supports, gU=None, gV=None, gL=None, stream=None):
     torch = _torch()
     m, n = X.shape
     r = A1.shape[1]
+    for name, t in (("X", X), ("A1", A1), ("gU", gU), ("gV", gV), ("gL", gL)):
+        if t is not None and (t.dtype != torch.float32 or not t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA float32 tensor")
+    if any(s.dtype != torch.int64 or not s.is_cuda for s in supports):
+        raise ValueError("supports must be CUDA int64 tensors")
     X = _pad_rows(X)
     A1 = A1.contiguous()
     if len(supports) != T - 1:

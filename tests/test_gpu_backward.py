@@ -104,3 +104,38 @@ def test_backward_rejects_bad_arguments():
         G.backward(X, A1, 2, [], gU=gU, gV=gU)           # T - 1 supports missing (binding)
     with pytest.raises(G.GodecError):                    # r above 64 (library)
         G.backward(X, torch.ones((128, 65), device="cuda"), 1, [], gU=gU, gV=gU)
+    with pytest.raises(ValueError):                      # float64 gradient factors
+        G.backward(X, A1, 1, [], gU=gU.double(), gV=gU.double())
+
+
+@pytest.mark.slow
+def test_backward_c5_full_size():
+    """C5 (4096 x 4096, r = 20, k = 2 %, q = 0, T = 10, loss ||L_T - L*||^2 with a rank-20
+    L*): the GPU gradient (low-rank dL/dL_T = [2 U sigma | -2 U*] [V | V*]^T) against the
+    float64 oracle gradient on the GPU's supports."""
+    torch = pytest.importorskip("torch")
+    import paper_1309_0302_gb300 as G
+    d = synth.config_c5()
+    m, n, r, k, T = 4096, 4096, d["r"], d["k"], d["T"]
+    X = torch.from_numpy(d["X"]).cuda()
+    A1 = torch.from_numpy(d["A1"]).cuda()
+    gpu = G.GoDec(X, A1, r, k, 0, tol=0.0, max_iter=T)
+    masks, sup = [], []
+    for t in range(T):
+        gpu.iterate(1)
+        idx = gpu.S()[0]
+        masks.append(idx.cpu().numpy())
+        if t < T - 1:
+            sup.append(idx.clone())
+    U, s, V = gpu.L()
+    gpu.close()
+    Us = torch.from_numpy(d["Ustar"]).float().cuda()
+    Vs = torch.from_numpy(d["Vstar"]).float().cuda()
+    gU = torch.cat([2.0 * U * s, -2.0 * Us], dim=1).contiguous()
+    gV = torch.cat([V, Vs], dim=1).contiguous()
+    dX = G.backward(X, A1, T, sup, gU=gU, gV=gV).cpu().numpy().astype(np.float64)
+    Lstar = d["Ustar"].astype(np.float64) @ d["Vstar"].astype(np.float64).T
+    ref = O.unrolled_vjp(d["X"].astype(np.float64), d["A1"].astype(np.float64), k, T, Lstar, masks)
+    err = _rel(dX, ref)
+    print(f"C5 dX rel err {err:.2e}")
+    assert err <= TOL_DX
