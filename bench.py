@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward"], default=None,
+    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
@@ -327,6 +327,33 @@ def run_kernel_case(args):
             torch.cuda.synchronize()
         print(f"C5 forward {T} iterations (incl. context setup): {ev[0].elapsed_time(ev[1]):.2f} ms, "
               f"backward: {ev[2].elapsed_time(ev[3]):.2f} ms")
+    elif args.kernel == "precision":
+        # precision form at C3 (76800 x 1000, r = 3, k = 1.2e6, q = 2) against the plain float32
+        # form on the same input: iterations/s of each (CUDA events over 10 iterations after 2
+        # warm-up ones) and the distance between the two L factors after those iterations
+        d = synth.config_c3()
+        X = torch.from_numpy(d["X"]).cuda()
+        A1 = torch.from_numpy(d["A1"]).cuda()
+        res = {}
+        for name, prec in (("float32", G.PREC_FP32), ("float16 chain + float32 correction", G.PREC_BF16_REFINE)):
+            g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=0.0, max_iter=100, precision=prec)
+            g.iterate(2)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record(torch.cuda.current_stream())
+            g.iterate(10)
+            ev[1].record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            res[name] = (ev[0].elapsed_time(ev[1]) / 10, [t.double().cpu().numpy() for t in g.L()])
+            g.close()
+        (ta, (Ua, sa, Va)), (tb, (Ub, sb, Vb)) = res.values()
+        Aa, Ab = Ua * sa, Ub * sb
+        aa = np.sum((Aa.T @ Aa) * (Va.T @ Va))
+        bb = np.sum((Ab.T @ Ab) * (Vb.T @ Vb))
+        ab = np.sum((Aa.T @ Ab) * (Va.T @ Vb))
+        dist = float(np.sqrt(max(aa + bb - 2 * ab, 0.0)) / np.sqrt(aa))
+        print(f"C3 float32 form: {ta:.3f} ms/iteration ({1e3 / ta:.1f} it/s); precision form: {tb:.3f} "
+              f"ms/iteration ({1e3 / tb:.1f} it/s); L distance after 12 iterations {dist:.2e}")
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
         run = G.GoDec(torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda(), R, d["k"], Q)

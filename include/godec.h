@@ -47,8 +47,11 @@ typedef enum godec_status {
 /* Arithmetic of the X-streaming products. */
 enum {
   GODEC_PREC_FP32 = 0,        /* float32 X, float32 accumulation */
-  GODEC_PREC_BF16_REFINE = 1  /* bf16 copy of X - S for the power chain, then
-                                 one float32 correction visit (see below) */
+  GODEC_PREC_BF16_REFINE = 1  /* precision form (r <= 32): the power chain streams a
+                                 16-bit (float16, scaled by the power of two s_Z) copy of
+                                 X - S with float32 accumulation; then one float32 visit
+                                 of X - S computes Z V and Z^T U and the tangent-space
+                                 correction of the factors, re-truncated to rank r */
 };
 
 /* Maximum target rank handled by the kernels. */
@@ -71,6 +74,9 @@ typedef struct godec_params {
 
 /* Record per-iteration factors and supports so godec_backward can run. */
 #define GODEC_FLAG_TAPE 1
+/* Precision form only: skip the float32 correction (diagnostic: the float16 chain's own
+   accuracy). */
+#define GODEC_FLAG_NO_REFINE 2
 
 typedef struct godec_ctx godec_ctx;
 
@@ -212,11 +218,13 @@ godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz,
  * and Gram partials), 1 Gram sums, 2 r x r Cholesky (critical path), 3 tall x
  * r x r products, 4 lagged-normaliser updates (side stream), 5 rank test (side
  * stream), 6 core SVD and root, 7 residual pass (S-step), 8 selection control,
- * radix-select rounds and S emit, 9 sparse update of X - S and its transpose.
+ * radix-select rounds and S emit, 9 sparse update of X - S and its transpose,
+ * 10 the precision form's float32 correction apart from its two streaming
+ * products (which count in class 0).
  * bytes_product (host, nullable) receives the algorithmic bytes of one
  * streaming product at the current rank: 4*m*n (X - S) + 4*(m + n)*r.
  */
-#define GODEC_PROF_CLASSES 10
+#define GODEC_PROF_CLASSES 11
 godec_status godec_profile(godec_ctx* ctx, int32_t n_iter, double* ms, int64_t* launches,
                            double* bytes_product);
 

@@ -6,6 +6,6 @@ There is no CPU fallback: if the library cannot be loaded, calls raise.
 """
 from ._binding import (  # noqa: F401
     GoDec, GodecError, library, mul_ZB, mul_ZtC, run_host, hard_threshold, header_symbols, backward,
-    PREC_FP32, PREC_BF16_REFINE, MAX_RANK,
+    PREC_FP32, PREC_BF16_REFINE, FLAG_NO_REFINE, MAX_RANK,
 )
 from .autograd import UnrolledGoDec, unrolled_godec  # noqa: F401

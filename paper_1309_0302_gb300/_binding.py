@@ -12,6 +12,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "godec.h")
 
 PREC_FP32 = 0
 PREC_BF16_REFINE = 1
+FLAG_NO_REFINE = 2
 MAX_RANK = 64
 
 
@@ -126,7 +127,7 @@ class GoDec:
     """
 
     def __init__(self, X, A1, r: int, k: int, q: int, tol: float = 1e-7, max_iter: int = 50,
-                 rank_tol: float = 0.0, precision: int = PREC_FP32, stream=None):
+                 rank_tol: float = 0.0, precision: int = PREC_FP32, stream=None, flags: int = 0):
         torch = _torch()
         lib = library()
         if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
@@ -142,7 +143,7 @@ class GoDec:
         self.stream = stream
         p = GodecParams(m=m, n=n, ldx=X.stride(0), r=int(r), q=int(q), k=int(k), tol=float(tol),
                         max_iter=int(max_iter), precision=int(precision), rank_tol=float(rank_tol),
-                        flags=0, reserved=0)
+                        flags=int(flags), reserved=0)
         h = C.c_void_p()
         st = lib.godec_init(C.byref(h), C.byref(p), _ptr(X), _ptr(self._A1), _stream_ptr(stream))
         _check(st, "godec_init", None)
@@ -174,7 +175,7 @@ class GoDec:
         return {f: getattr(inf, f) for f, _ in GodecInfo._fields_}
 
     PROF_CLASSES = ["product", "gram_sum", "chol", "tall_small", "slot_update", "rank_test",
-                    "svd_root", "residual", "select_emit", "z_update"]
+                    "svd_root", "residual", "select_emit", "z_update", "refine"]
 
     def profile(self, n_iter: int):
         """Run n_iter iterations with per-kernel CUDA events; returns per-class totals."""

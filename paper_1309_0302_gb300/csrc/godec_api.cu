@@ -27,6 +27,8 @@ using namespace godec;
 
 namespace {
 constexpr int kEvents = 160;
+constexpr int kRefineParts = 1024;   // row partitions of the correction's cross Grams (128 rows each)
+constexpr int kMaxBackoff = 32;       // longest run of exact iterations after repeated alarms
 constexpr float kAlarmRatio = 30.f;   // lagged normaliser: max/min Cholesky diagonal of Q~
 // Fast path, Q2 and Q1: one CholeskyQR pass on the lagged-normalised product; a
 // diagonal spread of its factor above this ratio (condition number of the product)
@@ -70,7 +72,13 @@ struct godec_ctx {
   int RPp = 0;
   float* cs = nullptr;                 // [2][RP] output factors: A1's column scales, 1 / kSkinnyScale
   float* rescale_tmp = nullptr;        // 2 floats: factor applied by rescale_z
-  alignas(64) unsigned char tmap[8][128];   // tensor maps: Z, Z^T, bt2[0], bt2[1], bt2[2], X, Lsplit A, B
+  // tensor maps: 0 Z, 1 Z^T, 2-4 bt2[0..2], 5 X, 6-7 Lsplit A, B; precision form: 8 Z16,
+  // 9 Z16^T, 13-14 bt2[3] over K = n and K = m (10-12 unused)
+  alignas(64) unsigned char tmap[16][128];
+  // precision form: float32 correction scratch
+  float *RA = nullptr, *RB = nullptr, *Wa = nullptr, *Wb = nullptr, *Qa = nullptr, *Qb = nullptr, *Qtmp = nullptr;
+  float *Rf = nullptr, *cs_ref = nullptr;
+  double *rf_part = nullptr, *rf_g = nullptr, *rf_C = nullptr, *rf_core = nullptr, *rf_U = nullptr, *rf_V = nullptr;
   void* LA = nullptr;                  // m x 128 halves: float16 split of U diag(sqrt(sigma s_Z))
   void* LB = nullptr;                  // n x 128 halves: float16 split of V diag(sqrt(sigma s_Z))
   TcGeom tg[2];                        // work split of even (Z) and odd (Z^T) products
@@ -100,6 +108,8 @@ struct godec_ctx {
   int graph_r[2] = {-1, -1};
   int graph_nodes = 0;
   bool need_exact = true;
+  int exact_left = 0;   // exact iterations still owed after an alarm of the lagged normalisers
+  int backoff = 1;      // exact iterations owed at the next alarm (doubles while alarms repeat)
   int rank_drops = 0;
   int exact_iters = 0;
   int rescales = 0;
@@ -205,6 +215,13 @@ void join_side(godec_ctx* c) {
 
 char* gpart(godec_ctx* c, int i) { return c->gparts + (size_t)i * c->gpart_stride; }
 void* bt2(godec_ctx* c, int b) { return static_cast<char*>(c->bt2) + (size_t)b * 2 * c->RP * c->ldb * 2; }
+
+// The float16 copies of the working matrices (precision form), from Z and Z^T.
+void refresh_z16(godec_ctx* c) {
+  if (!c->Z16) return;
+  launch_to_half(c->Z, c->p.m, c->p.n, c->ldz, c->Z16, c->ldz, c->nsm, c->st);
+  launch_to_half(c->Zt, c->p.n, c->p.m, c->ldzt, c->Zt16, c->ldzt, c->nsm, c->st);
+}
 double* g64(godec_ctx* c, int i) { return c->g64 + (size_t)i * c->RP * c->RP; }
 
 // Product i of the chain: even i streams Z (rows m, K n), odd i streams Z^T (rows n, K m).
@@ -215,6 +232,10 @@ void prod(godec_ctx* c, int i, float* out, bool want_bt2, const float* T0, const
   TcLaunch l{};
   l.mapA = c->tmap[even ? 0 : 1];
   l.mapB = c->tmap[i == 0 ? 4 : 2 + ((i - 1) & 1)];
+  if (c->Z16) {   // precision form: the chain streams the float16 copies
+    l.half_a = 1;
+    l.mapA = c->tmap[even ? 8 : 9];   // same two-term operand maps as the float32 chain
+  }
   l.rows = even ? c->p.m : c->p.n;
   l.K = even ? c->p.n : c->p.m;
   l.RP = c->RP;
@@ -269,6 +290,72 @@ void slot(godec_ctx* c, SlotLaunch& sl) {
   sl.ctl = c->ctl;
   sl.alarm_ratio = kAlarmRatio;
   PROF(c, 4, c->side_st, launch_slot(sl, c->side_st));
+}
+
+// ---------------------------------------------------------------------------------
+// Precision form: one float32 correction of the L factors from the float16 chain
+// (reading of the error control for the rounded chain).  With U, V orthonormal, one
+// float32-accurate visit of Z and of Z^T gives A = Z V and B = Z^T U; the tangent-space
+// correction P_U Z + Z P_V - P_U Z P_V = [U A] K [V B]^T, K = [[-C, I], [I, 0]],
+// C = U^T A, is re-truncated to rank r: CholeskyQR2 of [U A] and [V B], SVD of the
+// 2r x 2r core.  An error theta of the chain's subspaces moves the corrected L by about
+// theta sigma_{r+1} (the residual's spectral norm) instead of theta sigma_1: second order
+// when Z - L* is small, a reduction by sigma_{r+1} / sigma_1 otherwise.
+// ---------------------------------------------------------------------------------
+void cqr2(godec_ctx* c, const float* W, int64_t rows, int R2, int ld, float* Q, float* R1, float* T1, float* R2m,
+          float* T2) {
+  cudaStream_t st = c->st;
+  PROF(c, 10, st, launch_cross_gram(W, ld, R2, W, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st));
+  PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R1, T1, c->ctl, st, 0.f));
+  PROF(c, 10, st, launch_tall_small_f(W, ld, R2, T1, ld, 0, R2, rows, 1.f, 0.f, c->Qtmp, ld, st));
+  PROF(c, 10, st, launch_cross_gram(c->Qtmp, ld, R2, c->Qtmp, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st));
+  PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R2m, T2, c->ctl, st, 0.f));
+  PROF(c, 10, st, launch_tall_small_f(c->Qtmp, ld, R2, T2, ld, 0, R2, rows, 1.f, 0.f, Q, ld, st));
+}
+
+void refine(godec_ctx* c) {
+  const int r = c->r, RP = c->RP, R2 = 2 * r, ld = (R2 + 7) / 8 * 8;
+  const int64_t m = c->p.m, n = c->p.n;
+  cudaStream_t st = c->st;
+  // A = Z V, B = Z^T U (float32 product kernel on the float32 working copies)
+  TcLaunch l{};
+  l.RP = RP;
+  l.part = c->part;
+  l.counters = c->counters;
+  l.cscale = c->cs_ref;
+  l.zscale = c->ctl->zscale;
+  l.prescaled = 1;
+  l.pend = c->pend;
+  l.ctl = c->ctl;
+  launch_split_t(c->V, n, RP, bt2(c, 3), c->ldb, c->cs_ref, st);
+  l.mapA = c->tmap[0];
+  l.mapB = c->tmap[13];
+  l.rows = m;
+  l.K = n;
+  l.geom = c->tg[0];
+  l.out = c->RA;
+  PROF(c, 0, st, launch_prod_tc(l, st));
+  launch_split_t(c->U, m, RP, bt2(c, 3), c->ldb, c->cs_ref, st);
+  l.mapA = c->tmap[1];
+  l.mapB = c->tmap[14];
+  l.rows = n;
+  l.K = m;
+  l.geom = c->tg[1];
+  l.out = c->RB;
+  PROF(c, 0, st, launch_prod_tc(l, st));
+  // C = U^T A; [U A], [V B] (stride ld, zero padding)
+  PROF(c, 10, st, launch_cross_gram(c->U, RP, r, c->RA, RP, r, m, c->rf_part, kRefineParts, c->rf_C, r, st));
+  PROF(c, 10, st, launch_concat2(c->U, c->RA, RP, r, m, c->Wa, ld, st));
+  PROF(c, 10, st, launch_concat2(c->V, c->RB, RP, r, n, c->Wb, ld, st));
+  const size_t q = (size_t)64 * 64;
+  float *Ra1 = c->Rf, *Ta1 = Ra1 + q, *Ra2 = Ta1 + q, *Ta2 = Ra2 + q, *Rb1 = Ta2 + q, *Tb1 = Rb1 + q,
+        *Rb2 = Tb1 + q, *Tb2 = Rb2 + q;
+  cqr2(c, c->Wa, m, R2, ld, c->Qa, Ra1, Ta1, Ra2, Ta2);
+  cqr2(c, c->Wb, n, R2, ld, c->Qb, Rb1, Tb1, Rb2, Tb2);
+  PROF(c, 10, st, launch_refine_core(Ra1, Ra2, Rb1, Rb2, ld, c->rf_C, r, c->rf_core, st));
+  PROF(c, 10, st, launch_svd_small(c->rf_core, R2, r, c->rf_U, c->sigma, c->rf_V, st));
+  PROF(c, 10, st, launch_tall_small_d(c->Qa, ld, R2, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st));
+  PROF(c, 10, st, launch_tall_small_d(c->Qb, ld, R2, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st));
 }
 
 // ---------------------------------------------------------------------------------
@@ -385,6 +472,7 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
                   c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st));
   apply(c, c->Q1, m, c->Um, c->Um, c->U, nullptr);
   apply(c, c->Q2, n, c->Vm, c->Vm, c->V, nullptr);
+  if (c->Z16 && !(c->p.flags & GODEC_FLAG_NO_REFINE)) refine(c);
   // operands of the tensor-core residual pass
   PROF(c, 3, c->st, launch_lsplit(c->U, c->V, c->sigma, m, n, RP, c->r, c->ctl->zscale, c->LA, c->LB, c->st));
 }
@@ -527,6 +615,8 @@ godec_status reset_state(godec_ctx* c) {
   c->r = c->p.r;
   c->rank_drops = 0;
   c->need_exact = true;
+  c->exact_left = 0;
+  c->backoff = 1;
   c->exact_iters = 0;
   CK(cudaMemcpyAsync(c->A1, c->A1_orig, (size_t)c->p.n * c->RP * sizeof(float), cudaMemcpyDeviceToDevice,
                      c->st));
@@ -548,6 +638,7 @@ godec_status reset_state(godec_ctx* c) {
   launch_zscale(c->X, c->p.m, c->p.n, c->p.ldx, &c->ctl->zmax_bits, c->ctl->zscale, c->nsm, c->st);
   launch_scale_copy(c->X, c->p.m, c->p.n, c->p.ldx, c->Z, c->ldz, c->ctl->zscale, c->nsm, c->st);
   launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st, c->ctl->zscale);
+  refresh_z16(c);
   launch_reset_iter(c->ctl, c->st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
@@ -562,6 +653,7 @@ godec_status rescale_z(godec_ctx* c) {
   launch_scale_copy(c->Z, c->p.m, c->p.n, c->ldz, c->Z, c->ldz, f, c->nsm, c->st);
   launch_scale_copy(c->Zt, c->p.n, c->p.m, c->ldzt, c->Zt, c->ldzt, f, c->nsm, c->st);
   launch_scale_update(c->ctl->zscale, f, c->st);
+  refresh_z16(c);
   CK(cudaGetLastError());
   ++c->rescales;
   return GODEC_OK;
@@ -595,7 +687,11 @@ godec_status handle_abort(godec_ctx* c, const Ctl& h) {
     if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
     if ((s = drop_columns(c))) return s;
   } else if (h.alarm) {
+    // the lagged normalisers no longer condition the chain (its subspaces moved): stay on
+    // the exact path for `backoff` iterations, twice as many at each repeated alarm
     c->need_exact = true;
+    c->exact_left = c->backoff;
+    c->backoff = std::min(2 * c->backoff, kMaxBackoff);
   } else if (h.need_bigger_cand) {
     unsigned long long cap = c->cap * 2;
     const unsigned long long mn = (unsigned long long)(c->p.m * c->p.n);
@@ -609,6 +705,22 @@ godec_status handle_abort(godec_ctx* c, const Ctl& h) {
   launch_reset_iter(c->ctl, c->st);
   CK(cudaGetLastError());
   return GODEC_OK;
+}
+
+// Path bookkeeping after k completed iterations on the fast (lagged normalisers) or the
+// exact path.
+void note_done(godec_ctx* c, bool fast, int k) {
+  if (k <= 0) return;
+  if (fast) {
+    c->backoff = 1;
+    return;
+  }
+  c->exact_iters += k;
+  c->exact_left -= k;
+  if (c->exact_left <= 0) {
+    c->exact_left = 0;
+    c->need_exact = false;
+  }
 }
 
 // Run n iterations (graph launches), handling aborted iterations; with tol >= 0 stop early
@@ -628,15 +740,12 @@ godec_status run_iterations(godec_ctx* c, int n_iter, double tol) {
     if (!c->gexec[mode] || c->graph_r[mode] != c->r) {
       if ((s = build_graph(c, mode))) return s;
     }
-    const int want = mode == 0 ? 1 : std::min(chunk, n_iter - done);
+    const int want = std::min(mode == 0 ? std::max(c->exact_left, 1) : chunk, n_iter - done);
     for (int i = 0; i < want; ++i) CK(cudaGraphLaunch(c->gexec[mode], c->st));
     if ((s = read_ctl(c, &h))) return s;
     const int before = done;
     done = h.iter - start;
-    if (mode == 0 && done > before) {
-      c->need_exact = false;
-      ++c->exact_iters;
-    }
+    note_done(c, mode == 1, done - before);
     if (h.abort) {
       if (h.converged) return GODEC_OK;
       if ((s = handle_abort(c, h))) return s;
@@ -660,6 +769,9 @@ bool bad_params(const godec_params* p, char* why, size_t nwhy) {
   if (p->max_iter < 1) { snprintf(why, nwhy, "max_iter must be >= 1"); return true; }
   if (p->precision != GODEC_PREC_FP32 && p->precision != GODEC_PREC_BF16_REFINE) {
     snprintf(why, nwhy, "unknown precision"); return true;
+  }
+  if (p->precision == GODEC_PREC_BF16_REFINE && p->r > 32) {
+    snprintf(why, nwhy, "the precision form needs r <= 32"); return true;
   }
   if ((double)p->m * (double)p->n >= 281474976710656.0) { snprintf(why, nwhy, "m*n must be below 2^48"); return true; }
   return false;
@@ -688,7 +800,8 @@ void godec_destroy(godec_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   free_graphs(c);
   void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->bt2, c->cs, c->rescale_tmp, c->LA, c->LB, c->Q1, c->Q2,
-                  c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->pend, c->gparts, c->g64, c->gscr,
+                  c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->pend, c->gparts, c->RA, c->RB, c->Wa, c->Wb, c->Qa, c->Qb, c->Qtmp, c->Rf,
+                  c->cs_ref, c->rf_part, c->rf_g, c->rf_C, c->rf_core, c->rf_U, c->rf_V, c->g64, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
                   c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1]};
   for (void* p : ptrs) cudaFree(p);
@@ -712,10 +825,6 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   if (!X || !A1 || (reinterpret_cast<uintptr_t>(X) & 15)) {
     snprintf(g_static_err, sizeof(g_static_err), "godec_init: X must be a 16-byte aligned device pointer, A1 non-NULL");
     return GODEC_ERR_ARG;
-  }
-  if (p->precision == GODEC_PREC_BF16_REFINE) {
-    snprintf(g_static_err, sizeof(g_static_err), "godec_init: the bf16 precision form is not built in this library");
-    return GODEC_ERR_UNSUPPORTED;
   }
   godec_ctx* c = new (std::nothrow) godec_ctx;
   if (!c) return GODEC_ERR_OOM;
@@ -757,6 +866,27 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   c->ldzt = (m + 63) / 64 * 64;
   CKI(dalloc(&c->Z, (size_t)m * c->ldz));
   CKI(dalloc(&c->Zt, (size_t)n * c->ldzt));
+  if (p->precision == GODEC_PREC_BF16_REFINE) {
+    const size_t W = 64;   // columns of the correction's [U | A] and [V | B] (2r <= 64)
+    CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Z16), (size_t)m * c->ldz));
+    CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Zt16), (size_t)n * c->ldzt));
+    CKI(dalloc(&c->RA, (size_t)m * RP));
+    CKI(dalloc(&c->RB, (size_t)n * RP));
+    CKI(dalloc(&c->Wa, (size_t)m * W));
+    CKI(dalloc(&c->Wb, (size_t)n * W));
+    CKI(dalloc(&c->Qa, (size_t)m * W));
+    CKI(dalloc(&c->Qb, (size_t)n * W));
+    CKI(dalloc(&c->Qtmp, (size_t)mx * W));
+    CKI(dalloc(&c->Rf, (size_t)8 * W * W));
+    CKI(dalloc(&c->cs_ref, (size_t)RP));
+    CKI(dalloc(&c->rf_part, (size_t)kRefineParts * W * W));
+    CKI(dalloc(&c->rf_g, W * W));
+    CKI(dalloc(&c->rf_C, W * W));
+    CKI(dalloc(&c->rf_core, W * W));
+    CKI(dalloc(&c->rf_U, W * W));
+    CKI(dalloc(&c->rf_V, W * W));
+    CKI(prepare_refine_kernels());
+  }
   CKI(dalloc(&c->A1, (size_t)n * RP));
   CKI(dalloc(&c->A1_orig, (size_t)n * RP));
   CKI(dalloc(&c->P, (size_t)mx * RP));
@@ -769,8 +899,8 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(dalloc(&c->Vm, rr));
   c->RPp = tc_rpp(RP);
   c->ldb = (mx + 7) / 8 * 8;
-  CKI(dalloc(reinterpret_cast<unsigned short**>(&c->bt2), (size_t)3 * 2 * RP * c->ldb));
-  CKI(cudaMemsetAsync(c->bt2, 0, (size_t)3 * 2 * RP * c->ldb * 2, c->st));
+  CKI(dalloc(reinterpret_cast<unsigned short**>(&c->bt2), (size_t)4 * 2 * RP * c->ldb));
+  CKI(cudaMemsetAsync(c->bt2, 0, (size_t)4 * 2 * RP * c->ldb * 2, c->st));
   CKI(dalloc(&c->cs, (size_t)2 * RP));
   CKI(dalloc(&c->rescale_tmp, 2));
   {
@@ -802,7 +932,12 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
                     make_tmap_f16(c->tmap[2], bt2(c, 0), 2 * RP, m, c->ldb, 2 * RP) &&
                     make_tmap_f16(c->tmap[3], bt2(c, 1), 2 * RP, n, c->ldb, 2 * RP) &&
                     make_tmap_f16(c->tmap[4], bt2(c, 2), 2 * RP, n, c->ldb, 2 * RP);
-    if (!ok) {
+    const bool ok16 = !c->Z16 ||
+                      (make_tmap_f16(c->tmap[8], c->Z16, m, n, c->ldz, 128) &&
+                       make_tmap_f16(c->tmap[9], c->Zt16, n, m, c->ldzt, 128) &&
+                       make_tmap_f16(c->tmap[13], bt2(c, 3), 2 * RP, n, c->ldb, 2 * RP) &&
+                       make_tmap_f16(c->tmap[14], bt2(c, 3), 2 * RP, m, c->ldb, 2 * RP));
+    if (!ok || !ok16) {
       fail(c, GODEC_ERR_CUDA, "tensor map encoding failed");
       return bail(GODEC_ERR_CUDA);
     }
@@ -912,7 +1047,7 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
     }
     const int before = h.iter;
     if ((s = read_ctl(c, &h))) return s;
-    if (!fast && h.iter > before) c->need_exact = false;
+    note_done(c, fast, h.iter - before);
     if (h.abort) {
       if (h.converged) break;
       if ((s = handle_abort(c, h))) return s;

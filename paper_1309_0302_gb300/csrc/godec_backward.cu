@@ -26,12 +26,6 @@
 #include "godec_internal.cuh"
 
 namespace godec {
-void launch_cross_gram(const float* A, int64_t lda, int a, const float* B, int64_t ldb, int b, int64_t rows,
-                       double* part, int G, double* out, int ldo, cudaStream_t st);
-void launch_tall_small_f(const float* A, int64_t lda, int a, const float* Bm, int ldbm, int trans, int c, int64_t rows,
-                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st);
-void launch_tall_small_d(const float* A, int64_t lda, int a, const double* Bm, int ldbm, int trans, int c,
-                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st);
 void launch_spmm(const int64_t* idx, const float* val, int64_t nnz, int64_t n, const float* B, int64_t ldb, int c,
                  int trans, float* out, int64_t ldo, cudaStream_t st);
 void launch_eval_lr(const int64_t* idx, int64_t nnz, int64_t n, const float* U, int64_t ldu, const float* V,
@@ -47,7 +41,7 @@ namespace {
 
 using namespace godec;
 
-constexpr int kCrossParts = 64;
+constexpr int kCrossParts = 256;
 
 // Stream-ordered scratch of one call; freed (stream-ordered) on destruction.
 struct Scratch {

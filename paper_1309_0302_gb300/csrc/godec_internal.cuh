@@ -170,6 +170,8 @@ struct TcLaunch {
   void* gram_part;
   int gram_mode;
   int t_upper;             // Tn upper triangular (inverse of an upper-triangular factor)
+  int half_a;              // mapA is the float16 copy Z16 (box 64 halves x 128 rows); mapB's box
+                           // then spans only RP rounded up to 16 rows of the operand (its c1 terms)
   int* pend;               // G x geom.maxpend ints of scratch
   Ctl* ctl;
 };
@@ -281,6 +283,31 @@ void set_static_error(const char* fmt, ...);
 // Kernel attributes (dynamic shared memory limits); call before launching or capturing.
 cudaError_t prepare_small_kernels();
 cudaError_t prepare_select_kernels();
+
+// Tall x small and sparse kernels (k_backward.cu), shared by the differentiated form and
+// the precision form's correction.
+// C (a x b, float64, row stride ldo) = A^T B for tall A (rows x a, lda) and B (rows x b,
+// ldb), a, b <= 64, over fixed row partitions of about 128 rows, at most G of them (part
+// holds G x a x b doubles); deterministic.
+void launch_cross_gram(const float* A, int64_t lda, int a, const float* B, int64_t ldb, int b, int64_t rows,
+                       double* part, int G, double* out, int ldo, cudaStream_t st);
+// C (rows x c, ldc) = beta C + alpha A (rows x a, lda) Bm (a x c, ldbm; Bm^T if trans), a, c <= 64
+void launch_tall_small_f(const float* A, int64_t lda, int a, const float* Bm, int ldbm, int trans, int c, int64_t rows,
+                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st);
+void launch_tall_small_d(const float* A, int64_t lda, int a, const double* Bm, int ldbm, int trans, int c,
+                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st);
+// Precision form (k_refine.cu): the bases [P | Q] of the correction; float16 copy of a
+// float32 matrix; the 2r x 2r core Ra K Rb^T of the tangent-space correction; SVD of an
+// n x n float64 matrix (n <= 64), leading r triplets.
+// W (rows x ld, float32) = [P | Q | 0] for P, Q rows x r with row stride ldp (2r <= ld).
+void launch_concat2(const float* P, const float* Q, int64_t ldp, int r, int64_t rows, float* W, int ld,
+                    cudaStream_t st);
+void launch_to_half(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd, int nsm,
+                    cudaStream_t st);
+cudaError_t prepare_refine_kernels();
+void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, const float* Rb2, int ld,
+                        const double* C, int r, double* core, cudaStream_t st);
+void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st);
 
 // Small helpers.
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t st);

@@ -11,7 +11,8 @@ namespace {
 constexpr int BW_THREADS = 256;
 
 // C = A^T B over a fixed row partition: block g adds rows [g R / G, (g+1) R / G) into
-// part[g] (a x b, float64); a, b <= 64.  Each thread owns entries tid + 256 k of a x b.
+// part[g] (a x b, float64), 32-row chunks staged in shared memory (only the a and b
+// columns in use); a, b <= 64.  Each thread owns entries tid + 256 k of a x b.
 __global__ void __launch_bounds__(BW_THREADS)
 k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __restrict__ B, int64_t ldb, int b,
              int64_t rows, double* __restrict__ part) {
@@ -26,11 +27,8 @@ k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __res
   for (int64_t c0 = r0; c0 < r1; c0 += CH) {
     const int nr = (int)(r1 - c0 < CH ? r1 - c0 : CH);
     __syncthreads();
-    for (int e = tid; e < CH * kMaxRP; e += BW_THREADS) {
-      const int rr = e / kMaxRP, cc = e % kMaxRP;
-      sA[rr][cc] = (rr < nr && cc < a) ? A[(c0 + rr) * lda + cc] : 0.f;
-      sB[rr][cc] = (rr < nr && cc < b) ? B[(c0 + rr) * ldb + cc] : 0.f;
-    }
+    for (int e = tid; e < nr * a; e += BW_THREADS) sA[e / a][e % a] = A[(c0 + e / a) * lda + e % a];
+    for (int e = tid; e < nr * b; e += BW_THREADS) sB[e / b][e % b] = B[(c0 + e / b) * ldb + e % b];
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -38,8 +36,7 @@ k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __res
       if (e < ne) {
         const int i = e / b, j = e % b;
         float s = 0.f;
-#pragma unroll 8
-        for (int rr = 0; rr < CH; ++rr) s = fmaf(sA[rr][i], sB[rr][j], s);
+        for (int rr = 0; rr < nr; ++rr) s = fmaf(sA[rr][i], sB[rr][j], s);
         acc[k] += (double)s;
       }
     }
@@ -51,14 +48,23 @@ k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __res
   }
 }
 
-// out[e] = sum over the partition partials in partition order (deterministic); with a
-// row stride ldo for the a x b result (ldo >= b).
-__global__ void k_cross_sum(const double* __restrict__ part, int G, int a, int b, double* __restrict__ out, int ldo) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x, ne = a * b;
-  if (e >= ne) return;
+// out[e] = sum over the G partition partials (one block per entry e, a fixed reduction
+// tree: deterministic); with a row stride ldo for the a x b result (ldo >= b).
+constexpr int kSumThreads = 128;
+__global__ void __launch_bounds__(kSumThreads)
+k_cross_sum(const double* __restrict__ part, int G, int a, int b, double* __restrict__ out, int ldo) {
+  __shared__ double red[kSumThreads / 32];
+  const int e = blockIdx.x, ne = a * b;
   double t = 0.0;
-  for (int g = 0; g < G; ++g) t += part[(int64_t)g * ne + e];
-  out[(e / b) * ldo + e % b] = t;
+  for (int g = threadIdx.x; g < G; g += kSumThreads) t += part[(int64_t)g * ne + e];
+  for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kSumThreads / 32; ++w) s += red[w];
+    out[(e / b) * ldo + e % b] = s;
+  }
 }
 
 // C[i][c] = beta C[i][c] + alpha sum_l A[i][l] Bm[l][c] (Bm small, a x c, row stride ldbm;
@@ -187,8 +193,13 @@ unsigned blocks_for(int64_t n) { return (unsigned)((n + BW_THREADS - 1) / BW_THR
 
 void launch_cross_gram(const float* A, int64_t lda, int a, const float* B, int64_t ldb, int b, int64_t rows,
                        double* part, int G, double* out, int ldo, cudaStream_t st) {
-  k_cross_part<<<G, BW_THREADS, 0, st>>>(A, lda, a, B, ldb, b, rows, part);
-  k_cross_sum<<<blocks_for((int64_t)a * b), BW_THREADS, 0, st>>>(part, G, a, b, out, ldo);
+  if (a * b == 0) return;
+  // about 128 rows per partition (short serial chains), at most the G the buffer holds
+  int64_t gu = (rows + 127) / 128;
+  if (gu > G) gu = G;
+  if (gu < 1) gu = 1;
+  k_cross_part<<<(unsigned)gu, BW_THREADS, 0, st>>>(A, lda, a, B, ldb, b, rows, part);
+  k_cross_sum<<<(unsigned)(a * b), kSumThreads, 0, st>>>(part, (int)gu, a, b, out, ldo);
 }
 
 void launch_tall_small_f(const float* A, int64_t lda, int a, const float* Bm, int ldbm, int trans, int c, int64_t rows,

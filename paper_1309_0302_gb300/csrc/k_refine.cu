@@ -1,0 +1,185 @@
+// Kernels of the precision form's float32 correction (reading of the paper's error
+// control for the rounded chain; the oracle is tangent_refine): the 16-bit copies of the
+// working matrix, the 2r x 2r core of the tangent-space re-truncation and its SVD.
+#include <cuda_fp16.h>
+
+#include "godec_internal.cuh"
+
+namespace godec {
+
+namespace {
+
+// dst (rows x cols, float16, row stride ldd) = src (float32, row stride lds), rounded to
+// nearest (src holds (X - S) s_Z, inside the float16 range).
+__global__ void k_to_half(const float* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                          __half* __restrict__ dst, int64_t ldd) {
+  for (int64_t i = blockIdx.x; i < rows; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) dst[i * ldd + j] = __float2half_rn(src[i * lds + j]);
+}
+
+// W (rows x ld) = [P | Q | 0]: P and Q rows x r (row stride ldp), zero columns 2r..ld-1.
+__global__ void k_concat2(const float* __restrict__ P, const float* __restrict__ Q, int64_t ldp, int r, int64_t rows,
+                          float* __restrict__ W, int ld) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * ld) return;
+  const int64_t i = e / ld;
+  const int j = (int)(e % ld);
+  W[e] = j < r ? P[i * ldp + j] : (j < 2 * r ? Q[i * ldp + j - r] : 0.f);
+}
+
+// core = Ra K Rb^T, n2 = 2r:  Ra = Ra2 Ra1 and Rb = Rb2 Rb1 (upper, stride ld), K = [[-C, I],
+// [I, 0]] with C (r x r, float64, stride r).  One block; the result in float64 (stride n2).
+__global__ void k_refine_core(const float* __restrict__ Ra1, const float* __restrict__ Ra2,
+                              const float* __restrict__ Rb1, const float* __restrict__ Rb2, int ld,
+                              const double* __restrict__ C, int r, double* __restrict__ core) {
+  extern __shared__ double smd[];   // Ra, Rb, K: 3 x 64 x 65 doubles (dynamic)
+  double (*Ra)[kMaxRP + 1] = reinterpret_cast<double (*)[kMaxRP + 1]>(smd);
+  double (*Rb)[kMaxRP + 1] = Ra + kMaxRP;
+  double (*Km)[kMaxRP + 1] = Rb + kMaxRP;
+  const int n2 = 2 * r, tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < n2 * n2; e += nt) {
+    const int i = e / n2, j = e % n2;
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < n2; ++k) {
+      sa += (double)Ra2[i * ld + k] * (double)Ra1[k * ld + j];
+      sb += (double)Rb2[i * ld + k] * (double)Rb1[k * ld + j];
+    }
+    Ra[i][j] = sa;
+    Rb[i][j] = sb;
+    double kv = 0.0;
+    if (i < r && j < r) kv = -C[i * r + j];
+    else if (i < r && j == i + r) kv = 1.0;
+    else if (i >= r && j == i - r) kv = 1.0;
+    Km[i][j] = kv;
+  }
+  __syncthreads();
+  // core[i][j] = sum_p Ra[i][p] sum_q K[p][q] Rb[j][q]
+  for (int e = tid; e < n2 * n2; e += nt) {
+    const int i = e / n2, j = e % n2;
+    double s = 0.0;
+    for (int p = 0; p < n2; ++p) {
+      double t = 0.0;
+      for (int q = 0; q < n2; ++q) t += Km[p][q] * Rb[j][q];
+      s += Ra[i][p] * t;
+    }
+    core[i * n2 + j] = s;
+  }
+}
+
+constexpr double kJacobiTol = 1e-14;
+
+// SVD of an n x n float64 matrix (n <= 64) by one-sided Jacobi (Hestenes): columns of
+// W = A V are rotated pairwise until orthogonal; one block of 64 threads, thread i owns
+// row i of W and of V.  Outputs the r leading singular triplets, descending:
+// U[:, :r] (n x r, float64, stride r), sigma[:r] (float32), V[:, :r] (n x r, stride r).
+__global__ void __launch_bounds__(64) k_svd_small(const double* __restrict__ A, int n, int r, double* __restrict__ Uo,
+                                                  float* __restrict__ sigma, double* __restrict__ Vo) {
+  extern __shared__ double smd[];   // W, V: 2 x 64 x 65 doubles (dynamic)
+  double (*W)[kMaxRP + 1] = reinterpret_cast<double (*)[kMaxRP + 1]>(smd);
+  double (*V)[kMaxRP + 1] = W + kMaxRP;
+  __shared__ double red[3][2];
+  __shared__ double nrm[kMaxRP];
+  __shared__ int order[kMaxRP];
+  __shared__ int s_rot;
+  const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+  for (int j = 0; j < n; ++j) {
+    W[i][j] = (i < n) ? A[i * n + j] : 0.0;
+    V[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (i == 0) s_rot = 0;
+    __syncthreads();
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double a = W[i][p] * W[i][p], b = W[i][q] * W[i][q], g = W[i][p] * W[i][q];
+        for (int o = 16; o; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (lane == 0) {
+          red[0][w] = a;
+          red[1][w] = b;
+          red[2][w] = g;
+        }
+        __syncthreads();
+        a = red[0][0] + red[0][1];
+        b = red[1][0] + red[1][1];
+        g = red[2][0] + red[2][1];
+        __syncthreads();
+        // rotate unless the pair is orthogonal to the rounding level of a length-64 dot
+        // product in float64 (a tighter test never ends: rounding keeps |g| near it)
+        if (fabs(g) > kJacobiTol * sqrt(a * b) && g != 0.0) {
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double wp = W[i][p], wq = W[i][q], vp = V[i][p], vq = V[i][q];
+          W[i][p] = cs * wp - sn * wq;
+          W[i][q] = sn * wp + cs * wq;
+          V[i][p] = cs * vp - sn * vq;
+          V[i][q] = sn * vp + cs * vq;
+          if (i == 0) s_rot = 1;
+        }
+        __syncthreads();
+      }
+    if (!s_rot) break;
+  }
+  // column norms, descending order
+  if (i < n) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += W[k][i] * W[k][i];
+    nrm[i] = sqrt(s);
+  }
+  __syncthreads();
+  if (i < n) {
+    int rank = 0;
+    for (int k = 0; k < n; ++k) rank += (nrm[k] > nrm[i]) || (nrm[k] == nrm[i] && k < i);
+    order[rank] = i;
+  }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    const int col = order[j];
+    const double s = nrm[col];
+    if (i < n) {
+      Uo[i * r + j] = s > 0.0 ? W[i][col] / s : 0.0;
+      Vo[i * r + j] = V[i][col];
+    }
+    if (i == 0) sigma[j] = (float)s;
+  }
+}
+
+}  // namespace
+
+void launch_to_half(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd, int nsm,
+                     cudaStream_t st) {
+  int64_t grid = 4LL * nsm;
+  if (grid > rows) grid = rows;
+  if (grid > 0) k_to_half<<<(unsigned)grid, 256, 0, st>>>(src, rows, cols, lds, static_cast<__half*>(dst), ldd);
+}
+
+void launch_concat2(const float* P, const float* Q, int64_t ldp, int r, int64_t rows, float* W, int ld,
+                    cudaStream_t st) {
+  const int64_t total = rows * ld;
+  if (total > 0) k_concat2<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, Q, ldp, r, rows, W, ld);
+}
+
+constexpr size_t kCoreSmem = 3 * kMaxRP * (kMaxRP + 1) * sizeof(double);
+constexpr size_t kSvdSmem = 2 * kMaxRP * (kMaxRP + 1) * sizeof(double);
+
+cudaError_t prepare_refine_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_refine_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSvdSmem);
+  return e;
+}
+
+void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, const float* Rb2, int ld,
+                        const double* C, int r, double* core, cudaStream_t st) {
+  k_refine_core<<<1, 256, kCoreSmem, st>>>(Ra1, Ra2, Rb1, Rb2, ld, C, r, core);
+}
+
+void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st) {
+  k_svd_small<<<1, 64, kSvdSmem, st>>>(A, n, r, U, sigma, V);
+}
+
+}  // namespace godec

@@ -10,6 +10,8 @@
 // exact k-th key and the tie cut, and the emit step writes S as COO.
 #include <cuda_bf16.h>
 
+#include <cuda_fp16.h>
+
 #include "godec_internal.cuh"
 
 namespace godec {
@@ -539,8 +541,8 @@ __device__ __forceinline__ void z_write(const EmitArgs& a, long long i, long lon
   bad |= fabsf(v) >= kZRange && isfinite(v);
   a.Z[i * a.ldz + j] = v;
   if (a.Zt) a.Zt[j * a.ldzt + i] = v;
-  if (a.Z16) reinterpret_cast<__nv_bfloat16*>(a.Z16)[i * a.ldz + j] = __float2bfloat16(z);
-  if (a.Zt16) reinterpret_cast<__nv_bfloat16*>(a.Zt16)[j * a.ldzt + i] = __float2bfloat16(z);
+  if (a.Z16) reinterpret_cast<__half*>(a.Z16)[i * a.ldz + j] = __float2half_rn(v);     // precision form's copies
+  if (a.Zt16) reinterpret_cast<__half*>(a.Zt16)[j * a.ldzt + i] = __float2half_rn(v);
 }
 
 __device__ __forceinline__ void z_flag(Ctl* ctl, bool bad) {

@@ -646,6 +646,233 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   }
 }
 
+// ---- 16-bit streaming product (precision form) -------------------------------------------
+// part/out = Z16 (rows x K, float16 copy of (X - S) s_Z, rounded) * B with B in its two-term
+// split c1 + 2^-11 c2 (rows 0..2RP-1 of bt2): one float16 MMA of N = 2 RP per stage gives
+// Z16 c1 and Z16 c2 side by side in tensor memory, summed as hi + 2^-11 lo in the
+// epilogue, float32 accumulation.  Z16 carries about 2^-12 relative rounding per element
+// (fixed for the whole chain); B is exact to about 2^-22, so the chain's error is that of
+// X's rounding alone (rounding B to one float16 term as well adds a fresh 2^-12 per
+// product, which the float32 correction pass can no longer remove when sigma_r and
+// sigma_{r+1} are close).  The Z16 tile of a stage is one 128-row x 64-column box that
+// the MMA reads straight from shared memory (no conversion), so the stream moves half
+// the bytes of the float32 kernel.  Same stream-K split, partial slots and deferred tile
+// completion as k_prod_tc.  RP <= 32 (the precision form's bound on r).
+// Warps: 0 TMA producer of Z16 tiles, 1 MMA issuer (TMEM owner), 2-5 epilogue, 6 TMA
+// producer of the skinny operand, 7 spare (completion only).
+constexpr int NA16 = 10, NS16 = 6, kThreads16 = 256;
+constexpr size_t kStageA16 = (size_t)BM * 128;                 // 64 halves x 128 rows = 16 KB
+constexpr int kMaxRP16 = 32;                                   // RP bound of the 16-bit kernel
+constexpr size_t kStageB16 = (size_t)2 * kMaxRP16 * 128;       // up to 2 x 32 rows of 64 halves = 8 KB
+constexpr size_t kOffB16 = NA16 * kStageA16;
+constexpr size_t kTc16Smem = kOffB16 + NS16 * kStageB16 + 1024;
+static_assert(kEpiBytes <= NA16 * kStageA16, "completion staging fits the 16-bit ring");
+static_assert(kTc16Smem <= 232448 - 1024, "shared memory of the 16-bit product");
+
+template <int RPp>
+__global__ void __launch_bounds__(kThreads16, 1)
+k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+  Ctl* ctl = a.ctl;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + kOffB16;
+  float* Ps = reinterpret_cast<float*>(sm);   // completion staging: the ring, once idle
+  float* Ts = Ps + BM * EPI_LD;
+  __shared__ uint64_t afull[NA16], aempty[NA16], bfull[NS16], bempty[NS16];
+  __shared__ uint64_t accfull[2], accempty[2], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_err;
+  __shared__ int s_stop, s_last, s_npend;
+  __shared__ float s_csc[kMaxRP];
+  __shared__ float s_zi;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x;
+  const int64_t S = a.S, ks = a.ks;
+  const int G = a.G;
+  const int64_t g0 = (int64_t)c * S / G, g1 = (int64_t)(c + 1) * S / G;
+  static_assert(RPp <= kMaxRP16, "16-bit kernel: RP <= 32");
+  const uint32_t bbytes = (uint32_t)(2 * a.RP * 128);   // c1 and c2 rows of the stage
+  if (tid == 0) {
+    for (int s = 0; s < NA16; ++s) {
+      mbar_init(&afull[s], 1);
+      mbar_init(&aempty[s], 1);
+    }
+    for (int s = 0; s < NS16; ++s) {
+      mbar_init(&bfull[s], 1);
+      mbar_init(&bempty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 4);
+    }
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+    s_err = (ctl && (ctl->abort || ctl->range_err)) ? 2 : 0;
+    if (ctl && ctl->range_err) ctl->abort = 1;
+    s_npend = 0;
+    s_zi = a.zscale ? a.zscale[1] : 1.f;
+  }
+  if (tid < kMaxRP) s_csc[tid] = (tid < a.RP && a.cscale) ? a.cscale[tid] : 1.f;
+  if (warp == 1) tmem_alloc(&tmem_base, 128);
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  if (warp == 0 || warp == 6) {
+    // ---------------- TMA producers: Z16 tiles (warp 0), skinny-operand tiles (warp 6) ----------
+    if (lane == 0) {
+      const bool isA = warp == 0;
+      const int nslot = isA ? NA16 : NS16;
+      uint64_t* fullb = isA ? afull : bfull;
+      uint64_t* emptyb = isA ? aempty : bempty;
+      int64_t t = g0 / ks, kst = g0 % ks, issued = 0;
+      int s = 0;
+      uint32_t ph = 0;
+      for (int64_t g = g0; g < g1 && !s_err; ++g) {
+        if (!mbar_wait(&emptyb[s], ph ^ 1u, kWaitLimit)) { note_timeout(ctl, &s_err); break; }
+        if (isA) {
+          mbar_expect_tx(&fullb[s], (uint32_t)kStageA16);
+          tma_load_2d(sA + (size_t)s * kStageA16, &mapA, &fullb[s], (int)(kst * BK), (int)(t * BM));
+        } else {
+          mbar_expect_tx(&fullb[s], bbytes);
+          tma_load_2d(sB + (size_t)s * kStageB16, &mapB, &fullb[s], (int)(kst * BK), 0);
+        }
+        ++issued;
+        if (++kst == ks) { kst = 0; ++t; }
+        if (++s == nslot) { s = 0; ph ^= 1u; }
+      }
+      for (int64_t j = (issued > nslot ? issued - nslot : 0); j < issued; ++j)
+        if (!mbar_wait(&fullb[(int)(j % nslot)], (uint32_t)((j / nslot) & 1), kWaitLimit)) note_timeout(ctl, &s_err);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t id = idesc_f16(BM, 2 * a.RP);   // [Z16 c1 | Z16 c2], RP multiple of 8
+      int ch = 0, sa = 0, sb = 0;
+      uint32_t pha = 0, phb = 0;
+      int64_t kst = g0 % ks, g = g0;
+      while (g < g1 && !s_err) {
+        int64_t n = ks - kst;
+        if (n > kChunk) n = kChunk;
+        if (n > g1 - g) n = g1 - g;
+        const int b = ch & 1;
+        if (!mbar_wait(&accempty[b], (uint32_t)(((ch >> 1) & 1) ^ 1), kWaitLimit)) { note_timeout(ctl, &s_err); break; }
+        tc_fence_after();
+        const uint32_t dcol = tbase + (uint32_t)(b * 64);
+        uint32_t acc = 0;
+        for (int64_t e = 0; e < n; ++e) {
+          if (!mbar_wait(&afull[sa], pha, kWaitLimit) || !mbar_wait(&bfull[sb], phb, kWaitLimit)) {
+            note_timeout(ctl, &s_err);
+            break;
+          }
+          tc_fence_after();
+          const uint64_t da = sdesc_k128(sA + (size_t)sa * kStageA16), db = sdesc_k128(sB + (size_t)sb * kStageB16);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t off = (uint64_t)((kk * 16 * 2) >> 4);   // 32 bytes per 16-wide K step
+            mma_bf16(dcol, da + off, db + off, id, acc);
+            acc = 1u;
+          }
+          mma_commit(&aempty[sa]);
+          mma_commit(&bempty[sb]);
+          if (++sa == NA16) { sa = 0; pha ^= 1u; }
+          if (++sb == NS16) { sb = 0; phb ^= 1u; }
+        }
+        if (s_err) break;
+        mma_commit(&accfull[b]);
+        ++ch;
+        g += n;
+        kst += n;
+        if (kst == ks) kst = 0;
+      }
+      mma_commit(&mma_done);
+      if (!mbar_wait(&mma_done, 0, kWaitLimit)) note_timeout(ctl, &s_err);
+    }
+  } else if (warp >= 2 && warp < 6) {
+    // ---------------- epilogue: TMEM -> running sums -> partial slot ----------------
+    const int et = tid - 64;
+    const int q4 = warp & 3;
+    const int row = q4 * 32 + lane;
+    const uint32_t tlane = (uint32_t)(q4 * 32) << 16;
+    int ch = 0, npend = 0;
+    int64_t g = g0;
+    for (;;) {
+      named_sync(1, BM);
+      if (et == 0) s_stop = (g >= g1) || s_err;
+      named_sync(1, BM);
+      if (s_stop) break;
+      const int64_t t = g / ks;
+      const int64_t tend = ((t + 1) * ks < g1) ? (t + 1) * ks : g1;
+      float y[RPp];
+#pragma unroll
+      for (int l = 0; l < RPp; ++l) y[l] = 0.f;
+      bool failed = false;
+      for (; g < tend; g = (g + kChunk < tend) ? g + kChunk : tend, ++ch) {
+        if (failed) continue;
+        const int b = ch & 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&accfull[b], (uint32_t)((ch >> 1) & 1), kWaitLimit))) {
+          if (lane == 0) note_timeout(ctl, &s_err);
+          failed = true;
+          continue;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tbase + (uint32_t)(b * 64) + tlane;
+#pragma unroll
+        for (int c0 = 0; c0 < RPp; c0 += 8) {
+          if (c0 < a.RP) {
+            float vh[8], vl[8];
+            tmem_ld8(taddr + c0, vh);
+            tmem_ld8(taddr + a.RP + c0, vl);
+#pragma unroll
+            for (int l = 0; l < 8; ++l) y[c0 + l] += fmaf(vl[l], kLoInv, vh[l]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accempty[b]);
+      }
+      named_sync(1, BM);
+      if (et == 0) s_stop = s_err;
+      named_sync(1, BM);
+      if (s_stop) break;
+      const int64_t c_first = cta_of(t * ks, S, G);
+      const int nseg = (int)(cta_of((t + 1) * ks - 1, S, G) - c_first + 1);
+      const int slot = (int)(c - c_first);
+      float* p = a.part + ((t * a.maxseg + slot) * BM + row) * (int64_t)a.RP;
+#pragma unroll
+      for (int l = 0; l < RPp; l += 4)
+        if (l < a.RP) *reinterpret_cast<float4*>(p + l) = make_float4(y[l], y[l + 1], y[l + 2], y[l + 3]);
+      __threadfence();
+      named_sync(1, BM);
+      if (et == 0) s_last = (atomicAdd(&a.counters[t], 1u) == (unsigned)(nseg - 1));
+      named_sync(1, BM);
+      if (s_last) {
+        if (et == 0) {
+          if (npend < a.maxpend) a.pend[(int64_t)c * a.maxpend + npend] = (int)t;
+          else if (ctl) ctl->abort = 1;
+        }
+        ++npend;
+      }
+    }
+    if (et == 0) s_npend = npend;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 128);
+  }
+  const int np = s_err ? 0 : (s_npend < a.maxpend ? s_npend : a.maxpend);
+  for (int k = 0; k < np; ++k) {
+    const int64_t t = a.pend[(int64_t)c * a.maxpend + k];
+    const int64_t c_first = cta_of(t * ks, S, G);
+    const int nseg = (int)(cta_of((t + 1) * ks - 1, S, G) - c_first + 1);
+    tile_finish<RPp>(a, t, nseg, tid, kThreads16, 0, Ps, Ts, s_csc, s_zi);
+  }
+}
+
 // Column c of a row-major rows x RP operand B -> rows c and RP + c of the split
 // transposed float16 operand, scaled by the power of two 2^e_c that brings the column's
 // largest magnitude into [2^9, 2^10); cscale[c] = 2^-e_c undoes it.  One block per column.
@@ -754,8 +981,15 @@ static cudaError_t prep_one() {
   return cudaFuncSetAttribute(k_prod_tc<RPp, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
 }
 
+template <int RPp>
+static cudaError_t prep16() {
+  return cudaFuncSetAttribute(k_prod_h16<RPp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTc16Smem);
+}
+
 cudaError_t prepare_tc_kernels() {
   cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = prep16<16>();
+  if (e == cudaSuccess) e = prep16<32>();
   if (e == cudaSuccess) e = prep_one<16, false>();
   if (e == cudaSuccess) e = prep_one<32, false>();
   if (e == cudaSuccess) e = prep_one<48, false>();
@@ -795,7 +1029,13 @@ void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   const CUtensorMap& B = *reinterpret_cast<const CUtensorMap*>(l.mapB);
   a.prescaled = l.prescaled;
   const int rpp = tc_rpp(l.RP);
-  if (l.prescaled) {
+  if (l.half_a) {
+    switch (rpp) {
+      case 16: k_prod_h16<16><<<a.G, kThreads16, kTc16Smem, st>>>(A, B, a); break;
+      case 32: k_prod_h16<32><<<a.G, kThreads16, kTc16Smem, st>>>(A, B, a); break;
+      default: if (l.ctl) cudaMemsetAsync(&l.ctl->abort, 0xff, sizeof(int), st); break;   // RP > 32: rejected at init
+    }
+  } else if (l.prescaled) {
     switch (rpp) {
       case 16: k_prod_tc<16, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
       case 32: k_prod_tc<32, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
