@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision"], default=None,
+    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
@@ -354,6 +354,53 @@ def run_kernel_case(args):
         dist = float(np.sqrt(max(aa + bb - 2 * ab, 0.0)) / np.sqrt(aa))
         print(f"C3 float32 form: {ta:.3f} ms/iteration ({1e3 / ta:.1f} it/s); precision form: {tb:.3f} "
               f"ms/iteration ({1e3 / tb:.1f} it/s); L distance after 12 iterations {dist:.2e}")
+    elif args.kernel == "batched":
+        # batched form at C4 (64 problems, m, n log-uniform in [256, 4096], r in 2..32, q = 1):
+        # tuned batch, untuned batch (all SMs for every problem) and the same problems one by
+        # one through the single-problem API, 20 iterations each after 2 warm-up ones
+        import time
+        ds = synth.config_c4()
+        Xs = [torch.from_numpy(d["X"]).cuda() for d in ds]
+        A1s = [torch.from_numpy(d["A1"]).cuda() for d in ds]
+        rs, ks, qs = [d["r"] for d in ds], [d["k"] for d in ds], [d["q"] for d in ds]
+        nbytes = sum(4.0 * d["X"].size * (6 * d["q"] + 4) for d in ds)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        T = 20
+
+        def timed(f):
+            f(2)
+            torch.cuda.synchronize()
+            ev[0].record(torch.cuda.current_stream())
+            f(T)
+            ev[1].record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / T
+
+        res = {}
+        for tune in (True, False):
+            t0 = time.time()
+            b = G.GoDecBatch(Xs, A1s, rs, ks, qs, tune=tune)
+            t_init = time.time() - t0
+            rec0 = b.tuning()["recaptures"]
+            res[tune] = (timed(b.iterate), b.tuning(), t_init)
+            ex = [b.problem(j).info()["exact_iters"] for j in range(len(ds))]
+            print(f"C4 batch ({'tuned' if tune else 'untuned'}): graph captures during the timed run "
+                  f"{res[tune][1]['recaptures'] - rec0}, iterations on the exact path per problem {ex}")
+            b.close()
+        single = 0.0
+        for j in range(len(ds)):
+            g = G.GoDec(Xs[j], A1s[j], rs[j], ks[j], qs[j], tol=-1.0, max_iter=1 << 20)
+            single += timed(g.iterate)
+            g.close()
+        for tune in (True, False):
+            ms, tun, t_init = res[tune]
+            print(f"C4 batch ({'tuned, policy ' + str(tun['policy']) if tune else 'untuned'}): {ms:.3f} ms per batch "
+                  f"iteration, {64e3 / ms:.0f} problem-iterations/s, {nbytes / ms / 1e6:.0f} GB/s of "
+                  f"algorithmic traffic; init {t_init:.1f} s")
+        print("C4 tuner ms per batch iteration by policy:", [round(x, 3) for x in res[True][1]["policy_ms"]])
+        print("C4 budgets (SMs) of the tuned policy:", res[True][1]["sm"])
+        print(f"C4 one problem at a time: {single:.3f} ms per round of 64 iterations, "
+              f"{64e3 / single:.0f} problem-iterations/s")
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
         run = G.GoDec(torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda(), R, d["k"], Q)

@@ -300,6 +300,68 @@ godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t 
 godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t n, int64_t ldz,
                                   const float* B, int32_t r, float* Y, void* stream);
 
+/*
+ * Batched form: count independent GoDec-BRP problems (Algorithm 1 on each) of uneven
+ * m, n and r, advanced together.  One batch iteration is one launch of one CUDA graph
+ * that holds an iteration of every problem as a parallel branch, all on the exact-
+ * normaliser path of the chain (the graph is captured once, and again after a rank
+ * drop).  Each branch's kernels are sized for a share of the SMs (its budget: the
+ * stream-K grid of the products and the S-step's grids), so branches run side by side.
+ * An autotuner picks the budgets by timing the batch graph of each candidate policy on
+ * the problems themselves (two warm-up and three batch iterations each, then every
+ * problem is reset):
+ *   policy 0: every problem gets all SMs;
+ *   policy k = 1..4: problem i gets max(4, min(#SMs, ceil(2^(k-1) #SMs m_i n_i / sum m n))).
+ * Each problem's results equal those of a godec_init context run on its own, up to
+ * float32 rounding (grid sizes change the order of the stream-K partial sums).
+ *   count  : 1 <= count <= GODEC_BATCH_MAX
+ *   params : host array of count godec_params (precision GODEC_PREC_FP32)
+ *   X, A1  : host arrays of count device pointers, each as in godec_init (borrowed)
+ *   flags  : GODEC_BATCH_NO_TUNE gives every problem all SMs without timing
+ *   stream : the CUDA stream of every call on the batch (nullable)
+ * Device memory: that of count godec_init contexts.  Errors: as godec_init, with the
+ * failing problem's index in the message; on failure *out is NULL and nothing leaks.
+ */
+typedef struct godec_batch godec_batch;
+#define GODEC_BATCH_MAX 4096
+#define GODEC_BATCH_NO_TUNE 1
+#define GODEC_BATCH_POLICIES 5
+godec_status godec_batch_init(godec_batch** out, int32_t count, const godec_params* params,
+                              const float* const* X, const float* const* A1, int32_t flags, void* stream);
+
+/*
+ * n_iter more iterations of every problem: n_iter launches of the batch graph, then a
+ * problem whose iteration aborted in the graph (rank drop, candidate buffer growth,
+ * rescale of X - S) is handled as godec_iterate would and finishes its iterations on
+ * its own graphs.  A problem that converged or failed earlier sits out.  The stop
+ * test is off (each problem's tol is not used here).  Synchronises the stream.
+ */
+godec_status godec_batch_iterate(godec_batch* b, int32_t n_iter);
+
+/* Back to S = 0 for every problem (godec_reset on each). */
+godec_status godec_batch_reset(godec_batch* b);
+
+/*
+ * The context of problem i (0 <= i < count), owned by the batch: use it with
+ * godec_get_L, godec_get_S, godec_get_info, godec_residual and godec_iterate; never
+ * pass it to godec_destroy.  NULL if i is out of range.
+ */
+godec_ctx* godec_batch_problem(godec_batch* b, int32_t i);
+
+/*
+ * The tuner's result: sm (host, count entries, nullable) the budget of each problem;
+ * policy_ms (host, GODEC_BATCH_POLICIES entries, nullable) milliseconds per batch
+ * iteration of each timed policy (0 when not timed); policy (host, nullable) the one
+ * in use; recaptures (host, nullable) batch graphs captured since init, tuning included.
+ */
+godec_status godec_batch_tuning(godec_batch* b, int32_t* sm, double* policy_ms, int32_t* policy,
+                                int32_t* recaptures);
+
+void godec_batch_destroy(godec_batch* b);
+
+/* Message of the last failed call on b (b NULL: of the last failed godec_batch_init). */
+const char* godec_batch_last_error(godec_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

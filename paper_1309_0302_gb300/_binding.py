@@ -10,6 +10,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(HERE), "include", "godec.h")
 
+BATCH_NO_TUNE = 1
+BATCH_POLICIES = 5
 PREC_FP32 = 0
 PREC_BF16_REFINE = 1
 FLAG_NO_REFINE = 2
@@ -65,6 +67,14 @@ def _declare(lib):
         "godec_backward": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, C.c_int32, C.POINTER(_P), i64p,
                             _P, _P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
         "godec_mul_ZtC": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
+        "godec_batch_init": ([C.POINTER(_P), C.c_int32, C.POINTER(GodecParams), C.POINTER(_P), C.POINTER(_P),
+                              C.c_int32, _P], C.c_int),
+        "godec_batch_iterate": ([_P, C.c_int32], C.c_int),
+        "godec_batch_reset": ([_P], C.c_int),
+        "godec_batch_problem": ([_P, C.c_int32], _P),
+        "godec_batch_tuning": ([_P, i32p, f64p, i32p, i32p], C.c_int),
+        "godec_batch_destroy": ([_P], None),
+        "godec_batch_last_error": ([_P], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -355,3 +365,108 @@ def run_host(X: np.ndarray, A1: np.ndarray, r: int, k: int, q: int, n_iter: int,
     return {"U": U.reshape(-1)[: m * rr].reshape(m, rr), "sigma": s[:rr],
             "V": V.reshape(-1)[: n * rr].reshape(n, rr), "S_idx": Si[:kk], "S_val": Sv[:kk],
             "iters": it.value, "rel_err": e.value, "r_eff": rr}
+
+
+def _bcheck(status: int, where: str, b=None):
+    if status != 0:
+        msg = library().godec_batch_last_error(b).decode(errors="replace")
+        raise GodecError(status, where, msg)
+
+
+def _padded(X):
+    """X itself, or a copy whose row stride is a multiple of 4 elements (16 bytes)."""
+    torch = _torch()
+    if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
+        raise ValueError("X must be a 2-D CUDA float32 tensor")
+    m, n = X.shape
+    if X.stride(1) != 1 or X.stride(0) % 4 or X.stride(0) < n or X.data_ptr() % 16:
+        Xp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+        Xp[:, :n] = X
+        return Xp
+    return X
+
+
+class _Problem(GoDec):
+    """Problem i of a GoDecBatch: the GoDec methods on a context the batch owns."""
+
+    def __init__(self, batch, h, X, A1, r, k, q):
+        self._batch = batch          # keeps the batch (and its contexts) alive
+        self._X, self._A1 = X, A1
+        self.m, self.n = X.shape
+        self.r, self.k, self.q = int(r), int(k), int(q)
+        self.stream = batch.stream
+        self._h = h
+
+    def close(self):
+        self._h = None               # the batch destroys the context
+
+    __del__ = close
+
+
+class GoDecBatch:
+    """Many GoDec-BRP problems of uneven m, n and r, one CUDA-graph launch per batch
+    iteration (godec_batch_* in include/godec.h).
+
+    Xs, A1s: lists of CUDA float32 tensors (m_i, n_i) and (n_i, r_i), borrowed.
+    rs, ks, qs: per-problem rank, cardinality and power-step count (ints or lists).
+    tune: time the candidate SM-budget policies and keep the fastest (else every
+    problem gets all SMs).
+    """
+
+    def __init__(self, Xs, A1s, rs, ks, qs, tune: bool = True, rank_tol: float = 0.0, stream=None):
+        torch = _torch()
+        lib = library()
+        cnt = len(Xs)
+        if cnt < 1 or len(A1s) != cnt:
+            raise ValueError("need as many A1 as X, at least one")
+        as_list = lambda v: [int(x) for x in v] if hasattr(v, "__len__") else [int(v)] * cnt
+        rs, ks, qs = as_list(rs), as_list(ks), as_list(qs)
+        if not (len(rs) == len(ks) == len(qs) == cnt):
+            raise ValueError("rs, ks and qs need one entry per problem")
+        self._X = [_padded(X) for X in Xs]
+        self._A1 = [A.contiguous().to(torch.float32) for A in A1s]
+        self.rs, self.ks, self.qs = rs, ks, qs
+        self.stream = stream
+        params = (GodecParams * cnt)()
+        for i, X in enumerate(self._X):
+            m, n = Xs[i].shape
+            params[i] = GodecParams(m=m, n=n, ldx=X.stride(0), r=rs[i], q=qs[i], k=ks[i], tol=-1.0,
+                                    max_iter=1 << 30, precision=PREC_FP32, rank_tol=float(rank_tol), flags=0,
+                                    reserved=0)
+        xp = (_P * cnt)(*[X.data_ptr() for X in self._X])
+        ap = (_P * cnt)(*[A.data_ptr() for A in self._A1])
+        h = C.c_void_p()
+        st = lib.godec_batch_init(C.byref(h), cnt, params, xp, ap, 0 if tune else BATCH_NO_TUNE,
+                                  _stream_ptr(stream))
+        _bcheck(st, "godec_batch_init", None)
+        self._b = h
+        self.count = cnt
+        self._shapes = [tuple(X.shape) for X in Xs]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            library().godec_batch_destroy(self._b)
+            self._b = None
+
+    __del__ = close
+
+    def iterate(self, n_iter: int = 1):
+        _bcheck(library().godec_batch_iterate(self._b, int(n_iter)), "godec_batch_iterate", self._b)
+
+    def reset(self):
+        _bcheck(library().godec_batch_reset(self._b), "godec_batch_reset", self._b)
+
+    def problem(self, i: int) -> GoDec:
+        h = library().godec_batch_problem(self._b, int(i))
+        if not h:
+            raise IndexError(f"problem {i} out of range")
+        m, n = self._shapes[i]
+        return _Problem(self, C.c_void_p(h), self._X[i][:, :n], self._A1[i], self.rs[i], self.ks[i], self.qs[i])
+
+    def tuning(self) -> dict:
+        sm = (C.c_int32 * self.count)()
+        ms = (C.c_double * BATCH_POLICIES)()
+        pol, rec = C.c_int32(0), C.c_int32(0)
+        _bcheck(library().godec_batch_tuning(self._b, sm, ms, C.byref(pol), C.byref(rec)), "godec_batch_tuning",
+                self._b)
+        return {"sm": list(sm), "policy_ms": list(ms), "policy": pol.value, "recaptures": rec.value}

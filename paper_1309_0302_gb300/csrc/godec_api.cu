@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -46,7 +47,9 @@ struct godec_ctx {
   cudaStream_t side_st = nullptr;   // off-critical-path work of the power chain
   cudaEvent_t ev[kEvents] = {};
   int ev_used = 0;
-  int dev = 0, nsm = 0;
+  int dev = 0, nsm = 0;   // nsm: the SMs this problem's grids are sized for (its budget)
+  int nsm_dev = 0;          // SMs of the device
+  size_t npart_cap = 0, npend_cap = 0;   // stream-K buffers (sized for the whole device)
   const float* X = nullptr;
   float* Z = nullptr;                  // m x ldz   working X - S
   int64_t ldz = 0;
@@ -848,6 +851,7 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   } while (0)
   CKI(cudaGetDevice(&c->dev));
   CKI(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
+  c->nsm_dev = c->nsm;
   CKI(prepare_small_kernels());
   CKI(prepare_select_kernels());
   CKI(prepare_stream_kernels());
@@ -912,10 +916,12 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   size_t npart = 0;
   for (const TcGeom& g : c->tg) npart = std::max(npart, (size_t)g.tiles * g.maxseg * 128 * RP);
   CKI(dalloc(&c->part, npart));
+  c->npart_cap = npart;
   {
     size_t npend = 0;
     for (const TcGeom& g : c->tg) npend = std::max(npend, (size_t)g.G * g.maxpend);
     CKI(dalloc(&c->pend, npend));
+    c->npend_cap = npend;
   }
   const int64_t tiles = prod_tiles(mx);
   c->ncounters = tiles;
@@ -1398,5 +1404,320 @@ godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz, co
                            float* W, void* stream) {
   return mul_common(Z, m, n, ldz, C, r, W, stream, 1);
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Batched form: many independent problems of uneven m, n and r.  One batch iteration is
+// one launch of one CUDA graph holding an iteration of every problem as a parallel
+// branch, all on the exact-normaliser path: with lagged normalisers, problems shaped
+// like the batched workload (2-5 % of entries in S, whose support moves between
+// iterations) raised the normaliser alarm in nearly every iteration, and every change of
+// path means capturing the whole batch graph again.  So the graph is captured once (and
+// again only after a rank drop).  Each problem's grids are sized for a share of the SMs
+// (its budget), so the branches' kernels run side by side and one problem's
+// latency-bound r x r work overlaps another's streaming.  An autotuner picks the budget
+// policy by timing the batch graph of each candidate on the problems themselves.
+// ---------------------------------------------------------------------------------
+struct godec_batch {
+  std::vector<godec_ctx*> ctx;
+  std::vector<int> sm;           // budget of each problem
+  std::vector<int> graph_r;      // each problem's r when the graph was captured
+  int recaptures = 0;            // batch graphs captured since init
+  Ctl* hctl = nullptr;           // pinned host copies of the control blocks (count)
+  cudaStream_t st = nullptr;     // the caller's stream
+  cudaStream_t cap_st = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec = nullptr;
+  int policy = 0;
+  double policy_ms[GODEC_BATCH_POLICIES] = {};
+  char err[200] = {0};
+};
+
+namespace {
+
+godec_status bfail(godec_batch* b, godec_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b->err, sizeof(b->err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+// Size every grid of problem c for B SMs (the stream-K geometry of both product
+// orientations and the S-step's grids).  The stream-K buffers were sized for the whole
+// device at init; a smaller grid never needs more (fewer CTAs split each tile less).
+godec_status set_budget(godec_ctx* c, int B) {
+  B = std::max(1, std::min(B, c->nsm_dev));
+  const TcGeom g0 = tc_geometry(c->p.m, c->p.n, B), g1 = tc_geometry(c->p.n, c->p.m, B);
+  size_t npart = 0, npend = 0;
+  for (const TcGeom& g : {g0, g1}) {
+    npart = std::max(npart, (size_t)g.tiles * g.maxseg * 128 * c->RP);
+    npend = std::max(npend, (size_t)g.G * g.maxpend);
+  }
+  if (npart > c->npart_cap || npend > c->npend_cap)
+    return fail(c, GODEC_ERR_STATE, "budget %d needs larger stream-K buffers", B);
+  c->nsm = B;
+  c->tg[0] = g0;
+  c->tg[1] = g1;
+  free_graphs(c);
+  return GODEC_OK;
+}
+
+// Budgets of policy k: 0 gives every problem the whole device; 1..4 give problem i a
+// share of the SMs proportional to its m n, oversubscribed 1, 2, 4 and 8 times (at
+// least 4 SMs, at most all).
+void policy_budgets(const godec_batch* b, int k, std::vector<int>& out) {
+  const int N = b->ctx[0]->nsm_dev;
+  double W = 0.0;
+  for (godec_ctx* c : b->ctx) W += (double)c->p.m * (double)c->p.n;
+  out.resize(b->ctx.size());
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    if (k == 0) {
+      out[i] = N;
+      continue;
+    }
+    const double alpha = (double)(1 << (k - 1));
+    const double w = (double)b->ctx[i]->p.m * (double)b->ctx[i]->p.n;
+    const int B = (int)std::ceil(alpha * N * w / W);
+    out[i] = std::max(4, std::min(N, B));
+  }
+}
+
+godec_status apply_budgets(godec_batch* b, const std::vector<int>& bud) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    godec_status s = set_budget(b->ctx[i], bud[i]);
+    if (s) return bfail(b, s, "problem %zu: %s", i, b->ctx[i]->err);
+  }
+  b->sm = bud;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  return GODEC_OK;
+}
+
+// Capture one iteration of every problem, each a branch forked from and joined into the
+// batch's capture stream.
+godec_status build_batch_graph(godec_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return bfail(b, GODEC_ERR_CUDA, "stream synchronize failed");
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap_st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->cap_st);
+  for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i) {
+    godec_ctx* c = b->ctx[i];
+    cudaStream_t user = c->st;
+    c->st = c->cap_st;
+    e = cudaStreamWaitEvent(c->st, b->fork, 0);
+    if (e == cudaSuccess) {
+      enqueue_iteration(c, false);
+      e = cudaEventRecord(b->join[i], c->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap_st, b->join[i], 0);
+    c->st = user;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->cap_st, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, GODEC_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&b->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, GODEC_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+  b->graph_r.resize(b->ctx.size());
+  for (size_t i = 0; i < b->ctx.size(); ++i) b->graph_r[i] = b->ctx[i]->r;
+  ++b->recaptures;
+  return GODEC_OK;
+}
+
+// Control blocks of every problem: one copy each into pinned memory, one synchronise.
+godec_status read_all(godec_batch* b) {
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (cudaMemcpyAsync(&b->hctl[i], b->ctx[i]->ctl, offsetof(Ctl, hist), cudaMemcpyDeviceToHost, b->st) !=
+        cudaSuccess)
+      return bfail(b, GODEC_ERR_CUDA, "control block copy failed");
+  if (cudaStreamSynchronize(b->st) != cudaSuccess)
+    return bfail(b, GODEC_ERR_CUDA, "batch iteration: %s", cudaGetErrorString(cudaGetLastError()));
+  return GODEC_OK;
+}
+
+godec_status batch_reset(godec_batch* b) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    godec_status s = reset_state(b->ctx[i]);
+    if (s) return bfail(b, s, "problem %zu: %s", i, b->ctx[i]->err);
+  }
+  return GODEC_OK;
+}
+
+// n_iter launches of the batch graph; then a problem whose iteration aborted in the graph
+// (its later launches skipped it) is handled and catches up on its own graphs.
+godec_status batch_iterate(godec_batch* b, int n_iter) {
+  if (n_iter <= 0) return GODEC_OK;
+  const size_t P = b->ctx.size();
+  godec_status s = read_all(b);
+  if (s) return s;
+  std::vector<char> out(P);   // sits out: converged or failed before this call
+  std::vector<int> before(P);
+  bool rebuild = !b->gexec;
+  for (size_t i = 0; i < P; ++i) {
+    out[i] = b->hctl[i].abort ? 1 : 0;
+    before[i] = b->hctl[i].iter;
+    rebuild = rebuild || b->graph_r[i] != b->ctx[i]->r;
+  }
+  if (rebuild && (s = build_batch_graph(b))) return s;
+  for (int t = 0; t < n_iter; ++t)
+    if (cudaGraphLaunch(b->gexec, b->st) != cudaSuccess) return bfail(b, GODEC_ERR_CUDA, "batch graph launch failed");
+  if ((s = read_all(b))) return s;
+  for (size_t i = 0; i < P; ++i) {
+    if (out[i]) continue;
+    godec_ctx* c = b->ctx[i];
+    const Ctl& h = b->hctl[i];
+    const int done = h.iter - before[i];
+    c->exact_iters += done;
+    if (done < n_iter) {
+      if (!h.abort) return bfail(b, GODEC_ERR_STATE, "problem %zu: %d of %d iterations ran", i, done, n_iter);
+      if (h.converged) continue;
+      if ((s = handle_abort(c, h)) || (s = run_iterations(c, n_iter - done, -1.0)))
+        return bfail(b, s, "problem %zu: %s", i, c->err);
+    }
+  }
+  return GODEC_OK;
+}
+
+void batch_free(godec_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (godec_ctx* c : b->ctx) godec_destroy(c);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->cap_st) cudaStreamDestroy(b->cap_st);
+  if (b->hctl) cudaFreeHost(b->hctl);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+godec_status godec_batch_init(godec_batch** out, int32_t count, const godec_params* params, const float* const* X,
+                              const float* const* A1, int32_t flags, void* stream) {
+  if (!out) return GODEC_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || count > GODEC_BATCH_MAX || !params || !X || !A1) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_batch_init: need 1 <= count <= %d and non-NULL arrays",
+             GODEC_BATCH_MAX);
+    return GODEC_ERR_ARG;
+  }
+  for (int i = 0; i < count; ++i)
+    if (params[i].precision != GODEC_PREC_FP32) {
+      snprintf(g_static_err, sizeof(g_static_err), "godec_batch_init: problem %d: the batched form is float32", i);
+      return GODEC_ERR_ARG;
+    }
+  godec_batch* b = new (std::nothrow) godec_batch;
+  if (!b) return GODEC_ERR_OOM;
+  b->st = reinterpret_cast<cudaStream_t>(stream);
+  auto bail = [&](godec_status s, const char* why) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_batch_init: %.180s", why);
+    batch_free(b);
+    return s;
+  };
+  if (cudaStreamCreateWithFlags(&b->cap_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return bail(GODEC_ERR_CUDA, "stream or event creation failed");
+  if (cudaMallocHost(reinterpret_cast<void**>(&b->hctl), (size_t)count * sizeof(Ctl)) != cudaSuccess)
+    return bail(GODEC_ERR_OOM, "pinned control blocks");
+  b->join.assign(count, nullptr);
+  b->ctx.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
+      return bail(GODEC_ERR_CUDA, "event creation failed");
+    godec_ctx* c = nullptr;
+    godec_status s = godec_init(&c, &params[i], X[i], A1[i], stream);
+    if (s) {
+      char why[200];
+      snprintf(why, sizeof(why), "problem %d: %.150s", i, g_static_err);
+      return bail(s, why);
+    }
+    b->ctx.push_back(c);
+  }
+  std::vector<int> bud;
+  if (flags & GODEC_BATCH_NO_TUNE) {
+    policy_budgets(b, 0, bud);
+    if (apply_budgets(b, bud)) return bail(GODEC_ERR_STATE, b->err);
+    b->policy = 0;
+  } else {
+    // time 3 batch iterations of each policy after two warm-up ones (the first takes the
+    // exact path, the second the path the problems then keep), from the initial state
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return bail(GODEC_ERR_CUDA, "event creation failed");
+    double best = 0.0;
+    int best_k = 0;
+    godec_status s = GODEC_OK;
+    for (int k = 0; k < GODEC_BATCH_POLICIES && !s; ++k) {
+      policy_budgets(b, k, bud);
+      if ((s = apply_budgets(b, bud)) || (s = batch_iterate(b, 2))) break;
+      cudaEventRecord(e0, b->st);
+      for (int t = 0; t < 3; ++t) cudaGraphLaunch(b->gexec, b->st);
+      cudaEventRecord(e1, b->st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        s = bfail(b, GODEC_ERR_CUDA, "tuning launch failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      b->policy_ms[k] = ms / 3.0;
+      if (k == 0 || b->policy_ms[k] < best) {
+        best = b->policy_ms[k];
+        best_k = k;
+      }
+      s = batch_reset(b);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return bail(s, b->err);
+    policy_budgets(b, best_k, bud);
+    if (apply_budgets(b, bud) || batch_reset(b)) return bail(GODEC_ERR_STATE, b->err);
+    b->policy = best_k;
+  }
+  *out = b;
+  return GODEC_OK;
+}
+
+godec_status godec_batch_iterate(godec_batch* b, int32_t n_iter) {
+  if (!b) return GODEC_ERR_ARG;
+  if (n_iter < 0) return bfail(b, GODEC_ERR_ARG, "n_iter must be >= 0");
+  return batch_iterate(b, n_iter);
+}
+
+godec_status godec_batch_reset(godec_batch* b) {
+  if (!b) return GODEC_ERR_ARG;
+  return batch_reset(b);
+}
+
+godec_ctx* godec_batch_problem(godec_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->ctx.size()) return nullptr;
+  return b->ctx[i];
+}
+
+godec_status godec_batch_tuning(godec_batch* b, int32_t* sm, double* policy_ms, int32_t* policy,
+                                int32_t* recaptures) {
+  if (!b) return GODEC_ERR_ARG;
+  if (recaptures) *recaptures = b->recaptures;
+  if (sm)
+    for (size_t i = 0; i < b->sm.size(); ++i) sm[i] = b->sm[i];
+  if (policy_ms)
+    for (int k = 0; k < GODEC_BATCH_POLICIES; ++k) policy_ms[k] = b->policy_ms[k];
+  if (policy) *policy = b->policy;
+  return GODEC_OK;
+}
+
+void godec_batch_destroy(godec_batch* b) { batch_free(b); }
+
+const char* godec_batch_last_error(godec_batch* b) { return b ? b->err : g_static_err; }
 
 }  // extern "C"
