@@ -170,8 +170,7 @@ struct TcLaunch {
   void* gram_part;
   int gram_mode;
   int t_upper;             // Tn upper triangular (inverse of an upper-triangular factor)
-  int half_a;              // mapA is the float16 copy Z16 (box 64 halves x 128 rows); mapB's box
-                           // then spans only RP rounded up to 16 rows of the operand (its c1 terms)
+  int half_a;              // mapA is the float16 copy Z16 (box 64 halves x 128 rows)
   int* pend;               // G x geom.maxpend ints of scratch
   Ctl* ctl;
 };
