@@ -69,84 +69,110 @@ __global__ void k_refine_core(const float* __restrict__ Ra1, const float* __rest
 constexpr double kJacobiTol = 1e-14;
 
 // SVD of an n x n float64 matrix (n <= 64) by one-sided Jacobi (Hestenes): columns of
-// W = A V are rotated pairwise until orthogonal; one block of 64 threads, thread i owns
-// row i of W and of V.  Outputs the r leading singular triplets, descending:
-// U[:, :r] (n x r, float64, stride r), sigma[:r] (float32), V[:, :r] (n x r, stride r).
-__global__ void __launch_bounds__(64) k_svd_small(const double* __restrict__ A, int n, int r, double* __restrict__ Uo,
-                                                  float* __restrict__ sigma, double* __restrict__ Vo) {
+// W = A V are rotated pairwise until orthogonal.  Round-robin ordering: each round the
+// n/2 disjoint pairs go to one warp each (rows lane and lane + 32), one barrier per round.
+// Cyclic Jacobi converges quadratically, so a sweep whose largest |cos| between rotated
+// columns was below kJacobiQuad ends the iteration (the next would be near kJacobiTol).
+// Outputs the r leading singular triplets, descending: U[:, :r] (n x r, float64, stride
+// r), sigma[:r] (float32), V[:, :r] (n x r, stride r).  Launched with 32 ceil(n/2) threads.
+constexpr double kJacobiQuad = 1e-7;
+
+__global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A, int n, int r, double* __restrict__ Uo,
+                                                    float* __restrict__ sigma, double* __restrict__ Vo) {
   extern __shared__ double smd[];   // W, V: 2 x 64 x 65 doubles (dynamic)
   double (*W)[kMaxRP + 1] = reinterpret_cast<double (*)[kMaxRP + 1]>(smd);
   double (*V)[kMaxRP + 1] = W + kMaxRP;
-  __shared__ double red[3][2];
   __shared__ double nrm[kMaxRP];
   __shared__ int order[kMaxRP];
   __shared__ int s_rot;
-  const int i = threadIdx.x, lane = i & 31, w = i >> 5;
-  for (int j = 0; j < n; ++j) {
-    W[i][j] = (i < n) ? A[i * n + j] : 0.0;
+  __shared__ unsigned long long s_dmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    W[i][j] = A[e];
     V[i][j] = (i == j) ? 1.0 : 0.0;
   }
-  __syncthreads();
+  const int np = (n + 1) & ~1, npairs = np / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    if (i == 0) s_rot = 0;
     __syncthreads();
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double a = W[i][p] * W[i][p], b = W[i][q] * W[i][q], g = W[i][p] * W[i][q];
-        for (int o = 16; o; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (tid == 0) {
+      s_rot = 0;
+      s_dmax = 0ull;
+    }
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      if (warp < npairs) {
+        int p, q;
+        if (warp == 0) {
+          p = np - 1;
+          q = round;
+        } else {
+          p = (round + warp) % (np - 1);
+          q = (round - warp + np - 1) % (np - 1);
         }
-        if (lane == 0) {
-          red[0][w] = a;
-          red[1][w] = b;
-          red[2][w] = g;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
         }
-        __syncthreads();
-        a = red[0][0] + red[0][1];
-        b = red[1][0] + red[1][1];
-        g = red[2][0] + red[2][1];
-        __syncthreads();
-        // rotate unless the pair is orthogonal to the rounding level of a length-64 dot
-        // product in float64 (a tighter test never ends: rounding keeps |g| near it)
-        if (fabs(g) > kJacobiTol * sqrt(a * b) && g != 0.0) {
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          const double wp = W[i][p], wq = W[i][q], vp = V[i][p], vq = V[i][q];
-          W[i][p] = cs * wp - sn * wq;
-          W[i][q] = sn * wp + cs * wq;
-          V[i][p] = cs * vp - sn * vq;
-          V[i][q] = sn * vp + cs * vq;
-          if (i == 0) s_rot = 1;
+        if (q < n) {
+          double a = 0.0, b = 0.0, g = 0.0;
+          for (int i = lane; i < n; i += 32) {
+            const double wp = W[i][p], wq = W[i][q];
+            a += wp * wp;
+            b += wq * wq;
+            g += wp * wq;
+          }
+          for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
+          }
+          // rotate unless the pair is orthogonal to the rounding level of a length-64 dot
+          // product in float64 (a tighter test never ends: rounding keeps |g| near it)
+          if (fabs(g) > kJacobiTol * sqrt(a * b) && g != 0.0) {
+            const double zeta = (b - a) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+            for (int i = lane; i < n; i += 32) {
+              const double wp = W[i][p], wq = W[i][q], vp = V[i][p], vq = V[i][q];
+              W[i][p] = cs * wp - sn * wq;
+              W[i][q] = sn * wp + cs * wq;
+              V[i][p] = cs * vp - sn * vq;
+              V[i][q] = sn * vp + cs * vq;
+            }
+            if (lane == 0) {
+              s_rot = 1;
+              atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(fabs(g) / sqrt(a * b)));
+            }
+          }
         }
-        __syncthreads();
       }
-    if (!s_rot) break;
+      __syncthreads();
+    }
+    if (!s_rot || __longlong_as_double((long long)s_dmax) < kJacobiQuad) break;
   }
   // column norms, descending order
-  if (i < n) {
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s += W[k][i] * W[k][i];
-    nrm[i] = sqrt(s);
+  for (int i = tid; i < n; i += nt) {
+    double sm = 0.0;
+    for (int k = 0; k < n; ++k) sm += W[k][i] * W[k][i];
+    nrm[i] = sqrt(sm);
   }
   __syncthreads();
-  if (i < n) {
+  for (int i = tid; i < n; i += nt) {
     int rank = 0;
     for (int k = 0; k < n; ++k) rank += (nrm[k] > nrm[i]) || (nrm[k] == nrm[i] && k < i);
     order[rank] = i;
   }
   __syncthreads();
-  for (int j = 0; j < r; ++j) {
+  for (int e = tid; e < n * r; e += nt) {
+    const int i = e / r, j = e % r;
     const int col = order[j];
-    const double s = nrm[col];
-    if (i < n) {
-      Uo[i * r + j] = s > 0.0 ? W[i][col] / s : 0.0;
-      Vo[i * r + j] = V[i][col];
-    }
-    if (i == 0) sigma[j] = (float)s;
+    const double sv = nrm[col];
+    Uo[i * r + j] = sv > 0.0 ? W[i][col] / sv : 0.0;
+    Vo[i * r + j] = V[i][col];
   }
+  for (int j = tid; j < r; j += nt) sigma[j] = (float)nrm[order[j]];
 }
 
 }  // namespace
@@ -179,7 +205,7 @@ void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, co
 }
 
 void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st) {
-  k_svd_small<<<1, 64, kSvdSmem, st>>>(A, n, r, U, sigma, V);
+  k_svd_small<<<1, 32 * ((n + 1) / 2), kSvdSmem, st>>>(A, n, r, U, sigma, V);
 }
 
 }  // namespace godec

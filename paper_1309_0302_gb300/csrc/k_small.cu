@@ -540,6 +540,8 @@ struct SvdArgs2 {
   Ctl* ctl;
 };
 
+constexpr float kSvdQuad = 3e-4f;
+
 __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   Ctl* ctl = a.ctl;
   if (ctl->abort) return;
@@ -551,6 +553,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   __shared__ float s[kMaxRP];
   __shared__ int order[kMaxRP];
   __shared__ int rotated;
+  __shared__ unsigned s_dmax;        // largest |cos| between a rotated pair in this sweep (float bits)
   __shared__ float s_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, RP = a.RP;
@@ -601,7 +604,10 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   int sweeps = 0;
   for (; sweeps < 16; ++sweeps) {
     __syncthreads();                  // every thread has read the previous flag
-    if (tid == 0) rotated = 0;
+    if (tid == 0) {
+      rotated = 0;
+      s_dmax = 0u;
+    }
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
       if (warp < npairs) {
@@ -637,13 +643,23 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
               V[i][p] = c * vp - sn * vq;
               V[i][q] = sn * vp + c * vq;
             }
-            if (lane == 0) rotated = 1;
+            if (lane == 0) {
+              rotated = 1;
+              atomicMax(&s_dmax, __float_as_uint(fabsf(ga) / (sqrtf(al) * sqrtf(be))));
+            }
           }
         }
       }
       __syncthreads();
     }
+    // Cyclic Jacobi converges quadratically: after a sweep whose largest |cos| was below
+    // kSvdQuad, the next would see about its square (1e-7), far under the rotation test,
+    // and would rotate nothing; it is not run.
     if (!rotated) break;
+    if (__uint_as_float(s_dmax) < kSvdQuad) {
+      ++sweeps;
+      break;
+    }
   }
   // Newton-Schulz: V := V (3I - V^T V) / 2 restores orthonormality lost to rounding
   mm_1024(V, V, X1, r, true);                       // X1 = V^T V
