@@ -151,6 +151,27 @@ def oracle_rate(iters: int, seed: int = 1309):
     return (SAMPLE_ROWS / M) / per_iter, times, os.cpu_count()
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of rank r's replica: every rank solves its own problem of the same shape."""
+    return 1309 + rank
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time: the slowest rank's (all-reduce MAX; CUDA tensor under NCCL, CPU
+    tensor under gloo).  Without a process group, the local time."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, steps: int, ms: float) -> float:
+    """Whole-job iterations/s: the iterations of all ws replicas over the slowest rank's time."""
+    return ws * steps / (ms / 1000.0)
+
+
 def emit(line: dict):
     print(json.dumps(line), flush=True)
 
@@ -183,7 +204,7 @@ def run_gb300(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    d = synth.lowrank_sparse(M, N, R, K_CARD, -20.0, 20.0, 1e-2, 1309 + rank, "c2")
+    d = synth.lowrank_sparse(M, N, R, K_CARD, -20.0, 20.0, 1e-2, replica_seed(rank), "c2")
     X = torch.from_numpy(d["X"]).cuda()
     A1 = torch.from_numpy(d["A1"]).cuda()
     stream = torch.cuda.Stream()
@@ -203,18 +224,15 @@ def run_gb300(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ck = clocks.stop()
-        ms = e0.elapsed_time(e1)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         info = g.info()
         # per-kernel device times of the same iterations (eager launches bracketed by events)
         g.reset()
         prof = g.profile(args.steps)
         g.close()
-    value = ws * args.steps / (ms / 1000.0)
+    value = job_value(ws, args.steps, ms)
     npass = prof["launches"]["product"]
     pass_ms = prof["ms"]["product"] / max(npass, 1)
     achieved = prof["bytes_product"] / (pass_ms / 1000.0) / 1e9
