@@ -286,12 +286,13 @@ cudaError_t prepare_prod_t() {
 
 // ----------------------------------------------------------------------------------
 // Q = P T (T dense RP x RP; a triangular inverse is passed as a dense matrix), for
-// rows x RP row-major P.  64 rows per block, four threads per row (16 output columns
-// each); the block's rows are staged in shared memory before any output is written,
-// so P and Q may alias.  Optional outputs: Q itself, the float16 split transposed
-// copy for the tensor-core product, and the block's float Gram partial QᵀQ.
+// rows x RP row-major P.  32 rows per block, eight threads per row (8 output columns
+// each, RP a multiple of 8), two blocks per SM at the chain's sizes; the block's rows
+// are staged in shared memory before any output is written, so P and Q may alias.
+// Optional outputs: Q itself, the float16 split transposed copy for the tensor-core
+// product, and the block's float Gram partial QᵀQ.
 // ----------------------------------------------------------------------------------
-constexpr int RB = 64;              // rows per block
+constexpr int RB = 32;              // rows per block
 constexpr int AP_THREADS = 256;
 constexpr int AP_LD = kMaxRP + 1;   // odd stride: rows of a warp fall in different banks
 
@@ -305,37 +306,36 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * RB;
   const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
-  for (int e = tid; e < kMaxRP * kMaxRP; e += AP_THREADS) {
-    const int a = e / kMaxRP, c = e % kMaxRP;
-    Ts[a][c] = (a < RP && c < RP) ? T[a * RP + c] : 0.f;
-  }
+  for (int e = tid; e < RP * RP; e += AP_THREADS) Ts[e / RP][e % RP] = __ldg(T + e);
   for (int e = tid; e < RB * RP; e += AP_THREADS) {
     const int i = e / RP, c = e % RP;
     Ps[i][c] = (i < nrow) ? P[(r0 + i) * RP + c] : 0.f;
   }
   __syncthreads();
-  const int row = tid >> 2, cg = (tid & 3) * 16;   // this thread: row, columns cg .. cg+15
-  float q[16];
+  const int row = tid >> 3, cg = (tid & 7) * 8;   // this thread: row, columns cg .. cg+7
+  float q[8];
 #pragma unroll
-  for (int l = 0; l < 16; ++l) q[l] = 0.f;
+  for (int l = 0; l < 8; ++l) q[l] = 0.f;
   if (cg < RP) {
+#pragma unroll 4
     for (int a = 0; a < RP; ++a) {
       const float pa = Ps[row][a];
-      const float4* tr = reinterpret_cast<const float4*>(&Ts[a][cg]);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float4 t = tr[v];
-        q[4 * v] = fmaf(pa, t.x, q[4 * v]);
-        q[4 * v + 1] = fmaf(pa, t.y, q[4 * v + 1]);
-        q[4 * v + 2] = fmaf(pa, t.z, q[4 * v + 2]);
-        q[4 * v + 3] = fmaf(pa, t.w, q[4 * v + 3]);
-      }
+      const float4 t0 = *reinterpret_cast<const float4*>(&Ts[a][cg]);
+      const float4 t1 = *reinterpret_cast<const float4*>(&Ts[a][cg + 4]);
+      q[0] = fmaf(pa, t0.x, q[0]);
+      q[1] = fmaf(pa, t0.y, q[1]);
+      q[2] = fmaf(pa, t0.z, q[2]);
+      q[3] = fmaf(pa, t0.w, q[3]);
+      q[4] = fmaf(pa, t1.x, q[4]);
+      q[5] = fmaf(pa, t1.y, q[5]);
+      q[6] = fmaf(pa, t1.z, q[6]);
+      q[7] = fmaf(pa, t1.w, q[7]);
     }
   }
   __syncthreads();   // every thread has read its P row: Ps now holds Q
+  if (cg < RP)
 #pragma unroll
-  for (int l = 0; l < 16; ++l)
-    if (cg + l < RP) Ps[row][cg + l] = (row < nrow) ? q[l] : 0.f;
+    for (int l = 0; l < 8; ++l) Ps[row][cg + l] = (row < nrow) ? q[l] : 0.f;
   __syncthreads();
   if (Q)
     for (int e = tid; e < nrow * RP; e += AP_THREADS) Q[(r0 + e / RP) * RP + e % RP] = Ps[e / RP][e % RP];
@@ -360,6 +360,7 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
 #pragma unroll
     for (int v = 0; v < 4; ++v) g[u][v] = 0.f;
   if (4 * bi < RP && 4 * bj < RP) {
+#pragma unroll 4
     for (int i = 0; i < nrow; ++i) {
       float x[4], y[4];
 #pragma unroll
