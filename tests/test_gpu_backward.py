@@ -73,6 +73,41 @@ def test_backward_matches_oracle(m, n, rank, r, T, seed):
     assert err <= TOL_DX
 
 
+def test_backward_finite_differences_64_directions():
+    """The GPU adjoint against central differences of the loss (h = 1e-3, 64 random
+    directions), the loss evaluated in float64 on the GPU's own supports: the directional
+    derivatives dX . v agree with the differences to 1e-4 (relative, over all 64)."""
+    torch = pytest.importorskip("torch")
+    import paper_1309_0302_gb300 as G
+    m, n, r, T = 256, 192, 4, 3
+    d, X, A1, Us, Vs = _case(m, n, 4, 0.02, r, T, 11)
+    k = d["k"]
+    Lstar = Us @ Vs.T
+    Xg = X.clone().requires_grad_(True)
+    L = G.unrolled_godec(Xg, A1, r, k, T)
+    ((L - torch.from_numpy(Lstar).float().cuda()) ** 2).sum().backward()
+    dX = Xg.grad.cpu().numpy().astype(np.float64)
+    gpu = G.GoDec(X, A1, r, k, 0, tol=0.0, max_iter=T)
+    masks = []
+    for _ in range(T):
+        gpu.iterate(1)
+        masks.append(gpu.S()[0].cpu().numpy())
+    gpu.close()
+    X64, A64 = d["X"].astype(np.float64), d["A1"].astype(np.float64)
+    g = np.random.default_rng(12)
+    fd, dots = [], []
+    for _ in range(64):
+        v = g.standard_normal((m, n))
+        h = 1e-3
+        fd.append((O.unrolled_loss(X64 + h * v, A64, k, T, Lstar, masks)
+                   - O.unrolled_loss(X64 - h * v, A64, k, T, Lstar, masks)) / (2 * h))
+        dots.append(np.sum(dX * v))
+    fd, dots = np.array(fd), np.array(dots)
+    err = float(np.linalg.norm(fd - dots) / np.linalg.norm(fd))
+    print(f"finite differences, 64 directions: rel err {err:.2e}")
+    assert err <= 1e-4
+
+
 def test_backward_lowrank_equals_dense():
     torch = pytest.importorskip("torch")
     import paper_1309_0302_gb300 as G

@@ -214,6 +214,31 @@ def test_tangent_refine_exact_and_second_order():
     assert errs[1][1] < 0.05 * errs[0][1]                               # shrinks ~ theta^2
 
 
+def test_tangent_refine_first_order_in_the_tail():
+    """With a tail (Z - L* of spectral norm sigma_{r+1}), the correction's error stays first
+    order in the subspace error theta, but scaled by about sigma_{r+1} / sigma_1: the ratio
+    after / before is proportional to the tail level and independent of theta."""
+    g = np.random.default_rng(12)
+    Uf, _ = np.linalg.qr(g.standard_normal((80, 30)))
+    Vf, _ = np.linalg.qr(g.standard_normal((30, 30)))
+    ratios = {}
+    for tail in (1e-1, 1e-2, 1e-3):
+        lam = np.r_[[10.0, 6.0, 3.0], tail * 10.0 * (0.5 + 0.5 * g.uniform(size=27))]
+        Z = (Uf * lam) @ Vf.T
+        best = (Uf[:, :3] * lam[:3]) @ Vf[:, :3].T
+        for th in (1e-3, 1e-4):
+            gg = np.random.default_rng(7)
+            Up, _ = np.linalg.qr(Uf[:, :3] + th * gg.standard_normal((80, 3)))
+            Vp, _ = np.linalg.qr(Vf[:, :3] + th * gg.standard_normal((30, 3)))
+            before = _rel((Up @ Up.T) @ Z @ (Vp @ Vp.T), best)
+            after = _rel(O.dense_L(*O.tangent_refine(Z, Up, Vp)), best)
+            ratios[(tail, th)] = after / before
+            assert after / before <= 1.5 * lam[3:].max() / lam[0]
+    for tail in (1e-1, 1e-2, 1e-3):
+        assert ratios[(tail, 1e-4)] == pytest.approx(ratios[(tail, 1e-3)], rel=0.05)   # first order in theta
+    assert ratios[(1e-1, 1e-3)] / ratios[(1e-3, 1e-3)] == pytest.approx(100.0, rel=0.2)  # linear in the tail
+
+
 # --- P8: gradient of the unrolled q = 0 iterations (reading R14) ------------------------
 @pytest.fixture(scope="module")
 def grad_case():
@@ -245,3 +270,20 @@ def test_gradient_finite_differences(grad_case):
         fd = (O.unrolled_loss(X + h * v, A1, k, T, Lstar, masks)
               - O.unrolled_loss(X - h * v, A1, k, T, Lstar, masks)) / (2 * h)
         assert abs(fd - np.sum(gX * v)) <= 1e-6 * abs(fd)
+
+
+def test_gradient_finite_differences_64_directions(grad_case):
+    """The stated check of the adjoint: central differences with h = 1e-3 along 64 random
+    directions, against the reverse-mode gradient's directional derivatives."""
+    X, A1, k, T, Lstar, masks = grad_case
+    gX = O.unrolled_vjp(X, A1, k, T, Lstar, masks)
+    g = np.random.default_rng(9)
+    fd, dots = [], []
+    for _ in range(64):
+        v = g.standard_normal(X.shape)
+        h = 1e-3
+        fd.append((O.unrolled_loss(X + h * v, A1, k, T, Lstar, masks)
+                   - O.unrolled_loss(X - h * v, A1, k, T, Lstar, masks)) / (2 * h))
+        dots.append(np.sum(gX * v))
+    fd, dots = np.array(fd), np.array(dots)
+    assert np.linalg.norm(fd - dots) <= 1e-5 * np.linalg.norm(fd)
