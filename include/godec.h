@@ -67,7 +67,7 @@ typedef struct godec_params {
   int32_t max_iter;  /* iteration cap of godec_solve, >= 1 */
   int32_t precision; /* GODEC_PREC_* */
   double rank_tol;   /* relative singular-value tolerance of the rank test of
-                        Algorithm 1 (line 7); <= 0 selects 1e-4 */
+                        Algorithm 1; <= 0 selects 1e-4 */
   int32_t flags;     /* GODEC_FLAG_* */
   int32_t reserved;  /* must be 0 */
 } godec_params;
@@ -85,7 +85,8 @@ typedef struct godec_ctx godec_ctx;
  *   X  : device, m x ldx float32, BORROWED: it must stay valid and unchanged
  *        until godec_destroy.  ldx*4 must be a multiple of 16 bytes.
  *   A1 : device, n x r float32 (row-major), the random test matrix of
- *        Algorithm 1 line 5; copied.  Reading of the paper: A1 is drawn once
+ *        Algorithm 1 (the first factor of the power chain); copied.  Reading of the
+ *        paper: A1 is drawn once
  *        by the caller (e.g. standard Gaussian) and kept for all iterations.
  *   stream : cudaStream_t (as void*) on which all work of the context runs.
  * The context owns its workspace (about 4*m*n bytes for the working copy of
@@ -100,7 +101,7 @@ godec_status godec_init(godec_ctx** ctx, const godec_params* params,
 godec_status godec_reset(godec_ctx* ctx);
 
 /*
- * Run exactly n_iter iterations of Algorithm 1 (lines 3-9), ignoring the
+ * Run exactly n_iter iterations of Algorithm 1, ignoring the
  * stop test.  Each iteration: Z = X - S_{t-1}; L_t from the BRP power chain
  * with the rank test; S_t = P_Omega(X - L_t) with Omega the nonzero subset of
  * the k largest |X - L_t| (ties by ascending linear index).
@@ -140,7 +141,7 @@ godec_status godec_get_S(godec_ctx* ctx, int64_t* idx, float* val, int64_t cap, 
 
 /*
  * Dense residual R = X - L_t of the current state (the matrix the S-step of
- * Algorithm 1, line 9, thresholds), computed by the same tensor-core kernel and
+ * Algorithm 1 thresholds, eq. raw_lss), computed by the same tensor-core kernel and
  * arithmetic as the S-step's residual pass.
  *   R : device, m x ldr float32, ldr >= n.
  * GODEC_ERR_STATE before the first iteration.  Synchronises the stream.
@@ -192,7 +193,7 @@ godec_status godec_run_host(const godec_params* params, const float* X_host,
 
 /*
  * Streaming tall-skinny products (the "(X - S) A" contractions of Sec. 3.1,
- * Algorithm 1 lines 5-6), exposed for testing and benchmarking.
+ * the power chain of Algorithm 1), exposed for testing and benchmarking.
  *   godec_mul_ZB : Y = Z B,    Z m x n (row stride ldz), B n x r, Y m x r
  *   godec_mul_ZtC: W = Z^T C,  Z m x n (row stride ldz), C m x r, W n x r
  * All pointers are device float32, row-major with row stride r for B, C, Y,
@@ -266,8 +267,8 @@ godec_status godec_backward(const float* X, int64_t m, int64_t n, int64_t ldx, c
                             float* dX, int64_t lddx, void* stream);
 
 /*
- * Entry-wise hard threshold of a dense matrix (eq. raw_lss, Algorithm 1
- * line 9, with L = 0): the nonzero subset of the k largest |R|, ties by
+ * Entry-wise hard threshold of a dense matrix (eq. raw_lss, the S-step of
+ * Algorithm 1 with L = 0): the nonzero subset of the k largest |R|, ties by
  * ascending linear index, runs the same kernels as the S-step.
  *   R : device, m x ldr float32 (ldr*4 a multiple of 16 bytes, 16-byte aligned)
  *   idx, val : device int64[cap] / float32[cap], receive the COO sorted by

@@ -16,10 +16,10 @@ RANK_TOL = 1e-4
 
 
 # ----------------------------------------------------------------------------
-# L-step (Sec. 3.1.1-3.1.3, eqs. lr_app / mlr_app, Algorithm 1 lines 4-8)
+# L-step (Sec. 3.1.1-3.1.3, eqs. lr_app / mlr_app, Algorithm 1)
 # ----------------------------------------------------------------------------
 def ltilde_times(Z: np.ndarray, B: np.ndarray, q: int) -> np.ndarray:
-    """L~ B = (Z Z^T)^q Z B, evaluated right to left (Algorithm 1, line 4)."""
+    """L~ B = (Z Z^T)^q Z B, evaluated right to left (Algorithm 1, the product L~ A1)."""
     Y = Z @ B
     for _ in range(q):
         Y = Z @ (Z.T @ Y)
@@ -27,7 +27,7 @@ def ltilde_times(Z: np.ndarray, B: np.ndarray, q: int) -> np.ndarray:
 
 
 def ltilde_t_times(Z: np.ndarray, B: np.ndarray, q: int) -> np.ndarray:
-    """L~^T B = Z^T (Z Z^T)^q B (Algorithm 1, line 6)."""
+    """L~^T B = Z^T (Z Z^T)^q B (Algorithm 1, the product L~^T Y1)."""
     Y = B
     for _ in range(q):
         Y = Z @ (Z.T @ Y)
@@ -35,7 +35,7 @@ def ltilde_t_times(Z: np.ndarray, B: np.ndarray, q: int) -> np.ndarray:
 
 
 def numerical_rank(Z: np.ndarray, Q2: np.ndarray, tol: float = RANK_TOL) -> int:
-    """Numerical rank used by the test 'rank(A2^T Y1) < r' (Algorithm 1, line 7).
+    """Numerical rank used by the test 'rank(A2^T Y1) < r' (Algorithm 1's rank test).
 
     Reading R6: A2^T Y1 = Y2^T Y2 (since Y1 = L~ Y2 and A2 = Y1^0 = L~ A1), so
     its rank is rank(Y2) = rank(Z Q2) with Q2 an orthonormal basis of
@@ -134,7 +134,7 @@ def dense_L(U, sigma, V):
 
 
 # ----------------------------------------------------------------------------
-# S-step (eq. raw_lss, Algorithm 1 line 9)
+# S-step (eq. raw_lss, Algorithm 1)
 # ----------------------------------------------------------------------------
 def hard_threshold(R: np.ndarray, k: int):
     """Omega = the nonzero subset of the k largest entries of |R|.

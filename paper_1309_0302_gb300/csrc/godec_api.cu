@@ -276,7 +276,7 @@ void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const fl
   PROF(c, 3, c->st, launch_apply(P, rows, c->RP, T0, T1, Q, gram, c->ctl, c->st, bt2out, c->ldb));
 }
 
-// Exact CholeskyQR2 of c->P (rows x RP) with the round-1 Gram g1: Q = P Ra^{-1} Rb^{-1},
+// Exact CholeskyQR2 of c->P (rows x RP) with the first-pass Gram g1: Q = P Ra^{-1} Rb^{-1},
 // written to fin and, if bt2out is set, as the next product's operand.
 void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* Rb, float* fin, double* g2,
                 void* bt2out) {
@@ -362,7 +362,7 @@ void refine(godec_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------------
-// L-step (Algorithm 1 lines 4-8)
+// L-step of Algorithm 1 (power chain, rank test, core and root)
 // ---------------------------------------------------------------------------------
 void enqueue_lstep(godec_ctx* c, bool fast) {
   const int q = c->p.q, RP = c->RP;
@@ -480,7 +480,7 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
   PROF(c, 3, c->st, launch_lsplit(c->U, c->V, c->sigma, m, n, RP, c->r, c->ctl->zscale, c->LA, c->LB, c->st));
 }
 
-// S-step of one iteration (Algorithm 1 line 9) on the current L factors; r = 0 means L = 0.
+// S-step of one iteration (Algorithm 1, eq. raw_lss) on the current L factors; r = 0 means L = 0.
 void enqueue_sstep(godec_ctx* c, int r) {
   const int64_t m = c->p.m, n = c->p.n;
   cudaStream_t st = c->st;

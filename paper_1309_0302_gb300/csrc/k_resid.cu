@@ -1,4 +1,4 @@
-// Residual pass of the S-step on the tensor cores (Algorithm 1, line 9).
+// Residual pass of the S-step on the tensor cores (Algorithm 1, eq. raw_lss).
 //
 //   R = X - L,   L = U diag(sigma) V^T = (A B^T) / s_Z,
 //   A = U diag(sqrt(sigma s_Z)),  B = V diag(sqrt(sigma s_Z))

@@ -1,4 +1,4 @@
-// S-step of Algorithm 1 (line 9, eq. raw_lss): S_t = P_Omega(X - L_t) with Omega
+// S-step of Algorithm 1 (eq. raw_lss): S_t = P_Omega(X - L_t) with Omega
 // the nonzero subset of the k largest |X - L_t|, ties by ascending linear index.
 //
 // One pass over X rebuilds R = X - U diag(sigma) V^T tile by tile.  Magnitudes

@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
   }
 }
 
-// ---- off the critical path: rank test (Algorithm 1 line 7) -----------------------------
+// ---- off the critical path: the rank test of Algorithm 1 --------------------------------
 // Reading of "rank(A2^T Y1) < r": A2^T Y1 = Y2^T Y2, whose rank is that of Z Q2.  Count
 // the pivots of a pivoted Cholesky of (Z Q2)^T (Z Q2) (exact float32 products summed in
 // double-float, reduced in float64) above rank_tol^2 of the largest.

@@ -1,4 +1,4 @@
-// Streaming tall-skinny products over X - S (Algorithm 1, lines 5-6).
+// Streaming tall-skinny products over X - S (the power chain of Algorithm 1).
 //
 // Both products of the power chain, Z B and Z^T C, are computed as
 // "row-major source times skinny matrix": Z^T C streams the transposed copy

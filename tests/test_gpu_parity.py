@@ -32,7 +32,7 @@ def _lib():
     G.library()
 
 
-# --- streaming products (Algorithm 1 lines 5-6) ---------------------------------------
+# --- streaming products (the power chain of Algorithm 1) ------------------------------
 @pytest.mark.parametrize("m,n,r", [(1000, 777, 50), (777, 1000, 3), (64, 64, 1), (2049, 131, 64),
                                    (5, 3000, 8), (3000, 7, 13), (130, 129, 33)])
 def test_mul_primitives(m, n, r):
@@ -147,7 +147,7 @@ def test_odd_shapes_trajectory(m, n, rank, r, q, dens):
     assert inside, nb
 
 
-# --- rank test (Algorithm 1 line 7) -------------------------------------------------------
+# --- rank test of Algorithm 1 ------------------------------------------------------------
 @pytest.mark.parametrize("q", [0, 1, 2])
 def test_rank_drop_exact_recovery(q):
     g = np.random.default_rng(40 + q)

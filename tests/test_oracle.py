@@ -99,7 +99,7 @@ def test_deterministic_error_bound(q, decay_hi):
     assert worst <= 1.0 + 1e-9
 
 
-# --- P4: rank check (Algorithm 1, line 7) -------------------------------------------
+# --- P4: rank check (Algorithm 1's rank test) ---------------------------------------
 @pytest.mark.parametrize("q", [0, 1, 2])
 def test_rank_check_reduces_r(q):
     X = _lowrank(50, 40, 4, seed=20)
@@ -121,7 +121,7 @@ def test_godec_rank_drop_keeps_reduced_r():
     assert _rel(O.dense_L(res["U"], res["sigma"], res["V"]), X) < 1e-12
 
 
-# --- P5: S-step = exhaustive top-k with ties and zeros (eq. raw_lss, Algorithm 1 line 9)
+# --- P5: S-step = exhaustive top-k with ties and zeros (eq. raw_lss, Algorithm 1)
 def _brute_topk(R, k):
     n = R.shape[1]
     cells = [(abs(R[i, j]), i * n + j) for i in range(R.shape[0]) for j in range(n)]
