@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched"], default=None,
+    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched", "c1"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
@@ -375,7 +375,6 @@ def run_kernel_case(args):
         # batched form at C4 (64 problems, m, n log-uniform in [256, 4096], r in 2..32, q = 1):
         # tuned batch, untuned batch (all SMs for every problem) and the same problems one by
         # one through the single-problem API, 20 iterations each after 2 warm-up ones
-        import time
         ds = synth.config_c4()
         Xs = [torch.from_numpy(d["X"]).cuda() for d in ds]
         A1s = [torch.from_numpy(d["A1"]).cuda() for d in ds]
@@ -418,6 +417,41 @@ def run_kernel_case(args):
         print("C4 budgets (SMs) of the tuned policy:", res[True][1]["sm"])
         print(f"C4 one problem at a time: {single:.3f} ms per round of 64 iterations, "
               f"{64e3 / single:.0f} problem-iterations/s")
+    elif args.kernel == "c1":
+        # C1 (500 x 500, rank 10, k = 12500, q = 1): L2-resident, so iterations/s only.  GPU:
+        # 50 graph-replayed iterations after 3 warm-up ones, and a solve to tol 1e-7; the
+        # float64 oracle on all host cores and, in a child process, on one core
+        d = synth.config_c1()
+        X = torch.from_numpy(d["X"]).cuda()
+        A1 = torch.from_numpy(d["A1"]).cuda()
+        g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=-1.0, max_iter=1 << 20)
+        g.iterate(3)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(torch.cuda.current_stream())
+        g.iterate(50)
+        ev[1].record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / 50
+        g.close()
+        g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=1e-7, max_iter=50)
+        t0 = time.time()
+        it, rel = g.solve()
+        t_solve = time.time() - t0
+        g.close()
+        import oracle as O
+        t0 = time.time()
+        O.godec(d["X"], d["A1"], d["k"], d["q"], tol=-1.0, max_iter=5)
+        o_all = (time.time() - t0) / 5
+        code = ("import sys, time; sys.path.insert(0, %r); import synth, oracle as O; d = synth.config_c1(); "
+                "t0 = time.time(); O.godec(d['X'], d['A1'], d['k'], d['q'], tol=-1.0, max_iter=5); "
+                "print((time.time() - t0) / 5)") % ROOT
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        o_one = float(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                                     check=True).stdout.strip().splitlines()[-1])
+        print(f"C1 GPU: {ms:.3f} ms/iteration ({1e3 / ms:.0f} it/s); solve to tol 1e-7: {it} iterations, "
+              f"rel err {rel:.2e}, {t_solve * 1e3:.1f} ms wall; float64 oracle: {1.0 / o_all:.1f} it/s on "
+              f"{os.cpu_count()} cores, {1.0 / o_one:.1f} it/s on one core")
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
         run = G.GoDec(torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda(), R, d["k"], Q)
