@@ -363,6 +363,25 @@ void godec_batch_destroy(godec_batch* b);
 /* Message of the last failed call on b (b NULL: of the last failed godec_batch_init). */
 const char* godec_batch_last_error(godec_batch* b);
 
+/*
+ * The tuner's budget rule, host logic only (no device work): sm[i] (host, count entries)
+ * receives the SMs policy gives problem i of shape m[i] x n[i] (host arrays) on a device
+ * of nsm SMs: policy 0 -> nsm; policy k = 1..4 -> max(min(4, nsm), min(nsm,
+ * ceil(2^(k-1) nsm m_i n_i / sum m n))).  GODEC_ERR_ARG on a bad argument.
+ */
+godec_status godec_batch_budgets(int32_t count, const int64_t* m, const int64_t* n, int32_t nsm, int32_t policy,
+                                 int32_t* sm);
+
+/*
+ * Stream-K geometry of the tensor-core product over a rows x K operand on nsm SMs, host
+ * logic only (no device work).  out (host, 6 entries) receives: row tiles of 128,
+ * K-stages of 64 per tile, stages S = tiles x stages, CTAs G (all SMs, or four fewer
+ * above 16, at most S; CTA c owns stages [c S / G, (c+1) S / G)), the most CTAs that
+ * share one tile (partial slots per tile), and the most tiles one CTA's range touches
+ * (completions it may owe).  GODEC_ERR_ARG on a bad argument.
+ */
+godec_status godec_tc_geometry(int64_t rows, int64_t K, int32_t nsm, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

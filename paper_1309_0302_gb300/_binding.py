@@ -75,6 +75,8 @@ def _declare(lib):
         "godec_batch_tuning": ([_P, i32p, f64p, i32p, i32p], C.c_int),
         "godec_batch_destroy": ([_P], None),
         "godec_batch_last_error": ([_P], C.c_char_p),
+        "godec_batch_budgets": ([C.c_int32, i64p, i64p, C.c_int32, C.c_int32, i32p], C.c_int),
+        "godec_tc_geometry": ([C.c_int64, C.c_int64, C.c_int32, i64p], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -470,3 +472,20 @@ class GoDecBatch:
         _bcheck(library().godec_batch_tuning(self._b, sm, ms, C.byref(pol), C.byref(rec)), "godec_batch_tuning",
                 self._b)
         return {"sm": list(sm), "policy_ms": list(ms), "policy": pol.value, "recaptures": rec.value}
+
+
+def batch_budgets(shapes, nsm: int, policy: int):
+    """The batched form's SM budgets of one tuner policy (host logic, no device work)."""
+    cnt = len(shapes)
+    m = (C.c_int64 * cnt)(*[int(a) for a, _ in shapes])
+    n = (C.c_int64 * cnt)(*[int(b) for _, b in shapes])
+    out = (C.c_int32 * cnt)()
+    _check(library().godec_batch_budgets(cnt, m, n, int(nsm), int(policy), out), "godec_batch_budgets")
+    return list(out)
+
+
+def tc_geometry(rows: int, K: int, nsm: int) -> dict:
+    """Stream-K geometry of the tensor-core product (host logic, no device work)."""
+    out = (C.c_int64 * 6)()
+    _check(library().godec_tc_geometry(int(rows), int(K), int(nsm), out), "godec_tc_geometry")
+    return dict(zip(("tiles", "ks", "S", "G", "maxseg", "maxpend"), list(out)))

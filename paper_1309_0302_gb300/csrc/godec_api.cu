@@ -1465,24 +1465,31 @@ godec_status set_budget(godec_ctx* c, int B) {
   return GODEC_OK;
 }
 
-// Budgets of policy k: 0 gives every problem the whole device; 1..4 give problem i a
-// share of the SMs proportional to its m n, oversubscribed 1, 2, 4 and 8 times (at
-// least 4 SMs, at most all).
-void policy_budgets(const godec_batch* b, int k, std::vector<int>& out) {
-  const int N = b->ctx[0]->nsm_dev;
+// Budgets of policy k on N SMs: 0 gives every problem the whole device; 1..4 give problem i
+// a share of the SMs proportional to its m n, oversubscribed 1, 2, 4 and 8 times (at least
+// 4 SMs, at most all).
+void budgets_of(int count, const int64_t* m, const int64_t* n, int N, int k, int* out) {
   double W = 0.0;
-  for (godec_ctx* c : b->ctx) W += (double)c->p.m * (double)c->p.n;
-  out.resize(b->ctx.size());
-  for (size_t i = 0; i < b->ctx.size(); ++i) {
+  for (int i = 0; i < count; ++i) W += (double)m[i] * (double)n[i];
+  for (int i = 0; i < count; ++i) {
     if (k == 0) {
       out[i] = N;
       continue;
     }
     const double alpha = (double)(1 << (k - 1));
-    const double w = (double)b->ctx[i]->p.m * (double)b->ctx[i]->p.n;
-    const int B = (int)std::ceil(alpha * N * w / W);
-    out[i] = std::max(4, std::min(N, B));
+    const int B = (int)std::ceil(alpha * N * ((double)m[i] * (double)n[i]) / W);
+    out[i] = std::max(std::min(4, N), std::min(N, B));
   }
+}
+
+void policy_budgets(const godec_batch* b, int k, std::vector<int>& out) {
+  std::vector<int64_t> m(b->ctx.size()), n(b->ctx.size());
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    m[i] = b->ctx[i]->p.m;
+    n[i] = b->ctx[i]->p.n;
+  }
+  out.resize(b->ctx.size());
+  budgets_of((int)b->ctx.size(), m.data(), n.data(), b->ctx[0]->nsm_dev, k, out.data());
 }
 
 godec_status apply_budgets(godec_batch* b, const std::vector<int>& bud) {
@@ -1717,6 +1724,30 @@ godec_status godec_batch_tuning(godec_batch* b, int32_t* sm, double* policy_ms, 
 }
 
 void godec_batch_destroy(godec_batch* b) { batch_free(b); }
+
+godec_status godec_batch_budgets(int32_t count, const int64_t* m, const int64_t* n, int32_t nsm, int32_t policy,
+                                 int32_t* sm) {
+  if (count < 1 || !m || !n || !sm || nsm < 1 || policy < 0 || policy >= GODEC_BATCH_POLICIES)
+    return GODEC_ERR_ARG;
+  for (int i = 0; i < count; ++i)
+    if (m[i] < 1 || n[i] < 1) return GODEC_ERR_ARG;
+  std::vector<int> out(count);
+  budgets_of(count, m, n, nsm, policy, out.data());
+  for (int i = 0; i < count; ++i) sm[i] = out[i];
+  return GODEC_OK;
+}
+
+godec_status godec_tc_geometry(int64_t rows, int64_t K, int32_t nsm, int64_t* out) {
+  if (rows < 1 || K < 1 || nsm < 1 || !out) return GODEC_ERR_ARG;
+  const TcGeom g = tc_geometry(rows, K, nsm);
+  out[0] = g.tiles;
+  out[1] = g.ks;
+  out[2] = g.S;
+  out[3] = g.G;
+  out[4] = g.maxseg;
+  out[5] = g.maxpend;
+  return GODEC_OK;
+}
 
 const char* godec_batch_last_error(godec_batch* b) { return b ? b->err : g_static_err; }
 
