@@ -109,6 +109,7 @@ struct godec_ctx {
   int idx_bits = 1;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // 0 exact path, 1 fast path
   int graph_r[2] = {-1, -1};
+  unsigned graph_epoch = 0;   // bumped whenever captured graphs become invalid (buffers, geometry)
   int graph_nodes = 0;
   bool need_exact = true;
   int exact_left = 0;   // exact iterations still owed after an alarm of the lagged normalisers
@@ -180,6 +181,7 @@ cudaError_t dalloc(T** p, size_t elems) {
 }
 
 void free_graphs(godec_ctx* c) {
+  ++c->graph_epoch;
   for (int k = 0; k < 2; ++k) {
     if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
     c->gexec[k] = nullptr;
@@ -1423,6 +1425,7 @@ struct godec_batch {
   std::vector<godec_ctx*> ctx;
   std::vector<int> sm;           // budget of each problem
   std::vector<int> graph_r;      // each problem's r when the graph was captured
+  std::vector<unsigned> graph_epoch;   // each problem's graph epoch at the capture
   int recaptures = 0;            // batch graphs captured since init
   Ctl* hctl = nullptr;           // pinned host copies of the control blocks (count)
   cudaStream_t st = nullptr;     // the caller's stream
@@ -1534,7 +1537,11 @@ godec_status build_batch_graph(godec_batch* b) {
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, GODEC_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
   b->graph_r.resize(b->ctx.size());
-  for (size_t i = 0; i < b->ctx.size(); ++i) b->graph_r[i] = b->ctx[i]->r;
+  b->graph_epoch.resize(b->ctx.size());
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    b->graph_r[i] = b->ctx[i]->r;
+    b->graph_epoch[i] = b->ctx[i]->graph_epoch;
+  }
   ++b->recaptures;
   return GODEC_OK;
 }
@@ -1571,7 +1578,9 @@ godec_status batch_iterate(godec_batch* b, int n_iter) {
   for (size_t i = 0; i < P; ++i) {
     out[i] = b->hctl[i].abort ? 1 : 0;
     before[i] = b->hctl[i].iter;
-    rebuild = rebuild || b->graph_r[i] != b->ctx[i]->r;
+    // a rank drop, a candidate buffer grown, a new budget or a reset: the captured
+    // graph holds stale sizes or pointers of that problem
+    rebuild = rebuild || b->graph_r[i] != b->ctx[i]->r || b->graph_epoch[i] != b->ctx[i]->graph_epoch;
   }
   if (rebuild && (s = build_batch_graph(b))) return s;
   for (int t = 0; t < n_iter; ++t)
