@@ -7,6 +7,8 @@ library routines (full SVD, sorting).
 """
 import itertools
 
+import os
+
 import numpy as np
 import pytest
 
@@ -191,6 +193,34 @@ def test_c1_end_state():
     # noise floor ||G||^2 (1 - k/mn)(1 - 2r/n) / ||X||^2 of reading P7
     floor = 0.25 * (1 - 0.05) * (1 - 0.04) / res["normX2"]
     assert 0.5 * floor < res["rel_err"][-1] < 1e-7
+
+
+# --- P7b: the paper's own figures (Table 1, first row; reading R16) ------------------------
+def test_table1_first_row_magnitudes():
+    """The oracle on Table 1's recipe (500 x 500, rank 25, card 12500, noise 1e-3, q = 2),
+    run to convergence, lands at the magnitudes the paper prints for GoDec (squared
+    relative errors of X, L and S).  The bounds are factor-level: a dropped term, a wrong
+    sign or an index slip moves them by orders of magnitude."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_godec_500.txt")
+    ref = dict(line.strip().split("=") for line in open(path) if "=" in line and not line.startswith("#"))
+    n, r, k = int(ref["size"]), int(ref["rank"]), int(ref["card"])
+    g = np.random.default_rng(100)
+    L = g.standard_normal((n, r)) @ g.standard_normal((r, n))
+    S = np.zeros(n * n)
+    S[g.choice(n * n, k, replace=False)] = g.standard_normal(k)
+    S = S.reshape(n, n)
+    X = L + S + 1e-3 * g.standard_normal((n, n))
+    res = O.godec(X, g.standard_normal((n, r)), k, 2, tol=-1.0, max_iter=30)
+    Lh = O.dense_L(res["U"], res["sigma"], res["V"])
+    Sh = np.zeros(n * n)
+    Sh[res["S_idx"]] = res["S_val"]
+    Sh = Sh.reshape(n, n)
+    ex = np.sum((X - Lh - Sh) ** 2) / np.sum(X ** 2)
+    el = np.sum((L - Lh) ** 2) / np.sum(L ** 2)
+    es = np.sum((S - Sh) ** 2) / np.sum(S ** 2)
+    assert 0.5 <= ex / float(ref["rel_err_X"]) <= 3.0
+    assert 0.1 <= el / float(ref["rel_err_L"]) <= 10.0
+    assert 0.5 <= es / float(ref["rel_err_S"]) <= 2.0
 
 
 # --- precision form: the tangent-space correction is second order (reading R11) ----------
