@@ -237,9 +237,10 @@ def run_gb300(args, ws, rank, local):
     achieved = prof["bytes_product"] / (pass_ms / 1000.0) / 1e9
     peak, peak_src = peaks()
     passes_per_iter = npass / args.steps
-    # algorithmic bytes of one iteration: every streaming product reads X - S once, the
-    # S-step pass reads X once (plus one more per extra selection pass), factors and S
-    bytes_iter = 4.0 * M * N * (passes_per_iter + prof["launches"]["residual"] / args.steps) \
+    # algorithmic bytes of one steady-state iteration: every streaming product reads X - S
+    # once, each residual pass the S-step used reads X once (the graph also holds passes that
+    # exit at once when the selection needs none: those are not counted), factors and S
+    bytes_iter = 4.0 * M * N * (passes_per_iter + max(1, int(info["select_passes"]))) \
         + 12.0 * K_CARD * 2 + 4.0 * (M + N) * R * passes_per_iter
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -255,7 +256,8 @@ def run_gb300(args, ws, rank, local):
                      "bytes_per_launch": prof["bytes_product"]},
         "iteration_roofline": {"achieved": bytes_iter * (value / ws) / 1e9, "unit": "GB/s",
                                "frac": bytes_iter * (value / ws) / 1e9 / peak,
-                               "bytes_per_iter": bytes_iter},
+                               "bytes_per_iter": bytes_iter,
+                               "residual_passes_per_iter": max(1, int(info["select_passes"]))},
         "kernel_ms_per_iter": {k: v / args.steps for k, v in prof["ms"].items()},
         "clocks": ck,
         "gpu_launches": int(info["launches_per_iter"]) * args.steps,
