@@ -9,6 +9,13 @@
  * (Sec. 3.1, eqs. lr_app and mlr_app), the S-step is the entry-wise hard
  * threshold keeping the k largest |X - L| (eq. raw_lss).
  *
+ * Forms: the plain float32 form (godec_init / iterate / solve); the precision form
+ * (godec_params.precision = GODEC_PREC_BF16_REFINE: a float16 power chain and one
+ * float32 correction per iteration); the batched form (godec_batch_*: many problems of
+ * uneven m, n, r in one CUDA graph per batch iteration); the differentiated form
+ * (godec_backward: the gradient with respect to X of a loss of T unrolled q = 0
+ * iterations); godec_run_host (host buffers in and out).
+ *
  * Conventions for every entry point:
  *  - Matrices are row-major.  "Device" pointers are CUDA global memory on the
  *    device that is current when godec_init is called; "host" pointers are
