@@ -11,8 +11,8 @@ Greedy Decomposition", arXiv:1309.0302): Algorithm 1 (GoDec by BRP), eq.
 (lr_app) and eq. (mlr_app) of Sec. 3.1, the entry-wise hard threshold of eq.
 (raw_lss), and the objective of eq. (ls_app).  Library primitives used as
 single steps: matrix product, Householder QR, SVD, solve, partition.
-``oracle.grebsmo`` holds GreBsmo (Sec. 3.2.1, Algorithm 2) and ``oracle.lingodec``
-LinGoDec (Sec. 4.3), the same way.
+``oracle.grebsmo`` holds GreBsmo (Sec. 3.2.1, Algorithm 2), ``oracle.lingodec`` LinGoDec
+(Sec. 4.3) and ``oracle.mse`` MSE training (Sec. 4.2.1, Algorithm 4), the same way.
 """
 from .godec import (  # noqa: F401
     ltilde_times, ltilde_t_times, numerical_rank, brp_literal, brp_stable,
