@@ -317,3 +317,23 @@ def test_gradient_finite_differences_64_directions(grad_case):
         dots.append(np.sum(gX * v))
     fd, dots = np.array(fd), np.array(dots)
     assert np.linalg.norm(fd - dots) <= 1e-5 * np.linalg.norm(fd)
+
+
+# --- degenerate cases the method defines ----------------------------------------------------
+def test_oracle_degenerate_cases():
+    """k = 0: S stays empty and every iteration is the same BRP of X; k = m n: S takes the
+    whole residual and the fit is exact; an all-zero X: the rank test finds rank 0 (nothing
+    to fit) and no entry is ever selected (zeros are never part of Omega, reading R7)."""
+    g = np.random.default_rng(21)
+    X = (g.standard_normal((40, 3)) @ g.standard_normal((3, 30)) + 0.1 * g.standard_normal((40, 30)))
+    A1 = g.standard_normal((30, 3))
+    r0 = O.godec(X, A1, 0, 1, tol=-1.0, max_iter=3)
+    assert r0["S_idx"].size == 0
+    U, s, V, _ = O.brp_stable(X, A1, 1)
+    assert _rel(O.dense_L(r0["U"], r0["sigma"], r0["V"]), O.dense_L(U, s, V)) <= 1e-12
+    rf = O.godec(X, A1, X.size, 1, tol=-1.0, max_iter=2)
+    assert rf["S_idx"].size == X.size and rf["rel_err"][-1] <= 1e-28
+    idx, val = O.hard_threshold(np.zeros((5, 4)), 7)
+    assert idx.size == 0 and val.size == 0
+    U0, s0, V0, r = O.brp_stable(np.zeros((20, 15)), g.standard_normal((15, 4)), 1)
+    assert r == 0 and s0.size == 0
