@@ -25,3 +25,30 @@ def test_status_strings_and_bad_args_without_gpu():
     p = g._binding.GodecParams(m=10, n=10, ldx=10, r=2, q=0, k=5, tol=1e-7, max_iter=5)
     assert lib.godec_init(ctypes.byref(h), ctypes.byref(p), None, None, None) == 1   # ldx*4 % 16
     assert h.value is None
+
+
+def _header_arity():
+    """Parameter count of every function prototype in include/godec.h."""
+    import re
+    txt = open(g._binding.HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(godec_\w+)\s*\(([^;{]*?)\)\s*;", txt):
+        args = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature the binding declares has the header prototype's number of
+    parameters (a drift would pass arguments in the wrong slots on the GPU)."""
+    lib = g.library()
+    arity = _header_arity()
+    checked = 0
+    for name in g.header_symbols():
+        f = getattr(lib, name)
+        if f.argtypes is None:
+            continue                       # not used by the binding
+        assert len(f.argtypes) == arity[name], name
+        checked += 1
+    assert checked >= 20
