@@ -52,3 +52,30 @@ def test_binding_signatures_match_the_header():
         assert len(f.argtypes) == arity[name], name
         checked += 1
     assert checked >= 20
+
+
+def _header_struct(name):
+    """(type, field) pairs of `typedef struct name { ... } name;` in include/godec.h."""
+    import re
+    txt = open(g._binding.HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), txt, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        typ, names = decl.split(" ", 1)
+        out += [(typ, n.strip()) for n in names.split(",")]
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """GodecParams and GodecInfo have the header's fields, in order, with the same widths
+    (a drift would shift every later field)."""
+    import ctypes as C
+    width = {"int32_t": 4, "int64_t": 8, "double": 8}
+    for hname, cls in (("godec_params", g._binding.GodecParams), ("godec_info", g._binding.GodecInfo)):
+        fields = _header_struct(hname)
+        assert [f for _, f in fields] == [f for f, _ in cls._fields_], hname
+        assert [width[t] for t, _ in fields] == [C.sizeof(t) for _, t in cls._fields_], hname
