@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from oracle.godec import _lstep_q0
 import synth
 
 
@@ -337,3 +338,66 @@ def test_oracle_degenerate_cases():
     assert idx.size == 0 and val.size == 0
     U0, s0, V0, r = O.brp_stable(np.zeros((20, 15)), g.standard_normal((15, 4)), 1)
     assert r == 0 and s0.size == 0
+
+
+# --- pins of the differentiated form's forward pass (Algorithm 1 at q = 0, reading R14) ----
+def test_lstep_q0_equals_algorithm1_literal():
+    """The differentiated form's L-step, L = Z P with P the projector on range(Y2), is the
+    q = 0 L-step of Algorithm 1 as printed (eq. lr_app: L = Y1 (A2^T Y1)^{-1} Y2^T)."""
+    g = np.random.default_rng(31)
+    for (m, n, r) in [(30, 22, 3), (22, 30, 5), (40, 40, 1)]:
+        Z = g.standard_normal((m, 4)) @ g.standard_normal((4, n)) + 0.3 * g.standard_normal((m, n))
+        A1 = g.standard_normal((n, r))
+        L_q0 = _lstep_q0(Z, A1)[0]
+        U, s, V, r_eff = O.brp_literal(Z, A1, 0)
+        assert r_eff == r
+        assert _rel(L_q0, O.dense_L(U, s, V)) <= 1e-12
+
+
+def test_unrolled_forward_equals_godec_q0():
+    """With the supports the GoDec loop chose, the frozen-mask recurrence
+    Z_{t+1} = (1 - M_t) X + M_t L_t reproduces Algorithm 1's iterates at q = 0: the same
+    L_T, and (masks left free) the same supports Omega_t in every iteration."""
+    d = synth.small_case(46, 38, 3, 0.04, 3, 0, tag="unrolled_pin")
+    X, A1 = d["X"].astype(float), d["A1"].astype(float)
+    T = 5
+    res = O.godec(X, A1, d["k"], 0, tol=-1.0, max_iter=T, keep_history=True)
+    assert all(h["r"] == 3 for h in res["history"])
+    masks = [h["S_idx"] for h in res["history"]]
+    L_T, _, _ = O.unrolled_forward(X, A1, d["k"], T, masks=masks)
+    assert _rel(L_T, O.dense_L(res["U"], res["sigma"], res["V"])) <= 1e-12
+    _, free_masks, _ = O.unrolled_forward(X, A1, d["k"], T)
+    for a, b in zip(free_masks, masks):
+        assert np.array_equal(np.sort(a), b)
+
+
+# --- naive GoDec (Sec. 2.1, eq. raw_lss): exact truncated SVD L-step, exhaustive S-step ----
+def _topr_by_eigh(Z, r):
+    """Rank-r truncation of Z through the eigenvectors of Z^T Z (the right singular
+    vectors), a route independent of the SVD routine the oracle calls."""
+    w, Vf = np.linalg.eigh(Z.T @ Z)
+    Vr = Vf[:, np.argsort(w)[::-1][:r]]
+    return Z @ Vr @ Vr.T
+
+
+def test_naive_godec_first_iterations_closed_form():
+    """From S_0 = 0 the first L-step of naive GoDec is the Eckart-Young truncation of X,
+    known in closed form for an X built from its own SVD; S_1 is the exhaustive top-k of
+    X - L_1; the second L-step truncates X - S_1 and S_2 thresholds X - L_2 (not Z - L_2)."""
+    g = np.random.default_rng(41)
+    m, n, r, k = 24, 18, 3, 20
+    Uf, _ = np.linalg.qr(g.standard_normal((m, n)))
+    Vf, _ = np.linalg.qr(g.standard_normal((n, n)))
+    lam = np.concatenate([[40.0, 25.0, 12.0], 2.0 * 0.7 ** np.arange(n - 3)])
+    X = (Uf * lam) @ Vf.T
+    L1 = (Uf[:, :r] * lam[:r]) @ Vf[:, :r].T
+    res1 = O.naive_godec(X, r, k, tol=-1.0, max_iter=1)
+    assert _rel(res1["L"], L1) <= 1e-12
+    assert res1["S_idx"].tolist() == _brute_topk(X - L1, k)
+    assert np.allclose(res1["S_val"], (X - L1).ravel()[res1["S_idx"]], rtol=0, atol=1e-12)
+    res2 = O.naive_godec(X, r, k, tol=-1.0, max_iter=2)
+    Z2 = X.copy()
+    Z2.ravel()[res1["S_idx"]] -= res1["S_val"]
+    L2 = _topr_by_eigh(Z2, r)
+    assert _rel(res2["L"], L2) <= 1e-10
+    assert res2["S_idx"].tolist() == _brute_topk(X - res2["L"], k)
