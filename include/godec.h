@@ -65,7 +65,8 @@ enum {
 #define GODEC_MAX_RANK 64
 
 typedef struct godec_params {
-  int64_t m, n;      /* X is m x n (any m, n >= 1) */
+  int64_t m, n;      /* X is m x n (m, n >= 1, m*n < 2^32: the S-step's histograms
+                        count entries in 32 bits) */
   int64_t ldx;       /* row stride of X in elements, >= n */
   int32_t r;         /* target rank, 1 <= r <= min(m, n, GODEC_MAX_RANK) */
   int32_t q;         /* power-scheme exponent of eq. mlr_app, 0 <= q <= 8 */
@@ -79,7 +80,8 @@ typedef struct godec_params {
   int32_t reserved;  /* must be 0 */
 } godec_params;
 
-/* Record per-iteration factors and supports so godec_backward can run. */
+/* Reserved; ignored.  godec_backward needs no tape: it recomputes the per-iteration
+   factors from X, A1 and the supports. */
 #define GODEC_FLAG_TAPE 1
 /* Precision form only: skip the float32 correction (diagnostic: the float16 chain's own
    accuracy). */
@@ -281,7 +283,7 @@ godec_status godec_backward(const float* X, int64_t m, int64_t n, int64_t ldx, c
  *   idx, val : device int64[cap] / float32[cap], receive the COO sorted by
  *              linear index; nnz (host) receives min(k, #nonzeros of R).
  * Scratch is allocated and freed inside the call (stream-ordered); the call
- * synchronises the stream.  GODEC_ERR_ARG if cap < the result size.
+ * synchronises the stream.  GODEC_ERR_ARG if cap < the result size or m*n >= 2^32.
  */
 godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t ldr, int64_t k,
                                   int64_t* idx, float* val, int64_t cap, int64_t* nnz,
@@ -295,12 +297,16 @@ godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t 
  * counterpart; this is a library convenience.
  *   Same arguments and layout as godec_mul_ZB; computed with float32 FMAs on
  *   the CUDA cores (results agree with godec_mul_ZB to float32 rounding).
- *   Scratch: a fixed 32 MiB device array inside the library, reserved on every
- *   GPU that loads it until the process exits; no allocation or free happens in
- *   the call.  Problems whose scratch (padded B, split-K partials, padded Y)
- *   exceeds 32 MiB are rejected with GODEC_ERR_UNSUPPORTED and a message in
- *   godec_last_error(NULL).  The first call on each device looks up the array's
- *   device address; make that first call before any stream capture.
+ *   Scratch: a fixed 32 MiB array in the library's device code.  A GPU holds it
+ *   from the time that code is loaded there (with CUDA's default lazy loading, at
+ *   the first use of the library on that device) until the process exits; no
+ *   allocation or free happens in the call.  Problems whose scratch (padded B,
+ *   split-K partials, padded Y) exceeds 32 MiB are rejected with
+ *   GODEC_ERR_UNSUPPORTED and a message in godec_last_error(NULL).  Each call
+ *   outside stream capture looks up the array's device address; a call made
+ *   while `stream` is capturing reuses the address found by an earlier call on
+ *   the same device, so make one call on each device before any capture (a
+ *   first call under capture returns GODEC_ERR_STATE).
  *   All calls on a device share the array and leave its contents behind:
  *   calls that overlap on the GPU (different streams, threads or processes
  *   without ordering) race and corrupt each other's results.

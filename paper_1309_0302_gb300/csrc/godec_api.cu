@@ -778,7 +778,8 @@ bool bad_params(const godec_params* p, char* why, size_t nwhy) {
   if (p->precision == GODEC_PREC_BF16_REFINE && p->r > 32) {
     snprintf(why, nwhy, "the precision form needs r <= 32"); return true;
   }
-  if ((double)p->m * (double)p->n >= 281474976710656.0) { snprintf(why, nwhy, "m*n must be below 2^48"); return true; }
+  // the S-step's radix histograms count entries in 32 bits
+  if ((double)p->m * (double)p->n >= 4294967296.0) { snprintf(why, nwhy, "m*n must be below 2^32"); return true; }
   return false;
 }
 
@@ -1250,7 +1251,7 @@ godec_status godec_hard_threshold(const float* R, int64_t m, int64_t n, int64_t 
                                   int64_t* idx, float* val, int64_t cap, int64_t* nnz, void* stream) {
   // A context with r = 0 (L = 0) and no working copy of X - S: only the S-step runs.
   if (!R || m < 1 || n < 1 || ldr < n || (ldr * 4) % 16 || k < 0 || k > m * n ||
-      (reinterpret_cast<uintptr_t>(R) & 15)) {
+      (double)m * (double)n >= 4294967296.0 || (reinterpret_cast<uintptr_t>(R) & 15)) {
     snprintf(g_static_err, sizeof(g_static_err), "godec_hard_threshold: invalid argument");
     return GODEC_ERR_ARG;
   }
@@ -1354,8 +1355,14 @@ static godec_status mul_common(const float* Z, int64_t m, int64_t n, int64_t ldz
     alignas(64) unsigned char mapA[128], mapB[128];
     mapped = make_tmap_f32(mapA, trans ? Zt : Z, rows, K, trans ? ldt : ldz, 128) &&
              make_tmap_f16(mapB, Bs, 2 * RP, K, ldb, 2 * RP);
+    if (mapped && cudaMemsetAsync(cnt, 0, (size_t)geom.tiles * sizeof(unsigned), st) != cudaSuccess) {
+      for (void* q : {(void*)Bp, Bs, (void*)aux, (void*)part, (void*)Yp, (void*)cnt, (void*)pend, (void*)Zt})
+        if (q) cudaFreeAsync(q, st);
+      snprintf(g_static_err, sizeof(g_static_err), "godec_mul: clearing the tile counters: %s",
+               cudaGetErrorString(cudaGetLastError()));
+      return GODEC_ERR_CUDA;
+    }
     if (mapped) {
-      cudaMemsetAsync(cnt, 0, (size_t)geom.tiles * sizeof(unsigned), st);
       // aux: {s_Z, 1/s_Z}, max-|Z| scratch, pad, then RP column factors of B
       launch_zscale(Z, m, n, ldz, reinterpret_cast<unsigned*>(aux + 2), aux, nsm, st);
       launch_pad_copy(B, K, r, r, Bp, RP, st);

@@ -6,8 +6,10 @@
 // to allocate afterwards, or a latency-critical loop where an allocation may
 // synchronise the device or fragment a pool.  For them this entry point keeps
 // the padded copy of B, the split-K partial products and the padded result in
-// one file-scope array of kNoAllocScratchBytes bytes.  Every GPU that loads
-// this library reserves that array until the process exits.
+// one file-scope array of kNoAllocScratchBytes bytes.  The array belongs to the
+// library's device code: a GPU holds it from the moment that code is loaded there
+// (under CUDA's default lazy loading, at the first use of the library's kernels or
+// symbols on that device) until the process exits.
 #include <mutex>
 
 #include "godec_internal.cuh"
@@ -23,9 +25,12 @@ std::mutex g_scratch_mu;
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Device address of the array on the current device, looked up once per device
-// (host code cannot use the symbol itself: it names a host-side stand-in).
-godec_status scratch_address(void** out) {
+// Device address of the array on the current device (host code cannot use the symbol
+// itself: it names a host-side stand-in).  Outside stream capture the address is looked
+// up again on every call, so a new primary context (after cudaDeviceReset) is picked
+// up; while `st` is capturing, the address cached by an earlier call on this device is
+// used, and a first call under capture is refused.
+godec_status scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -36,8 +41,19 @@ godec_status scratch_address(void** out) {
     godec::set_static_error("godec_mul_ZB_noalloc: device ordinal %d above %d", dev, kMaxDevices - 1);
     return GODEC_ERR_UNSUPPORTED;
   }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) {
+    godec::set_static_error("godec_mul_ZB_noalloc: cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+    return GODEC_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  if (cap != cudaStreamCaptureStatusNone && !g_scratch_addr[dev]) {
+    godec::set_static_error("godec_mul_ZB_noalloc: the first call on device %d must come before any stream "
+                            "capture", dev);
+    return GODEC_ERR_STATE;
+  }
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_mul_scratch);
     if (e != cudaSuccess || !p) {
@@ -87,7 +103,7 @@ extern "C" godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t 
     return GODEC_ERR_CUDA;
   }
   void* base = nullptr;
-  godec_status s = scratch_address(&base);
+  godec_status s = scratch_address(st, &base);
   if (s) return s;
   char* p = reinterpret_cast<char*>(base);
   float* Bp = reinterpret_cast<float*>(p);
@@ -97,7 +113,11 @@ extern "C" godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t 
   // Every scratch element read below is written first in the same call (all K x RP
   // of Bp, all splits x m x RP partials, all m x RP of Yp), except the per-tile
   // arrival counters, which must start at zero: clear them on every call.
-  cudaMemsetAsync(cnt, 0, (size_t)tiles * sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)tiles * sizeof(unsigned), st);
+  if (e != cudaSuccess) {
+    set_static_error("godec_mul_ZB_noalloc: clearing the tile counters: %s", cudaGetErrorString(e));
+    return GODEC_ERR_CUDA;
+  }
   launch_pad_copy(B, n, r, r, Bp, RP, st);
   ProdArgs pa{};
   pa.Z = Z;
@@ -113,7 +133,7 @@ extern "C" godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t 
   pa.RP = RP;
   launch_prod(pa, st);
   launch_unpad_copy(Yp, m, RP, Y, r, st);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_static_error("godec_mul_ZB_noalloc: %s", cudaGetErrorString(e));
     return GODEC_ERR_CUDA;
