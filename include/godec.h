@@ -141,6 +141,16 @@ godec_status godec_solve(godec_ctx* ctx, int32_t* iters, double* rel_err);
 godec_status godec_get_L(godec_ctx* ctx, float* U, float* sigma, float* V, int32_t* r_eff);
 
 /*
+ * L_t as a dense matrix, L = U diag(sigma) V^T (eq. mlr_app: L = Q1 M^{1/(2q+1)} Q2^T,
+ * with the factors godec_get_L returns), written by the library's own kernel in float32
+ * (each entry a sum of r_eff products).  For callers that need L itself (a dense loss, the
+ * differentiated form's output); the iteration never forms it.
+ *   L : device, m x ldl float32 (ldl >= n), caller-owned, overwritten.
+ * GODEC_ERR_STATE before the first iteration.  Synchronises the stream.
+ */
+godec_status godec_get_L_dense(godec_ctx* ctx, float* L, int64_t ldl);
+
+/*
  * Copy S_t as COO sorted by ascending linear index i*n + j.
  *   idx : device int64[cap], val : device float32[cap] (both nullable when
  *   cap = 0), nnz : host, receives |Omega| (<= k).

@@ -51,6 +51,7 @@ def _declare(lib):
         "godec_iterate": ([_P, C.c_int32, f64p], C.c_int),
         "godec_solve": ([_P, i32p, f64p], C.c_int),
         "godec_get_L": ([_P, _P, _P, _P, i32p], C.c_int),
+        "godec_get_L_dense": ([_P, _P, C.c_int64], C.c_int),
         "godec_get_S": ([_P, _P, _P, C.c_int64, i64p], C.c_int),
         "godec_residual": ([_P, _P, C.c_int64], C.c_int),
         "godec_get_info": ([_P, C.POINTER(GodecInfo)], C.c_int),
@@ -222,6 +223,13 @@ class GoDec:
         _check(library().godec_get_L(self._h, _ptr(U), _ptr(s), _ptr(V), C.byref(re)), "godec_get_L", self._h)
         r = re.value
         return U.view(-1)[: self.m * r].view(self.m, r), s[:r], V.view(-1)[: self.n * r].view(self.n, r)
+
+    def L_dense(self):
+        """L_t = U diag(sigma) V^T as a dense (m, n) CUDA float32 tensor, written by the library."""
+        torch = _torch()
+        L = torch.empty((self.m, self.n), dtype=torch.float32, device=self._X.device)
+        _check(library().godec_get_L_dense(self._h, _ptr(L), self.n), "godec_get_L_dense", self._h)
+        return L
 
     def S(self):
         """(idx int64 ascending linear indices, val float32) of S as CUDA tensors."""

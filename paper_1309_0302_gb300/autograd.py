@@ -25,8 +25,7 @@ class UnrolledGoDec(torch.autograd.Function):
             if g.info()["r_eff"] != r:
                 raise RuntimeError("the rank test lowered r during the unrolled iterations; "
                                    "the differentiated form needs a fixed r")
-            U, s, V = g.L()
-            L = (U * s) @ V.T
+            L = g.L_dense()
         finally:
             g.close()
         ctx.save_for_backward(X, A1, *supports)

@@ -1120,6 +1120,19 @@ godec_status godec_get_L(godec_ctx* c, float* U, float* sigma, float* V, int32_t
   return GODEC_OK;
 }
 
+godec_status godec_get_L_dense(godec_ctx* c, float* L, int64_t ldl) {
+  if (!c) return GODEC_ERR_ARG;
+  if (!L || ldl < c->p.n) return fail(c, GODEC_ERR_ARG, "godec_get_L_dense: L must be non-NULL with ldl >= n");
+  Ctl h;
+  godec_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (h.iter == 0) return fail(c, GODEC_ERR_STATE, "no iteration has run yet");
+  launch_lowrank_dense(c->U, c->RP, c->sigma, c->V, c->RP, c->p.m, c->p.n, c->r, L, ldl, c->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  return GODEC_OK;
+}
+
 godec_status godec_residual(godec_ctx* c, float* R, int64_t ldr) {
   if (!c || !R || ldr < c->p.n) {
     if (c) fail(c, GODEC_ERR_ARG, "godec_residual: R must be non-NULL with ldr >= n");

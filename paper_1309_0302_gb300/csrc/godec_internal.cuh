@@ -308,6 +308,10 @@ void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, co
                         const double* C, int r, double* core, cudaStream_t st);
 void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st);
 
+// L (m x n, row stride ldl) = U diag(sigma) V^T, U m x r (ldu), V n x r (ldv) (k_dense.cu).
+void launch_lowrank_dense(const float* U, int64_t ldu, const float* sigma, const float* V, int64_t ldv, int64_t m,
+                          int64_t n, int r, float* L, int64_t ldl, cudaStream_t st);
+
 // Small helpers.
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
 // dst (n x ldd) = src^T (src m x n with stride lds)

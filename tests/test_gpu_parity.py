@@ -242,3 +242,24 @@ def test_c2_full_size_same_step():
     assert flips <= 1e-4 * d["k"]
     assert inside, nb
     assert abs(info["obj"] - st["E2"]) <= 1e-4 * st["E2"]
+
+
+# --- dense L from the library's own kernel (eq. mlr_app, L = U diag(sigma) V^T) ------------
+@pytest.mark.parametrize("m,n,r,q", [(300, 257, 6, 1), (129, 700, 3, 0), (67, 65, 9, 2)])
+def test_get_L_dense_matches_factors(m, n, r, q):
+    """godec_get_L_dense writes U diag(sigma) V^T of the context's factors: every entry within
+    float32 rounding of the float64 product of the factors godec_get_L returns, including the
+    ragged tile edges (m, n not multiples of the 64 x 128 tile, odd row stride)."""
+    import paper_1309_0302_gb300 as G
+    d = synth.small_case(m, n, r, 0.03, r, q, tag=f"dense{m}x{n}")
+    g = G.GoDec(to_gpu(d["X"]), to_gpu(d["A1"]), r, d["k"], q)
+    try:
+        g.iterate(2)
+        U, s, V = (to_np(t).astype(np.float64) for t in g.L())
+        L = to_np(g.L_dense()).astype(np.float64)
+    finally:
+        g.close()
+    Lr = (U * s) @ V.T
+    bound = 4 * r * 2.0 ** -24 * (np.abs(U) * s) @ np.abs(V).T + 1e-30
+    assert L.shape == (m, n)
+    assert np.all(np.abs(L - Lr) <= bound)
