@@ -8,8 +8,13 @@ X resident in HBM (X and X - S are 400 MB each, above the 129 MB L2, so no
 flush is needed between iterations).  Multi-GPU runs are independent replicas
 (one problem per rank, no collective on the data path): weak scaling.
 
---impl reference times the float64 CPU oracle on a bounded row sample of the
-same workload and scales it to the full workload's iterations/s.
+--impl reference times the float64 CPU oracle on the same full-size workload: each
+step is one oracle iteration of Algorithm 1 on the whole 10000 x 10000 matrix.
+
+The default line also carries "forms": clocked timing records of the other
+configurations, each against its stated comparison (the 500 x 500 case against the
+oracle, the precision form against the float32 form, the batched form against the
+same problems one by one, the differentiated form's backward against its forward).
 """
 from __future__ import annotations
 
@@ -31,7 +36,7 @@ M = N = 10000
 R, K_CARD, Q = 50, 1000000, 2
 WORKLOAD = ("plain GoDec-BRP float32, X = U V^T + S + G, m = n = 10000, rank-50 N(0,1) factors, "
             "1% sparse U[-20,20], noise sigma 1e-2; r = 50, k = 1e6, q = 2, iterations from S = 0")
-SAMPLE_ROWS = 1000
+BASELINE_ITERS = 3        # full-size oracle iterations of the GPU arm's cpu_baseline
 
 
 def parse():
@@ -42,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the C1/C3/C4/C5 timing records")
     ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched", "c1"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
@@ -129,25 +135,32 @@ def pass_traffic():
     return float(kv["dram_bytes_per_launch"]) if kv.get("source_sha") == h else None
 
 
-def oracle_rate(iters: int, seed: int = 1309):
-    """float64 oracle on the first SAMPLE_ROWS rows of the workload (same n, r, q, density);
-    returns full-workload iterations/s (cost scales linearly with m at fixed n, r)."""
+def oracle_steps(X32, A1_32, steps: int, warmup: int):
+    """The float64 oracle on the full workload: `warmup` untimed then `steps` timed
+    iterations of Algorithm 1 (one oracle.godec_step each, continuing the trajectory from
+    S = 0).  Returns (iterations/s, per-iteration seconds, threads used)."""
     import numpy as np
 
     import oracle
-    import synth
-    d = synth.lowrank_sparse(SAMPLE_ROWS, N, R, int(K_CARD * SAMPLE_ROWS / M), -20.0, 20.0, 1e-2, seed, "c2")
-    X, A1 = d["X"].astype(np.float64), d["A1"].astype(np.float64)
-    k = int(K_CARD * SAMPLE_ROWS / M)
+    X, A1 = X32.astype(np.float64), A1_32.astype(np.float64)
     S_idx, S_val = np.zeros(0, np.int64), np.zeros(0)
     times = []
-    for _ in range(iters):
+    for i in range(warmup + steps):
         t0 = time.perf_counter()
-        st = oracle.godec_step(X, A1, S_idx, S_val, k, Q)
-        times.append(time.perf_counter() - t0)
+        st = oracle.godec_step(X, A1, S_idx, S_val, K_CARD, Q)
+        if i >= warmup:
+            times.append(time.perf_counter() - t0)
         S_idx, S_val = st["S_idx"], st["S_val"]
-    per_iter = sum(times) / len(times)
-    return (SAMPLE_ROWS / M) / per_iter, times, os.cpu_count()
+    return len(times) / sum(times), times, blas_threads()
+
+
+def blas_threads() -> int:
+    """Threads the oracle's BLAS runs on (numpy's OpenBLAS honours OMP/OPENBLAS env)."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    return os.cpu_count()
 
 
 def replica_seed(rank: int) -> int:
@@ -178,16 +191,20 @@ def emit(line: dict):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
+    import synth
+    d = synth.lowrank_sparse(M, N, R, K_CARD, -20.0, 20.0, 1e-2, replica_seed(0), "c2")
     warm = min(args.warmup, 1)
-    oracle_rate(warm) if warm else None
-    rate, times, cores = oracle_rate(args.steps)
+    t0 = time.perf_counter()
+    rate, times, cores = oracle_steps(d["X"], d["A1"], args.steps, warm)
+    wall = time.perf_counter() - t0
     emit({"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
           "steps": args.steps, "warmup": warm, "ms_per_step": 1000.0 / rate, "higher_is_better": True,
           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
           "config": {"workload": WORKLOAD, "m": M, "n": N, "r": R, "k": K_CARD, "q": Q},
           "cpu_baseline": {"kind": "oracle", "cores": cores, "value": rate, "unit": UNIT,
-                           "sample": f"each step: one float64 oracle iteration on the first {SAMPLE_ROWS} rows "
-                                     f"(n, r, q and density unchanged), time scaled by m/{SAMPLE_ROWS}"},
+                           "sample": f"the whole workload: {warm} untimed and {args.steps} timed float64 "
+                                     f"oracle iterations of the full {M} x {N} matrix from S = 0 "
+                                     f"({wall:.1f} s wall in all)"},
           "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
@@ -237,11 +254,7 @@ def run_gb300(args, ws, rank, local):
     achieved = prof["bytes_product"] / (pass_ms / 1000.0) / 1e9
     peak, peak_src = peaks()
     passes_per_iter = npass / args.steps
-    # algorithmic bytes of one steady-state iteration: every streaming product reads X - S
-    # once, each residual pass the S-step used reads X once (the graph also holds passes that
-    # exit at once when the selection needs none: those are not counted), factors and S
-    bytes_iter = 4.0 * M * N * (passes_per_iter + max(1, int(info["select_passes"]))) \
-        + 12.0 * K_CARD * 2 + 4.0 * (M + N) * R * passes_per_iter
+    bytes_iter = iteration_bytes(M, N, R, K_CARD, Q)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -257,6 +270,10 @@ def run_gb300(args, ws, rank, local):
         "iteration_roofline": {"achieved": bytes_iter * (value / ws) / 1e9, "unit": "GB/s",
                                "frac": bytes_iter * (value / ws) / 1e9 / peak,
                                "bytes_per_iter": bytes_iter,
+                               "bytes_rule": "algorithmic: (6q+3) passes over the 4mn-byte matrix (6q+2 "
+                                             "products with X A1 cached, one S-step pass), (6q+2) reads and "
+                                             "one write of the 12k-byte COO S, skinny operands in and out",
+                               "product_launches_per_iter": passes_per_iter,
                                "residual_passes_per_iter": max(1, int(info["select_passes"]))},
         "kernel_ms_per_iter": {k: v / args.steps for k, v in prof["ms"].items()},
         "clocks": ck,
@@ -265,11 +282,14 @@ def run_gb300(args, ws, rank, local):
     }
     if not args.no_e2e:
         line["e2e"] = e2e(args, d)
+    if rank == 0 and ws == 1 and not args.no_forms:
+        line["forms"] = {"c1": form_c1(), "c3_precision": form_c3(), "c4_batched": form_c4(),
+                         "c5_differentiated": form_c5()}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, times, cores = oracle_rate(5)
+        rate, times, cores = oracle_steps(d["X"], d["A1"], BASELINE_ITERS, 0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"5 float64 oracle iterations from S = 0 on the first {SAMPLE_ROWS} "
-                                          f"rows (n, r, q and density unchanged), time scaled by m/{SAMPLE_ROWS}"}
+                                "sample": f"{BASELINE_ITERS} float64 oracle iterations of the full {M} x {N} "
+                                          f"workload from S = 0 ({sum(times):.1f} s)"}
     if dist:
         dist.destroy_process_group()
     if rank == 0:
@@ -303,6 +323,183 @@ def e2e(args, d):
                     "factors and sorted S; bytes per step = bytes per call / K"}
 
 
+def iteration_bytes(m, n, r, k, q) -> float:
+    """Algorithmic bytes of one iteration of Algorithm 1 in the streaming design: 6q+3 passes
+    over the 4mn-byte matrix (6q+2 chain products once X A1 is cached, plus one S-step pass),
+    6q+2 reads and one write of the 12-byte-per-entry COO S, and the skinny operands read and
+    written by each of the 6q+3 products."""
+    P = 6 * q + 3
+    return P * 4.0 * m * n + (P - 1) * 12.0 * k + 12.0 * k + P * 2 * 4.0 * (m + n) * r
+
+
+def _timed(stream, f, reps: int):
+    """Milliseconds per call of f over reps calls, CUDA events on `stream`, with nvidia-smi
+    clock samples over the same region."""
+    import torch
+    ck = Clocks(torch.cuda.current_device())
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ck.start()
+    ev[0].record(stream)
+    for _ in range(reps):
+        f()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / reps, ck.stop()
+
+
+def form_c1():
+    """C1 (500 x 500, rank 10, k = 12500, q = 1; L2-resident, so iterations/s only): GPU
+    iterations (graph replays) against the float64 oracle on all host cores and on one, and a
+    solve to tol 1e-7."""
+    import torch
+
+    import oracle as O
+    import paper_1309_0302_gb300 as G
+    import synth
+    d = synth.config_c1()
+    X, A1 = torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda()
+    st = torch.cuda.current_stream()
+    g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=-1.0, max_iter=1 << 30)
+    g.iterate(3)
+    ms, ck = _timed(st, lambda: g.iterate(200), 10)
+    ms /= 200
+    g.close()
+    g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=1e-7, max_iter=50)
+    t0 = time.perf_counter()
+    it, rel = g.solve()
+    t_solve = time.perf_counter() - t0
+    g.close()
+    t0 = time.perf_counter()
+    O.godec(d["X"], d["A1"], d["k"], d["q"], tol=-1.0, max_iter=10)
+    o_all = (time.perf_counter() - t0) / 10
+    code = ("import sys, time; sys.path.insert(0, %r); import synth, oracle as O; d = synth.config_c1(); "
+            "t0 = time.perf_counter(); O.godec(d['X'], d['A1'], d['k'], d['q'], tol=-1.0, max_iter=10); "
+            "print((time.perf_counter() - t0) / 10)") % ROOT
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    o_one = float(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                                 check=True).stdout.strip().splitlines()[-1])
+    return {"workload": "500 x 500, rank 10, k = 12500 U[-10,10], sigma 1e-3; r = 10, q = 1",
+            "gpu_iterations_per_s": 1e3 / ms, "gpu_ms_per_iter": ms, "gpu_timed_iterations": 2000,
+            "solve_tol_1e-7": {"iterations": it, "rel_err": rel, "wall_ms": t_solve * 1e3},
+            "oracle_iterations_per_s": {"all_cores": 1.0 / o_all, "cores": blas_threads(), "one_core": 1.0 / o_one},
+            "note": "L2-resident (1 MB matrix): no HBM roofline", "clocks": ck}
+
+
+def form_c3():
+    """C3 (76800 x 1000, r = 3, k = 1.2e6, q = 2): the precision form (float16 chain +
+    float32 correction) against the plain float32 form on the same input, 100 timed
+    iterations each after 2 warm-up ones; the two L's distance afterwards."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    d = synth.config_c3()
+    X, A1 = torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda()
+    st = torch.cuda.current_stream()
+    out, Ls = {}, {}
+    for name, prec in (("float32", G.PREC_FP32), ("precision", G.PREC_BF16_REFINE)):
+        g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=-1.0, max_iter=1 << 30, precision=prec)
+        g.iterate(2)
+        ms, ck = _timed(st, lambda: g.iterate(20), 5)
+        ms /= 20
+        out[name] = {"ms_per_iter": ms, "iterations_per_s": 1e3 / ms, "clocks": ck,
+                     "exact_path_iterations": g.info()["exact_iters"]}
+        Ls[name] = [t.double().cpu().numpy() for t in g.L()]
+        g.close()
+    (Ua, sa, Va), (Ub, sb, Vb) = Ls["float32"], Ls["precision"]
+    Aa, Ab = Ua * sa, Ub * sb
+    aa, bb, ab = (np.sum((P.T @ Q) * (R_.T @ S_)) for P, Q, R_, S_ in
+                  ((Aa, Aa, Va, Va), (Ab, Ab, Vb, Vb), (Aa, Ab, Va, Vb)))
+    m, n = d["X"].shape
+    return {"workload": "76800 x 1000 video-shaped synthetic, r = 3, k = 1.2e6, q = 2",
+            "float32": out["float32"], "precision": out["precision"],
+            "speedup_precision_over_float32": out["float32"]["ms_per_iter"] / out["precision"]["ms_per_iter"],
+            "L_distance_after_102_iterations": float(np.sqrt(max(aa + bb - 2 * ab, 0.0)) / np.sqrt(aa)),
+            "algorithmic_bytes_per_iter": {"precision": 14 * 2.0 * m * n + 2 * 4.0 * m * n,
+                                           "float32": 15 * 4.0 * m * n}}
+
+
+def form_c4():
+    """C4 (64 problems, m, n log-uniform in [256, 4096], r in 2..32, q = 1): the tuned batch
+    (one graph launch per batch iteration) against the same problems one by one."""
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    ds = synth.config_c4()
+    Xs = [torch.from_numpy(d["X"]).cuda() for d in ds]
+    A1s = [torch.from_numpy(d["A1"]).cuda() for d in ds]
+    rs, ks, qs = [d["r"] for d in ds], [d["k"] for d in ds], [d["q"] for d in ds]
+    nbytes = sum(iteration_bytes(*d["X"].shape, d["r"], d["k"], d["q"]) for d in ds)
+    st = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    b = G.GoDecBatch(Xs, A1s, rs, ks, qs, tune=True)
+    t_init = time.perf_counter() - t0
+    b.iterate(2)
+    ms_b, ck_b = _timed(st, lambda: b.iterate(20), 10)
+    ms_b /= 20
+    tun = b.tuning()
+    b.close()
+    single = 0.0
+    cks = []
+    for j in range(len(ds)):
+        g = G.GoDec(Xs[j], A1s[j], rs[j], ks[j], qs[j], tol=-1.0, max_iter=1 << 30)
+        g.iterate(2)
+        ms, ck = _timed(st, lambda: g.iterate(20), 1)
+        single += ms / 20
+        cks.append(ck)
+        g.close()
+    ck_single = {"sm_mhz": statistics.median([c["sm_mhz"] for c in cks if c.get("sm_mhz")] or [0]),
+                 "sm_max_mhz": max([c["sm_max_mhz"] or 0 for c in cks]),
+                 "reasons": sorted({r_ for c in cks for r_ in c["reasons"]})}
+    return {"workload": "64 problems, m, n log-uniform in [256, 4096], r in 2..32, 2-5 % sparse, q = 1",
+            "batch": {"ms_per_batch_iter": ms_b, "problem_iterations_per_s": 64e3 / ms_b,
+                      "algorithmic_GBps": nbytes / ms_b / 1e6, "policy": tun["policy"],
+                      "policy_ms": tun["policy_ms"], "init_s_with_tuning": t_init, "clocks": ck_b},
+            "one_by_one": {"ms_per_round_of_64": single, "problem_iterations_per_s": 64e3 / single,
+                           "clocks": ck_single},
+            "speedup_batch_over_one_by_one": single / ms_b}
+
+
+def form_c5():
+    """C5 (4096 x 4096, r = 20, q = 0, T = 10): the differentiated form's backward
+    (godec_backward) against its forward (T iterations, context set-up included)."""
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    d = synth.config_c5()
+    r, k, T = d["r"], d["k"], d["T"]
+    X, A1 = torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda()
+    st = torch.cuda.current_stream()
+    box = {}
+
+    def forward():
+        g = G.GoDec(X, A1, r, k, 0, tol=0.0, max_iter=T)
+        sup = []
+        for t in range(T):
+            g.iterate(1)
+            if t < T - 1:
+                sup.append(g.S()[0].clone())
+        box["L"] = g.L()
+        box["sup"] = sup
+        g.close()
+
+    forward()
+    ms_f, ck_f = _timed(st, forward, 10)
+    U, s, V = box["L"]
+    gU = torch.cat([2.0 * U * s, -2.0 * torch.from_numpy(d["Ustar"]).float().cuda()], 1).contiguous()
+    gV = torch.cat([V, torch.from_numpy(d["Vstar"]).float().cuda()], 1).contiguous()
+    G.backward(X, A1, T, box["sup"], gU=gU, gV=gV)
+    ms_b, ck_b = _timed(st, lambda: G.backward(X, A1, T, box["sup"], gU=gU, gV=gV), 40)
+    m, n = d["X"].shape
+    return {"workload": "4096 x 4096, rank 20, 2 % sparse, r = 20, q = 0, T = 10, loss ||L_T - L*||^2",
+            "forward_ms": ms_f, "backward_ms": ms_b, "backward_over_forward": ms_b / ms_f,
+            "forward_algorithmic_bytes": T * 3 * 4.0 * m * n, "clocks_forward": ck_f, "clocks_backward": ck_b}
+
+
 def run_kernel_case(args):
     """Small cases for ncu captures: the streaming product on a size x size matrix
     (above the L2 size for size >= 6000), or two full iterations at size x size, r = 50."""
@@ -319,141 +516,9 @@ def run_kernel_case(args):
         f = G.mul_ZB if args.kernel == "product" else G.mul_ZtC
         for _ in range(3):
             f(Z, B)
-    elif args.kernel == "backward":
-        # differentiated form at C5 (4096 x 4096, r = 20, q = 0, T = 10): forward iterations and
-        # godec_backward, each timed with CUDA events after one warm-up
-        d = synth.config_c5()
-        r, k, T = d["r"], d["k"], d["T"]
-        X = torch.from_numpy(d["X"]).cuda()
-        A1 = torch.from_numpy(d["A1"]).cuda()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        for rep in range(2):
-            ev[0].record()
-            g = G.GoDec(X, A1, r, k, 0, tol=0.0, max_iter=T)
-            sup = []
-            for t in range(T):
-                g.iterate(1)
-                if t < T - 1:
-                    sup.append(g.S()[0].clone())
-            U, s, V = g.L()
-            g.close()
-            ev[1].record()
-            gU = torch.cat([2.0 * U * s, -2.0 * torch.from_numpy(d["Ustar"]).float().cuda()], 1).contiguous()
-            gV = torch.cat([V, torch.from_numpy(d["Vstar"]).float().cuda()], 1).contiguous()
-            ev[2].record()
-            G.backward(X, A1, T, sup, gU=gU, gV=gV)
-            ev[3].record()
-            torch.cuda.synchronize()
-        print(f"C5 forward {T} iterations (incl. context setup): {ev[0].elapsed_time(ev[1]):.2f} ms, "
-              f"backward: {ev[2].elapsed_time(ev[3]):.2f} ms")
-    elif args.kernel == "precision":
-        # precision form at C3 (76800 x 1000, r = 3, k = 1.2e6, q = 2) against the plain float32
-        # form on the same input: iterations/s of each (CUDA events over 10 iterations after 2
-        # warm-up ones) and the distance between the two L factors after those iterations
-        d = synth.config_c3()
-        X = torch.from_numpy(d["X"]).cuda()
-        A1 = torch.from_numpy(d["A1"]).cuda()
-        res = {}
-        for name, prec in (("float32", G.PREC_FP32), ("float16 chain + float32 correction", G.PREC_BF16_REFINE)):
-            g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=0.0, max_iter=100, precision=prec)
-            g.iterate(2)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            torch.cuda.synchronize()
-            ev[0].record(torch.cuda.current_stream())
-            g.iterate(10)
-            ev[1].record(torch.cuda.current_stream())
-            torch.cuda.synchronize()
-            res[name] = (ev[0].elapsed_time(ev[1]) / 10, [t.double().cpu().numpy() for t in g.L()])
-            g.close()
-        (ta, (Ua, sa, Va)), (tb, (Ub, sb, Vb)) = res.values()
-        Aa, Ab = Ua * sa, Ub * sb
-        aa = np.sum((Aa.T @ Aa) * (Va.T @ Va))
-        bb = np.sum((Ab.T @ Ab) * (Vb.T @ Vb))
-        ab = np.sum((Aa.T @ Ab) * (Va.T @ Vb))
-        dist = float(np.sqrt(max(aa + bb - 2 * ab, 0.0)) / np.sqrt(aa))
-        print(f"C3 float32 form: {ta:.3f} ms/iteration ({1e3 / ta:.1f} it/s); precision form: {tb:.3f} "
-              f"ms/iteration ({1e3 / tb:.1f} it/s); L distance after 12 iterations {dist:.2e}")
-    elif args.kernel == "batched":
-        # batched form at C4 (64 problems, m, n log-uniform in [256, 4096], r in 2..32, q = 1):
-        # tuned batch, untuned batch (all SMs for every problem) and the same problems one by
-        # one through the single-problem API, 20 iterations each after 2 warm-up ones
-        ds = synth.config_c4()
-        Xs = [torch.from_numpy(d["X"]).cuda() for d in ds]
-        A1s = [torch.from_numpy(d["A1"]).cuda() for d in ds]
-        rs, ks, qs = [d["r"] for d in ds], [d["k"] for d in ds], [d["q"] for d in ds]
-        nbytes = sum(4.0 * d["X"].size * (6 * d["q"] + 4) for d in ds)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        T = 20
-
-        def timed(f):
-            f(2)
-            torch.cuda.synchronize()
-            ev[0].record(torch.cuda.current_stream())
-            f(T)
-            ev[1].record(torch.cuda.current_stream())
-            torch.cuda.synchronize()
-            return ev[0].elapsed_time(ev[1]) / T
-
-        res = {}
-        for tune in (True, False):
-            t0 = time.time()
-            b = G.GoDecBatch(Xs, A1s, rs, ks, qs, tune=tune)
-            t_init = time.time() - t0
-            rec0 = b.tuning()["recaptures"]
-            res[tune] = (timed(b.iterate), b.tuning(), t_init)
-            ex = [b.problem(j).info()["exact_iters"] for j in range(len(ds))]
-            print(f"C4 batch ({'tuned' if tune else 'untuned'}): graph captures during the timed run "
-                  f"{res[tune][1]['recaptures'] - rec0}, iterations on the exact path per problem {ex}")
-            b.close()
-        single = 0.0
-        for j in range(len(ds)):
-            g = G.GoDec(Xs[j], A1s[j], rs[j], ks[j], qs[j], tol=-1.0, max_iter=1 << 20)
-            single += timed(g.iterate)
-            g.close()
-        for tune in (True, False):
-            ms, tun, t_init = res[tune]
-            print(f"C4 batch ({'tuned, policy ' + str(tun['policy']) if tune else 'untuned'}): {ms:.3f} ms per batch "
-                  f"iteration, {64e3 / ms:.0f} problem-iterations/s, {nbytes / ms / 1e6:.0f} GB/s of "
-                  f"algorithmic traffic; init {t_init:.1f} s")
-        print("C4 tuner ms per batch iteration by policy:", [round(x, 3) for x in res[True][1]["policy_ms"]])
-        print("C4 budgets (SMs) of the tuned policy:", res[True][1]["sm"])
-        print(f"C4 one problem at a time: {single:.3f} ms per round of 64 iterations, "
-              f"{64e3 / single:.0f} problem-iterations/s")
-    elif args.kernel == "c1":
-        # C1 (500 x 500, rank 10, k = 12500, q = 1): L2-resident, so iterations/s only.  GPU:
-        # 50 graph-replayed iterations after 3 warm-up ones, and a solve to tol 1e-7; the
-        # float64 oracle on all host cores and, in a child process, on one core
-        d = synth.config_c1()
-        X = torch.from_numpy(d["X"]).cuda()
-        A1 = torch.from_numpy(d["A1"]).cuda()
-        g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=-1.0, max_iter=1 << 20)
-        g.iterate(3)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        torch.cuda.synchronize()
-        ev[0].record(torch.cuda.current_stream())
-        g.iterate(50)
-        ev[1].record(torch.cuda.current_stream())
-        torch.cuda.synchronize()
-        ms = ev[0].elapsed_time(ev[1]) / 50
-        g.close()
-        g = G.GoDec(X, A1, d["r"], d["k"], d["q"], tol=1e-7, max_iter=50)
-        t0 = time.time()
-        it, rel = g.solve()
-        t_solve = time.time() - t0
-        g.close()
-        import oracle as O
-        t0 = time.time()
-        O.godec(d["X"], d["A1"], d["k"], d["q"], tol=-1.0, max_iter=5)
-        o_all = (time.time() - t0) / 5
-        code = ("import sys, time; sys.path.insert(0, %r); import synth, oracle as O; d = synth.config_c1(); "
-                "t0 = time.time(); O.godec(d['X'], d['A1'], d['k'], d['q'], tol=-1.0, max_iter=5); "
-                "print((time.time() - t0) / 5)") % ROOT
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-        o_one = float(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                                     check=True).stdout.strip().splitlines()[-1])
-        print(f"C1 GPU: {ms:.3f} ms/iteration ({1e3 / ms:.0f} it/s); solve to tol 1e-7: {it} iterations, "
-              f"rel err {rel:.2e}, {t_solve * 1e3:.1f} ms wall; float64 oracle: {1.0 / o_all:.1f} it/s on "
-              f"{os.cpu_count()} cores, {1.0 / o_one:.1f} it/s on one core")
+    elif args.kernel in ("backward", "precision", "batched", "c1"):
+        f = {"backward": form_c5, "precision": form_c3, "batched": form_c4, "c1": form_c1}[args.kernel]
+        print(json.dumps(f(), indent=1))
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
         run = G.GoDec(torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda(), R, d["k"], Q)
