@@ -104,6 +104,8 @@ struct godec_ctx {
   long long* cand_idx = nullptr;
   float* cand_val = nullptr;
   unsigned long long cap = 0;
+  unsigned* sbits = nullptr;           // m n bits: the support of the S-step in flight (clear between S-steps)
+  size_t sbits_bytes = 0;
   long long* S_idx[2] = {nullptr, nullptr};
   float* S_val[2] = {nullptr, nullptr};
   int idx_bits = 1;
@@ -260,6 +262,7 @@ void prod(godec_ctx* c, int i, float* out, bool want_bt2, const float* T0, const
   l.t_upper = 1;     // slot normalisers are inverses of upper-triangular factors
   l.pend = c->pend;
   l.ctl = c->ctl;
+  l.pdl = 1;
   PROF(c, 0, c->st, launch_prod_tc(l, c->st));
 }
 
@@ -550,6 +553,7 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ea.Zt16 = c->Zt16;
   ea.zscale = c->ctl->zscale;
   ea.max_nnz = c->p.k;
+  ea.sbits = c->sbits;
   PROF(c, 8, st, launch_emit(ea, c->nsm, st));
   if (c->Z) PROF(c, 9, st, launch_z_update(ea, c->nsm, st));
 }
@@ -627,6 +631,7 @@ godec_status reset_state(godec_ctx* c) {
                      c->st));
   launch_split_t(c->A1, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
   if (godec_status s = clear_counters(c)) return s;
+  if (c->sbits) CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
   std::vector<float> eye((size_t)c->RP * c->RP, 0.f);
   for (int i = 0; i < c->RP; ++i) eye[(size_t)i * c->RP + i] = 1.f;
   CK(cudaMemcpyAsync(c->Vprev, eye.data(), eye.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
@@ -668,6 +673,8 @@ godec_status rescale_z(godec_ctx* c) {
 godec_status handle_abort(godec_ctx* c, const Ctl& h) {
   godec_status s;
   if ((s = clear_counters(c))) return s;
+  // an S-step cut short may leave support bits behind
+  if (c->sbits) CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
   if (h.timeout) {
     launch_reset_iter(c->ctl, c->st);
     return fail(c, GODEC_ERR_TIMEOUT, "a device-side wait of the tensor-core product timed out (iteration %d)",
@@ -809,7 +816,7 @@ void godec_destroy(godec_ctx* c) {
                   c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->pend, c->gparts, c->RA, c->RB, c->Wa, c->Wb, c->Qa, c->Qb, c->Qtmp, c->Rf,
                   c->cs_ref, c->rf_part, c->rf_g, c->rf_C, c->rf_core, c->rf_U, c->rf_V, c->g64, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
-                  c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1]};
+                  c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1], c->sbits};
   for (void* p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev)
@@ -971,6 +978,8 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
     CKI(dalloc(&c->S_idx[b], (size_t)p->k));
     CKI(dalloc(&c->S_val[b], (size_t)p->k));
   }
+  c->sbits_bytes = (size_t)((mn + 31) / 32) * sizeof(unsigned);
+  CKI(dalloc(reinterpret_cast<char**>(&c->sbits), c->sbits_bytes));
   c->idx_bits = 1;
   while ((1ull << c->idx_bits) < mn) ++c->idx_bits;
   launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), c->st);

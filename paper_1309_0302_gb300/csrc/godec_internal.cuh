@@ -173,6 +173,7 @@ struct TcLaunch {
   int half_a;              // mapA is the float16 copy Z16 (box 64 halves x 128 rows)
   int* pend;               // G x geom.maxpend ints of scratch
   Ctl* ctl;
+  int pdl = 0;             // programmatic dependent launch on the preceding kernel of the stream
 };
 void launch_prod_tc(const TcLaunch& l, cudaStream_t st);
 int64_t apply_blocks(int64_t rows);
@@ -270,6 +271,8 @@ struct EmitArgs {
   void* Zt16;
   const float* zscale;     // Z and Zt are stored scaled by zscale[0]
   long long max_nnz;       // bound on the support of S (k): the z-update grid
+  unsigned* sbits;         // m n bits, all clear between S-steps: the emit marks Omega_t so the
+                           // restore of Omega_{t-1} skips entries the scatter rewrites anyway
 };
 void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st);
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);

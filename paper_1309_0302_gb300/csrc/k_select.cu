@@ -462,8 +462,10 @@ k_emit(EmitArgs a) {
       if (sel & (1u << j)) {
         unsigned long long c = t0 + (unsigned long long)j * EMIT_THREADS + tid;
         if (pos < (unsigned long long)ctl->k_req) {   // never past the S buffers
-          Sidx[pos] = a.cand_idx[c];
+          const long long idx = a.cand_idx[c];
+          Sidx[pos] = idx;
           Sval[pos] = a.cand_val[c];
+          if (a.sbits) atomicOr(&a.sbits[idx >> 5], 1u << (idx & 31));
         }
         ++pos;
       }
@@ -569,34 +571,47 @@ __device__ __forceinline__ void split_idx(long long idx, long long n, float ninv
   j = r;
 }
 
-// One entry per thread (the grid covers the largest possible support, k).
+// One entry per thread (the grid covers the largest possible support, k).  The update
+// also runs after the iteration that met the stop test (converged sets abort only to
+// stop the iterations after it), so Z always matches the committed S.
+__device__ __forceinline__ bool z_skip(const Ctl* ctl) { return ctl->abort && !ctl->converged; }
+
+// Entries of Omega_{t-1} that left the support get Z = X back; those still in Omega_t
+// (their bit set by the emit) are left to the scatter, which writes them anyway.
 __global__ void k_z_restore(EmitArgs a) {
   Ctl* ctl = a.ctl;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ctl->abort || (long long)blockIdx.x * blockDim.x >= ctl->nnz_prev) return;
+  if (z_skip(ctl) || (long long)blockIdx.x * blockDim.x >= ctl->nnz_prev) return;
   const long long nnz = ctl->nnz_prev;
   const float zs = a.zscale ? a.zscale[0] : 1.f;
   bool bad = false;
   if (e < nnz) {
-    long long i, j;
-    split_idx(a.S_idx[ctl->cur ^ 1][e], a.n, 1.f / (float)a.n, i, j);
-    z_write(a, i, j, a.X[i * a.ldx + j], zs, bad);
+    const long long idx = a.S_idx[ctl->cur ^ 1][e];
+    if (!a.sbits || !((__ldcg(&a.sbits[idx >> 5]) >> (idx & 31)) & 1u)) {
+      long long i, j;
+      split_idx(idx, a.n, 1.f / (float)a.n, i, j);
+      z_write(a, i, j, a.X[i * a.ldx + j], zs, bad);
+    }
   }
   z_flag(ctl, bad);
 }
 
+// Z = X - S_t on Omega_t; clears the support bits again (every set bit of a word belongs
+// to Omega_t, so the word is simply zeroed).
 __global__ void k_z_scatter(EmitArgs a) {
   Ctl* ctl = a.ctl;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ctl->abort || (long long)blockIdx.x * blockDim.x >= ctl->nnz_cur) return;
+  if (z_skip(ctl) || (long long)blockIdx.x * blockDim.x >= ctl->nnz_cur) return;
   const int cb = ctl->cur;
   const long long nnz = ctl->nnz_cur;
   const float zs = a.zscale ? a.zscale[0] : 1.f;
   bool bad = false;
   if (e < nnz) {
+    const long long idx = a.S_idx[cb][e];
     long long i, j;
-    split_idx(a.S_idx[cb][e], a.n, 1.f / (float)a.n, i, j);
+    split_idx(idx, a.n, 1.f / (float)a.n, i, j);
     z_write(a, i, j, a.X[i * a.ldx + j] - a.S_val[cb][e], zs, bad);
+    if (a.sbits) a.sbits[idx >> 5] = 0u;
   }
   z_flag(ctl, bad);
 }

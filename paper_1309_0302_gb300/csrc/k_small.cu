@@ -7,9 +7,14 @@
 // chain is orthonormalised by Cholesky factors of Gram matrices (CholeskyQR);
 // every product of chain 3 contributes the factor it was normalised with.
 //
-// GB300 runs float64 at about 2 FMA per clock per SM, so float64 is used only
-// for the rank test (a pivoted Cholesky on an exactly accumulated Gram) and
-// for the Gram sums over row tiles; factorisations run in float32.
+// GB300 runs float64 at about 2 FMA per clock per SM.  float64 is used for the Gram
+// sums over row tiles, the rank test (a pivoted Cholesky on an exactly accumulated
+// Gram) and the Cholesky factor of every orthonormalisation on the critical path
+// (k_chol: each power-step product of the exact path, the CholeskyQR2 of Q1 and Q2, the
+// precision form's correction bases); that factor is then applied in float32.  The
+// lagged normalisers (k_slot, off the critical path: they only precondition the next
+// iteration's chain, whose Q1 and Q2 are re-orthonormalised exactly) and the core SVD
+// run in float32.
 #include <math.h>
 
 #include "godec_internal.cuh"
@@ -319,6 +324,36 @@ __device__ void normalise_into(float (*M)[LD], float* dst, int RP, Ctl* ctl, boo
   for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) dst[e] = M[e / RP][e % RP] * inv;
 }
 
+// float64 upper Cholesky G = R^T R of the RP x RP Gram in Gd (padded block = identity),
+// right-looking, one column per barrier: the trailing update uses the unscaled pivot row
+// (G[a][c] -= G[j][a] G[j][c] / G[j][j]), and the rows are scaled by 1 / sqrt(pivot) at
+// the end.  Pivots j < r below thr are raised to thr and reported through *bad.  The
+// float32 factor goes to R (lower triangle zero).
+__device__ void chol64(double (*Gd)[LD], float (*R)[LD], int r, int RP, double thr, int* bad) {
+  __shared__ double piv[kMaxRP];
+  const int tid = threadIdx.x;
+  for (int j = 0; j < RP; ++j) {
+    double d = Gd[j][j];
+    if (j < r && !(d > thr)) {
+      if (tid == 0) *bad = 1;
+      d = thr > 0.0 ? thr : 1e-300;
+    }
+    if (tid == 0) piv[j] = d;
+    const double inv = 1.0 / d;
+    const int w = RP - j - 1;
+    for (int e = tid; e < w * w; e += SMALL_THREADS) {
+      const int a = j + 1 + e / w, c = j + 1 + e % w;
+      if (c >= a) Gd[a][c] -= Gd[j][a] * Gd[j][c] * inv;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+    const int i = e / kMaxRP, c = e % kMaxRP;
+    R[i][c] = (i < RP && c >= i && c < RP) ? (float)(Gd[i][c] / sqrt(piv[i])) : 0.f;
+  }
+  __syncthreads();
+}
+
 // ---- critical path: R from a Gram --------------------------------------------------------
 // R (upper) with Rᵀ R = G and its inverse T = R^{-1}.  With alarm_ratio > 0 the
 // factor of an almost orthonormal input is checked: a diagonal spread above the ratio
@@ -329,14 +364,45 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
                                                         float alarm_ratio, Ctl* ctl) {
   if (ctl->abort) return;
   extern __shared__ __align__(16) float smf[];
-  float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
-  float (*R)[LD] = G + kMaxRP;
+  double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);            // 2 float blocks
+  float (*R)[LD] = reinterpret_cast<float (*)[LD]>(smf) + 2 * kMaxRP;
   float (*Ri)[LD] = R + kMaxRP;
-  if (!load_gram(G, g64, r, RP)) {
+  __shared__ double s_gmax;
+  __shared__ int s_bad;
+  // the Gram in float64, padded block set to the identity; a non-finite Gram aborts
+  int nf = 0;
+  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+    const int i = e / kMaxRP, j = e % kMaxRP;
+    const double v = (i < r && j < r) ? __ldcg(g64 + i * RP + j) : (i == j ? 1.0 : 0.0);
+    nf |= !isfinite(v);
+  }
+  if (__syncthreads_or(nf)) {
     if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
     return;
   }
-  robust_chol(G, R, r, RP, ctl);
+  if (threadIdx.x == 0) {
+    double gm = 0.0;
+    for (int j = 0; j < r; ++j) gm = fmax(gm, __ldcg(g64 + j * RP + j));
+    s_gmax = gm;
+  }
+  // Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
+  // numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
+  // factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+      const int i = e / kMaxRP, j = e % kMaxRP;
+      double v = (i < r && j < r) ? __ldcg(g64 + i * RP + j) : (i == j ? 1.0 : 0.0);
+      if (attempt == 1 && i == j && i < r) v += 1e-5 * s_gmax;
+      Gd[i][j] = v;
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    chol64(Gd, R, r, RP, 1e-6 * s_gmax, &s_bad);
+    if (!s_bad) break;
+    if (threadIdx.x == 0) ctl->chol_shifts += 1;
+  }
+  __syncthreads();
   if (alarm_ratio > 0.f && threadIdx.x < 32) {
     float lo = 3.4e38f, hi = 0.f;
     for (int j = threadIdx.x; j < r; j += 32) { lo = fminf(lo, R[j][j]); hi = fmaxf(hi, R[j][j]); }
@@ -598,11 +664,33 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   }
   __syncthreads();
   mm_1024(X2, V, W, RP, false);       // W = M V
+  // In the steady state the warm start already leaves W's columns orthogonal to the
+  // rotation test's resolution, and a sweep would only confirm it (49 dependent rounds at
+  // r = 50).  One Gram W^T W (all pairs at once) decides instead: below half the rotation
+  // threshold no pair of the sweep could rotate, and the sweeps are skipped.
+  mm_1024(W, W, X1, r, true);         // X1 = W^T W
+  if (tid == 0) s_dmax = 0u;
+  __syncthreads();
+  {
+    float cmax = 0.f;
+    for (int e = tid; e < r * r; e += SVD_THREADS) {
+      const int i = e / r, j = e % r;
+      if (i < j) {
+        const float d = sqrtf(X1[i][i]) * sqrtf(X1[j][j]);
+        cmax = fmaxf(cmax, d > 0.f ? fabsf(X1[i][j]) / d : 0.f);
+      }
+    }
+    for (int o = 16; o; o >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    if (lane == 0 && cmax > 0.f) atomicMax(&s_dmax, __float_as_uint(cmax));
+  }
+  __syncthreads();
+  const bool warm_done = __uint_as_float(s_dmax) < 2e-6f;
+  __syncthreads();
 
   const int np = (r + 1) & ~1;
   const int npairs = np / 2;
   int sweeps = 0;
-  for (; sweeps < 16; ++sweeps) {
+  for (; sweeps < 16 && !warm_done; ++sweeps) {
     __syncthreads();                  // every thread has read the previous flag
     if (tid == 0) {
       rotated = 0;

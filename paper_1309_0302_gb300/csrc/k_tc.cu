@@ -419,6 +419,12 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
     mbar_init(&mma_done, 1);
     fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
+  // Launched as a programmatic dependent of the previous product: everything above ran
+  // while that product completed its tiles; no global memory is touched before this.
+  pdl_wait();
+  if (tid == 0) {
     // Iteration already abandoned, or Z outgrew its scale in the last S-step (the caller
     // rescales it): do nothing, and make the rest of the iteration skip too.
     s_err = (ctl && (ctl->abort || ctl->range_err)) ? 2 : 0;
@@ -427,7 +433,6 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     s_zi = a.zscale ? a.zscale[1] : 1.f;
   }
   if (tid < kMaxRP) s_csc[tid] = (tid < a.RP && a.cscale) ? a.cscale[tid] : 1.f;
-  if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
@@ -632,6 +637,7 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
   tc_fence_before();
   __syncthreads();
+  pdl_launch_dependents();   // the stream is done: the next product may start its prologue
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tbase, kTmemCols);
@@ -708,13 +714,16 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     }
     mbar_init(&mma_done, 1);
     fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, 128);
+  pdl_wait();   // see k_prod_tc
+  if (tid == 0) {
     s_err = (ctl && (ctl->abort || ctl->range_err)) ? 2 : 0;
     if (ctl && ctl->range_err) ctl->abort = 1;
     s_npend = 0;
     s_zi = a.zscale ? a.zscale[1] : 1.f;
   }
   if (tid < kMaxRP) s_csc[tid] = (tid < a.RP && a.cscale) ? a.cscale[tid] : 1.f;
-  if (warp == 1) tmem_alloc(&tmem_base, 128);
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
@@ -860,6 +869,7 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 
   tc_fence_before();
   __syncthreads();
+  pdl_launch_dependents();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tbase, 128);
@@ -1001,6 +1011,25 @@ cudaError_t prepare_tc_kernels() {
   return e;
 }
 
+// Launch with the programmatic-stream-serialization attribute when pdl is set: the kernel
+// may begin (barrier set-up, tensor-memory allocation) while the preceding kernel of the
+// stream finishes, and waits for it in pdl_wait() before its first global access.
+template <typename Kern>
+static void launch_tc(Kern kern, unsigned grid, unsigned block, size_t smem, cudaStream_t st, bool pdl,
+                      const CUtensorMap& A, const CUtensorMap& B, const TcArgs& a) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, A, B, a);
+}
+
 void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   TcArgs a;
   a.rows = l.rows;
@@ -1029,25 +1058,27 @@ void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   const CUtensorMap& B = *reinterpret_cast<const CUtensorMap*>(l.mapB);
   a.prescaled = l.prescaled;
   const int rpp = tc_rpp(l.RP);
+  const bool pdl = l.pdl != 0;
+  const unsigned G = (unsigned)a.G;
   if (l.half_a) {
     switch (rpp) {
-      case 16: k_prod_h16<16><<<a.G, kThreads16, kTc16Smem, st>>>(A, B, a); break;
-      case 32: k_prod_h16<32><<<a.G, kThreads16, kTc16Smem, st>>>(A, B, a); break;
+      case 16: launch_tc(k_prod_h16<16>, G, kThreads16, kTc16Smem, st, pdl, A, B, a); break;
+      case 32: launch_tc(k_prod_h16<32>, G, kThreads16, kTc16Smem, st, pdl, A, B, a); break;
       default: if (l.ctl) cudaMemsetAsync(&l.ctl->abort, 0xff, sizeof(int), st); break;   // RP > 32: rejected at init
     }
   } else if (l.prescaled) {
     switch (rpp) {
-      case 16: k_prod_tc<16, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
-      case 32: k_prod_tc<32, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
-      case 48: k_prod_tc<48, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
-      default: k_prod_tc<64, true><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      case 16: launch_tc(k_prod_tc<16, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
+      case 32: launch_tc(k_prod_tc<32, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
+      case 48: launch_tc(k_prod_tc<48, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
+      default: launch_tc(k_prod_tc<64, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
     }
   } else {
     switch (rpp) {
-      case 16: k_prod_tc<16, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
-      case 32: k_prod_tc<32, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
-      case 48: k_prod_tc<48, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
-      default: k_prod_tc<64, false><<<a.G, kThreads, kTcSmem, st>>>(A, B, a); break;
+      case 16: launch_tc(k_prod_tc<16, false>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
+      case 32: launch_tc(k_prod_tc<32, false>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
+      case 48: launch_tc(k_prod_tc<48, false>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
+      default: launch_tc(k_prod_tc<64, false>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
     }
   }
 }

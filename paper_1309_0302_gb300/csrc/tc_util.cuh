@@ -235,6 +235,13 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float* va,
   }
 }
 
+// Programmatic dependent launch: wait until the preceding kernel of the stream has
+// completed and its memory is visible (returns at once when this launch has no
+// programmatic dependency), and let the next kernel of the stream start its prologue
+// once every CTA of this grid has signalled or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 __device__ __forceinline__ void named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
