@@ -276,7 +276,7 @@ __device__ bool load_gram(float (*G)[LD], const double* g64, int r, int RP) {
 
 // Largest |M[i][j]| over the n x n block (all threads get it).
 __device__ float block_absmax(const float (*M)[LD], int n) {
-  __shared__ float red[SMALL_THREADS / 32];
+  __shared__ float red[32];   // one slot per warp of a block of up to 1024 threads
   float m = 0.f;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) m = fmaxf(m, fabsf(M[e / n][e % n]));
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -329,21 +329,33 @@ __device__ void normalise_into(float (*M)[LD], float* dst, int RP, Ctl* ctl, boo
 // (G[a][c] -= G[j][a] G[j][c] / G[j][j]), and the rows are scaled by 1 / sqrt(pivot) at
 // the end.  Pivots j < r below thr are raised to thr and reported through *bad.  The
 // float32 factor goes to R (lower triangle zero).
-__device__ void chol64(double (*Gd)[LD], float (*R)[LD], int r, int RP, double thr, int* bad) {
+// GB300 issues a warp's float64 FMA over many cycles, so the trailing update runs over a
+// dense list of the upper-triangle entries (a, c), a >= c's row, ordered by decreasing row
+// a: the entries with a > j are the first (RP-1-j)(RP-j)/2 of the list, and no lane of a
+// warp idles on a masked-out entry.  The list (tri, built by the caller) holds a << 8 | c.
+__device__ void chol64(double (*Gd)[LD], float (*R)[LD], int r, int RP, double thr, int* bad,
+                       const unsigned short* tri) {
   __shared__ double piv[kMaxRP];
+  __shared__ double sc[kMaxRP];
   const int tid = threadIdx.x;
   for (int j = 0; j < RP; ++j) {
-    double d = Gd[j][j];
-    if (j < r && !(d > thr)) {
-      if (tid == 0) *bad = 1;
-      d = thr > 0.0 ? thr : 1e-300;
-    }
-    if (tid == 0) piv[j] = d;
-    const double inv = 1.0 / d;
     const int w = RP - j - 1;
-    for (int e = tid; e < w * w; e += SMALL_THREADS) {
-      const int a = j + 1 + e / w, c = j + 1 + e % w;
-      if (c >= a) Gd[a][c] -= Gd[j][a] * Gd[j][c] * inv;
+    // pivot and the scaled pivot row: sc[a] = G[j][a] / G[j][j]
+    if (tid < kMaxRP) {
+      double d = Gd[j][j];
+      if (j < r && !(d > thr)) {
+        if (tid == 0) *bad = 1;
+        d = thr > 0.0 ? thr : 1e-300;
+      }
+      if (tid == 0) piv[j] = d;
+      const int a = j + 1 + tid;
+      if (tid < w) sc[a] = Gd[j][a] / d;
+    }
+    __syncthreads();
+    const int nt = w * (w + 1) / 2;
+    for (int e = tid; e < nt; e += SMALL_THREADS) {
+      const int a = tri[e] >> 8, c = tri[e] & 255;
+      Gd[a][c] = fma(-sc[a], Gd[j][c], Gd[a][c]);
     }
     __syncthreads();
   }
@@ -369,6 +381,16 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
   float (*Ri)[LD] = R + kMaxRP;
   __shared__ double s_gmax;
   __shared__ int s_bad;
+  __shared__ unsigned short tri[kMaxRP * (kMaxRP + 1) / 2];
+  // upper-triangle entries (a, c), c >= a, of rows RP-1 down to 0 (see chol64)
+  for (int e = threadIdx.x; e < RP * (RP + 1) / 2; e += SMALL_THREADS) {
+    // e -> (a, c): rows from the bottom, row a = RP-1-k holding k+1 entries
+    int k = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    while (k * (k + 1) / 2 > e) --k;
+    while ((k + 1) * (k + 2) / 2 <= e) ++k;
+    const int a = RP - 1 - k, c = a + (e - k * (k + 1) / 2);
+    tri[e] = (unsigned short)(a << 8 | c);
+  }
   // the Gram in float64, padded block set to the identity; a non-finite Gram aborts
   int nf = 0;
   for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
@@ -398,7 +420,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
     }
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    chol64(Gd, R, r, RP, 1e-6 * s_gmax, &s_bad);
+    chol64(Gd, R, r, RP, 1e-6 * s_gmax, &s_bad, tri);
     if (!s_bad) break;
     if (threadIdx.x == 0) ctl->chol_shifts += 1;
   }
@@ -578,12 +600,28 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_rank(const double* __restrict
 constexpr int SVD_THREADS = 1024;
 
 __device__ void mm_1024(const float (*A)[LD], const float (*B)[LD], float (*C)[LD], int n, bool a_transposed) {
-  // C = A B (or A^T B); C must not alias A or B
-  for (int e = threadIdx.x; e < n * n; e += SVD_THREADS) {
-    const int i = e / n, j = e % n;
-    float s = 0.f;
-    for (int t = 0; t < n; ++t) s = fmaf(a_transposed ? A[t][i] : A[i][t], B[t][j], s);
-    C[i][j] = s;
+  // C = A B (or A^T B); C must not alias A or B.  Thread (ty, tx) of the 32 x 32 grid owns
+  // rows ty, ty + 32 and columns tx, tx + 32: a warp shares its rows (broadcast loads of A)
+  // and reads consecutive columns of B (conflict-free).
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+  const int r0 = ty, r1 = ty + 32, c0 = tx, c1 = tx + 32;
+  if (r0 < n) {
+    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+    const bool h1 = r1 < n;
+#pragma unroll 4
+    for (int t = 0; t < n; ++t) {
+      const float a0 = a_transposed ? A[t][r0] : A[r0][t];
+      const float a1 = h1 ? (a_transposed ? A[t][r1] : A[r1][t]) : 0.f;
+      const float b0 = B[t][c0], b1 = B[t][c1];
+      s00 = fmaf(a0, b0, s00);
+      s01 = fmaf(a0, b1, s01);
+      s10 = fmaf(a1, b0, s10);
+      s11 = fmaf(a1, b1, s11);
+    }
+    if (c0 < n) C[r0][c0] = s00;
+    if (c1 < n) C[r0][c1] = s01;
+    if (h1 && c0 < n) C[r1][c0] = s10;
+    if (h1 && c1 < n) C[r1][c1] = s11;
   }
   __syncthreads();
 }
