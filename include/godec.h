@@ -86,6 +86,12 @@ typedef struct godec_params {
 /* Precision form only: skip the float32 correction (diagnostic: the float16 chain's own
    accuracy). */
 #define GODEC_FLAG_NO_REFINE 2
+/* Factor the Gram of every critical-path orthonormalisation (the power-step products of
+   the exact path, the CholeskyQR2 of Q1 and Q2, the precision form's correction) in
+   float64 instead of float32.  GB300's float64 rate makes each such factorisation about
+   3.5 times slower (about 110 us against 31 us at r = 50); the factor is applied in
+   float32 either way. */
+#define GODEC_FLAG_FP64_FACTOR 4
 
 typedef struct godec_ctx godec_ctx;
 

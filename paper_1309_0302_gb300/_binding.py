@@ -15,6 +15,7 @@ BATCH_POLICIES = 5
 PREC_FP32 = 0
 PREC_BF16_REFINE = 1
 FLAG_NO_REFINE = 2
+FLAG_FP64_FACTOR = 4
 MAX_RANK = 64
 
 

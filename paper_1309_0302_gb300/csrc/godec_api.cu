@@ -272,7 +272,8 @@ void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out
 
 // R with Rᵀ R = Gram, and T = R^{-1} stored right after R.
 void chol(godec_ctx* c, const double* g, float* R, float alarm_ratio = 0.f) {
-  PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, R + (size_t)c->RP * c->RP, c->ctl, c->st, alarm_ratio));
+  PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, R + (size_t)c->RP * c->RP, c->ctl, c->st, alarm_ratio,
+                                (c->p.flags & GODEC_FLAG_FP64_FACTOR) != 0));
 }
 const float* inv_of(godec_ctx* c, const float* R) { return R + (size_t)c->RP * c->RP; }
 
@@ -314,10 +315,11 @@ void cqr2(godec_ctx* c, const float* W, int64_t rows, int R2, int ld, float* Q, 
           float* T2) {
   cudaStream_t st = c->st;
   PROF(c, 10, st, launch_cross_gram(W, ld, R2, W, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st));
-  PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R1, T1, c->ctl, st, 0.f));
+  const bool f64 = (c->p.flags & GODEC_FLAG_FP64_FACTOR) != 0;
+  PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R1, T1, c->ctl, st, 0.f, f64));
   PROF(c, 10, st, launch_tall_small_f(W, ld, R2, T1, ld, 0, R2, rows, 1.f, 0.f, c->Qtmp, ld, st));
   PROF(c, 10, st, launch_cross_gram(c->Qtmp, ld, R2, c->Qtmp, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st));
-  PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R2m, T2, c->ctl, st, 0.f));
+  PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R2m, T2, c->ctl, st, 0.f, f64));
   PROF(c, 10, st, launch_tall_small_f(c->Qtmp, ld, R2, T2, ld, 0, R2, rows, 1.f, 0.f, Q, ld, st));
 }
 

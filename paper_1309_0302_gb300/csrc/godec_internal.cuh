@@ -183,7 +183,7 @@ void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, do
                      cudaStream_t st);
 // R (upper, Rᵀ R = Gram) and T = R^{-1}, both RP x RP.
 void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
-                 float alarm_ratio = 0.f);
+                 float alarm_ratio = 0.f, bool fp64 = false);
 struct SlotLaunch {
   const double* g64 = nullptr;
   int g_is_p = 0;

@@ -7,14 +7,13 @@
 // chain is orthonormalised by Cholesky factors of Gram matrices (CholeskyQR);
 // every product of chain 3 contributes the factor it was normalised with.
 //
-// GB300 runs float64 at about 2 FMA per clock per SM.  float64 is used for the Gram
-// sums over row tiles, the rank test (a pivoted Cholesky on an exactly accumulated
-// Gram) and the Cholesky factor of every orthonormalisation on the critical path
-// (k_chol: each power-step product of the exact path, the CholeskyQR2 of Q1 and Q2, the
-// precision form's correction bases); that factor is then applied in float32.  The
-// lagged normalisers (k_slot, off the critical path: they only precondition the next
-// iteration's chain, whose Q1 and Q2 are re-orthonormalised exactly) and the core SVD
-// run in float32.
+// GB300's float64 rate is a small fraction of its float32 rate: a float64 Cholesky of a
+// 56 x 56 Gram takes about 110 us on one SM against 31 us for the blocked float32 one.
+// float64 is used for the Gram sums over row tiles and the rank test (a pivoted Cholesky
+// on an exactly accumulated Gram).  The Cholesky factors of the critical-path
+// orthonormalisations (k_chol) run in float32 by default and in float64 with
+// GODEC_FLAG_FP64_FACTOR; the factor is applied in float32 either way.  The lagged
+// normalisers (k_slot, off the critical path) and the core SVD run in float32.
 #include <math.h>
 
 #include "godec_internal.cuh"
@@ -371,14 +370,25 @@ __device__ void chol64(double (*Gd)[LD], float (*R)[LD], int r, int RP, double t
 // factor of an almost orthonormal input is checked: a diagonal spread above the ratio
 // means one CholeskyQR pass would not restore orthonormality, and the iteration is
 // sent back to the exact path (alarm).
+// F64: the factorisation runs in float64 (chol64) instead of the blocked float32 Cholesky;
+// either way R and T = R^{-1} are stored in float32 and T is formed in float32.
+template <bool F64>
 __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict__ g64, int r, int RP,
                                                         float* __restrict__ Rout, float* __restrict__ Tout,
                                                         float alarm_ratio, Ctl* ctl) {
   if (ctl->abort) return;
   extern __shared__ __align__(16) float smf[];
-  double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);            // 2 float blocks
   float (*R)[LD] = reinterpret_cast<float (*)[LD]>(smf) + 2 * kMaxRP;
   float (*Ri)[LD] = R + kMaxRP;
+  if (!F64) {
+    float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
+    if (!load_gram(G, g64, r, RP)) {
+      if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
+      return;
+    }
+    robust_chol(G, R, r, RP, ctl);
+  } else {
+  double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);            // 2 float blocks
   __shared__ double s_gmax;
   __shared__ int s_bad;
   __shared__ unsigned short tri[kMaxRP * (kMaxRP + 1) / 2];
@@ -407,9 +417,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
     for (int j = 0; j < r; ++j) gm = fmax(gm, __ldcg(g64 + j * RP + j));
     s_gmax = gm;
   }
-  // Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
-  // numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
-  // factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.
+  // Cholesky with a shifted fallback, as robust_chol
   for (int attempt = 0; attempt < 2; ++attempt) {
     __syncthreads();
     for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
@@ -425,6 +433,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
     if (threadIdx.x == 0) ctl->chol_shifts += 1;
   }
   __syncthreads();
+  }
   if (alarm_ratio > 0.f && threadIdx.x < 32) {
     float lo = 3.4e38f, hi = 0.f;
     for (int j = threadIdx.x; j < r; j += 32) { lo = fminf(lo, R[j][j]); hi = fmaxf(hi, R[j][j]); }
@@ -858,7 +867,8 @@ constexpr size_t kSmall8 = 8 * kMaxRP * LD * sizeof(float);
 }  // namespace
 
 cudaError_t prepare_small_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  cudaError_t e = cudaFuncSetAttribute(k_chol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall8);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
@@ -878,8 +888,9 @@ void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, do
 }
 
 void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
-                 float alarm_ratio) {
-  k_chol<<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, T, alarm_ratio, ctl);
+                 float alarm_ratio, bool fp64) {
+  if (fp64) k_chol<true><<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, T, alarm_ratio, ctl);
+  else k_chol<false><<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, T, alarm_ratio, ctl);
 }
 
 void launch_slot(const SlotLaunch& l, cudaStream_t st) {

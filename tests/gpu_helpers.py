@@ -37,11 +37,11 @@ def fma32(a, b, c):
 
 
 class GpuRun:
-    def __init__(self, d, tol=1e-7, max_iter=50, rank_tol=0.0):
+    def __init__(self, d, tol=1e-7, max_iter=50, rank_tol=0.0, flags=0):
         import paper_1309_0302_gb300 as G
         self.d = d
         self.g = G.GoDec(to_gpu(d["X"]), to_gpu(d["A1"]), d["r"], d["k"], d["q"], tol=tol,
-                         max_iter=max_iter, rank_tol=rank_tol)
+                         max_iter=max_iter, rank_tol=rank_tol, flags=flags)
 
     def factors(self):
         U, s, V = self.g.L()

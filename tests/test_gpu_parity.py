@@ -218,11 +218,15 @@ def test_run_host_matches_device_path():
 
 # --- the 10000 x 10000 workload in the bench's launch configuration ------------------------
 @pytest.mark.slow
-def test_c2_full_size_same_step():
+@pytest.mark.parametrize("fp64_factor", [False, True])
+def test_c2_full_size_same_step(fp64_factor):
     """Full-size check: GPU iterations 1..3 of the bench workload, then one float64
-    oracle step from the GPU's S_2 compared with the GPU's iteration 3."""
+    oracle step from the GPU's S_2 compared with the GPU's iteration 3; with the default
+    float32 Cholesky factors and with float64 ones (GODEC_FLAG_FP64_FACTOR), whose errors
+    are printed side by side."""
+    import paper_1309_0302_gb300 as G
     d = synth.config_c2()
-    run = GpuRun(d)
+    run = GpuRun(d, flags=G.FLAG_FP64_FACTOR if fp64_factor else 0)
     run.g.iterate(2)
     i2, v2 = run.sparse()
     assert i2.size == d["k"]
@@ -235,8 +239,8 @@ def test_c2_full_size_same_step():
     e_full = s_rel(i, v, st["S_idx"], st["S_val"])
     nb, inside = selection_within_band(d["X"], U, s, V, i, d["k"])
     info = run.g.info()
-    print(f"c2 same-step: L {eL:.2e}, S common {e_common:.2e}, S with flips {e_full:.2e}, "
-          f"flips {flips}, band mismatches {nb}")
+    print(f"c2 same-step ({'float64' if fp64_factor else 'float32'} factors): L {eL:.2e}, "
+          f"S common {e_common:.2e}, S with flips {e_full:.2e}, flips {flips}, band mismatches {nb}")
     assert eL <= TOL_L
     assert e_common <= TOL_S
     assert flips <= 1e-4 * d["k"]
