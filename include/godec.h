@@ -331,6 +331,62 @@ godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t n, int64_t 
                                   const float* B, int32_t r, float* Y, void* stream);
 
 /*
+ * GreBsmo, greedy bilateral smoothing (Sec. 3.2.1, Algorithm 2): X = U V + S + G with U
+ * orthonormal (m x r), V (r x n) and S from the element-wise soft threshold (eq. softt).
+ * Each inner step (eq. GreBsmoA), with Z = X - S:
+ *   U = Q of QR(Z V^T) (CholeskyQR2),  V = U^T Z,  S = S_lambda(X - U V);
+ * after K inner steps the relative error ||X - U V - S||^2 / ||X||^2 is tested against
+ * tau; if it is above tau and r < r_max, dr rows are appended to V: the dr top right
+ * singular vectors of X - U V - S (eq. GreBsmoD), here by the random-projection variant
+ * the paper allows (a randomized subspace iteration: B = orth(Omega_s), q_inc times
+ * B = orth(D^T orth(D B)), then the dr top right singular vectors of D B mapped back by
+ * B).  The first V comes the same way from X (the greedy direction from U = 0, S = 0).
+ * The products stream X - S through the same tensor-core kernel as GoDec; the soft
+ * threshold runs in the residual pass (candidates |R| > lambda, S = R - lambda sgn R).
+ */
+typedef struct godec_grebsmo_params {
+  int64_t m, n;        /* X is m x n, m n < 2^32 */
+  int64_t ldx;         /* row stride of X in elements, >= n, ldx*4 a multiple of 16 */
+  double lambda;       /* soft threshold of eq. softt, > 0 (exactly representable in
+                          float32 keeps the GPU's support test |R| > lambda exact) */
+  double tau;          /* stop when ||X - U V - S||^2 / ||X||^2 <= tau */
+  int64_t s_cap;       /* initial capacity of S (entries); grown when the support is larger */
+  int32_t dr;          /* rank increment, >= 1 */
+  int32_t K;           /* inner steps per rank stage, >= 1 */
+  int32_t r_max;       /* rank cap, dr <= r_max <= min(m, n, GODEC_MAX_RANK) */
+  int32_t oversample;  /* extra columns of the random projection: p = dr + oversample <=
+                          min(m, n, GODEC_MAX_RANK) */
+  int32_t q_inc;       /* power steps of the increment's subspace iteration, 0..16 */
+  int32_t flags;       /* GODEC_FLAG_FP64_FACTOR or 0 */
+} godec_grebsmo_params;
+
+/*
+ * Create a GreBsmo context on X.
+ *   X     : device, m x ldx float32, BORROWED (unchanged until godec_destroy)
+ *   Omega : device, the random test matrices of the increments, BORROWED: stage s
+ *           (s = 0 for the first V, then one per increment; at most
+ *           1 + ceil((r_max - dr) / dr) stages) is the n x p row-major block at
+ *           Omega + s n p, p = dr + oversample.
+ * The context is a godec_ctx: after godec_grebsmo_run use godec_get_L (L = U diag(sigma)
+ * V^T in the same orthonormal factored form as GoDec's), godec_get_L_dense, godec_get_S
+ * (the support of S and its values), godec_residual, godec_get_info (iter = inner steps
+ * run, rel_err of the last one) and godec_destroy.  godec_iterate, godec_solve and
+ * godec_profile return GODEC_ERR_STATE on it.  Errors as godec_init.
+ */
+godec_status godec_grebsmo_init(godec_ctx** ctx, const godec_grebsmo_params* params, const float* X,
+                                const float* Omega, void* stream);
+
+/*
+ * Run GreBsmo from U = 0, S = 0 to its stop (error <= tau or rank r_max).
+ *   r_out     : host, receives the final rank
+ *   stage_err : host array of cap entries (nullable): the relative error after each
+ *               rank stage, in order; n_stages (host, nullable) receives their number
+ * Synchronises the stream (the host tests the error after every stage).
+ */
+godec_status godec_grebsmo_run(godec_ctx* ctx, int32_t* r_out, double* stage_err, int32_t cap,
+                               int32_t* n_stages);
+
+/*
  * Batched form: count independent GoDec-BRP problems (Algorithm 1 on each) of uneven
  * m, n and r, advanced together.  One batch iteration is one launch of one CUDA graph
  * that holds an iteration of every problem as a parallel branch, all on the exact-

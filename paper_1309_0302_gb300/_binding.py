@@ -34,6 +34,12 @@ class GodecInfo(C.Structure):
                 ("svd_sweeps", C.c_int32), ("chol_shifts", C.c_int32)]
 
 
+class GrebsmoParams(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("ldx", C.c_int64), ("lambda", C.c_double),
+                ("tau", C.c_double), ("s_cap", C.c_int64), ("dr", C.c_int32), ("K", C.c_int32),
+                ("r_max", C.c_int32), ("oversample", C.c_int32), ("q_inc", C.c_int32), ("flags", C.c_int32)]
+
+
 class GodecError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: status {status}: {msg}")
@@ -79,6 +85,8 @@ def _declare(lib):
         "godec_batch_last_error": ([_P], C.c_char_p),
         "godec_batch_budgets": ([C.c_int32, i64p, i64p, C.c_int32, C.c_int32, i32p], C.c_int),
         "godec_tc_geometry": ([C.c_int64, C.c_int64, C.c_int32, i64p], C.c_int),
+        "godec_grebsmo_init": ([C.POINTER(_P), C.POINTER(GrebsmoParams), _P, _P, _P], C.c_int),
+        "godec_grebsmo_run": ([_P, i32p, f64p, C.c_int32, i32p], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -251,6 +259,60 @@ class GoDec:
         R = torch.empty((m, n), dtype=torch.float32, device=self._X.device)
         _check(library().godec_residual(self._h, _ptr(R), n), "godec_residual", self._h)
         return R
+
+
+class GreBsmo(GoDec):
+    """GreBsmo (Sec. 3.2.1, Algorithm 2) on the GPU: X = U V + S + G with a soft-thresholded S
+    and a rank found by greedy increments.
+
+    X: CUDA float32 (m, n), borrowed.  omegas: CUDA float32 (stages, n, dr + oversample), the
+    test matrices of the random-projection increments (the first gives the initial V).
+    run() returns (rank, errors after each rank stage); then L(), L_dense(), S(), residual()
+    and info() read the result as for GoDec.
+    """
+
+    def __init__(self, X, omegas, lam: float, dr: int, K: int, tau: float, r_max: int,
+                 oversample: int = 6, q_inc: int = 4, s_cap: int = 0, flags: int = 0, stream=None):
+        torch = _torch()
+        lib = library()
+        if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
+            raise ValueError("X must be a 2-D CUDA float32 tensor")
+        m, n = X.shape
+        if X.stride(1) != 1 or X.stride(0) % 4 or X.stride(0) < n or X.data_ptr() % 16:
+            Xp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+            Xp[:, :n] = X
+            X = Xp
+        p_cols = int(dr) + int(oversample)
+        if omegas.dim() != 3 or omegas.shape[1] != n or omegas.shape[2] != p_cols:
+            raise ValueError("omegas must be (stages, n, dr + oversample)")
+        self._X = X
+        self._omegas = omegas.contiguous().to(torch.float32)
+        self.m, self.n, self.r = m, n, int(r_max)
+        self.stream = stream
+        self._stages = int(omegas.shape[0])
+        p = GrebsmoParams(**{"m": m, "n": n, "ldx": X.stride(0), "lambda": float(lam), "tau": float(tau),
+                             "s_cap": int(s_cap if s_cap > 0 else max(1, m * n // 20)), "dr": int(dr),
+                             "K": int(K), "r_max": int(r_max), "oversample": int(oversample),
+                             "q_inc": int(q_inc), "flags": int(flags)})
+        need = 1 + -(-(int(r_max) - int(dr)) // int(dr))
+        if self._stages < need:
+            raise ValueError(f"omegas needs {need} stages")
+        h = C.c_void_p()
+        st = lib.godec_grebsmo_init(C.byref(h), C.byref(p), _ptr(X), _ptr(self._omegas), _stream_ptr(stream))
+        _check(st, "godec_grebsmo_init", None)
+        self._h = h
+
+    def run(self):
+        """Run to the stop; returns (rank, list of the relative errors after each stage)."""
+        r = C.c_int32(0)
+        ns = C.c_int32(0)
+        errs = (C.c_double * max(self._stages, 1))()
+        _check(library().godec_grebsmo_run(self._h, C.byref(r), errs, self._stages, C.byref(ns)),
+               "godec_grebsmo_run", self._h)
+        return r.value, [errs[i] for i in range(min(ns.value, self._stages))]
+
+    def iterate(self, n_iter: int = 1):
+        raise RuntimeError("GreBsmo runs through run()")
 
 
 def _mul(name, Z, B, stream=None):

@@ -125,6 +125,10 @@ struct godec_ctx {
   std::vector<int> prof_cls;
   std::vector<int> prof_side;   // launch on the side stream
   size_t prof_used = 0;
+  // GreBsmo (godec_grebsmo_*): parameters, the borrowed test matrices of the increments
+  bool greb = false;
+  godec_grebsmo_params gp{};
+  const float* omega = nullptr;
   char err[200] = {0};
 };
 
@@ -828,21 +832,14 @@ void godec_destroy(godec_ctx* c) {
   delete c;
 }
 
-godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, const float* A1,
-                        void* stream) {
-  if (!out) return GODEC_ERR_ARG;
-  *out = nullptr;
-  char why[200];
-  if (bad_params(p, why, sizeof(why))) {
-    snprintf(g_static_err, sizeof(g_static_err), "godec_init: %s", why);
-    return GODEC_ERR_ARG;
-  }
-  if (!X || !A1 || (reinterpret_cast<uintptr_t>(X) & 15)) {
-    snprintf(g_static_err, sizeof(g_static_err), "godec_init: X must be a 16-byte aligned device pointer, A1 non-NULL");
-    return GODEC_ERR_ARG;
-  }
+// Context set-up shared by GoDec (godec_init) and GreBsmo (godec_grebsmo_init, greb: the
+// correction scratch of the precision form and the second skinny-operand maps are also
+// allocated, A1 may be NULL).
+static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float* X, const float* A1,
+                             void* stream, bool greb) {
   godec_ctx* c = new (std::nothrow) godec_ctx;
   if (!c) return GODEC_ERR_OOM;
+  c->greb = greb;
   c->p = *p;
   c->r = p->r;
   c->RP = round_up(p->r, 8);
@@ -883,9 +880,11 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   CKI(dalloc(&c->Z, (size_t)m * c->ldz));
   CKI(dalloc(&c->Zt, (size_t)n * c->ldzt));
   if (p->precision == GODEC_PREC_BF16_REFINE) {
-    const size_t W = 64;   // columns of the correction's [U | A] and [V | B] (2r <= 64)
     CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Z16), (size_t)m * c->ldz));
     CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Zt16), (size_t)n * c->ldzt));
+  }
+  if (p->precision == GODEC_PREC_BF16_REFINE || greb) {
+    const size_t W = 64;   // columns of the correction's [U | A] and [V | B] (2r <= 64)
     CKI(dalloc(&c->RA, (size_t)m * RP));
     CKI(dalloc(&c->RB, (size_t)n * RP));
     CKI(dalloc(&c->Wa, (size_t)m * W));
@@ -952,10 +951,11 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
                     make_tmap_f16(c->tmap[4], bt2(c, 2), 2 * RP, n, c->ldb, 2 * RP);
     const bool ok16 = !c->Z16 ||
                       (make_tmap_f16(c->tmap[8], c->Z16, m, n, c->ldz, 128) &&
-                       make_tmap_f16(c->tmap[9], c->Zt16, n, m, c->ldzt, 128) &&
-                       make_tmap_f16(c->tmap[13], bt2(c, 3), 2 * RP, n, c->ldb, 2 * RP) &&
-                       make_tmap_f16(c->tmap[14], bt2(c, 3), 2 * RP, m, c->ldb, 2 * RP));
-    if (!ok || !ok16) {
+                       make_tmap_f16(c->tmap[9], c->Zt16, n, m, c->ldzt, 128));
+    const bool ok3 = !(c->Z16 || greb) ||
+                     (make_tmap_f16(c->tmap[13], bt2(c, 3), 2 * RP, n, c->ldb, 2 * RP) &&
+                      make_tmap_f16(c->tmap[14], bt2(c, 3), 2 * RP, m, c->ldb, 2 * RP));
+    if (!ok || !ok16 || !ok3) {
       fail(c, GODEC_ERR_CUDA, "tensor map encoding failed");
       return bail(GODEC_ERR_CUDA);
     }
@@ -986,13 +986,30 @@ godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, 
   while ((1ull << c->idx_bits) < mn) ++c->idx_bits;
   launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), c->st);
   launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), c->st);
-  launch_pad_copy(A1, n, p->r, p->r, c->A1_orig, RP, c->st);
+  if (A1) launch_pad_copy(A1, n, p->r, p->r, c->A1_orig, RP, c->st);
+  else launch_fill_zero(c->A1_orig, (size_t)n * RP * sizeof(float), c->st);
   CKI(cudaGetLastError());
   godec_status s = reset_state(c);
   if (s) return bail(s);
   *out = c;
   return GODEC_OK;
 #undef CKI
+}
+
+godec_status godec_init(godec_ctx** out, const godec_params* p, const float* X, const float* A1,
+                        void* stream) {
+  if (!out) return GODEC_ERR_ARG;
+  *out = nullptr;
+  char why[200];
+  if (bad_params(p, why, sizeof(why))) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_init: %s", why);
+    return GODEC_ERR_ARG;
+  }
+  if (!X || !A1 || (reinterpret_cast<uintptr_t>(X) & 15)) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_init: X must be a 16-byte aligned device pointer, A1 non-NULL");
+    return GODEC_ERR_ARG;
+  }
+  return init_ctx(out, p, X, A1, stream, false);
 }
 
 godec_status godec_reset(godec_ctx* c) {
@@ -1002,6 +1019,7 @@ godec_status godec_reset(godec_ctx* c) {
 
 godec_status godec_iterate(godec_ctx* c, int32_t n_iter, double* rel_err) {
   if (!c) return GODEC_ERR_ARG;
+  if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
   if (n_iter < 0) return fail(c, GODEC_ERR_ARG, "n_iter must be >= 0");
   godec_status s = run_iterations(c, n_iter, -1.0);
   if (s) return s;
@@ -1015,6 +1033,7 @@ godec_status godec_iterate(godec_ctx* c, int32_t n_iter, double* rel_err) {
 
 godec_status godec_solve(godec_ctx* c, int32_t* iters, double* rel_err) {
   if (!c) return GODEC_ERR_ARG;
+  if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
   Ctl h;
   godec_status s = read_ctl(c, &h);
   if (s) return s;
@@ -1036,6 +1055,7 @@ godec_status godec_solve(godec_ctx* c, int32_t* iters, double* rel_err) {
 godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* launches,
                            double* bytes_product) {
   if (!c || n_iter < 0) return GODEC_ERR_ARG;
+  if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
   for (int k = 0; k < GODEC_PROF_CLASSES; ++k) {
     if (ms) ms[k] = 0.0;
     if (launches) launches[k] = 0;
@@ -1436,6 +1456,314 @@ godec_status godec_mul_ZB(const float* Z, int64_t m, int64_t n, int64_t ldz, con
 godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz, const float* C, int32_t r,
                            float* W, void* stream) {
   return mul_common(Z, m, n, ldz, C, r, W, stream, 1);
+}
+
+// ---- GreBsmo (Sec. 3.2.1, Algorithm 2) --------------------------------------------------
+// The context's buffers take these roles: V holds the unit-column V^T (n x RP) that the
+// next product reads, Q1 the orthonormal U (m x RP), Q2 W = Z^T U (n x RP, so that
+// L = U W^T), sigma the column norms of W; A1, Qa, Qb, P are work space of the increments.
+// Columns at and beyond the current rank are zero everywhere.
+
+// Product over Z (even: m rows, K = n) or Z^T (odd: n rows, K = m) with the operand of
+// tensor map map_b, its column scales cscale, Gram partials into slot gslot (gram_mode 1).
+static void greb_prod(godec_ctx* c, bool even, int map_b, const float* cscale, float* out, int gram_mode, int gslot) {
+  TcLaunch l{};
+  l.mapA = c->tmap[even ? 0 : 1];
+  l.mapB = c->tmap[map_b];
+  l.rows = even ? c->p.m : c->p.n;
+  l.K = even ? c->p.n : c->p.m;
+  l.RP = c->RP;
+  l.geom = c->tg[even ? 0 : 1];
+  l.part = c->part;
+  l.counters = c->counters;
+  l.out = out;
+  l.ldb = c->ldb;
+  l.cscale = cscale;
+  l.zscale = c->ctl->zscale;
+  l.prescaled = 1;
+  l.gram_part = gpart(c, gslot);
+  l.gram_mode = gram_mode;
+  l.t_upper = 1;
+  l.pend = c->pend;
+  l.ctl = c->ctl;
+  launch_prod_tc(l, c->st);
+}
+
+// out (m x RP) = D B with D = Z - U W^T (the derivative of eq. GreBsmoD; U = 0 at rank 0);
+// B (n x RP) has p nonzero columns.
+static void greb_apply_D(godec_ctx* c, int ri, int p, const float* B, float* out) {
+  const int RP = c->RP;
+  launch_split_t(B, c->p.n, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
+  greb_prod(c, true, 13, c->cs_ref, out, 0, 0);
+  if (ri > 0) {
+    launch_cross_gram(c->Q2, RP, ri, B, RP, p, c->p.n, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
+    launch_tall_small_d(c->Q1, RP, ri, c->rf_C, RP, 0, p, c->p.m, -1.f, 1.f, out, RP, c->st);
+  }
+}
+
+// out (n x RP) = D^T Y for Y (m x RP) with p nonzero columns.
+static void greb_apply_Dt(godec_ctx* c, int ri, int p, const float* Y, float* out) {
+  const int RP = c->RP;
+  launch_split_t(Y, c->p.m, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
+  greb_prod(c, false, 14, c->cs_ref, out, 0, 0);
+  if (ri > 0) {
+    launch_cross_gram(c->Q1, RP, ri, Y, RP, p, c->p.m, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
+    launch_tall_small_d(c->Q2, RP, ri, c->rf_C, RP, 0, p, c->p.n, -1.f, 1.f, out, RP, c->st);
+  }
+}
+
+// The random-projection increment: `add` new unit rows of V (columns ri .. ri+add-1 of
+// c->V), the top right singular vectors of D from test matrix Omega_stage.
+static void greb_increment(godec_ctx* c, int ri, int add, int stage) {
+  const int RP = c->RP, p = c->gp.dr + c->gp.oversample;
+  const int64_t m = c->p.m, n = c->p.n;
+  cudaStream_t st = c->st;
+  const size_t q = (size_t)64 * 64;
+  float *R1 = c->Rf, *T1 = R1 + q, *R2m = T1 + q, *T2 = R2m + q;
+  launch_fill_zero(c->A1, (size_t)n * RP * sizeof(float), st);
+  launch_pad_copy(c->omega + (size_t)stage * n * p, n, p, p, c->A1, RP, st);
+  cqr2(c, c->A1, n, p, RP, c->Qb, R1, T1, R2m, T2);                 // B = orth(Omega)
+  for (int s = 0; s < c->gp.q_inc; ++s) {
+    greb_apply_D(c, ri, p, c->Qb, c->P);
+    cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);                // orth(D B)
+    greb_apply_Dt(c, ri, p, c->Qa, c->P);
+    cqr2(c, c->P, n, p, RP, c->Qb, R1, T1, R2m, T2);                // B = orth(D^T orth(D B))
+  }
+  greb_apply_D(c, ri, p, c->Qb, c->P);                               // Y = D B = Qa R2m R1
+  cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);
+  launch_rmul(R2m, R1, RP, p, c->rf_core, 0, nullptr, st);
+  launch_svd_small(c->rf_core, p, add, c->rf_U, c->cs_ref + 0, c->rf_V, st);   // right vectors of Y
+  launch_tall_small_d(c->Qb, RP, p, c->rf_V, add, 0, add, n, 1.f, 0.f, c->V + ri, RP, st);
+}
+
+// The factor updates of one inner step of eq. GreBsmoA at rank ri: U = orth(Z V^T),
+// W = Z^T U (V = W^T), kept as sigma (column norms of W) and its unit columns.
+static void greb_lstep(godec_ctx* c, int ri) {
+  const int RP = c->RP;
+  const int64_t m = c->p.m, n = c->p.n;
+  const size_t rr = (size_t)RP * RP;
+  cudaStream_t st = c->st;
+  launch_split_t(c->V, n, RP, bt2(c, 2), c->ldb, c->cs, st);
+  greb_prod(c, true, 4, c->cs, c->P, 1, 0);
+  gram_sum(c, gpart(c, 0), 0, prod_tiles(m), g64(c, 0), st);
+  final_cqr2(c, m, g64(c, 0), c->Rfin, c->Rfin + 2 * rr, c->Q1, g64(c, 2), bt2(c, 0));
+  greb_prod(c, false, 2, c->cs + RP, c->Q2, 1, 1);
+  gram_sum(c, gpart(c, 1), 0, prod_tiles(n), g64(c, 1), st);
+  launch_colnorm(c->Q2, g64(c, 1), n, RP, ri, c->V, c->sigma, c->nsm, st);
+}
+
+// The S-step of the inner step: S = S_lambda(X - U W^T) (eq. softt) and the sparse update
+// of Z = X - S.  L = U diag(sigma) V^T with V the unit columns of W.
+static void greb_sstep(godec_ctx* c, int ri, unsigned guess) {
+  const int RP = c->RP;
+  const int64_t m = c->p.m, n = c->p.n;
+  cudaStream_t st = c->st;
+  launch_reset_iter(c->ctl, st);
+  launch_soft_plan(c->ctl, guess, st);
+  launch_lsplit(c->Q1, c->V, c->sigma, m, n, RP, ri, c->ctl->zscale, c->LA, c->LB, st);
+  ResidTcLaunch rl{};
+  rl.ra.X = c->X;
+  rl.ra.m = m;
+  rl.ra.n = n;
+  rl.ra.ldx = c->p.ldx;
+  rl.ra.r = ri;
+  rl.ra.RP = RP;
+  rl.ra.pass = 0;
+  rl.ra.ctl = c->ctl;
+  rl.ra.cand_key = c->cand_key;
+  rl.ra.cand_idx = c->cand_idx;
+  rl.ra.cand_val = c->cand_val;
+  rl.ra.cand_cap = c->cap;
+  rl.mapX = c->tmap[5];
+  rl.mapA = c->tmap[6];
+  rl.mapB = c->tmap[7];
+  rl.zscale = c->ctl->zscale;
+  rl.nsm = c->nsm;
+  launch_resid_tc(rl, st);
+  SoftEmitArgs se{};
+  se.ctl = c->ctl;
+  se.cand_idx = c->cand_idx;
+  se.cand_val = c->cand_val;
+  se.cand_cap = c->cap;
+  se.s_cap = c->p.k;
+  for (int b = 0; b < 2; ++b) {
+    se.S_idx[b] = c->S_idx[b];
+    se.S_val[b] = c->S_val[b];
+  }
+  se.sbits = c->sbits;
+  se.lambda = (float)c->gp.lambda;
+  launch_emit_soft(se, c->nsm, st);
+  EmitArgs ea{};
+  ea.ctl = c->ctl;
+  ea.S_idx[0] = c->S_idx[0];
+  ea.S_idx[1] = c->S_idx[1];
+  ea.S_val[0] = c->S_val[0];
+  ea.S_val[1] = c->S_val[1];
+  ea.X = c->X;
+  ea.n = n;
+  ea.ldx = c->p.ldx;
+  ea.Z = c->Z;
+  ea.ldz = c->ldz;
+  ea.Zt = c->Zt;
+  ea.ldzt = c->ldzt;
+  ea.zscale = c->ctl->zscale;
+  ea.max_nnz = c->p.k;
+  ea.sbits = c->sbits;
+  launch_z_update(ea, c->nsm, st);
+}
+
+// Grow the S and candidate buffers to hold `need` entries (keeping the committed S).
+static godec_status greb_grow(godec_ctx* c, const Ctl& h, unsigned long long need) {
+  unsigned long long cap = std::max<unsigned long long>(2 * c->cap, need + 65536ull);
+  const unsigned long long mn = (unsigned long long)(c->p.m * c->p.n);
+  if (cap > mn) cap = mn;
+  if (godec_status s = alloc_candidates(c, cap)) return s;
+  const long long k = (long long)std::min<unsigned long long>(mn, std::max<unsigned long long>(2 * (unsigned long long)c->p.k, need + 65536ull));
+  for (int b = 0; b < 2; ++b) {
+    long long* ni = nullptr;
+    float* nv = nullptr;
+    CK(dalloc(&ni, (size_t)k));
+    CK(dalloc(&nv, (size_t)k));
+    if (b == h.cur && h.nnz_cur > 0) {
+      CK(cudaMemcpyAsync(ni, c->S_idx[b], (size_t)h.nnz_cur * sizeof(long long), cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(nv, c->S_val[b], (size_t)h.nnz_cur * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(c->S_idx[b]);
+    cudaFree(c->S_val[b]);
+    c->S_idx[b] = ni;
+    c->S_val[b] = nv;
+  }
+  c->p.k = k;
+  return GODEC_OK;
+}
+
+godec_status godec_grebsmo_init(godec_ctx** out, const godec_grebsmo_params* gp, const float* X,
+                                const float* Omega, void* stream) {
+  if (!out) return GODEC_ERR_ARG;
+  *out = nullptr;
+  const char* why = nullptr;
+  if (!gp) why = "params is NULL";
+  else if (gp->m < 1 || gp->n < 1 || (double)gp->m * (double)gp->n >= 4294967296.0) why = "need m, n >= 1, m*n < 2^32";
+  else if (gp->ldx < gp->n || (gp->ldx * 4) % 16) why = "ldx must be >= n and ldx*4 a multiple of 16";
+  else if (!(gp->lambda > 0.0) || !std::isfinite(gp->lambda)) why = "lambda must be finite and > 0";
+  else if (gp->dr < 1 || gp->K < 1) why = "dr and K must be >= 1";
+  else if (gp->r_max < gp->dr || gp->r_max > GODEC_MAX_RANK || gp->r_max > gp->m || gp->r_max > gp->n)
+    why = "need dr <= r_max <= min(m, n, GODEC_MAX_RANK)";
+  else if (gp->oversample < 0 || gp->dr + gp->oversample > GODEC_MAX_RANK || gp->dr + gp->oversample > gp->m ||
+           gp->dr + gp->oversample > gp->n)
+    why = "need dr + oversample <= min(m, n, GODEC_MAX_RANK)";
+  else if (gp->q_inc < 0 || gp->q_inc > 16) why = "q_inc must be in [0, 16]";
+  else if (gp->s_cap < 0) why = "s_cap must be >= 0";
+  else if (gp->flags & ~GODEC_FLAG_FP64_FACTOR) why = "unknown flags";
+  else if (!X || !Omega || (reinterpret_cast<uintptr_t>(X) & 15)) why = "X (16-byte aligned) and Omega must be device pointers";
+  if (why) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_grebsmo_init: %s", why);
+    return GODEC_ERR_ARG;
+  }
+  godec_params p{};
+  p.m = gp->m;
+  p.n = gp->n;
+  p.ldx = gp->ldx;
+  p.r = std::max(gp->r_max, gp->dr + gp->oversample);
+  p.q = 0;
+  p.k = std::min<int64_t>(std::max<int64_t>(gp->s_cap, 1), gp->m * gp->n);
+  p.tol = -1.0;
+  p.max_iter = 1;
+  p.precision = GODEC_PREC_FP32;
+  p.flags = gp->flags;
+  godec_status s = init_ctx(out, &p, X, nullptr, stream, true);
+  if (s) return s;
+  (*out)->gp = *gp;
+  (*out)->omega = Omega;
+  return GODEC_OK;
+}
+
+godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, int32_t cap, int32_t* n_stages) {
+  if (!c || !c->greb) {
+    if (c) fail(c, GODEC_ERR_STATE, "godec_grebsmo_run needs a context from godec_grebsmo_init");
+    return c ? GODEC_ERR_STATE : GODEC_ERR_ARG;
+  }
+  godec_status s = reset_state(c);
+  if (s) return s;
+  const int64_t m = c->p.m, n = c->p.n;
+  const int RP = c->RP;
+  const size_t rr = (size_t)RP * RP;
+  cudaStream_t st = c->st;
+  launch_fill_zero(c->V, (size_t)n * RP * sizeof(float), st);
+  launch_fill_zero(c->Q2, (size_t)n * RP * sizeof(float), st);
+  launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), st);
+  launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), st);
+  launch_fill_zero(c->P, (size_t)std::max(m, n) * RP * sizeof(float), st);
+  launch_fill_zero(c->Qa, (size_t)m * 64 * sizeof(float), st);
+  launch_fill_zero(c->Qb, (size_t)n * 64 * sizeof(float), st);
+  // Reading of eq. softt on the GPU: S is nonzero where |R| > lambda, i.e. where the key
+  // (bits of |R|) exceeds that of (float) lambda.
+  const float lamf = (float)c->gp.lambda;
+  unsigned guess;
+  memcpy(&guess, &lamf, sizeof(guess));
+  guess += 1u;
+  int ri = std::min(c->gp.dr, c->gp.r_max), stage = 0, nst = 0;
+  c->r = ri;
+  greb_increment(c, 0, ri, 0);   // Reading R18: the first V from X itself
+  CK(cudaGetLastError());
+  for (;;) {
+    c->r = ri;
+    for (int k = 0; k < c->gp.K; ++k) {
+      greb_lstep(c, ri);
+      for (int attempt = 0;; ++attempt) {
+        greb_sstep(c, ri, guess);
+        CK(cudaGetLastError());
+        Ctl h;
+        if ((s = read_ctl(c, &h))) return s;
+        if (h.timeout) return fail(c, GODEC_ERR_TIMEOUT, "a device-side wait of the tensor-core product timed out");
+        if (h.nonfinite) return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - U V");
+        if (h.abort && h.need_bigger_cand && attempt < 8) {
+          if ((s = clear_counters(c))) return s;
+          CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, st));
+          if ((s = greb_grow(c, h, h.cand_count))) return s;
+          continue;
+        }
+        if (h.abort) return fail(c, GODEC_ERR_STATE, "GreBsmo inner step aborted");
+        if (h.range_err) {
+          if ((s = rescale_z(c))) return s;
+          if ((s = SET_CTL(range_err, 0))) return s;
+        }
+        break;
+      }
+    }
+    Ctl h;
+    if ((s = read_ctl(c, &h))) return s;
+    if (stage_err && nst < cap) stage_err[nst] = h.rel_err;
+    ++nst;
+    if (h.rel_err <= c->gp.tau || ri >= c->gp.r_max) break;   // Reading R17
+    const int add = std::min(c->gp.dr, c->gp.r_max - ri);
+    ++stage;
+    c->r = ri;
+    greb_increment(c, ri, add, stage);
+    ri += add;
+  }
+  // the factored form of L = U W^T = U diag(sigma) Vh^T: Vh = Qv Rv, M = diag(sigma) Rv^T
+  // = Ur S Vr^T, L = (U Ur) S (Qv Vr)^T
+  {
+    const size_t q = (size_t)64 * 64;
+    float *R1 = c->Rf, *T1 = R1 + q, *R2m = T1 + q, *T2 = R2m + q;
+    c->r = ri;
+    cqr2(c, c->V, n, ri, RP, c->Qb, R1, T1, R2m, T2);
+    launch_rmul(R2m, R1, RP, ri, c->rf_core, 1, c->sigma, st);
+    launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), st);
+    launch_fill_zero(c->V, (size_t)n * RP * sizeof(float), st);
+    launch_fill_zero(c->sigma, (size_t)RP * sizeof(float), st);
+    launch_svd_small(c->rf_core, ri, ri, c->rf_U, c->sigma, c->rf_V, st);
+    launch_tall_small_d(c->Q1, RP, ri, c->rf_U, ri, 0, ri, m, 1.f, 0.f, c->U, RP, st);
+    launch_tall_small_d(c->Qb, RP, ri, c->rf_V, ri, 0, ri, n, 1.f, 0.f, c->V, RP, st);
+    (void)rr;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  if (r_out) *r_out = ri;
+  if (n_stages) *n_stages = nst;
+  return GODEC_OK;
 }
 
 }  // extern "C"

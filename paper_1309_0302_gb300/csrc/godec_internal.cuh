@@ -311,6 +311,29 @@ void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, co
                         const double* C, int r, double* core, cudaStream_t st);
 void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st);
 
+// GreBsmo (k_grebsmo.cu): the S-step's plan (one candidate pass at the key of lambda + 1
+// ulp), the soft-threshold emit S = R - lambda sgn R over every candidate, column norms
+// from a Gram, and a small float64 product of two r x r factors.
+struct SoftEmitArgs {
+  Ctl* ctl;
+  const long long* cand_idx;
+  const float* cand_val;
+  unsigned long long cand_cap;
+  long long s_cap;         // entries the S buffers hold
+  long long* S_idx[2];
+  float* S_val[2];
+  unsigned* sbits;
+  float lambda;
+};
+void launch_soft_plan(Ctl* ctl, unsigned guess, cudaStream_t st);
+void launch_emit_soft(const SoftEmitArgs& a, int nsm, cudaStream_t st);
+void launch_colnorm(const float* W, const double* g64, int64_t n, int RP, int r, float* Vh, float* sigma, int nsm,
+                    cudaStream_t st);
+// out (r x r, float64) = A B (A, B float32, stride ld), transposed with trans, then row i
+// scaled by rowscale[i] (nullable).
+void launch_rmul(const float* A, const float* B, int ld, int r, double* out, int trans, const float* rowscale,
+                 cudaStream_t st);
+
 // L (m x n, row stride ldl) = U diag(sigma) V^T, U m x r (ldu), V n x r (ldv) (k_dense.cu).
 void launch_lowrank_dense(const float* U, int64_t ldu, const float* sigma, const float* V, int64_t ldv, int64_t m,
                           int64_t n, int r, float* L, int64_t ldl, cudaStream_t st);

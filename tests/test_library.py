@@ -71,11 +71,12 @@ def _header_struct(name):
 
 
 def test_binding_structs_match_the_header():
-    """GodecParams and GodecInfo have the header's fields, in order, with the same widths
+    """GodecParams, GodecInfo and GrebsmoParams have the header's fields, in order, with the same widths
     (a drift would shift every later field)."""
     import ctypes as C
     width = {"int32_t": 4, "int64_t": 8, "double": 8}
-    for hname, cls in (("godec_params", g._binding.GodecParams), ("godec_info", g._binding.GodecInfo)):
+    for hname, cls in (("godec_params", g._binding.GodecParams), ("godec_info", g._binding.GodecInfo),
+                       ("godec_grebsmo_params", g._binding.GrebsmoParams)):
         fields = _header_struct(hname)
         assert [f for _, f in fields] == [f for f, _ in cls._fields_], hname
         assert [width[t] for t, _ in fields] == [C.sizeof(t) for _, t in cls._fields_], hname
