@@ -331,6 +331,26 @@ godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t n, int64_t 
                                   const float* B, int32_t r, float* Y, void* stream);
 
 /*
+ * Naive GoDec (Sec. 2.1, eq. raw_lss): the L-step is the rank-r truncated SVD of
+ * Z = X - S itself instead of BRP; the S-step is the same exact top-k as Algorithm 1's.
+ * The truncated SVD runs as a block subspace iteration over p = godec_naive_columns(m, n,
+ * r) columns (r plus up to 8 oversampling columns): from the basis B the previous
+ * iteration ended with (orth(Omega) in the first), q times B = orth(Z^T orth(Z B)), then
+ * the Rayleigh-Ritz step (Z B = Q R, SVD of the p x p R in float64, the leading r
+ * triplets).  It converges to the exact truncated SVD at the rate
+ * (sigma_{p+1} / sigma_r)^(2q) per iteration and, being warm-started, keeps converging
+ * across iterations.
+ *   params : as godec_init, with q = power steps per L-step (1..8) and precision
+ *            GODEC_PREC_FP32; there is no rank test (r stays fixed)
+ *   Omega  : device, n x p float32 row-major, the first test matrix (copied)
+ * The context runs with godec_iterate / godec_solve and the getters as a GoDec context
+ * (godec_profile returns GODEC_ERR_STATE).  Errors as godec_init.
+ */
+int godec_naive_columns(int64_t m, int64_t n, int32_t r);
+godec_status godec_naive_init(godec_ctx** ctx, const godec_params* params, const float* X, const float* Omega,
+                              void* stream);
+
+/*
  * GreBsmo, greedy bilateral smoothing (Sec. 3.2.1, Algorithm 2): X = U V + S + G with U
  * orthonormal (m x r), V (r x n) and S from the element-wise soft threshold (eq. softt).
  * Each inner step (eq. GreBsmoA), with Z = X - S:

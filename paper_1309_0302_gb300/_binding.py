@@ -86,6 +86,8 @@ def _declare(lib):
         "godec_batch_budgets": ([C.c_int32, i64p, i64p, C.c_int32, C.c_int32, i32p], C.c_int),
         "godec_tc_geometry": ([C.c_int64, C.c_int64, C.c_int32, i64p], C.c_int),
         "godec_grebsmo_init": ([C.POINTER(_P), C.POINTER(GrebsmoParams), _P, _P, _P], C.c_int),
+        "godec_naive_init": ([C.POINTER(_P), C.POINTER(GodecParams), _P, _P, _P], C.c_int),
+        "godec_naive_columns": ([C.c_int64, C.c_int64, C.c_int32], C.c_int),
         "godec_grebsmo_run": ([_P, i32p, f64p, C.c_int32, i32p], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -259,6 +261,43 @@ class GoDec:
         R = torch.empty((m, n), dtype=torch.float32, device=self._X.device)
         _check(library().godec_residual(self._h, _ptr(R), n), "godec_residual", self._h)
         return R
+
+
+def naive_columns(m: int, n: int, r: int) -> int:
+    """Columns p of naive GoDec's subspace iteration (r plus up to 8 oversampling columns)."""
+    return int(library().godec_naive_columns(int(m), int(n), int(r)))
+
+
+class NaiveGoDec(GoDec):
+    """Naive GoDec (Sec. 2.1, eq. raw_lss) on the GPU: the L-step is the rank-r truncated SVD of
+    X - S by warm-started block subspace iteration (q power steps per iteration), the S-step
+    the exact top-k.  omega: CUDA float32 (n, naive_columns(m, n, r)), the first test matrix.
+    iterate(), solve(), L(), S() and info() as for GoDec."""
+
+    def __init__(self, X, omega, r: int, k: int, q: int = 2, tol: float = 1e-7, max_iter: int = 50,
+                 stream=None, flags: int = 0):
+        torch = _torch()
+        lib = library()
+        if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
+            raise ValueError("X must be a 2-D CUDA float32 tensor")
+        m, n = X.shape
+        if X.stride(1) != 1 or X.stride(0) % 4 or X.stride(0) < n or X.data_ptr() % 16:
+            Xp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+            Xp[:, :n] = X
+            X = Xp
+        p_cols = naive_columns(m, n, r)
+        if tuple(omega.shape) != (n, p_cols):
+            raise ValueError(f"omega must be ({n}, {p_cols})")
+        self._X = X
+        self._A1 = omega.contiguous().to(torch.float32)
+        self.m, self.n, self.r, self.k, self.q = m, n, int(r), int(k), int(q)
+        self.stream = stream
+        p = GodecParams(m=m, n=n, ldx=X.stride(0), r=int(r), q=int(q), k=int(k), tol=float(tol),
+                        max_iter=int(max_iter), precision=PREC_FP32, rank_tol=0.0, flags=int(flags), reserved=0)
+        h = C.c_void_p()
+        st = lib.godec_naive_init(C.byref(h), C.byref(p), _ptr(X), _ptr(self._A1), _stream_ptr(stream))
+        _check(st, "godec_naive_init", None)
+        self._h = h
 
 
 class GreBsmo(GoDec):

@@ -129,6 +129,10 @@ struct godec_ctx {
   bool greb = false;
   godec_grebsmo_params gp{};
   const float* omega = nullptr;
+  // naive GoDec (godec_naive_init): the L-step is a truncated SVD by subspace iteration
+  // over np_cols columns (rank + oversampling), warm-started from the last iteration's basis
+  bool naive = false;
+  int np_cols = 0;
   char err[200] = {0};
 };
 
@@ -564,7 +568,85 @@ void enqueue_sstep(godec_ctx* c, int r) {
   if (c->Z) PROF(c, 9, st, launch_z_update(ea, c->nsm, st));
 }
 
+// Product over Z (even: m rows, K = n) or Z^T (odd: n rows, K = m) with the operand of
+// tensor map map_b, its column scales cscale, Gram partials into slot gslot (gram_mode 1).
+void greb_prod(godec_ctx* c, bool even, int map_b, const float* cscale, float* out, int gram_mode, int gslot) {
+  TcLaunch l{};
+  l.mapA = c->tmap[even ? 0 : 1];
+  l.mapB = c->tmap[map_b];
+  l.rows = even ? c->p.m : c->p.n;
+  l.K = even ? c->p.n : c->p.m;
+  l.RP = c->RP;
+  l.geom = c->tg[even ? 0 : 1];
+  l.part = c->part;
+  l.counters = c->counters;
+  l.out = out;
+  l.ldb = c->ldb;
+  l.cscale = cscale;
+  l.zscale = c->ctl->zscale;
+  l.prescaled = 1;
+  l.gram_part = gpart(c, gslot);
+  l.gram_mode = gram_mode;
+  l.t_upper = 1;
+  l.pend = c->pend;
+  l.ctl = c->ctl;
+  launch_prod_tc(l, c->st);
+}
+
+// out (m x RP) = D B with D = Z - U W^T (the derivative of eq. GreBsmoD; U = 0 at rank 0);
+// B (n x RP) has p nonzero columns.
+void greb_apply_D(godec_ctx* c, int ri, int p, const float* B, float* out) {
+  const int RP = c->RP;
+  launch_split_t(B, c->p.n, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
+  greb_prod(c, true, 13, c->cs_ref, out, 0, 0);
+  if (ri > 0) {
+    launch_cross_gram(c->Q2, RP, ri, B, RP, p, c->p.n, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
+    launch_tall_small_d(c->Q1, RP, ri, c->rf_C, RP, 0, p, c->p.m, -1.f, 1.f, out, RP, c->st);
+  }
+}
+
+// out (n x RP) = D^T Y for Y (m x RP) with p nonzero columns.
+void greb_apply_Dt(godec_ctx* c, int ri, int p, const float* Y, float* out) {
+  const int RP = c->RP;
+  launch_split_t(Y, c->p.m, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
+  greb_prod(c, false, 14, c->cs_ref, out, 0, 0);
+  if (ri > 0) {
+    launch_cross_gram(c->Q1, RP, ri, Y, RP, p, c->p.m, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
+    launch_tall_small_d(c->Q2, RP, ri, c->rf_C, RP, 0, p, c->p.n, -1.f, 1.f, out, RP, c->st);
+  }
+}
+
+// L-step of naive GoDec (eq. raw_lss: L = the rank-r truncated SVD of Z = X - S) by block
+// subspace iteration over np_cols = r + oversampling columns: from the basis B the last
+// iteration ended with, q times B = orth(Z^T orth(Z B)), then the Rayleigh-Ritz step
+// Z B = Qa R, R = Ur S Vr^T, L = (Qa Ur) S (B Vr)^T truncated to r (float64 SVD of R).
+void enqueue_naive_lstep(godec_ctx* c) {
+  const int RP = c->RP, p = c->np_cols, r = c->r;
+  const int64_t m = c->p.m, n = c->p.n;
+  cudaStream_t st = c->st;
+  const size_t q = (size_t)64 * 64;
+  float *R1 = c->Rf, *T1 = R1 + q, *R2m = T1 + q, *T2 = R2m + q;
+  for (int s = 0; s < c->p.q; ++s) {
+    greb_apply_D(c, 0, p, c->Qb, c->P);
+    cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);
+    greb_apply_Dt(c, 0, p, c->Qa, c->P);
+    cqr2(c, c->P, n, p, RP, c->Qb, R1, T1, R2m, T2);
+  }
+  greb_apply_D(c, 0, p, c->Qb, c->P);
+  cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);
+  launch_rmul(R2m, R1, RP, p, c->rf_core, 0, nullptr, st);
+  launch_svd_small(c->rf_core, p, r, c->rf_U, c->sigma, c->rf_V, st);
+  launch_tall_small_d(c->Qa, RP, p, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st);
+  launch_tall_small_d(c->Qb, RP, p, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st);
+  launch_lsplit(c->U, c->V, c->sigma, m, n, RP, r, c->ctl->zscale, c->LA, c->LB, st);
+}
+
 void enqueue_iteration(godec_ctx* c, bool fast) {
+  if (c->naive) {
+    enqueue_naive_lstep(c);
+    enqueue_sstep(c, c->r);
+    return;
+  }
   enqueue_lstep(c, fast);
   enqueue_sstep(c, c->r);
 }
@@ -656,6 +738,18 @@ godec_status reset_state(godec_ctx* c) {
   launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st, c->ctl->zscale);
   refresh_z16(c);
   launch_reset_iter(c->ctl, c->st);
+  if (c->naive) {
+    // the first subspace iteration starts from orth(Omega); later ones from the basis the
+    // previous iteration ended with
+    const size_t q = (size_t)64 * 64;
+    float *R1 = c->Rf, *T1 = R1 + q, *R2m = T1 + q, *T2 = R2m + q;
+    launch_fill_zero(c->Qb, (size_t)c->p.n * 64 * sizeof(float), c->st);
+    launch_fill_zero(c->Qa, (size_t)c->p.m * 64 * sizeof(float), c->st);
+    launch_fill_zero(c->U, (size_t)c->p.m * c->RP * sizeof(float), c->st);
+    launch_fill_zero(c->V, (size_t)c->p.n * c->RP * sizeof(float), c->st);
+    launch_fill_zero(c->sigma, (size_t)c->RP * sizeof(float), c->st);
+    cqr2(c, c->A1, c->p.n, c->np_cols, c->RP, c->Qb, R1, T1, R2m, T2);
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
   return GODEC_OK;
@@ -836,13 +930,15 @@ void godec_destroy(godec_ctx* c) {
 // correction scratch of the precision form and the second skinny-operand maps are also
 // allocated, A1 may be NULL).
 static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float* X, const float* A1,
-                             void* stream, bool greb) {
+                             void* stream, bool greb, int naive_cols = 0) {
   godec_ctx* c = new (std::nothrow) godec_ctx;
   if (!c) return GODEC_ERR_OOM;
   c->greb = greb;
+  c->naive = naive_cols > 0;
+  c->np_cols = naive_cols;
   c->p = *p;
   c->r = p->r;
-  c->RP = round_up(p->r, 8);
+  c->RP = round_up(std::max(p->r, naive_cols), 8);
   c->nprod = 6 * p->q + 3;
   c->st = reinterpret_cast<cudaStream_t>(stream);
   auto bail = [&](godec_status s) {
@@ -883,7 +979,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
     CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Z16), (size_t)m * c->ldz));
     CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Zt16), (size_t)n * c->ldzt));
   }
-  if (p->precision == GODEC_PREC_BF16_REFINE || greb) {
+  if (p->precision == GODEC_PREC_BF16_REFINE || greb || c->naive) {
     const size_t W = 64;   // columns of the correction's [U | A] and [V | B] (2r <= 64)
     CKI(dalloc(&c->RA, (size_t)m * RP));
     CKI(dalloc(&c->RB, (size_t)n * RP));
@@ -952,7 +1048,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
     const bool ok16 = !c->Z16 ||
                       (make_tmap_f16(c->tmap[8], c->Z16, m, n, c->ldz, 128) &&
                        make_tmap_f16(c->tmap[9], c->Zt16, n, m, c->ldzt, 128));
-    const bool ok3 = !(c->Z16 || greb) ||
+    const bool ok3 = !(c->Z16 || greb || c->naive) ||
                      (make_tmap_f16(c->tmap[13], bt2(c, 3), 2 * RP, n, c->ldb, 2 * RP) &&
                       make_tmap_f16(c->tmap[14], bt2(c, 3), 2 * RP, m, c->ldb, 2 * RP));
     if (!ok || !ok16 || !ok3) {
@@ -986,7 +1082,10 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
   while ((1ull << c->idx_bits) < mn) ++c->idx_bits;
   launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), c->st);
   launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), c->st);
-  if (A1) launch_pad_copy(A1, n, p->r, p->r, c->A1_orig, RP, c->st);
+  if (A1) {
+    const int a1c = c->naive ? c->np_cols : p->r;
+    launch_pad_copy(A1, n, a1c, a1c, c->A1_orig, RP, c->st);
+  }
   else launch_fill_zero(c->A1_orig, (size_t)n * RP * sizeof(float), c->st);
   CKI(cudaGetLastError());
   godec_status s = reset_state(c);
@@ -1056,6 +1155,7 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
                            double* bytes_product) {
   if (!c || n_iter < 0) return GODEC_ERR_ARG;
   if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
+  if (c->naive) return fail(c, GODEC_ERR_STATE, "godec_profile covers the BRP form only");
   for (int k = 0; k < GODEC_PROF_CLASSES; ++k) {
     if (ms) ms[k] = 0.0;
     if (launches) launches[k] = 0;
@@ -1464,54 +1564,6 @@ godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz, co
 // L = U W^T), sigma the column norms of W; A1, Qa, Qb, P are work space of the increments.
 // Columns at and beyond the current rank are zero everywhere.
 
-// Product over Z (even: m rows, K = n) or Z^T (odd: n rows, K = m) with the operand of
-// tensor map map_b, its column scales cscale, Gram partials into slot gslot (gram_mode 1).
-static void greb_prod(godec_ctx* c, bool even, int map_b, const float* cscale, float* out, int gram_mode, int gslot) {
-  TcLaunch l{};
-  l.mapA = c->tmap[even ? 0 : 1];
-  l.mapB = c->tmap[map_b];
-  l.rows = even ? c->p.m : c->p.n;
-  l.K = even ? c->p.n : c->p.m;
-  l.RP = c->RP;
-  l.geom = c->tg[even ? 0 : 1];
-  l.part = c->part;
-  l.counters = c->counters;
-  l.out = out;
-  l.ldb = c->ldb;
-  l.cscale = cscale;
-  l.zscale = c->ctl->zscale;
-  l.prescaled = 1;
-  l.gram_part = gpart(c, gslot);
-  l.gram_mode = gram_mode;
-  l.t_upper = 1;
-  l.pend = c->pend;
-  l.ctl = c->ctl;
-  launch_prod_tc(l, c->st);
-}
-
-// out (m x RP) = D B with D = Z - U W^T (the derivative of eq. GreBsmoD; U = 0 at rank 0);
-// B (n x RP) has p nonzero columns.
-static void greb_apply_D(godec_ctx* c, int ri, int p, const float* B, float* out) {
-  const int RP = c->RP;
-  launch_split_t(B, c->p.n, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
-  greb_prod(c, true, 13, c->cs_ref, out, 0, 0);
-  if (ri > 0) {
-    launch_cross_gram(c->Q2, RP, ri, B, RP, p, c->p.n, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
-    launch_tall_small_d(c->Q1, RP, ri, c->rf_C, RP, 0, p, c->p.m, -1.f, 1.f, out, RP, c->st);
-  }
-}
-
-// out (n x RP) = D^T Y for Y (m x RP) with p nonzero columns.
-static void greb_apply_Dt(godec_ctx* c, int ri, int p, const float* Y, float* out) {
-  const int RP = c->RP;
-  launch_split_t(Y, c->p.m, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
-  greb_prod(c, false, 14, c->cs_ref, out, 0, 0);
-  if (ri > 0) {
-    launch_cross_gram(c->Q1, RP, ri, Y, RP, p, c->p.m, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
-    launch_tall_small_d(c->Q2, RP, ri, c->rf_C, RP, 0, p, c->p.n, -1.f, 1.f, out, RP, c->st);
-  }
-}
-
 // The random-projection increment: `add` new unit rows of V (columns ri .. ri+add-1 of
 // c->V), the top right singular vectors of D from test matrix Omega_stage.
 static void greb_increment(godec_ctx* c, int ri, int add, int stage) {
@@ -1636,6 +1688,33 @@ static godec_status greb_grow(godec_ctx* c, const Ctl& h, unsigned long long nee
   }
   c->p.k = k;
   return GODEC_OK;
+}
+
+int godec_naive_columns(int64_t m, int64_t n, int32_t r) {
+  int64_t p = (int64_t)r + 8;
+  p = std::min<int64_t>(p, GODEC_MAX_RANK);
+  p = std::min<int64_t>(p, std::min(m, n));
+  return (int)std::max<int64_t>(p, r);
+}
+
+godec_status godec_naive_init(godec_ctx** out, const godec_params* p, const float* X, const float* Omega,
+                              void* stream) {
+  if (!out) return GODEC_ERR_ARG;
+  *out = nullptr;
+  char why[200];
+  if (bad_params(p, why, sizeof(why))) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_naive_init: %s", why);
+    return GODEC_ERR_ARG;
+  }
+  if (p->precision != GODEC_PREC_FP32 || p->q < 1) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_naive_init: needs precision GODEC_PREC_FP32 and q >= 1");
+    return GODEC_ERR_ARG;
+  }
+  if (!X || !Omega || (reinterpret_cast<uintptr_t>(X) & 15)) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_naive_init: X must be a 16-byte aligned device pointer, Omega non-NULL");
+    return GODEC_ERR_ARG;
+  }
+  return init_ctx(out, p, X, Omega, stream, false, godec_naive_columns(p->m, p->n, p->r));
 }
 
 godec_status godec_grebsmo_init(godec_ctx** out, const godec_grebsmo_params* gp, const float* X,
