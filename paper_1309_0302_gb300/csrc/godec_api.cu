@@ -322,19 +322,21 @@ void slot(godec_ctx* c, SlotLaunch& sl) {
 void cqr2(godec_ctx* c, const float* W, int64_t rows, int R2, int ld, float* Q, float* R1, float* T1, float* R2m,
           float* T2) {
   cudaStream_t st = c->st;
-  PROF(c, 10, st, launch_cross_gram(W, ld, R2, W, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st));
+  const int* ab = &c->ctl->abort;
+  PROF(c, 10, st, launch_cross_gram(W, ld, R2, W, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st, ab));
   const bool f64 = (c->p.flags & GODEC_FLAG_FP64_FACTOR) != 0;
   PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R1, T1, c->ctl, st, 0.f, f64));
-  PROF(c, 10, st, launch_tall_small_f(W, ld, R2, T1, ld, 0, R2, rows, 1.f, 0.f, c->Qtmp, ld, st));
-  PROF(c, 10, st, launch_cross_gram(c->Qtmp, ld, R2, c->Qtmp, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st));
+  PROF(c, 10, st, launch_tall_small_f(W, ld, R2, T1, ld, 0, R2, rows, 1.f, 0.f, c->Qtmp, ld, st, ab));
+  PROF(c, 10, st, launch_cross_gram(c->Qtmp, ld, R2, c->Qtmp, ld, R2, rows, c->rf_part, kRefineParts, c->rf_g, ld, st, ab));
   PROF(c, 10, st, launch_chol(c->rf_g, R2, ld, R2m, T2, c->ctl, st, 0.f, f64));
-  PROF(c, 10, st, launch_tall_small_f(c->Qtmp, ld, R2, T2, ld, 0, R2, rows, 1.f, 0.f, Q, ld, st));
+  PROF(c, 10, st, launch_tall_small_f(c->Qtmp, ld, R2, T2, ld, 0, R2, rows, 1.f, 0.f, Q, ld, st, ab));
 }
 
 void refine(godec_ctx* c) {
   const int r = c->r, RP = c->RP, R2 = 2 * r, ld = (R2 + 7) / 8 * 8;
   const int64_t m = c->p.m, n = c->p.n;
   cudaStream_t st = c->st;
+  const int* ab = &c->ctl->abort;   // an abandoned iteration skips the correction too
   // A = Z V, B = Z^T U (float32 product kernel on the float32 working copies)
   TcLaunch l{};
   l.RP = RP;
@@ -345,7 +347,7 @@ void refine(godec_ctx* c) {
   l.prescaled = 1;
   l.pend = c->pend;
   l.ctl = c->ctl;
-  launch_split_t(c->V, n, RP, bt2(c, 3), c->ldb, c->cs_ref, st);
+  launch_split_t(c->V, n, RP, bt2(c, 3), c->ldb, c->cs_ref, st, ab);
   l.mapA = c->tmap[0];
   l.mapB = c->tmap[13];
   l.rows = m;
@@ -353,7 +355,7 @@ void refine(godec_ctx* c) {
   l.geom = c->tg[0];
   l.out = c->RA;
   PROF(c, 0, st, launch_prod_tc(l, st));
-  launch_split_t(c->U, m, RP, bt2(c, 3), c->ldb, c->cs_ref, st);
+  launch_split_t(c->U, m, RP, bt2(c, 3), c->ldb, c->cs_ref, st, ab);
   l.mapA = c->tmap[1];
   l.mapB = c->tmap[14];
   l.rows = n;
@@ -362,18 +364,18 @@ void refine(godec_ctx* c) {
   l.out = c->RB;
   PROF(c, 0, st, launch_prod_tc(l, st));
   // C = U^T A; [U A], [V B] (stride ld, zero padding)
-  PROF(c, 10, st, launch_cross_gram(c->U, RP, r, c->RA, RP, r, m, c->rf_part, kRefineParts, c->rf_C, r, st));
-  PROF(c, 10, st, launch_concat2(c->U, c->RA, RP, r, m, c->Wa, ld, st));
-  PROF(c, 10, st, launch_concat2(c->V, c->RB, RP, r, n, c->Wb, ld, st));
+  PROF(c, 10, st, launch_cross_gram(c->U, RP, r, c->RA, RP, r, m, c->rf_part, kRefineParts, c->rf_C, r, st, ab));
+  PROF(c, 10, st, launch_concat2(c->U, c->RA, RP, r, m, c->Wa, ld, st, ab));
+  PROF(c, 10, st, launch_concat2(c->V, c->RB, RP, r, n, c->Wb, ld, st, ab));
   const size_t q = (size_t)64 * 64;
   float *Ra1 = c->Rf, *Ta1 = Ra1 + q, *Ra2 = Ta1 + q, *Ta2 = Ra2 + q, *Rb1 = Ta2 + q, *Tb1 = Rb1 + q,
         *Rb2 = Tb1 + q, *Tb2 = Rb2 + q;
   cqr2(c, c->Wa, m, R2, ld, c->Qa, Ra1, Ta1, Ra2, Ta2);
   cqr2(c, c->Wb, n, R2, ld, c->Qb, Rb1, Tb1, Rb2, Tb2);
-  PROF(c, 10, st, launch_refine_core(Ra1, Ra2, Rb1, Rb2, ld, c->rf_C, r, c->rf_core, st));
-  PROF(c, 10, st, launch_svd_small(c->rf_core, R2, r, c->rf_U, c->sigma, c->rf_V, st));
-  PROF(c, 10, st, launch_tall_small_d(c->Qa, ld, R2, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st));
-  PROF(c, 10, st, launch_tall_small_d(c->Qb, ld, R2, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st));
+  PROF(c, 10, st, launch_refine_core(Ra1, Ra2, Rb1, Rb2, ld, c->rf_C, r, c->rf_core, st, ab));
+  PROF(c, 10, st, launch_svd_small(c->rf_core, R2, r, c->rf_U, c->sigma, c->rf_V, st, ab));
+  PROF(c, 10, st, launch_tall_small_d(c->Qa, ld, R2, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st, ab));
+  PROF(c, 10, st, launch_tall_small_d(c->Qb, ld, R2, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st, ab));
 }
 
 // ---------------------------------------------------------------------------------
@@ -597,22 +599,22 @@ void greb_prod(godec_ctx* c, bool even, int map_b, const float* cscale, float* o
 // B (n x RP) has p nonzero columns.
 void greb_apply_D(godec_ctx* c, int ri, int p, const float* B, float* out) {
   const int RP = c->RP;
-  launch_split_t(B, c->p.n, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
+  launch_split_t(B, c->p.n, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st, &c->ctl->abort);
   greb_prod(c, true, 13, c->cs_ref, out, 0, 0);
   if (ri > 0) {
-    launch_cross_gram(c->Q2, RP, ri, B, RP, p, c->p.n, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
-    launch_tall_small_d(c->Q1, RP, ri, c->rf_C, RP, 0, p, c->p.m, -1.f, 1.f, out, RP, c->st);
+    launch_cross_gram(c->Q2, RP, ri, B, RP, p, c->p.n, c->rf_part, kRefineParts, c->rf_C, RP, c->st, &c->ctl->abort);
+    launch_tall_small_d(c->Q1, RP, ri, c->rf_C, RP, 0, p, c->p.m, -1.f, 1.f, out, RP, c->st, &c->ctl->abort);
   }
 }
 
 // out (n x RP) = D^T Y for Y (m x RP) with p nonzero columns.
 void greb_apply_Dt(godec_ctx* c, int ri, int p, const float* Y, float* out) {
   const int RP = c->RP;
-  launch_split_t(Y, c->p.m, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st);
+  launch_split_t(Y, c->p.m, RP, bt2(c, 3), c->ldb, c->cs_ref, c->st, &c->ctl->abort);
   greb_prod(c, false, 14, c->cs_ref, out, 0, 0);
   if (ri > 0) {
-    launch_cross_gram(c->Q1, RP, ri, Y, RP, p, c->p.m, c->rf_part, kRefineParts, c->rf_C, RP, c->st);
-    launch_tall_small_d(c->Q2, RP, ri, c->rf_C, RP, 0, p, c->p.n, -1.f, 1.f, out, RP, c->st);
+    launch_cross_gram(c->Q1, RP, ri, Y, RP, p, c->p.m, c->rf_part, kRefineParts, c->rf_C, RP, c->st, &c->ctl->abort);
+    launch_tall_small_d(c->Q2, RP, ri, c->rf_C, RP, 0, p, c->p.n, -1.f, 1.f, out, RP, c->st, &c->ctl->abort);
   }
 }
 
@@ -634,11 +636,12 @@ void enqueue_naive_lstep(godec_ctx* c) {
   }
   greb_apply_D(c, 0, p, c->Qb, c->P);
   cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);
-  launch_rmul(R2m, R1, RP, p, c->rf_core, 0, nullptr, st);
-  launch_svd_small(c->rf_core, p, r, c->rf_U, c->sigma, c->rf_V, st);
-  launch_tall_small_d(c->Qa, RP, p, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st);
-  launch_tall_small_d(c->Qb, RP, p, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st);
-  launch_lsplit(c->U, c->V, c->sigma, m, n, RP, r, c->ctl->zscale, c->LA, c->LB, st);
+  const int* ab = &c->ctl->abort;   // an abandoned iteration leaves U, V and the basis as they were
+  launch_rmul(R2m, R1, RP, p, c->rf_core, 0, nullptr, st, ab);
+  launch_svd_small(c->rf_core, p, r, c->rf_U, c->sigma, c->rf_V, st, ab);
+  launch_tall_small_d(c->Qa, RP, p, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st, ab);
+  launch_tall_small_d(c->Qb, RP, p, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st, ab);
+  launch_lsplit(c->U, c->V, c->sigma, m, n, RP, r, c->ctl->zscale, c->LA, c->LB, st, ab);
 }
 
 void enqueue_iteration(godec_ctx* c, bool fast) {

@@ -16,6 +16,16 @@
 
 namespace godec {
 
+// Block-uniform early exit of a kernel launched inside an iteration that may have been
+// abandoned (flag = &ctl->abort; NULL never skips): thread 0 reads the flag once, since
+// another stream may set it while the block runs.
+__device__ __forceinline__ bool block_skip(const int* flag) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = flag ? *reinterpret_cast<const volatile int*>(flag) : 0;
+  __syncthreads();
+  return s_skip != 0;
+}
+
 constexpr int kMaxRP = 64;          // maximum padded rank
 // Scale of the orthonormalised skinny operands in their float16 split form.  Entries
 // of a unit column are at most 1, and a lagged normaliser can leave a column far from
@@ -139,7 +149,8 @@ int tc_rpp(int RP);
 // Float16 split transposed operand of a row-major rows x RP matrix B (2 RP x ldb
 // halves), each column scaled by a power of two; cscale (RP) receives the factors that
 // undo the scaling.
-void launch_split_t(const float* B, int64_t rows, int RP, void* bt2, int64_t ldb, float* cscale, cudaStream_t st);
+void launch_split_t(const float* B, int64_t rows, int RP, void* bt2, int64_t ldb, float* cscale, cudaStream_t st,
+                    const int* skip = nullptr);
 // zscale = {s, 1/s}: the power of two with max |Z| s in [2^12, 2^13) (1 if Z is zero or
 // not finite); zmax is scratch.
 void launch_zscale(const float* Z, int64_t rows, int64_t cols, int64_t ld, unsigned* zmax, float* zscale, int nsm,
@@ -226,7 +237,7 @@ void launch_residual(const ResidualArgs& a, int nsm, cudaStream_t st);
 // U diag(sqrt(sigma s_Z)) and V diag(sqrt(sigma s_Z)), rows of 128 halves (64 high,
 // 64 low; K padded to 64), written by launch_lsplit after each L-step.
 void launch_lsplit(const float* U, const float* V, const float* sigma, int64_t m, int64_t n, int RP, int r,
-                   const float* zscale, void* A, void* B, cudaStream_t st);
+                   const float* zscale, void* A, void* B, cudaStream_t st, const int* skip = nullptr);
 struct ResidTcLaunch {
   ResidualArgs ra;         // X, m, n, pass, ctl and the candidate buffers are used
   const void* mapX;        // CUtensorMap over X (m x n float32), box 32 x 128
@@ -292,24 +303,26 @@ cudaError_t prepare_select_kernels();
 // ldb), a, b <= 64, over fixed row partitions of about 128 rows, at most G of them (part
 // holds G x a x b doubles); deterministic.
 void launch_cross_gram(const float* A, int64_t lda, int a, const float* B, int64_t ldb, int b, int64_t rows,
-                       double* part, int G, double* out, int ldo, cudaStream_t st);
+                       double* part, int G, double* out, int ldo, cudaStream_t st, const int* skip = nullptr);
 // C (rows x c, ldc) = beta C + alpha A (rows x a, lda) Bm (a x c, ldbm; Bm^T if trans), a, c <= 64
 void launch_tall_small_f(const float* A, int64_t lda, int a, const float* Bm, int ldbm, int trans, int c, int64_t rows,
-                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st);
+                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st, const int* skip = nullptr);
 void launch_tall_small_d(const float* A, int64_t lda, int a, const double* Bm, int ldbm, int trans, int c,
-                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st);
+                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st,
+                         const int* skip = nullptr);
 // Precision form (k_refine.cu): the bases [P | Q] of the correction; float16 copy of a
 // float32 matrix; the 2r x 2r core Ra K Rb^T of the tangent-space correction; SVD of an
 // n x n float64 matrix (n <= 64), leading r triplets.
 // W (rows x ld, float32) = [P | Q | 0] for P, Q rows x r with row stride ldp (2r <= ld).
 void launch_concat2(const float* P, const float* Q, int64_t ldp, int r, int64_t rows, float* W, int ld,
-                    cudaStream_t st);
+                    cudaStream_t st, const int* skip = nullptr);
 void launch_to_half(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd, int nsm,
                     cudaStream_t st);
 cudaError_t prepare_refine_kernels();
 void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, const float* Rb2, int ld,
-                        const double* C, int r, double* core, cudaStream_t st);
-void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st);
+                        const double* C, int r, double* core, cudaStream_t st, const int* skip = nullptr);
+void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st,
+                      const int* skip = nullptr);
 
 // GreBsmo (k_grebsmo.cu): the S-step's plan (one candidate pass at the key of lambda + 1
 // ulp), the soft-threshold emit S = R - lambda sgn R over every candidate, column norms
@@ -328,11 +341,11 @@ struct SoftEmitArgs {
 void launch_soft_plan(Ctl* ctl, unsigned guess, cudaStream_t st);
 void launch_emit_soft(const SoftEmitArgs& a, int nsm, cudaStream_t st);
 void launch_colnorm(const float* W, const double* g64, int64_t n, int RP, int r, float* Vh, float* sigma, int nsm,
-                    cudaStream_t st);
+                    cudaStream_t st, const int* skip = nullptr);
 // out (r x r, float64) = A B (A, B float32, stride ld), transposed with trans, then row i
 // scaled by rowscale[i] (nullable).
 void launch_rmul(const float* A, const float* B, int ld, int r, double* out, int trans, const float* rowscale,
-                 cudaStream_t st);
+                 cudaStream_t st, const int* skip = nullptr);
 
 // L (m x n, row stride ldl) = U diag(sigma) V^T, U m x r (ldu), V n x r (ldv) (k_dense.cu).
 void launch_lowrank_dense(const float* U, int64_t ldu, const float* sigma, const float* V, int64_t ldv, int64_t m,

@@ -15,7 +15,8 @@ constexpr int BW_THREADS = 256;
 // columns in use); a, b <= 64.  Each thread owns entries tid + 256 k of a x b.
 __global__ void __launch_bounds__(BW_THREADS)
 k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __restrict__ B, int64_t ldb, int b,
-             int64_t rows, double* __restrict__ part) {
+             int64_t rows, double* __restrict__ part, const int* skip) {
+  if (block_skip(skip)) return;
   constexpr int CH = 32;
   __shared__ float sA[CH][kMaxRP + 1], sB[CH][kMaxRP + 1];
   const int tid = threadIdx.x, G = gridDim.x, g = blockIdx.x;
@@ -52,7 +53,8 @@ k_cross_part(const float* __restrict__ A, int64_t lda, int a, const float* __res
 // tree: deterministic); with a row stride ldo for the a x b result (ldo >= b).
 constexpr int kSumThreads = 128;
 __global__ void __launch_bounds__(kSumThreads)
-k_cross_sum(const double* __restrict__ part, int G, int a, int b, double* __restrict__ out, int ldo) {
+k_cross_sum(const double* __restrict__ part, int G, int a, int b, double* __restrict__ out, int ldo, const int* skip) {
+  if (block_skip(skip)) return;
   __shared__ double red[kSumThreads / 32];
   const int e = blockIdx.x, ne = a * b;
   double t = 0.0;
@@ -72,7 +74,8 @@ k_cross_sum(const double* __restrict__ part, int G, int a, int b, double* __rest
 template <typename TB>
 __global__ void __launch_bounds__(BW_THREADS)
 k_tall_small(const float* __restrict__ A, int64_t lda, int a, const TB* __restrict__ Bm, int ldbm, int trans, int c,
-             int64_t rows, float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+             int64_t rows, float alpha, float beta, float* __restrict__ C, int64_t ldc, const int* skip) {
+  if (block_skip(skip)) return;
   __shared__ float sB[kMaxRP][kMaxRP + 1];   // a, c <= 64
   for (int e = threadIdx.x; e < a * c; e += BW_THREADS) {
     const int l = e / c, cc = e % c;
@@ -192,28 +195,29 @@ unsigned blocks_for(int64_t n) { return (unsigned)((n + BW_THREADS - 1) / BW_THR
 }  // namespace
 
 void launch_cross_gram(const float* A, int64_t lda, int a, const float* B, int64_t ldb, int b, int64_t rows,
-                       double* part, int G, double* out, int ldo, cudaStream_t st) {
+                       double* part, int G, double* out, int ldo, cudaStream_t st, const int* skip) {
   if (a * b == 0) return;
   // about 128 rows per partition (short serial chains), at most the G the buffer holds
   int64_t gu = (rows + 127) / 128;
   if (gu > G) gu = G;
   if (gu < 1) gu = 1;
-  k_cross_part<<<(unsigned)gu, BW_THREADS, 0, st>>>(A, lda, a, B, ldb, b, rows, part);
-  k_cross_sum<<<(unsigned)(a * b), kSumThreads, 0, st>>>(part, (int)gu, a, b, out, ldo);
+  k_cross_part<<<(unsigned)gu, BW_THREADS, 0, st>>>(A, lda, a, B, ldb, b, rows, part, skip);
+  k_cross_sum<<<(unsigned)(a * b), kSumThreads, 0, st>>>(part, (int)gu, a, b, out, ldo, skip);
 }
 
 void launch_tall_small_f(const float* A, int64_t lda, int a, const float* Bm, int ldbm, int trans, int c, int64_t rows,
-                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st) {
+                         float alpha, float beta, float* C, int64_t ldc, cudaStream_t st, const int* skip) {
   if (rows * c == 0) return;
   k_tall_small<float><<<blocks_for(rows * c), BW_THREADS, 0, st>>>(A, lda, a, Bm, ldbm, trans, c, rows, alpha, beta,
-                                                                   C, ldc);
+                                                                   C, ldc, skip);
 }
 
 void launch_tall_small_d(const float* A, int64_t lda, int a, const double* Bm, int ldbm, int trans, int c,
-                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st) {
+                         int64_t rows, float alpha, float beta, float* C, int64_t ldc, cudaStream_t st,
+                         const int* skip) {
   if (rows * c == 0) return;
   k_tall_small<double><<<blocks_for(rows * c), BW_THREADS, 0, st>>>(A, lda, a, Bm, ldbm, trans, c, rows, alpha, beta,
-                                                                    C, ldc);
+                                                                    C, ldc, skip);
 }
 
 void launch_spmm(const int64_t* idx, const float* val, int64_t nnz, int64_t n, const float* B, int64_t ldb, int c,

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(SOFT_THREADS) k_emit_soft(SoftEmitArgs a) {
 // sigma_l = sqrt(G_ll) (the column norms of W, from its Gram) for l < r, else 0;
 // Vh = W diag(1 / sigma) (unit columns; zero beyond r).
 __global__ void k_colnorm(const float* __restrict__ W, const double* __restrict__ g64, int64_t n, int RP, int r,
-                          float* __restrict__ Vh, float* __restrict__ sigma) {
+                          float* __restrict__ Vh, float* __restrict__ sigma, const int* skip) {
+  if (block_skip(skip)) return;
   const int64_t total = n * RP;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)(e % RP);
@@ -83,7 +84,8 @@ __global__ void k_colnorm(const float* __restrict__ W, const double* __restrict_
 // out (r x r, float64, row-major) = A B, or (A B)^T with trans, then row i times rowscale[i];
 // A, B float32 with stride ld.
 __global__ void k_rmul(const float* __restrict__ A, const float* __restrict__ B, int ld, int r, double* __restrict__ out,
-                       int trans, const float* __restrict__ rowscale) {
+                       int trans, const float* __restrict__ rowscale, const int* skip) {
+  if (block_skip(skip)) return;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
     double s = 0.0;
@@ -102,15 +104,15 @@ void launch_emit_soft(const SoftEmitArgs& a, int nsm, cudaStream_t st) {
 }
 
 void launch_colnorm(const float* W, const double* g64, int64_t n, int RP, int r, float* Vh, float* sigma, int nsm,
-                    cudaStream_t st) {
+                    cudaStream_t st, const int* skip) {
   int64_t blocks = (n * RP + 255) / 256;
   if (blocks > 8LL * nsm) blocks = 8LL * nsm;
-  k_colnorm<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(W, g64, n, RP, r, Vh, sigma);
+  k_colnorm<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(W, g64, n, RP, r, Vh, sigma, skip);
 }
 
 void launch_rmul(const float* A, const float* B, int ld, int r, double* out, int trans, const float* rowscale,
-                 cudaStream_t st) {
-  k_rmul<<<1, 256, 0, st>>>(A, B, ld, r, out, trans, rowscale);
+                 cudaStream_t st, const int* skip) {
+  k_rmul<<<1, 256, 0, st>>>(A, B, ld, r, out, trans, rowscale, skip);
 }
 
 }  // namespace godec

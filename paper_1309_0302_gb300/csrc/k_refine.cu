@@ -19,7 +19,8 @@ __global__ void k_to_half(const float* __restrict__ src, int64_t rows, int64_t c
 
 // W (rows x ld) = [P | Q | 0]: P and Q rows x r (row stride ldp), zero columns 2r..ld-1.
 __global__ void k_concat2(const float* __restrict__ P, const float* __restrict__ Q, int64_t ldp, int r, int64_t rows,
-                          float* __restrict__ W, int ld) {
+                          float* __restrict__ W, int ld, const int* skip) {
+  if (block_skip(skip)) return;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * ld) return;
   const int64_t i = e / ld;
@@ -31,7 +32,8 @@ __global__ void k_concat2(const float* __restrict__ P, const float* __restrict__
 // [I, 0]] with C (r x r, float64, stride r).  One block; the result in float64 (stride n2).
 __global__ void k_refine_core(const float* __restrict__ Ra1, const float* __restrict__ Ra2,
                               const float* __restrict__ Rb1, const float* __restrict__ Rb2, int ld,
-                              const double* __restrict__ C, int r, double* __restrict__ core) {
+                              const double* __restrict__ C, int r, double* __restrict__ core, const int* skip) {
+  if (block_skip(skip)) return;
   extern __shared__ double smd[];   // Ra, Rb, K: 3 x 64 x 65 doubles (dynamic)
   double (*Ra)[kMaxRP + 1] = reinterpret_cast<double (*)[kMaxRP + 1]>(smd);
   double (*Rb)[kMaxRP + 1] = Ra + kMaxRP;
@@ -78,7 +80,9 @@ constexpr double kJacobiTol = 1e-14;
 constexpr double kJacobiQuad = 1e-7;
 
 __global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A, int n, int r, double* __restrict__ Uo,
-                                                    float* __restrict__ sigma, double* __restrict__ Vo) {
+                                                    float* __restrict__ sigma, double* __restrict__ Vo,
+                                                    const int* skip) {
+  if (block_skip(skip)) return;
   extern __shared__ double smd[];   // W, V: 2 x 64 x 65 doubles (dynamic)
   double (*W)[kMaxRP + 1] = reinterpret_cast<double (*)[kMaxRP + 1]>(smd);
   double (*V)[kMaxRP + 1] = W + kMaxRP;
@@ -185,9 +189,9 @@ void launch_to_half(const float* src, int64_t rows, int64_t cols, int64_t lds, v
 }
 
 void launch_concat2(const float* P, const float* Q, int64_t ldp, int r, int64_t rows, float* W, int ld,
-                    cudaStream_t st) {
+                    cudaStream_t st, const int* skip) {
   const int64_t total = rows * ld;
-  if (total > 0) k_concat2<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, Q, ldp, r, rows, W, ld);
+  if (total > 0) k_concat2<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, Q, ldp, r, rows, W, ld, skip);
 }
 
 constexpr size_t kCoreSmem = 3 * kMaxRP * (kMaxRP + 1) * sizeof(double);
@@ -200,12 +204,13 @@ cudaError_t prepare_refine_kernels() {
 }
 
 void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, const float* Rb2, int ld,
-                        const double* C, int r, double* core, cudaStream_t st) {
-  k_refine_core<<<1, 256, kCoreSmem, st>>>(Ra1, Ra2, Rb1, Rb2, ld, C, r, core);
+                        const double* C, int r, double* core, cudaStream_t st, const int* skip) {
+  k_refine_core<<<1, 256, kCoreSmem, st>>>(Ra1, Ra2, Rb1, Rb2, ld, C, r, core, skip);
 }
 
-void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st) {
-  k_svd_small<<<1, 32 * ((n + 1) / 2), kSvdSmem, st>>>(A, n, r, U, sigma, V);
+void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st,
+                      const int* skip) {
+  k_svd_small<<<1, 32 * ((n + 1) / 2), kSvdSmem, st>>>(A, n, r, U, sigma, V, skip);
 }
 
 }  // namespace godec

@@ -401,7 +401,8 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
 // Rows of A (i < m) and B (i >= m): 64 halves of h (K padded to 64), then 64 of l.
 __global__ void k_lsplit(const float* __restrict__ U, const float* __restrict__ V, const float* __restrict__ sigma,
                          int64_t m, int64_t n, int RP, int r, const float* __restrict__ zscale,
-                         __half* __restrict__ A, __half* __restrict__ B) {
+                         __half* __restrict__ A, __half* __restrict__ B, const int* skip) {
+  if (block_skip(skip)) return;
   __shared__ float sq[64];
   if (threadIdx.x < 64) {
     const float s = threadIdx.x < r ? sigma[threadIdx.x] * zscale[0] : 0.f;
@@ -435,10 +436,11 @@ cudaError_t prepare_resid_kernels() {
 }
 
 void launch_lsplit(const float* U, const float* V, const float* sigma, int64_t m, int64_t n, int RP, int r,
-                   const float* zscale, void* A, void* B, cudaStream_t st) {
+                   const float* zscale, void* A, void* B, cudaStream_t st, const int* skip) {
   const int64_t tot = m + n;
   k_lsplit<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(U, V, sigma, m, n, RP, r, zscale,
-                                                          reinterpret_cast<__half*>(A), reinterpret_cast<__half*>(B));
+                                                          reinterpret_cast<__half*>(A), reinterpret_cast<__half*>(B),
+                                                          skip);
 }
 
 void launch_resid_tc(const ResidTcLaunch& l, cudaStream_t st) {

@@ -887,7 +887,8 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 // transposed float16 operand, scaled by the power of two 2^e_c that brings the column's
 // largest magnitude into [2^9, 2^10); cscale[c] = 2^-e_c undoes it.  One block per column.
 __global__ void k_split_t(const float* __restrict__ B, int64_t rows, int RP, __half* __restrict__ bt2, int64_t ldb,
-                          float* __restrict__ cscale) {
+                          float* __restrict__ cscale, const int* skip) {
+  if (block_skip(skip)) return;
   const int col = blockIdx.x;
   __shared__ float red[32];
   __shared__ float s_scale;
@@ -959,8 +960,9 @@ bool make_tmap_f16(void* map, const void* base, int64_t rows, int64_t cols, int6
 
 int tc_rpp(int RP) { return (RP + 15) / 16 * 16; }
 
-void launch_split_t(const float* B, int64_t rows, int RP, void* bt2, int64_t ldb, float* cscale, cudaStream_t st) {
-  k_split_t<<<RP, 256, 0, st>>>(B, rows, RP, reinterpret_cast<__half*>(bt2), ldb, cscale);
+void launch_split_t(const float* B, int64_t rows, int RP, void* bt2, int64_t ldb, float* cscale, cudaStream_t st,
+                    const int* skip) {
+  k_split_t<<<RP, 256, 0, st>>>(B, rows, RP, reinterpret_cast<__half*>(bt2), ldb, cscale, skip);
 }
 
 TcGeom tc_geometry(int64_t rows, int64_t K, int nsm) {
