@@ -339,7 +339,8 @@ godec_status godec_mul_ZB_noalloc(const float* Z, int64_t m, int64_t n, int64_t 
  * the Rayleigh-Ritz step (Z B = Q R, SVD of the p x p R in float64, the leading r
  * triplets).  It converges to the exact truncated SVD at the rate
  * (sigma_{p+1} / sigma_r)^(2q) per iteration and, being warm-started, keeps converging
- * across iterations.
+ * across iterations; the cold start gets 6 more power steps on X when the context is
+ * created or reset.
  *   params : as godec_init, with q = power steps per L-step (1..8) and precision
  *            GODEC_PREC_FP32; there is no rank test (r stays fixed)
  *   Omega  : device, n x p float32 row-major, the first test matrix (copied)

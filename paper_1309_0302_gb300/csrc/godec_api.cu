@@ -35,6 +35,7 @@ constexpr float kAlarmRatio = 30.f;   // lagged normaliser: max/min Cholesky dia
 // diagonal spread of its factor above this ratio (condition number of the product)
 // sends the iteration to the exact path instead of a second pass.
 constexpr float kCqr1Ratio = 1.5f;
+constexpr int kNaiveColdSteps = 6;    // naive GoDec: power steps on X before the first L-step
 }
 
 struct godec_ctx {
@@ -752,6 +753,14 @@ godec_status reset_state(godec_ctx* c) {
     launch_fill_zero(c->V, (size_t)c->p.n * c->RP * sizeof(float), c->st);
     launch_fill_zero(c->sigma, (size_t)c->RP * sizeof(float), c->st);
     cqr2(c, c->A1, c->p.n, c->np_cols, c->RP, c->Qb, R1, T1, R2m, T2);
+    // a cold start from a random basis gets kNaiveColdSteps more power steps on X, so the
+    // first L-step is as converged as the warm-started ones that follow
+    for (int s = 0; s < kNaiveColdSteps; ++s) {
+      greb_apply_D(c, 0, c->np_cols, c->Qb, c->P);
+      cqr2(c, c->P, c->p.m, c->np_cols, c->RP, c->Qa, R1, T1, R2m, T2);
+      greb_apply_Dt(c, 0, c->np_cols, c->Qa, c->P);
+      cqr2(c, c->P, c->p.n, c->np_cols, c->RP, c->Qb, R1, T1, R2m, T2);
+    }
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->st));
