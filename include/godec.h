@@ -408,6 +408,31 @@ godec_status godec_grebsmo_run(godec_ctx* ctx, int32_t* r_out, double* stage_err
                                int32_t* n_stages);
 
 /*
+ * LinGoDec, linear functional GoDec (Sec. 4.3, eqs. LinGoDec and NLinGoDec): X (m users x
+ * n items) = W F^T + S + G with the item features F (n x d) given, rank(W) <= r and S from
+ * the soft threshold, by alternating exact minimisation of
+ *   1/2 ||X - W F^T - S||_F^2 + lambda ||vec S||_1:
+ * W = the rank-constrained least squares fit of X - S (with F = Qf Rf: W Rf^T is the rank-r
+ * truncation of (X - S) Qf, eqs. NLinGoDec), then S = S_lambda(X - W F^T) (eq. softt).
+ * (X - S) Qf streams through the tensor-core product; the truncation is a float64 SVD of
+ * the d x d factor of its CholeskyQR2; the soft threshold runs in the residual pass.
+ *   params : m, n, ldx, r (1 <= r <= d), k (initial capacity of S, grown as needed),
+ *            precision GODEC_PREC_FP32, flags; tol and max_iter are not used
+ *   lambda : the soft threshold, > 0 (exact in float32 keeps |R| > lambda exact)
+ *   X      : device m x ldx float32, BORROWED;  F : device n x d float32 row-major, copied
+ * The getters of a GoDec context apply (godec_get_L gives L = W F^T in factored form,
+ * godec_get_S, godec_get_info with rel_err = ||X - W F^T - S||^2 / ||X||^2); godec_iterate,
+ * godec_solve and godec_profile return GODEC_ERR_STATE.
+ */
+godec_status godec_lingodec_init(godec_ctx** ctx, const godec_params* params, double lambda, const float* X,
+                                 const float* F, int32_t d, void* stream);
+/* n_iter alternations (W-step, S-step) from the current state; rel_err (host, nullable) of
+   the last.  Synchronises the stream after every iteration. */
+godec_status godec_lingodec_iterate(godec_ctx* ctx, int32_t n_iter, double* rel_err);
+/* W (device, m x d float32 row-major) of the last iteration.  Synchronises the stream. */
+godec_status godec_lingodec_get_W(godec_ctx* ctx, float* W);
+
+/*
  * Batched form: count independent GoDec-BRP problems (Algorithm 1 on each) of uneven
  * m, n and r, advanced together.  One batch iteration is one launch of one CUDA graph
  * that holds an iteration of every problem as a parallel branch, all on the exact-

@@ -87,6 +87,9 @@ def _declare(lib):
         "godec_tc_geometry": ([C.c_int64, C.c_int64, C.c_int32, i64p], C.c_int),
         "godec_grebsmo_init": ([C.POINTER(_P), C.POINTER(GrebsmoParams), _P, _P, _P], C.c_int),
         "godec_naive_init": ([C.POINTER(_P), C.POINTER(GodecParams), _P, _P, _P], C.c_int),
+        "godec_lingodec_init": ([C.POINTER(_P), C.POINTER(GodecParams), C.c_double, _P, _P, C.c_int32, _P], C.c_int),
+        "godec_lingodec_iterate": ([_P, C.c_int32, f64p], C.c_int),
+        "godec_lingodec_get_W": ([_P, _P], C.c_int),
         "godec_naive_columns": ([C.c_int64, C.c_int64, C.c_int32], C.c_int),
         "godec_grebsmo_run": ([_P, i32p, f64p, C.c_int32, i32p], C.c_int),
     }
@@ -298,6 +301,51 @@ class NaiveGoDec(GoDec):
         st = lib.godec_naive_init(C.byref(h), C.byref(p), _ptr(X), _ptr(self._A1), _stream_ptr(stream))
         _check(st, "godec_naive_init", None)
         self._h = h
+
+
+class LinGoDec(GoDec):
+    """LinGoDec (Sec. 4.3) on the GPU: X (users x items) = W F^T + S + G with the item features F
+    (n x d) given, rank(W) <= r, S soft-thresholded at lam.  iterate(n) runs n alternations;
+    W() returns W (m x d); L(), S() and info() as for GoDec."""
+
+    def __init__(self, X, F, r: int, lam: float, s_cap: int = 0, stream=None, flags: int = 0):
+        torch = _torch()
+        lib = library()
+        if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
+            raise ValueError("X must be a 2-D CUDA float32 tensor")
+        m, n = X.shape
+        if X.stride(1) != 1 or X.stride(0) % 4 or X.stride(0) < n or X.data_ptr() % 16:
+            Xp = torch.zeros((m, (n + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+            Xp[:, :n] = X
+            X = Xp
+        if F.dim() != 2 or F.shape[0] != n:
+            raise ValueError("F must be (n, d)")
+        self._X = X
+        self._A1 = F.contiguous().to(torch.float32)
+        self.d = int(F.shape[1])
+        self.m, self.n, self.r, self.k, self.q = m, n, int(r), int(s_cap), 0
+        self.stream = stream
+        k = int(s_cap if s_cap > 0 else max(1, m * n // 20))
+        p = GodecParams(m=m, n=n, ldx=X.stride(0), r=int(r), q=0, k=k, tol=-1.0, max_iter=1,
+                        precision=PREC_FP32, rank_tol=0.0, flags=int(flags), reserved=0)
+        h = C.c_void_p()
+        st = lib.godec_lingodec_init(C.byref(h), C.byref(p), float(lam), _ptr(X), _ptr(self._A1), self.d,
+                                     _stream_ptr(stream))
+        _check(st, "godec_lingodec_init", None)
+        self._h = h
+
+    def iterate(self, n_iter: int = 1) -> float:
+        rel = C.c_double(0.0)
+        _check(library().godec_lingodec_iterate(self._h, int(n_iter), C.byref(rel)), "godec_lingodec_iterate",
+               self._h)
+        return rel.value
+
+    def W(self):
+        """W (m, d) as a CUDA float32 tensor."""
+        torch = _torch()
+        W = torch.empty((self.m, self.d), dtype=torch.float32, device=self._X.device)
+        _check(library().godec_lingodec_get_W(self._h, _ptr(W)), "godec_lingodec_get_W", self._h)
+        return W
 
 
 class GreBsmo(GoDec):

@@ -134,6 +134,11 @@ struct godec_ctx {
   // over np_cols columns (rank + oversampling), warm-started from the last iteration's basis
   bool naive = false;
   int np_cols = 0;
+  // LinGoDec (godec_lingodec_*): the item features' basis Qf = orth(F) (in Q2, d columns),
+  // its factors in Rf (R1, R1^{-1}, R2, R2^{-1}), the soft threshold lambda
+  bool lingo = false;
+  int lg_d = 0;
+  double lg_lambda = 0.0;
   char err[200] = {0};
 };
 
@@ -742,6 +747,18 @@ godec_status reset_state(godec_ctx* c) {
   launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st, c->ctl->zscale);
   refresh_z16(c);
   launch_reset_iter(c->ctl, c->st);
+  if (c->lingo) {
+    // the features' basis Qf = orth(F) (F was copied into A1) and its split operand, fixed
+    // for the whole run; Rf keeps F = Qf R2 R1 for the final W
+    const size_t q = (size_t)64 * 64;
+    float *R1 = c->Rf, *T1 = R1 + q, *R2m = T1 + q, *T2 = R2m + q;
+    launch_fill_zero(c->Q2, (size_t)c->p.n * c->RP * sizeof(float), c->st);
+    launch_fill_zero(c->U, (size_t)c->p.m * c->RP * sizeof(float), c->st);
+    launch_fill_zero(c->V, (size_t)c->p.n * c->RP * sizeof(float), c->st);
+    launch_fill_zero(c->sigma, (size_t)c->RP * sizeof(float), c->st);
+    cqr2(c, c->A1, c->p.n, c->lg_d, c->RP, c->Q2, R1, T1, R2m, T2);
+    launch_split_t(c->Q2, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
+  }
   if (c->naive) {
     // the first subspace iteration starts from orth(Omega); later ones from the basis the
     // previous iteration ended with
@@ -942,15 +959,18 @@ void godec_destroy(godec_ctx* c) {
 // correction scratch of the precision form and the second skinny-operand maps are also
 // allocated, A1 may be NULL).
 static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float* X, const float* A1,
-                             void* stream, bool greb, int naive_cols = 0) {
+                             void* stream, bool greb, int naive_cols = 0, int lingo_d = 0, double lingo_lambda = 0.0) {
   godec_ctx* c = new (std::nothrow) godec_ctx;
   if (!c) return GODEC_ERR_OOM;
   c->greb = greb;
   c->naive = naive_cols > 0;
   c->np_cols = naive_cols;
+  c->lingo = lingo_d > 0;
+  c->lg_d = lingo_d;
+  c->lg_lambda = lingo_lambda;
   c->p = *p;
   c->r = p->r;
-  c->RP = round_up(std::max(p->r, naive_cols), 8);
+  c->RP = round_up(std::max(std::max(p->r, naive_cols), lingo_d), 8);
   c->nprod = 6 * p->q + 3;
   c->st = reinterpret_cast<cudaStream_t>(stream);
   auto bail = [&](godec_status s) {
@@ -991,7 +1011,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
     CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Z16), (size_t)m * c->ldz));
     CKI(dalloc(reinterpret_cast<unsigned short**>(&c->Zt16), (size_t)n * c->ldzt));
   }
-  if (p->precision == GODEC_PREC_BF16_REFINE || greb || c->naive) {
+  if (p->precision == GODEC_PREC_BF16_REFINE || greb || c->naive || c->lingo) {
     const size_t W = 64;   // columns of the correction's [U | A] and [V | B] (2r <= 64)
     CKI(dalloc(&c->RA, (size_t)m * RP));
     CKI(dalloc(&c->RB, (size_t)n * RP));
@@ -1060,7 +1080,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
     const bool ok16 = !c->Z16 ||
                       (make_tmap_f16(c->tmap[8], c->Z16, m, n, c->ldz, 128) &&
                        make_tmap_f16(c->tmap[9], c->Zt16, n, m, c->ldzt, 128));
-    const bool ok3 = !(c->Z16 || greb || c->naive) ||
+    const bool ok3 = !(c->Z16 || greb || c->naive || c->lingo) ||
                      (make_tmap_f16(c->tmap[13], bt2(c, 3), 2 * RP, n, c->ldb, 2 * RP) &&
                       make_tmap_f16(c->tmap[14], bt2(c, 3), 2 * RP, m, c->ldb, 2 * RP));
     if (!ok || !ok16 || !ok3) {
@@ -1095,7 +1115,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
   launch_fill_zero(c->Q1, (size_t)m * RP * sizeof(float), c->st);
   launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), c->st);
   if (A1) {
-    const int a1c = c->naive ? c->np_cols : p->r;
+    const int a1c = c->naive ? c->np_cols : (c->lingo ? c->lg_d : p->r);
     launch_pad_copy(A1, n, a1c, a1c, c->A1_orig, RP, c->st);
   }
   else launch_fill_zero(c->A1_orig, (size_t)n * RP * sizeof(float), c->st);
@@ -1130,7 +1150,7 @@ godec_status godec_reset(godec_ctx* c) {
 
 godec_status godec_iterate(godec_ctx* c, int32_t n_iter, double* rel_err) {
   if (!c) return GODEC_ERR_ARG;
-  if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
+  if (c->greb || c->lingo) return fail(c, GODEC_ERR_STATE, "this context runs through its own entry points");
   if (n_iter < 0) return fail(c, GODEC_ERR_ARG, "n_iter must be >= 0");
   godec_status s = run_iterations(c, n_iter, -1.0);
   if (s) return s;
@@ -1144,7 +1164,7 @@ godec_status godec_iterate(godec_ctx* c, int32_t n_iter, double* rel_err) {
 
 godec_status godec_solve(godec_ctx* c, int32_t* iters, double* rel_err) {
   if (!c) return GODEC_ERR_ARG;
-  if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
+  if (c->greb || c->lingo) return fail(c, GODEC_ERR_STATE, "this context runs through its own entry points");
   Ctl h;
   godec_status s = read_ctl(c, &h);
   if (s) return s;
@@ -1166,8 +1186,8 @@ godec_status godec_solve(godec_ctx* c, int32_t* iters, double* rel_err) {
 godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* launches,
                            double* bytes_product) {
   if (!c || n_iter < 0) return GODEC_ERR_ARG;
-  if (c->greb) return fail(c, GODEC_ERR_STATE, "a GreBsmo context runs through godec_grebsmo_run");
-  if (c->naive) return fail(c, GODEC_ERR_STATE, "godec_profile covers the BRP form only");
+  if (c->greb || c->lingo) return fail(c, GODEC_ERR_STATE, "this context runs through its own entry points");
+  if (c->naive || c->lingo) return fail(c, GODEC_ERR_STATE, "godec_profile covers the BRP form only");
   for (int k = 0; k < GODEC_PROF_CLASSES; ++k) {
     if (ms) ms[k] = 0.0;
     if (launches) launches[k] = 0;
@@ -1618,13 +1638,13 @@ static void greb_lstep(godec_ctx* c, int ri) {
 
 // The S-step of the inner step: S = S_lambda(X - U W^T) (eq. softt) and the sparse update
 // of Z = X - S.  L = U diag(sigma) V^T with V the unit columns of W.
-static void greb_sstep(godec_ctx* c, int ri, unsigned guess) {
+static void greb_sstep(godec_ctx* c, int ri, unsigned guess, const float* U) {
   const int RP = c->RP;
   const int64_t m = c->p.m, n = c->p.n;
   cudaStream_t st = c->st;
   launch_reset_iter(c->ctl, st);
   launch_soft_plan(c->ctl, guess, st);
-  launch_lsplit(c->Q1, c->V, c->sigma, m, n, RP, ri, c->ctl->zscale, c->LA, c->LB, st);
+  launch_lsplit(U, c->V, c->sigma, m, n, RP, ri, c->ctl->zscale, c->LA, c->LB, st);
   ResidTcLaunch rl{};
   rl.ra.X = c->X;
   rl.ra.m = m;
@@ -1770,6 +1790,104 @@ godec_status godec_grebsmo_init(godec_ctx** out, const godec_grebsmo_params* gp,
   return GODEC_OK;
 }
 
+// ---- LinGoDec (Sec. 4.3, eqs. LinGoDec and NLinGoDec) -----------------------------------
+// W-step (readings R20, R21): with F = Qf Rf (fixed), Y = X - S:  Y Qf = Qy Ry (CholeskyQR2 of
+// the streamed product), Ry = Ur S Vr^T (float64), W = Qy Ur S Vr^T Rf^{-T}; then
+// L = W F^T = (Qy Ur) S (Qf Vr)^T, kept as U = Qy Ur, V = Qf Vr.  S-step: S_lambda(X - L).
+static void lingo_lstep(godec_ctx* c) {
+  const int RP = c->RP, d = c->lg_d, r = c->p.r;
+  const int64_t m = c->p.m, n = c->p.n;
+  const size_t rr = (size_t)RP * RP;
+  cudaStream_t st = c->st;
+  const int* ab = &c->ctl->abort;
+  greb_prod(c, true, 4, c->cs, c->P, 1, 0);                        // Y Qf (operand set at reset)
+  gram_sum(c, gpart(c, 0), 0, prod_tiles(m), g64(c, 0), st);
+  c->r = d;
+  final_cqr2(c, m, g64(c, 0), c->Rfin, c->Rfin + 2 * rr, c->Q1, g64(c, 2), nullptr);   // Y Qf = Qy Rb Ra
+  c->r = r;
+  launch_rmul(c->Rfin + 2 * rr, c->Rfin, RP, d, c->rf_core, 0, nullptr, st, ab);
+  launch_svd_small(c->rf_core, d, r, c->rf_U, c->sigma, c->rf_V, st, ab);
+  launch_tall_small_d(c->Q1, RP, d, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st, ab);
+  launch_tall_small_d(c->Q2, RP, d, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st, ab);
+}
+
+godec_status godec_lingodec_init(godec_ctx** out, const godec_params* p, double lambda, const float* X, const float* F,
+                                 int32_t d, void* stream) {
+  if (!out) return GODEC_ERR_ARG;
+  *out = nullptr;
+  char why[200];
+  if (bad_params(p, why, sizeof(why))) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_lingodec_init: %s", why);
+    return GODEC_ERR_ARG;
+  }
+  if (p->precision != GODEC_PREC_FP32 || d < 1 || d > GODEC_MAX_RANK || d > p->n || p->r > d ||
+      !(lambda > 0.0) || !std::isfinite(lambda) || !X || !F || (reinterpret_cast<uintptr_t>(X) & 15)) {
+    snprintf(g_static_err, sizeof(g_static_err),
+             "godec_lingodec_init: needs precision FP32, 1 <= r <= d <= min(n, %d), lambda > 0, X (16-byte "
+             "aligned) and F device pointers", GODEC_MAX_RANK);
+    return GODEC_ERR_ARG;
+  }
+  godec_params q = *p;
+  q.k = std::min<int64_t>(std::max<int64_t>(p->k, 1), p->m * p->n);
+  return init_ctx(out, &q, X, F, stream, false, 0, d, lambda);
+}
+
+godec_status godec_lingodec_iterate(godec_ctx* c, int32_t n_iter, double* rel_err) {
+  if (!c || !c->lingo) {
+    if (c) fail(c, GODEC_ERR_STATE, "godec_lingodec_iterate needs a context from godec_lingodec_init");
+    return c ? GODEC_ERR_STATE : GODEC_ERR_ARG;
+  }
+  if (n_iter < 0) return fail(c, GODEC_ERR_ARG, "n_iter must be >= 0");
+  const float lamf = (float)c->lg_lambda;
+  unsigned guess;
+  memcpy(&guess, &lamf, sizeof(guess));
+  guess += 1u;   // S is nonzero where |R| > lambda
+  godec_status s;
+  for (int it = 0; it < n_iter; ++it) {
+    lingo_lstep(c);
+    for (int attempt = 0;; ++attempt) {
+      greb_sstep(c, c->p.r, guess, c->U);
+      CK(cudaGetLastError());
+      Ctl h;
+      if ((s = read_ctl(c, &h))) return s;
+      if (h.timeout) return fail(c, GODEC_ERR_TIMEOUT, "a device-side wait of the tensor-core product timed out");
+      if (h.nonfinite) return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - W F^T");
+      if (h.abort && h.need_bigger_cand && attempt < 8) {
+        if ((s = clear_counters(c))) return s;
+        CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
+        if ((s = greb_grow(c, h, h.cand_count))) return s;
+        continue;
+      }
+      if (h.abort) return fail(c, GODEC_ERR_STATE, "LinGoDec iteration aborted");
+      if (h.range_err) {
+        if ((s = rescale_z(c))) return s;
+        if ((s = SET_CTL(range_err, 0))) return s;
+      }
+      if (rel_err) *rel_err = h.rel_err;
+      break;
+    }
+  }
+  return GODEC_OK;
+}
+
+godec_status godec_lingodec_get_W(godec_ctx* c, float* W) {
+  if (!c || !c->lingo || !W) {
+    if (c) fail(c, GODEC_ERR_ARG, "godec_lingodec_get_W needs a LinGoDec context and W");
+    return GODEC_ERR_ARG;
+  }
+  Ctl h;
+  godec_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (h.iter == 0) return fail(c, GODEC_ERR_STATE, "no iteration has run yet");
+  const size_t q = (size_t)64 * 64;
+  const float *T1 = c->Rf + q, *T2 = c->Rf + 3 * q;
+  launch_lingo_g(T1, T2, c->RP, c->rf_V, c->sigma, c->lg_d, c->p.r, c->rf_C, c->st);
+  launch_tall_small_d(c->U, c->RP, c->p.r, c->rf_C, c->p.r, 1, c->lg_d, c->p.m, 1.f, 0.f, W, c->lg_d, c->st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->st));
+  return GODEC_OK;
+}
+
 godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, int32_t cap, int32_t* n_stages) {
   if (!c || !c->greb) {
     if (c) fail(c, GODEC_ERR_STATE, "godec_grebsmo_run needs a context from godec_grebsmo_init");
@@ -1803,7 +1921,7 @@ godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, 
     for (int k = 0; k < c->gp.K; ++k) {
       greb_lstep(c, ri);
       for (int attempt = 0;; ++attempt) {
-        greb_sstep(c, ri, guess);
+        greb_sstep(c, ri, guess, c->Q1);
         CK(cudaGetLastError());
         Ctl h;
         if ((s = read_ctl(c, &h))) return s;

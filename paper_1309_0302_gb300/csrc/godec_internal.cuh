@@ -346,6 +346,10 @@ void launch_colnorm(const float* W, const double* g64, int64_t n, int RP, int r,
 // scaled by rowscale[i] (nullable).
 void launch_rmul(const float* A, const float* B, int ld, int r, double* out, int trans, const float* rowscale,
                  cudaStream_t st, const int* skip = nullptr);
+// LinGoDec: out (d x r, float64) = T1 T2 Vr diag(sigma) (T1, T2 upper triangular d x d,
+// stride ld; Vr d x r float64).
+void launch_lingo_g(const float* T1, const float* T2, int ld, const double* Vr, const float* sigma, int d, int r,
+                    double* out, cudaStream_t st);
 
 // L (m x n, row stride ldl) = U diag(sigma) V^T, U m x r (ldu), V n x r (ldv) (k_dense.cu).
 void launch_lowrank_dense(const float* U, int64_t ldu, const float* sigma, const float* V, int64_t ldv, int64_t m,

@@ -95,7 +95,34 @@ __global__ void k_rmul(const float* __restrict__ A, const float* __restrict__ B,
   }
 }
 
+// LinGoDec's W = U_L diag(sigma) (Rf^{-1} Vr)^T: out (d x r, float64, row-major) =
+// T1 T2 Vr diag(sigma) with T1, T2 the float32 inverses of F's two CholeskyQR factors
+// (stride ld, upper triangular, d x d) and Vr (d x r, float64, stride r).
+__global__ void k_lingo_g(const float* __restrict__ T1, const float* __restrict__ T2, int ld,
+                          const double* __restrict__ Vr, const float* __restrict__ sigma, int d, int r,
+                          double* __restrict__ out) {
+  __shared__ double tmp[kMaxRP * kMaxRP];
+  for (int e = threadIdx.x; e < d * r; e += blockDim.x) {   // tmp = T2 Vr diag(sigma)
+    const int i = e / r, j = e % r;
+    double s = 0.0;
+    for (int k = i; k < d; ++k) s += (double)T2[i * ld + k] * Vr[k * r + j];
+    tmp[e] = s * (double)sigma[j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < d * r; e += blockDim.x) {   // out = T1 tmp
+    const int i = e / r, j = e % r;
+    double s = 0.0;
+    for (int k = i; k < d; ++k) s += (double)T1[i * ld + k] * tmp[k * r + j];
+    out[e] = s;
+  }
+}
+
 }  // namespace
+
+void launch_lingo_g(const float* T1, const float* T2, int ld, const double* Vr, const float* sigma, int d, int r,
+                    double* out, cudaStream_t st) {
+  k_lingo_g<<<1, 256, 0, st>>>(T1, T2, ld, Vr, sigma, d, r, out);
+}
 
 void launch_soft_plan(Ctl* ctl, unsigned guess, cudaStream_t st) { k_soft_plan<<<1, 1, 0, st>>>(ctl, guess); }
 
