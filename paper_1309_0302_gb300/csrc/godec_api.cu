@@ -1638,7 +1638,7 @@ static void greb_lstep(godec_ctx* c, int ri) {
 
 // The S-step of the inner step: S = S_lambda(X - U W^T) (eq. softt) and the sparse update
 // of Z = X - S.  L = U diag(sigma) V^T with V the unit columns of W.
-static void greb_sstep(godec_ctx* c, int ri, unsigned guess, const float* U) {
+static void greb_sstep(godec_ctx* c, int ri, unsigned guess, const float* U, float lambda) {
   const int RP = c->RP;
   const int64_t m = c->p.m, n = c->p.n;
   cudaStream_t st = c->st;
@@ -1675,7 +1675,7 @@ static void greb_sstep(godec_ctx* c, int ri, unsigned guess, const float* U) {
     se.S_val[b] = c->S_val[b];
   }
   se.sbits = c->sbits;
-  se.lambda = (float)c->gp.lambda;
+  se.lambda = lambda;
   launch_emit_soft(se, c->nsm, st);
   EmitArgs ea{};
   ea.ctl = c->ctl;
@@ -1846,7 +1846,7 @@ godec_status godec_lingodec_iterate(godec_ctx* c, int32_t n_iter, double* rel_er
   for (int it = 0; it < n_iter; ++it) {
     lingo_lstep(c);
     for (int attempt = 0;; ++attempt) {
-      greb_sstep(c, c->p.r, guess, c->U);
+      greb_sstep(c, c->p.r, guess, c->U, (float)c->lg_lambda);
       CK(cudaGetLastError());
       Ctl h;
       if ((s = read_ctl(c, &h))) return s;
@@ -1921,7 +1921,7 @@ godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, 
     for (int k = 0; k < c->gp.K; ++k) {
       greb_lstep(c, ri);
       for (int attempt = 0;; ++attempt) {
-        greb_sstep(c, ri, guess, c->Q1);
+        greb_sstep(c, ri, guess, c->Q1, (float)c->gp.lambda);
         CK(cudaGetLastError());
         Ctl h;
         if ((s = read_ctl(c, &h))) return s;
