@@ -433,6 +433,35 @@ godec_status godec_lingodec_iterate(godec_ctx* ctx, int32_t n_iter, double* rel_
 godec_status godec_lingodec_get_W(godec_ctx* ctx, float* W);
 
 /*
+ * MSE training, the multi-label subspace ensemble (Sec. 4.2.1, eqs. ms, mssub, msinitial,
+ * Algorithm 4): X (n samples x p features) = sum_i L^i + S, L^i nonzero only on the rows
+ * Omega_i of the samples that carry label i, rank(L^i) <= r_i, card(S) <= K.  Block
+ * coordinate descent from L^i = (D^{-1} X) restricted to Omega_i (D = labels per sample),
+ * S = 0: for each label in turn, L^i = the q = 0 bilateral random projection of
+ * (X - sum_{j != i} L^j - S) on Omega_i with the Gaussian test matrix of that step (on the
+ * GPU through a q = 0 GoDec context over the gathered rows); then S = the K largest
+ * entries of X - sum L^i (the S-step of Algorithm 1).
+ *   X       : device n x ldx float32 (ldx*4 a multiple of 16), read only
+ *   labels  : host n x k int32, row-major, nonzero = the sample carries the label
+ *   ranks   : host k int32, 1 <= r_i <= min(|Omega_i|, p, r_stride)
+ *   K       : cardinality of S;  iters : outer iterations (>= 1)
+ *   A1s     : device float32, iters x k blocks of p x r_stride (row-major): the test
+ *             matrix of label i in iteration t is the first r_i columns of block t k + i
+ *   C       : device k x r_stride x p float32 (nullable): rows 0 .. r_i - 1 of block i are an
+ *             orthonormal basis of label i's subspace (the row space of L^i), the rest 0
+ *   Lsum    : device n x ldl float32 (nullable): sum_i L^i
+ *   S_idx, S_val : device, S_cap entries (nullable): S as COO sorted by linear index;
+ *             nnz (host, nullable) receives its size
+ *   history : host, iters entries (nullable): ||X - sum L^i - S||_F^2 after each iteration
+ * All device memory is allocated and freed inside the call; the call synchronises the
+ * stream.  GODEC_ERR_ARG on invalid arguments or S_cap < nnz (results written otherwise).
+ */
+godec_status godec_mse_train(const float* X, int64_t n, int64_t p, int64_t ldx, const int32_t* labels, int32_t k,
+                             const int32_t* ranks, int64_t K, int32_t iters, const float* A1s, int32_t r_stride,
+                             float* C, float* Lsum, int64_t ldl, int64_t* S_idx, float* S_val, int64_t S_cap,
+                             int64_t* nnz, double* history, void* stream);
+
+/*
  * Batched form: count independent GoDec-BRP problems (Algorithm 1 on each) of uneven
  * m, n and r, advanced together.  One batch iteration is one launch of one CUDA graph
  * that holds an iteration of every problem as a parallel branch, all on the exact-

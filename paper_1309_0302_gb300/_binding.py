@@ -90,6 +90,8 @@ def _declare(lib):
         "godec_lingodec_init": ([C.POINTER(_P), C.POINTER(GodecParams), C.c_double, _P, _P, C.c_int32, _P], C.c_int),
         "godec_lingodec_iterate": ([_P, C.c_int32, f64p], C.c_int),
         "godec_lingodec_get_W": ([_P, _P], C.c_int),
+        "godec_mse_train": ([_P, C.c_int64, C.c_int64, C.c_int64, i32p, C.c_int32, i32p, C.c_int64, C.c_int32, _P,
+                             C.c_int32, _P, _P, C.c_int64, _P, _P, C.c_int64, i64p, f64p, _P], C.c_int),
         "godec_naive_columns": ([C.c_int64, C.c_int64, C.c_int32], C.c_int),
         "godec_grebsmo_run": ([_P, i32p, f64p, C.c_int32, i32p], C.c_int),
     }
@@ -400,6 +402,43 @@ class GreBsmo(GoDec):
 
     def iterate(self, n_iter: int = 1):
         raise RuntimeError("GreBsmo runs through run()")
+
+
+def mse_train(X, labels, ranks, K: int, iters: int, A1s, stream=None):
+    """MSE training (Sec. 4.2.1, Algorithm 4) on the GPU.
+
+    X: CUDA float32 (n, p); labels: (n, k) 0/1 array (host); ranks: k ints; A1s: CUDA float32
+    (iters, k, p, r_stride), the Gaussian test matrix of each BRP step.  Returns a dict with
+    C (k, r_stride, p) orthonormal subspace rows, Lsum (n, p) = sum of the blocks, S_idx,
+    S_val (COO) and history (the objective after each outer iteration).
+    """
+    torch = _torch()
+    lib = library()
+    if X.dtype != torch.float32 or not X.is_cuda or X.dim() != 2:
+        raise ValueError("X must be a 2-D CUDA float32 tensor")
+    n, p = X.shape
+    if X.stride(1) != 1 or X.stride(0) % 4 or X.stride(0) < p or X.data_ptr() % 16:
+        Xp = torch.zeros((n, (p + 3) // 4 * 4), dtype=torch.float32, device=X.device)
+        Xp[:, :p] = X
+        X = Xp
+    lab = np.ascontiguousarray(np.asarray(labels) != 0, dtype=np.int32)
+    k = lab.shape[1]
+    rk = np.ascontiguousarray(ranks, dtype=np.int32)
+    A1s = A1s.contiguous().to(torch.float32)
+    r_stride = int(A1s.shape[3])
+    C_ = torch.zeros((k, r_stride, p), dtype=torch.float32, device=X.device)
+    Ls = torch.empty((n, p), dtype=torch.float32, device=X.device)
+    si = torch.empty((max(K, 1),), dtype=torch.int64, device=X.device)
+    sv = torch.empty((max(K, 1),), dtype=torch.float32, device=X.device)
+    nnz = C.c_int64(0)
+    hist = (C.c_double * iters)()
+    st = lib.godec_mse_train(_ptr(X), n, p, X.stride(0), lab.ctypes.data_as(C.POINTER(C.c_int32)), k,
+                             rk.ctypes.data_as(C.POINTER(C.c_int32)), int(K), int(iters), _ptr(A1s), r_stride,
+                             _ptr(C_), _ptr(Ls), p, _ptr(si), _ptr(sv), max(int(K), 1), C.byref(nnz), hist,
+                             _stream_ptr(stream))
+    _check(st, "godec_mse_train", None)
+    return {"C": C_, "Lsum": Ls, "S_idx": si[: nnz.value], "S_val": sv[: nnz.value],
+            "history": [hist[i] for i in range(iters)]}
 
 
 def _mul(name, Z, B, stream=None):

@@ -1888,6 +1888,168 @@ godec_status godec_lingodec_get_W(godec_ctx* c, float* W) {
   return GODEC_OK;
 }
 
+// ---- MSE training (Sec. 4.2.1, Algorithm 4) ----------------------------------------------
+// Block coordinate descent over the label blocks L^1 .. L^k and S, with R = X - sum L^i - S
+// kept densely.  Block i: N = R[Omega_i] + L^i[Omega_i] gathered into its own buffer, whose
+// GoDec context (q = 0) gives the q = 0 BRP of Algorithm 4 with the test matrix of this step
+// (one iteration from S = 0: its L-step is the BRP of N; its S-step is not used); then
+// R[Omega_i] = N - L^i_new.  S-step: the top-K of X - sum L^i = R + S_old.
+godec_status godec_mse_train(const float* X, int64_t n, int64_t p, int64_t ldx, const int32_t* labels, int32_t k,
+                             const int32_t* ranks, int64_t K, int32_t iters, const float* A1s, int32_t r_stride,
+                             float* C, float* Lsum, int64_t ldl, int64_t* S_idx, float* S_val, int64_t S_cap,
+                             int64_t* nnz, double* history, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const char* why = nullptr;
+  if (!X || !labels || !ranks || !A1s || n < 1 || p < 1 || ldx < p || (ldx * 4) % 16 || k < 1 || iters < 1 ||
+      K < 0 || K > n * p || r_stride < 1 || r_stride > GODEC_MAX_RANK || (double)n * (double)p >= 4294967296.0 ||
+      (reinterpret_cast<uintptr_t>(X) & 15) || (Lsum && ldl < p))
+    why = "invalid argument";
+  std::vector<std::vector<int64_t>> rows(k > 0 ? k : 0);
+  std::vector<float> invD(n > 0 ? n : 0, 0.f);
+  if (!why) {
+    for (int64_t i = 0; i < n; ++i) {
+      int d = 0;
+      for (int j = 0; j < k; ++j)
+        if (labels[i * k + j]) {
+          rows[j].push_back(i);
+          ++d;
+        }
+      invD[i] = d > 0 ? 1.f / (float)d : 0.f;
+    }
+    for (int j = 0; j < k && !why; ++j)
+      if (ranks[j] < 1 || ranks[j] > r_stride || (int64_t)ranks[j] > std::min<int64_t>((int64_t)rows[j].size(), p))
+        why = "every rank must satisfy 1 <= r_i <= min(|Omega_i|, p, r_stride)";
+  }
+  if (why) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mse_train: %s", why);
+    return GODEC_ERR_ARG;
+  }
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mse_train: no CUDA device");
+    return GODEC_ERR_CUDA;
+  }
+  const int64_t ldr = (p + 3) / 4 * 4;
+  std::vector<void*> owned;
+  std::vector<godec_ctx*> ctx(k, nullptr);
+  godec_status status = GODEC_OK;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (godec_ctx* c : ctx) godec_destroy(c);
+    for (void* q : owned) cudaFree(q);
+  };
+  auto alloc = [&](void** ptr, size_t bytes) -> bool {
+    if (cudaMalloc(ptr, bytes ? bytes : 16) != cudaSuccess) return false;
+    owned.push_back(*ptr);
+    return true;
+  };
+#define MSE_FAIL(code, ...)                                                  \
+  do {                                                                       \
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mse_train: " __VA_ARGS__); \
+    cleanup();                                                               \
+    return code;                                                             \
+  } while (0)
+  float *R = nullptr, *dinvD = nullptr, *Sv[2] = {nullptr, nullptr};
+  int64_t* Si[2] = {nullptr, nullptr};
+  double* dsum = nullptr;
+  if (!alloc((void**)&R, (size_t)n * ldr * 4) || !alloc((void**)&dinvD, (size_t)n * 4) ||
+      !alloc((void**)&dsum, 8) || !alloc((void**)&Si[0], (size_t)std::max<int64_t>(K, 1) * 8) ||
+      !alloc((void**)&Sv[0], (size_t)std::max<int64_t>(K, 1) * 4))
+    MSE_FAIL(GODEC_ERR_OOM, "out of device memory");
+  std::vector<int64_t*> drows(k, nullptr);
+  std::vector<float*> N(k, nullptr), U(k, nullptr), sg(k, nullptr), V(k, nullptr);
+  for (int j = 0; j < k; ++j) {
+    const int64_t nr = (int64_t)rows[j].size();
+    if (!alloc((void**)&drows[j], (size_t)nr * 8) || !alloc((void**)&N[j], (size_t)nr * ldr * 4) ||
+        !alloc((void**)&U[j], (size_t)nr * ranks[j] * 4) || !alloc((void**)&sg[j], (size_t)ranks[j] * 4) ||
+        !alloc((void**)&V[j], (size_t)p * ranks[j] * 4))
+      MSE_FAIL(GODEC_ERR_OOM, "out of device memory");
+    if (cudaMemcpyAsync(drows[j], rows[j].data(), (size_t)nr * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(N[j], 0, (size_t)nr * ldr * 4, st) != cudaSuccess)
+      MSE_FAIL(GODEC_ERR_CUDA, "copy of the label rows failed");
+  }
+  if (cudaMemcpyAsync(dinvD, invD.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    MSE_FAIL(GODEC_ERR_CUDA, "copy failed");
+  // one context per block, over its gathered rows
+  for (int j = 0; j < k; ++j) {
+    godec_params q{};
+    q.m = (int64_t)rows[j].size();
+    q.n = p;
+    q.ldx = ldr;
+    q.r = ranks[j];
+    q.q = 0;
+    q.k = 1;
+    q.tol = -1.0;
+    q.max_iter = 1 << 30;
+    q.precision = GODEC_PREC_FP32;
+    if ((status = init_ctx(&ctx[j], &q, N[j], nullptr, stream, false))) {
+      char why2[200];
+      snprintf(why2, sizeof(why2), "%s", g_static_err);
+      MSE_FAIL(status, "block %d: %s", j, why2);
+    }
+  }
+  launch_mse_init(X, ldx, dinvD, n, p, R, ldr, nsm, st);
+  int64_t nnz_cur = 0;
+  std::vector<int> r_eff(ranks, ranks + k);
+  for (int t = 0; t < iters; ++t) {
+    for (int j = 0; j < k; ++j) {
+      godec_ctx* c = ctx[j];
+      const int64_t nr = (int64_t)rows[j].size();
+      launch_mse_gather(R, ldr, drows[j], nr, p, X, ldx, dinvD, t == 0 ? nullptr : U[j], r_eff[j], sg[j], V[j],
+                        r_eff[j], r_eff[j], N[j], ldr, nsm, st);
+      launch_fill_zero(c->A1_orig, (size_t)p * c->RP * sizeof(float), st);
+      launch_pad_copy(A1s + ((size_t)t * k + j) * p * r_stride, p, ranks[j], r_stride, c->A1_orig, c->RP, st);
+      if ((status = reset_state(c)) || (status = run_iterations(c, 1, -1.0)))
+        MSE_FAIL(status, "block %d: %s", j, c->err);
+      int32_t re = 0;
+      if ((status = godec_get_L(c, U[j], sg[j], V[j], &re))) MSE_FAIL(status, "block %d: %s", j, c->err);
+      r_eff[j] = re;
+      launch_mse_scatter(R, ldr, drows[j], nr, p, N[j], ldr, U[j], re, sg[j], V[j], re, re, nsm, st);
+    }
+    // S-step on X - sum L^i = R + S_old
+    launch_sparse_axpy(R, ldr, p, Si[0], Sv[0], nnz_cur, 1.f, nsm, st);
+    int64_t got = 0;
+    godec_status hs = godec_hard_threshold(R, n, p, ldr, K, Si[0], Sv[0], std::max<int64_t>(K, 1), &got, stream);
+    if (hs) {
+      char why2[200];
+      snprintf(why2, sizeof(why2), "%s", g_static_err);
+      MSE_FAIL(hs, "S-step: %s", why2);
+    }
+    nnz_cur = got;
+    launch_sparse_axpy(R, ldr, p, Si[0], Sv[0], nnz_cur, -1.f, nsm, st);
+    launch_sumsq(R, n, p, ldr, dsum, nsm, st);
+    double obj = 0.0;
+    if (cudaMemcpyAsync(&obj, dsum, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+      MSE_FAIL(GODEC_ERR_CUDA, "objective read-back failed");
+    if (history) history[t] = obj;
+  }
+  if (C) {
+    launch_fill_zero(C, (size_t)k * r_stride * p * sizeof(float), st);
+    for (int j = 0; j < k; ++j) launch_transpose(V[j], p, r_eff[j], r_eff[j], C + (size_t)j * r_stride * p, p, st);
+  }
+  if (Lsum) {
+    launch_sub(X, ldx, R, ldr, n, p, Lsum, ldl, nsm, st);
+    launch_sparse_axpy(Lsum, ldl, p, Si[0], Sv[0], nnz_cur, -1.f, nsm, st);
+  }
+  if (nnz) *nnz = nnz_cur;
+  if (S_idx && S_val && S_cap >= nnz_cur && nnz_cur > 0) {
+    cudaMemcpyAsync(S_idx, Si[0], (size_t)nnz_cur * 8, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(S_val, Sv[0], (size_t)nnz_cur * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) MSE_FAIL(GODEC_ERR_CUDA, "%s", cudaGetErrorString(e));
+  const bool short_cap = (S_idx || S_val) && S_cap < nnz_cur;
+  cleanup();
+#undef MSE_FAIL
+  if (short_cap) {
+    snprintf(g_static_err, sizeof(g_static_err), "godec_mse_train: S_cap %lld < nnz %lld", (long long)S_cap,
+             (long long)nnz_cur);
+    return GODEC_ERR_ARG;
+  }
+  return GODEC_OK;
+}
+
 godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, int32_t cap, int32_t* n_stages) {
   if (!c || !c->greb) {
     if (c) fail(c, GODEC_ERR_STATE, "godec_grebsmo_run needs a context from godec_grebsmo_init");

@@ -351,6 +351,21 @@ void launch_rmul(const float* A, const float* B, int ld, int r, double* out, int
 void launch_lingo_g(const float* T1, const float* T2, int ld, const double* Vr, const float* sigma, int d, int r,
                     double* out, cudaStream_t st);
 
+// MSE training (k_mse.cu): gather of a label's rows of the residual plus its block, scatter
+// back minus the new block, sparse axpy, the initial residual, X - R.
+void launch_mse_gather(const float* R, int64_t ldr, const int64_t* rows, int64_t nrows, int64_t p, const float* X,
+                       int64_t ldx, const float* invD, const float* U, int64_t ldu, const float* sigma, const float* V,
+                       int64_t ldv, int r, float* N, int64_t ldn, int nsm, cudaStream_t st);
+void launch_mse_scatter(float* R, int64_t ldr, const int64_t* rows, int64_t nrows, int64_t p, const float* N,
+                        int64_t ldn, const float* U, int64_t ldu, const float* sigma, const float* V, int64_t ldv,
+                        int r, int nsm, cudaStream_t st);
+void launch_sparse_axpy(float* R, int64_t ldr, int64_t p, const int64_t* idx, const float* val, int64_t nnz,
+                        float alpha, int nsm, cudaStream_t st);
+void launch_mse_init(const float* X, int64_t ldx, const float* invD, int64_t rows, int64_t p, float* R, int64_t ldr,
+                     int nsm, cudaStream_t st);
+void launch_sub(const float* X, int64_t ldx, const float* R, int64_t ldr, int64_t rows, int64_t p, float* out,
+                int64_t ldo, int nsm, cudaStream_t st);
+
 // L (m x n, row stride ldl) = U diag(sigma) V^T, U m x r (ldu), V n x r (ldv) (k_dense.cu).
 void launch_lowrank_dense(const float* U, int64_t ldu, const float* sigma, const float* V, int64_t ldv, int64_t m,
                           int64_t n, int r, float* L, int64_t ldl, cudaStream_t st);
