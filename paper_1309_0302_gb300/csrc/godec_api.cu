@@ -2017,6 +2017,7 @@ godec_status godec_mse_train(const float* X, int64_t n, int64_t p, int64_t ldx, 
     }
     nnz_cur = got;
     launch_sparse_axpy(R, ldr, p, Si[0], Sv[0], nnz_cur, -1.f, nsm, st);
+    launch_fill_zero(dsum, sizeof(double), st);   // the sum accumulates atomically
     launch_sumsq(R, n, p, ldr, dsum, nsm, st);
     double obj = 0.0;
     if (cudaMemcpyAsync(&obj, dsum, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)

@@ -380,6 +380,7 @@ void launch_pad_copy(const float* src, int64_t rows, int cols, int64_t lds, floa
                      cudaStream_t st);
 void launch_unpad_copy(const float* src, int64_t rows, int RP, float* dst, int cols,
                        cudaStream_t st);
+// *out += sum of X^2 (float64 atomics: clear *out first for a fresh sum)
 void launch_sumsq(const float* X, int64_t m, int64_t n, int64_t ldx, double* out, int nsm,
                   cudaStream_t st);
 void launch_sort_coo(long long* idx, float* val, long long nnz, void* scratch, size_t scratch_bytes,
