@@ -2017,7 +2017,7 @@ godec_status godec_mse_train(const float* X, int64_t n, int64_t p, int64_t ldx, 
     }
     nnz_cur = got;
     launch_sparse_axpy(R, ldr, p, Si[0], Sv[0], nnz_cur, -1.f, nsm, st);
-    launch_fill_zero(dsum, sizeof(double), st);   // the sum accumulates atomically
+    cudaMemsetAsync(dsum, 0, sizeof(double), st);   // the sum accumulates atomically
     launch_sumsq(R, n, p, ldr, dsum, nsm, st);
     double obj = 0.0;
     if (cudaMemcpyAsync(&obj, dsum, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
@@ -2025,7 +2025,7 @@ godec_status godec_mse_train(const float* X, int64_t n, int64_t p, int64_t ldx, 
     if (history) history[t] = obj;
   }
   if (C) {
-    launch_fill_zero(C, (size_t)k * r_stride * p * sizeof(float), st);
+    cudaMemsetAsync(C, 0, (size_t)k * r_stride * p * sizeof(float), st);
     for (int j = 0; j < k; ++j) launch_transpose(V[j], p, r_eff[j], r_eff[j], C + (size_t)j * r_stride * p, p, st);
   }
   if (Lsum) {

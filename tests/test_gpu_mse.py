@@ -86,7 +86,7 @@ def test_mse_matches_oracle(n, p, k, r, K, iters):
     h = np.array(out["history"])
     eh = np.max(np.abs(h - np.array(ref["history"])) / np.array(ref["history"]))
     print(f"mse {n}x{p}: sum of blocks {eL:.2e}, |S| {idx.size} (oracle {ridx.size}), subspace sines "
-          f"{max(angles):.2e}, history {eh:.2e}")
+          f"{max(angles):.2e}, history {eh:.2e}: {h.tolist()} vs {ref['history']}")
     assert eL <= 1e-5
     assert np.array_equal(idx, ridx)
     assert np.linalg.norm(val - ref["S"].ravel()[ridx]) <= 1e-5 * np.linalg.norm(ref["S"].ravel()[ridx])
