@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the C1/C3/C4/C5 timing records")
-    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched", "c1"], default=None,
+    ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched", "c1",
+                                         "grebsmo", "naive", "lingodec", "mse"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
@@ -284,7 +285,8 @@ def run_gb300(args, ws, rank, local):
         line["e2e"] = e2e(args, d)
     if rank == 0 and ws == 1 and not args.no_forms:
         line["forms"] = {"c1": form_c1(), "c3_precision": form_c3(), "c4_batched": form_c4(),
-                         "c5_differentiated": form_c5()}
+                         "c5_differentiated": form_c5(), "grebsmo": form_grebsmo(), "naive": form_naive(),
+                         "lingodec": form_lingodec(), "mse": form_mse()}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, times, cores = oracle_steps(d["X"], d["A1"], BASELINE_ITERS, 0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -500,6 +502,123 @@ def form_c5():
             "forward_algorithmic_bytes": T * 3 * 4.0 * m * n, "clocks_forward": ck_f, "clocks_backward": ck_b}
 
 
+def form_grebsmo():
+    """GreBsmo (Sec. 3.2.1) on the video-shaped 76800 x 1000 matrix of the precision-form
+    workload: rank increments of 1 up to 3, 10 inner steps per stage, lambda = 0.15 (the blob
+    foreground goes to S); time to the stop, per inner step."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    d = synth.config_c3()
+    X = torch.from_numpy(d["X"]).cuda()
+    m, n = d["X"].shape
+    om = torch.from_numpy(synth.gaussian(1309, "bench/greb/omega", (3, n, 7)).astype(np.float32)).cuda()
+    st = torch.cuda.current_stream()
+    box = {}
+
+    def run():
+        g = G.GreBsmo(X, om, 0.15, 1, 10, 0.0, 3, oversample=6, q_inc=4, s_cap=16_000_000)
+        box["r"], box["errs"] = g.run()
+        box["iter"] = g.info()["iter"]
+        box["nnz"] = g.info()["nnz"]
+        g.close()
+
+    run()
+    ms, ck = _timed(st, run, 3)
+    return {"workload": "76800 x 1000 video-shaped synthetic, lambda 0.15, dr 1, K 10, r_max 3, "
+                        "random-projection increments (6 extra columns, 4 power steps)",
+            "ms_to_stop_incl_context": ms, "inner_steps": box["iter"], "ms_per_inner_step": ms / box["iter"],
+            "rank": box["r"], "stage_errors": box["errs"], "support_of_S": box["nnz"], "clocks": ck}
+
+
+def form_naive():
+    """Naive GoDec (eq. raw_lss, truncated-SVD L-step) at the 10000 x 10000, r = 50 workload,
+    2 power steps per L-step: iterations/s beside the BRP form's."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    d = synth.lowrank_sparse(M, N, R, K_CARD, -20.0, 20.0, 1e-2, replica_seed(0), "c2")
+    X = torch.from_numpy(d["X"]).cuda()
+    p = G.naive_columns(M, N, R)
+    om = torch.from_numpy(synth.gaussian(1309, "bench/naive/omega", (N, p)).astype(np.float32)).cuda()
+    st = torch.cuda.current_stream()
+    g = G.NaiveGoDec(X, om, R, K_CARD, q=2, tol=-1.0, max_iter=1 << 30)
+    g.iterate(3)
+    ms, ck = _timed(st, lambda: g.iterate(10), 3)
+    ms /= 10
+    rel = g.info()["rel_err"]
+    g.close()
+    return {"workload": "10000 x 10000, rank 50, 1 % sparse, r = 50, subspace iteration over 58 columns, "
+                        "2 power steps per L-step", "ms_per_iter": ms, "iterations_per_s": 1e3 / ms,
+            "rel_err_after_16_iterations": rel, "clocks": ck}
+
+
+def form_lingodec():
+    """LinGoDec (Sec. 4.3) on the paper's synthetic recipe at 20000 users x 5000 items,
+    d = 50 item features, rank 10, 5 % +-1 outliers: iterations/s."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    m, n, dd, r = 20000, 5000, 50, 10
+    W = synth.gaussian(1309, "bench/lingo/Wa", (m, r)) @ synth.gaussian(1309, "bench/lingo/Wb", (r, dd))
+    F = synth.gaussian(1309, "bench/lingo/F", (n, dd))
+    X = W @ F.T
+    pos = synth.sample_positions(1309, "bench/lingo/S", m * n, int(0.05 * m * n))
+    sg = np.where(synth.uniform(1309, "bench/lingo/sg", (pos.size,), 0.0, 1.0) < 0.5, -1.0, 1.0)
+    X.ravel()[pos] += sg
+    X += 1e-3 * synth.gaussian(1309, "bench/lingo/G", (m, n))
+    Xg = torch.from_numpy(X.astype(np.float32)).cuda()
+    Fg = torch.from_numpy(F.astype(np.float32)).cuda()
+    st = torch.cuda.current_stream()
+    g = G.LinGoDec(Xg, Fg, r, 0.25, s_cap=int(0.06 * m * n))
+    g.iterate(2)
+    ms, ck = _timed(st, lambda: g.iterate(10), 2)
+    ms /= 10
+    rel = g.info()["rel_err"]
+    g.close()
+    return {"workload": "20000 x 5000, d = 50, rank 10, 5 % +-1 outliers, lambda 0.25", "ms_per_iter": ms,
+            "iterations_per_s": 1e3 / ms, "rel_err": rel, "clocks": ck}
+
+
+def form_mse():
+    """MSE training (Algorithm 4) on synthetic multi-label data: 20000 samples x 2000
+    features, 8 labels (each sample carries each with probability 0.35), rank 5 per label,
+    K = 0.5 % outliers; time per outer iteration."""
+    import numpy as np
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    n, p, k, r = 20000, 2000, 8, 5
+    Y = (synth.uniform(1309, "bench/mse/labels", (n, k), 0.0, 1.0) < 0.35).astype(np.int32)
+    Y[Y.sum(axis=1) == 0, 0] = 1
+    X = np.zeros((n, p))
+    for i in range(k):
+        B = np.linalg.qr(synth.gaussian(1309, f"bench/mse/basis{i}", (p, r)))[0].T
+        rows = np.flatnonzero(Y[:, i])
+        X[rows] += synth.gaussian(1309, f"bench/mse/coef{i}", (rows.size, r)) @ B * 3.0
+    K = int(0.005 * n * p)
+    pos = synth.sample_positions(1309, "bench/mse/out", n * p, K)
+    X.ravel()[pos] += synth.uniform(1309, "bench/mse/mag", (K,), 5.0, 10.0)
+    X += 1e-3 * synth.gaussian(1309, "bench/mse/noise", (n, p))
+    Xg = torch.from_numpy(X.astype(np.float32)).cuda()
+    iters = 4
+    A1s = torch.from_numpy(synth.gaussian(1309, "bench/mse/A1", (iters, k, p, r)).astype(np.float32)).cuda()
+    st = torch.cuda.current_stream()
+    G.mse_train(Xg, Y, [r] * k, K, 1, A1s[:1])
+    box = {}
+    ms, ck = _timed(st, lambda: box.update(out=G.mse_train(Xg, Y, [r] * k, K, iters, A1s)), 1)
+    return {"workload": "20000 x 2000, 8 labels, rank 5 each, 0.5 % outliers, q = 0 BRP blocks",
+            "ms_per_outer_iteration_incl_setup": ms / iters, "outer_iterations": iters,
+            "objective_history": box["out"]["history"], "clocks": ck}
+
+
 def run_kernel_case(args):
     """Small cases for ncu captures: the streaming product on a size x size matrix
     (above the L2 size for size >= 6000), or two full iterations at size x size, r = 50."""
@@ -516,8 +635,9 @@ def run_kernel_case(args):
         f = G.mul_ZB if args.kernel == "product" else G.mul_ZtC
         for _ in range(3):
             f(Z, B)
-    elif args.kernel in ("backward", "precision", "batched", "c1"):
-        f = {"backward": form_c5, "precision": form_c3, "batched": form_c4, "c1": form_c1}[args.kernel]
+    elif args.kernel in ("backward", "precision", "batched", "c1", "grebsmo", "naive", "lingodec", "mse"):
+        f = {"backward": form_c5, "precision": form_c3, "batched": form_c4, "c1": form_c1, "grebsmo": form_grebsmo,
+             "naive": form_naive, "lingodec": form_lingodec, "mse": form_mse}[args.kernel]
         print(json.dumps(f(), indent=1))
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")

@@ -842,8 +842,6 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   }
   __syncthreads();
   mm_1024(X1, W, X2, r, false);                     // X2 = reorthonormalised U
-  const double inv_e = 1.0 / (double)(2 * a.q + 1);
-  const double lsc = (a.Pi ? ctl->m_logscale : 0.0) + log((double)s_scale);
   for (int e = tid; e < RP * RP; e += SVD_THREADS) {
     const int i = e / RP, j = e % RP;
     const bool in = i < r && j < r;
@@ -852,8 +850,12 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
     a.Vprev[e] = in ? V[i][j] : (i == j ? 1.f : 0.f);
   }
   if (tid < RP) {
+    // float64 only in the two warps that root the singular values (GB300 issues a warp's
+    // float64 instruction over many cycles)
     float sv = 0.f;
     if (tid < r) {
+      const double inv_e = 1.0 / (double)(2 * a.q + 1);
+      const double lsc = (a.Pi ? ctl->m_logscale : 0.0) + log((double)s_scale);
       const float sc = s[order[tid]];
       sv = (sc > 0.f) ? (float)exp((log((double)sc) + lsc) * inv_e) : 0.f;
     }
