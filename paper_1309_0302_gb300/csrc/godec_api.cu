@@ -644,7 +644,7 @@ void enqueue_naive_lstep(godec_ctx* c) {
   cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);
   const int* ab = &c->ctl->abort;   // an abandoned iteration leaves U, V and the basis as they were
   launch_rmul(R2m, R1, RP, p, c->rf_core, 0, nullptr, st, ab);
-  launch_svd_small(c->rf_core, p, r, c->rf_U, c->sigma, c->rf_V, st, ab);
+  launch_svd_small(c->rf_core, p, r, c->rf_U, c->sigma, c->rf_V, st, ab, true);
   launch_tall_small_d(c->Qa, RP, p, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st, ab);
   launch_tall_small_d(c->Qb, RP, p, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st, ab);
   launch_lsplit(c->U, c->V, c->sigma, m, n, RP, r, c->ctl->zscale, c->LA, c->LB, st, ab);
@@ -1616,7 +1616,7 @@ static void greb_increment(godec_ctx* c, int ri, int add, int stage) {
   greb_apply_D(c, ri, p, c->Qb, c->P);                               // Y = D B = Qa R2m R1
   cqr2(c, c->P, m, p, RP, c->Qa, R1, T1, R2m, T2);
   launch_rmul(R2m, R1, RP, p, c->rf_core, 0, nullptr, st);
-  launch_svd_small(c->rf_core, p, add, c->rf_U, c->cs_ref + 0, c->rf_V, st);   // right vectors of Y
+  launch_svd_small(c->rf_core, p, add, c->rf_U, c->cs_ref + 0, c->rf_V, st, nullptr, true);   // right vectors of Y
   launch_tall_small_d(c->Qb, RP, p, c->rf_V, add, 0, add, n, 1.f, 0.f, c->V + ri, RP, st);
 }
 
@@ -1806,7 +1806,7 @@ static void lingo_lstep(godec_ctx* c) {
   final_cqr2(c, m, g64(c, 0), c->Rfin, c->Rfin + 2 * rr, c->Q1, g64(c, 2), nullptr);   // Y Qf = Qy Rb Ra
   c->r = r;
   launch_rmul(c->Rfin + 2 * rr, c->Rfin, RP, d, c->rf_core, 0, nullptr, st, ab);
-  launch_svd_small(c->rf_core, d, r, c->rf_U, c->sigma, c->rf_V, st, ab);
+  launch_svd_small(c->rf_core, d, r, c->rf_U, c->sigma, c->rf_V, st, ab, true);
   launch_tall_small_d(c->Q1, RP, d, c->rf_U, r, 0, r, m, 1.f, 0.f, c->U, RP, st, ab);
   launch_tall_small_d(c->Q2, RP, d, c->rf_V, r, 0, r, n, 1.f, 0.f, c->V, RP, st, ab);
 }
@@ -2126,7 +2126,7 @@ godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, 
     launch_fill_zero(c->U, (size_t)m * RP * sizeof(float), st);
     launch_fill_zero(c->V, (size_t)n * RP * sizeof(float), st);
     launch_fill_zero(c->sigma, (size_t)RP * sizeof(float), st);
-    launch_svd_small(c->rf_core, ri, ri, c->rf_U, c->sigma, c->rf_V, st);
+    launch_svd_small(c->rf_core, ri, ri, c->rf_U, c->sigma, c->rf_V, st, nullptr, true);
     launch_tall_small_d(c->Q1, RP, ri, c->rf_U, ri, 0, ri, m, 1.f, 0.f, c->U, RP, st);
     launch_tall_small_d(c->Qb, RP, ri, c->rf_V, ri, 0, ri, n, 1.f, 0.f, c->V, RP, st);
     (void)rr;

@@ -321,8 +321,10 @@ void launch_to_half(const float* src, int64_t rows, int64_t cols, int64_t lds, v
 cudaError_t prepare_refine_kernels();
 void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, const float* Rb2, int ld,
                         const double* C, int r, double* core, cudaStream_t st, const int* skip = nullptr);
+// SVD of an n x n float64 matrix (n <= 64), leading r triplets, computed in float64 or,
+// with f32, in float32 (one-sided Jacobi either way).
 void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st,
-                      const int* skip = nullptr);
+                      const int* skip = nullptr, bool f32 = false);
 
 // GreBsmo (k_grebsmo.cu): the S-step's plan (one candidate pass at the key of lambda + 1
 // ulp), the soft-threshold emit S = R - lambda sgn R over every candidate, column norms

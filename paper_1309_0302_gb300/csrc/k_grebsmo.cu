@@ -72,26 +72,32 @@ __global__ void __launch_bounds__(SOFT_THREADS) k_emit_soft(SoftEmitArgs a) {
 __global__ void k_colnorm(const float* __restrict__ W, const double* __restrict__ g64, int64_t n, int RP, int r,
                           float* __restrict__ Vh, float* __restrict__ sigma, const int* skip) {
   if (block_skip(skip)) return;
-  const int64_t total = n * RP;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(e % RP);
-    const double s = l < r ? sqrt(fmax(g64[(size_t)l * RP + l], 0.0)) : 0.0;
-    Vh[e] = s > 0.0 ? (float)((double)W[e] / s) : 0.f;
-    if (e < RP) sigma[e] = (float)(e < r ? sqrt(fmax(g64[(size_t)e * RP + e], 0.0)) : 0.0);
+  // the column norms and their inverses once per block, in float32 (float64 arithmetic on
+  // every element would queue on GB300's slow float64 pipe)
+  __shared__ float inv[kMaxRP];
+  if (threadIdx.x < RP) {
+    const int l = threadIdx.x;
+    const float s = l < r ? sqrtf(fmaxf((float)g64[(size_t)l * RP + l], 0.f)) : 0.f;
+    inv[l] = s > 0.f ? 1.f / s : 0.f;
+    if (blockIdx.x == 0) sigma[l] = s;
   }
+  __syncthreads();
+  const int64_t total = n * RP;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    Vh[e] = W[e] * inv[e % RP];
 }
 
-// out (r x r, float64, row-major) = A B, or (A B)^T with trans, then row i times rowscale[i];
-// A, B float32 with stride ld.
+// out (r x r, stored as float64, row-major) = A B, or (A B)^T with trans, then row i times
+// rowscale[i]; A, B float32 with stride ld, accumulated in float32.
 __global__ void k_rmul(const float* __restrict__ A, const float* __restrict__ B, int ld, int r, double* __restrict__ out,
                        int trans, const float* __restrict__ rowscale, const int* skip) {
   if (block_skip(skip)) return;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, j = e % r;
-    double s = 0.0;
-    for (int k = 0; k < r; ++k) s += (double)A[i * ld + k] * (double)B[k * ld + j];
+    float s = 0.f;   // float32 accumulation: the factors are float32 and r <= 64
+    for (int k = 0; k < r; ++k) s = fmaf(A[i * ld + k], B[k * ld + j], s);
     const int oi = trans ? j : i, oj = trans ? i : j;
-    out[oi * r + oj] = rowscale ? s * (double)rowscale[oi] : s;
+    out[oi * r + oj] = rowscale ? (double)(s * rowscale[oi]) : (double)s;
   }
 }
 

@@ -78,23 +78,31 @@ constexpr double kJacobiTol = 1e-14;
 // Outputs the r leading singular triplets, descending: U[:, :r] (n x r, float64, stride
 // r), sigma[:r] (float32), V[:, :r] (n x r, stride r).  Launched with 32 ceil(n/2) threads.
 constexpr double kJacobiQuad = 1e-7;
+// float32: a length-64 dot product bottoms out near sqrt(64) 2^-24; a sweep whose largest
+// |cos| is below 3e-4 makes the next one rotate nothing (as in the core SVD)
+constexpr float kJacobiTolF = 4e-6f;
+constexpr double kJacobiQuadF = 3e-4;
 
+// T = double, or float for the larger cores of the subspace iterations (GB300 issues a
+// warp's float64 instruction over many cycles: a float64 sweep over 58 columns costs
+// hundreds of microseconds); float32 rotates down to kJacobiTolF.
+template <typename T>
 __global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A, int n, int r, double* __restrict__ Uo,
                                                     float* __restrict__ sigma, double* __restrict__ Vo,
                                                     const int* skip) {
   if (block_skip(skip)) return;
-  extern __shared__ double smd[];   // W, V: 2 x 64 x 65 doubles (dynamic)
-  double (*W)[kMaxRP + 1] = reinterpret_cast<double (*)[kMaxRP + 1]>(smd);
-  double (*V)[kMaxRP + 1] = W + kMaxRP;
-  __shared__ double nrm[kMaxRP];
+  extern __shared__ double smd[];   // W, V: 2 x 64 x 65 values (dynamic)
+  T (*W)[kMaxRP + 1] = reinterpret_cast<T (*)[kMaxRP + 1]>(smd);
+  T (*V)[kMaxRP + 1] = W + kMaxRP;
+  __shared__ T nrm[kMaxRP];
   __shared__ int order[kMaxRP];
   __shared__ int s_rot;
   __shared__ unsigned long long s_dmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e % n;
-    W[i][j] = A[e];
-    V[i][j] = (i == j) ? 1.0 : 0.0;
+    W[i][j] = (T)A[e];
+    V[i][j] = (i == j) ? (T)1 : (T)0;
   }
   const int np = (n + 1) & ~1, npairs = np / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
@@ -120,9 +128,9 @@ __global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A
           q = t;
         }
         if (q < n) {
-          double a = 0.0, b = 0.0, g = 0.0;
+          T a = 0, b = 0, g = 0;
           for (int i = lane; i < n; i += 32) {
-            const double wp = W[i][p], wq = W[i][q];
+            const T wp = W[i][p], wq = W[i][q];
             a += wp * wp;
             b += wq * wq;
             g += wp * wq;
@@ -134,12 +142,13 @@ __global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A
           }
           // rotate unless the pair is orthogonal to the rounding level of a length-64 dot
           // product in float64 (a tighter test never ends: rounding keeps |g| near it)
-          if (fabs(g) > kJacobiTol * sqrt(a * b) && g != 0.0) {
-            const double zeta = (b - a) / (2.0 * g);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const T tol = sizeof(T) == 8 ? (T)kJacobiTol : (T)kJacobiTolF;
+          if (fabs(g) > tol * sqrt(a * b) && g != (T)0) {
+            const T zeta = (b - a) / (2 * g);
+            const T t = (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt(1 + zeta * zeta));
+            const T cs = 1 / sqrt(1 + t * t), sn = cs * t;
             for (int i = lane; i < n; i += 32) {
-              const double wp = W[i][p], wq = W[i][q], vp = V[i][p], vq = V[i][q];
+              const T wp = W[i][p], wq = W[i][q], vp = V[i][p], vq = V[i][q];
               W[i][p] = cs * wp - sn * wq;
               W[i][q] = sn * wp + cs * wq;
               V[i][p] = cs * vp - sn * vq;
@@ -147,18 +156,18 @@ __global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A
             }
             if (lane == 0) {
               s_rot = 1;
-              atomicMax(&s_dmax, (unsigned long long)__double_as_longlong(fabs(g) / sqrt(a * b)));
+              atomicMax(&s_dmax, (unsigned long long)__double_as_longlong((double)(fabs(g) / sqrt(a * b))));
             }
           }
         }
       }
       __syncthreads();
     }
-    if (!s_rot || __longlong_as_double((long long)s_dmax) < kJacobiQuad) break;
+    if (!s_rot || __longlong_as_double((long long)s_dmax) < (sizeof(T) == 8 ? kJacobiQuad : kJacobiQuadF)) break;
   }
   // column norms, descending order
   for (int i = tid; i < n; i += nt) {
-    double sm = 0.0;
+    T sm = 0;
     for (int k = 0; k < n; ++k) sm += W[k][i] * W[k][i];
     nrm[i] = sqrt(sm);
   }
@@ -172,9 +181,9 @@ __global__ void __launch_bounds__(1024) k_svd_small(const double* __restrict__ A
   for (int e = tid; e < n * r; e += nt) {
     const int i = e / r, j = e % r;
     const int col = order[j];
-    const double sv = nrm[col];
-    Uo[i * r + j] = sv > 0.0 ? W[i][col] / sv : 0.0;
-    Vo[i * r + j] = V[i][col];
+    const double sv = (double)nrm[col];
+    Uo[i * r + j] = sv > 0.0 ? (double)W[i][col] / sv : 0.0;
+    Vo[i * r + j] = (double)V[i][col];
   }
   for (int j = tid; j < r; j += nt) sigma[j] = (float)nrm[order[j]];
 }
@@ -199,7 +208,8 @@ constexpr size_t kSvdSmem = 2 * kMaxRP * (kMaxRP + 1) * sizeof(double);
 
 cudaError_t prepare_refine_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_refine_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCoreSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSvdSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSvdSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSvdSmem);
   return e;
 }
 
@@ -209,8 +219,9 @@ void launch_refine_core(const float* Ra1, const float* Ra2, const float* Rb1, co
 }
 
 void launch_svd_small(const double* A, int n, int r, double* U, float* sigma, double* V, cudaStream_t st,
-                      const int* skip) {
-  k_svd_small<<<1, 32 * ((n + 1) / 2), kSvdSmem, st>>>(A, n, r, U, sigma, V, skip);
+                      const int* skip, bool f32) {
+  if (f32) k_svd_small<float><<<1, 32 * ((n + 1) / 2), kSvdSmem, st>>>(A, n, r, U, sigma, V, skip);
+  else k_svd_small<double><<<1, 32 * ((n + 1) / 2), kSvdSmem, st>>>(A, n, r, U, sigma, V, skip);
 }
 
 }  // namespace godec
