@@ -78,10 +78,11 @@ constexpr double kJacobiTol = 1e-14;
 // Outputs the r leading singular triplets, descending: U[:, :r] (n x r, float64, stride
 // r), sigma[:r] (float32), V[:, :r] (n x r, stride r).  Launched with 32 ceil(n/2) threads.
 constexpr double kJacobiQuad = 1e-7;
-// float32: a length-64 dot product bottoms out near sqrt(64) 2^-24; a sweep whose largest
-// |cos| is below 3e-4 makes the next one rotate nothing (as in the core SVD)
-constexpr float kJacobiTolF = 4e-6f;
-constexpr double kJacobiQuadF = 3e-4;
+// float32: a length-64 dot product bottoms out near sqrt(64) 2^-24, so pairs are rotated
+// down to 2e-6; the sweeps go on until one rotates nothing (no early stop on quadratic
+// convergence: the singular vectors feed least-squares factors whose error reaches S)
+constexpr float kJacobiTolF = 2e-6f;
+constexpr double kJacobiQuadF = 0.0;
 
 // T = double, or float for the larger cores of the subspace iterations (GB300 issues a
 // warp's float64 instruction over many cycles: a float64 sweep over 58 columns costs
