@@ -1889,6 +1889,28 @@ godec_status godec_lingodec_get_W(godec_ctx* c, float* W) {
 }
 
 // ---- MSE training (Sec. 4.2.1, Algorithm 4) ----------------------------------------------
+// One q = 0 BRP L-step of Algorithm 1 on the context's (re-gathered) matrix with test matrix
+// A1 (first r columns, row stride lda): refresh the working copies, set A1, run the L-step
+// eagerly (no S-step, no graph), leave the factors in U, sigma, V.
+static godec_status mse_block_brp(godec_ctx* c, const float* A1, int lda) {
+  cudaStream_t st = c->st;
+  const int64_t m = c->p.m, n = c->p.n;
+  launch_reset_iter(c->ctl, st);
+  launch_zscale(c->X, m, n, c->p.ldx, &c->ctl->zmax_bits, c->ctl->zscale, c->nsm, st);
+  launch_scale_copy(c->X, m, n, c->p.ldx, c->Z, c->ldz, c->ctl->zscale, c->nsm, st);
+  launch_transpose(c->X, m, n, c->p.ldx, c->Zt, c->ldzt, st, c->ctl->zscale);
+  launch_fill_zero(c->A1, (size_t)n * c->RP * sizeof(float), st);
+  launch_pad_copy(A1, n, c->p.r, lda, c->A1, c->RP, st);
+  launch_split_t(c->A1, n, c->RP, bt2(c, 2), c->ldb, c->cs, st);
+  c->r = c->p.r;
+  enqueue_lstep(c, false);
+  Ctl h;
+  if (godec_status s = read_ctl(c, &h)) return s;
+  if (h.abort) return fail(c, GODEC_ERR_STATE, "block L-step abandoned (rank %s%s)", h.rank_drop ? "drop" : "ok",
+                           h.nonfinite ? ", non-finite values" : "");
+  return GODEC_OK;
+}
+
 // Block coordinate descent over the label blocks L^1 .. L^k and S, with R = X - sum L^i - S
 // kept densely.  Block i: N = R[Omega_i] + L^i[Omega_i] gathered into its own buffer, whose
 // GoDec context (q = 0) gives the q = 0 BRP of Algorithm 4 with the test matrix of this step
@@ -1997,12 +2019,12 @@ godec_status godec_mse_train(const float* X, int64_t n, int64_t p, int64_t ldx, 
       const int64_t nr = (int64_t)rows[j].size();
       launch_mse_gather(R, ldr, drows[j], nr, p, X, ldx, dinvD, t == 0 ? nullptr : U[j], r_eff[j], sg[j], V[j],
                         r_eff[j], r_eff[j], N[j], ldr, nsm, st);
-      launch_fill_zero(c->A1_orig, (size_t)p * c->RP * sizeof(float), st);
-      launch_pad_copy(A1s + ((size_t)t * k + j) * p * r_stride, p, ranks[j], r_stride, c->A1_orig, c->RP, st);
-      if ((status = reset_state(c)) || (status = run_iterations(c, 1, -1.0)))
+      if ((status = mse_block_brp(c, A1s + ((size_t)t * k + j) * p * r_stride, r_stride)))
         MSE_FAIL(status, "block %d: %s", j, c->err);
-      int32_t re = 0;
-      if ((status = godec_get_L(c, U[j], sg[j], V[j], &re))) MSE_FAIL(status, "block %d: %s", j, c->err);
+      const int re = c->r;
+      launch_unpad_copy(c->U, c->p.m, c->RP, U[j], re, st);
+      launch_unpad_copy(c->V, c->p.n, c->RP, V[j], re, st);
+      cudaMemcpyAsync(sg[j], c->sigma, (size_t)re * sizeof(float), cudaMemcpyDeviceToDevice, st);
       r_eff[j] = re;
       launch_mse_scatter(R, ldr, drows[j], nr, p, N[j], ldr, U[j], re, sg[j], V[j], re, re, nsm, st);
     }
