@@ -297,14 +297,16 @@ void apply(godec_ctx* c, const float* P, int64_t rows, const float* T0, const fl
 }
 
 // Exact CholeskyQR2 of c->P (rows x RP) with the first-pass Gram g1: Q = P Ra^{-1} Rb^{-1},
-// written to fin and, if bt2out is set, as the next product's operand.
+// written to fin and, if bt2out is set, as the next product's operand.  With both null the
+// last apply is left out: c->P then holds P Ra^{-1} and Q = c->P Rb^{-1} is never formed
+// (the last chain product: its Rb^{-1} is folded into the core SVD's left factor).
 void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* Rb, float* fin, double* g2,
                 void* bt2out) {
   chol(c, g1, Ra);
   apply(c, c->P, rows, inv_of(c, Ra), inv_of(c, Ra), c->P, c->gscr);
   gram_sum(c, c->gscr, 0, apply_blocks(rows), g2, c->st);
   chol(c, g2, Rb);
-  apply(c, c->P, rows, inv_of(c, Rb), inv_of(c, Rb), fin, nullptr, bt2out);
+  if (fin || bt2out) apply(c, c->P, rows, inv_of(c, Rb), inv_of(c, Rb), fin, nullptr, bt2out);
 }
 
 void slot(godec_ctx* c, SlotLaunch& sl) {
@@ -417,7 +419,7 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       PROF(c, 5, c->side_st,
            launch_rank(g64(c, i), c->r, RP, c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4, c->ctl, c->side_st));
       if (i == last) {   // q = 0: this product is also the last one
-        final_cqr2(c, rows, g64(c, i), c->Rfin + 4 * rr, c->Rfin + 6 * rr, c->Q1, g64(c, nprod + 1), nullptr);
+        final_cqr2(c, rows, g64(c, i), c->Rfin + 4 * rr, c->Rfin + 6 * rr, nullptr, g64(c, nprod + 1), nullptr);
         continue;
       }
       if (fast) {
@@ -444,11 +446,13 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
       float* Ra = c->Rfin + (i == i_q2 ? 0 : 4) * rr;
       float* Rb = Ra + 2 * rr;
-      float* fin = (i == i_q2) ? c->Q2 : c->Q1;
+      // Q1 (the last product's basis) is never formed: U = Q1 Um = P (R^{-1} Um) with the
+      // factor's inverse folded into the core SVD's output
+      float* fin = (i == i_q2) ? c->Q2 : nullptr;
       if (fast) {
         // the lagged normaliser left P almost orthonormal: one CholeskyQR pass
         chol(c, g64(c, i), Ra, kCqr1Ratio);
-        apply(c, c->P, rows, inv_of(c, Ra), inv_of(c, Ra), fin, nullptr, i == i_q2 ? nextB : nullptr);
+        if (i == i_q2) apply(c, c->P, rows, inv_of(c, Ra), inv_of(c, Ra), fin, nullptr, nextB);
         Rb = nullptr;
       } else {
         final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)),
@@ -492,12 +496,18 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
     }
   }
   join_side(c);
-  // r x r core, SVD and singular-value root, then L = (Q1 Um) diag(sigma) (Q2 Vm)^T
+  // r x r core, SVD and singular-value root, then L = (Q1 Um) diag(sigma) (Q2 Vm)^T with
+  // Q1 Um = P (Rl^{-1} Um), Rl the last factor applied to P (Ra after one CholeskyQR pass,
+  // Rb after two): the SVD kernel returns Rl^{-1} Um; V is formed on the side stream
+  const float* Rb_last = (fast && last != i_rank) ? nullptr : c->Rfin + 6 * rr;
+  const float* Tl = inv_of(c, Rb_last ? Rb_last : c->Rfin + 4 * rr);
   PROF(c, 6, c->st,
-       launch_svd(c->Rfin + 4 * rr, (fast && last != i_rank) ? nullptr : c->Rfin + 6 * rr, rapp_last[0], rapp_last[1], have_pi ? c->Pi : nullptr,
-                  c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st));
-  apply(c, c->Q1, m, c->Um, c->Um, c->U, nullptr);
-  apply(c, c->Q2, n, c->Vm, c->Vm, c->V, nullptr);
+       launch_svd(c->Rfin + 4 * rr, Rb_last, rapp_last[0], rapp_last[1], have_pi ? c->Pi : nullptr,
+                  c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st, Tl));
+  fork_side(c);
+  PROF(c, 3, c->side_st, launch_apply(c->Q2, n, RP, c->Vm, c->Vm, c->V, nullptr, c->ctl, c->side_st));
+  apply(c, c->P, m, c->Um, c->Um, c->U, nullptr);
+  join_side(c);
   if (c->Z16 && !(c->p.flags & GODEC_FLAG_NO_REFINE)) refine(c);
   // operands of the tensor-core residual pass
   PROF(c, 3, c->st, launch_lsplit(c->U, c->V, c->sigma, m, n, RP, c->r, c->ctl->zscale, c->LA, c->LB, c->st));

@@ -213,8 +213,10 @@ struct SlotLaunch {
 };
 void launch_slot(const SlotLaunch& l, cudaStream_t st);
 void launch_rank(const double* g64, int r, int RP, double rank_tol, Ctl* ctl, cudaStream_t st);
+// Um is returned as Tl Um when Tl (upper triangular RP x RP) is given.
 void launch_svd(const float* Ra, const float* Rb, const float* Rapp0, const float* Rapp1, const float* Pi,
-                float* Vprev, int r, int RP, int q, float* Um, float* Vm, float* sigma, Ctl* ctl, cudaStream_t st);
+                float* Vprev, int r, int RP, int q, float* Um, float* Vm, float* sigma, Ctl* ctl, cudaStream_t st,
+                const float* Tl = nullptr);
 
 // --- S-step ---------------------------------------------------------------------
 struct ResidualArgs {

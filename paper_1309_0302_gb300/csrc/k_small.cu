@@ -651,6 +651,7 @@ struct SvdArgs2 {
   float* Vm;
   float* sigma;
   Ctl* ctl;
+  const float* Tl;         // nullable: Um is returned as Tl Um (Tl upper triangular, RP x RP)
 };
 
 constexpr float kSvdQuad = 3e-4f;
@@ -842,6 +843,12 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   }
   __syncthreads();
   mm_1024(X1, W, X2, r, false);                     // X2 = reorthonormalised U
+  if (a.Tl) {
+    load_1024(X1, a.Tl, RP);
+    mm_1024(X1, X2, W, r, false);                   // W = Tl U (Tl's padded block does not mix in)
+    for (int e = tid; e < r * r; e += SVD_THREADS) X2[e / r][e % r] = W[e / r][e % r];
+    __syncthreads();
+  }
   for (int e = tid; e < RP * RP; e += SVD_THREADS) {
     const int i = e / RP, j = e % RP;
     const bool in = i < r && j < r;
@@ -922,8 +929,9 @@ void launch_rank(const double* g64, int r, int RP, double rank_tol, Ctl* ctl, cu
 }
 
 void launch_svd(const float* Ra, const float* Rb, const float* Rapp0, const float* Rapp1, const float* Pi,
-                float* Vprev, int r, int RP, int q, float* Um, float* Vm, float* sigma, Ctl* ctl, cudaStream_t st) {
-  SvdArgs2 a{Ra, Rb, {Rapp0, Rapp1}, Pi, Vprev, r, RP, q, Um, Vm, sigma, ctl};
+                float* Vprev, int r, int RP, int q, float* Um, float* Vm, float* sigma, Ctl* ctl, cudaStream_t st,
+                const float* Tl) {
+  SvdArgs2 a{Ra, Rb, {Rapp0, Rapp1}, Pi, Vprev, r, RP, q, Um, Vm, sigma, ctl, Tl};
   k_svd<<<1, SVD_THREADS, kSmall4, st>>>(a);
 }
 
