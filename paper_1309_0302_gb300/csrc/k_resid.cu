@@ -409,14 +409,16 @@ __global__ void k_lsplit(const float* __restrict__ U, const float* __restrict__ 
     sq[threadIdx.x] = s > 0.f ? sqrtf(s) : 0.f;
   }
   __syncthreads();
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= m + n) return;
-  const bool isU = t < m;
-  const int64_t i = isU ? t : t - m;
-  const float* src = (isU ? U : V) + i * RP;
-  __half2* dst = reinterpret_cast<__half2*>((isU ? A : B) + i * 128);
-#pragma unroll 4
-  for (int l = 0; l < 64; l += 2) {
+  // one warp per row, lane l for the column pair (2l, 2l+1): loads and both 64-byte halves
+  // of the output row are written by coalesced warp-wide accesses
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < m + n; t += nwarps) {
+    const bool isU = t < m;
+    const int64_t i = isU ? t : t - m;
+    const float* src = (isU ? U : V) + i * RP;
+    __half2* dst = reinterpret_cast<__half2*>((isU ? A : B) + i * 128);
+    const int l = 2 * lane;
     float v[2], h[2], lo[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -424,8 +426,8 @@ __global__ void k_lsplit(const float* __restrict__ U, const float* __restrict__ 
       h[e] = __uint_as_float(__float_as_uint(v[e]) & 0xFFFFE000u);
       lo[e] = (v[e] - h[e]) * 2048.f;
     }
-    dst[l / 2] = __floats2half2_rn(h[0], h[1]);
-    dst[32 + l / 2] = __floats2half2_rn(lo[0], lo[1]);
+    dst[lane] = __floats2half2_rn(h[0], h[1]);
+    dst[32 + lane] = __floats2half2_rn(lo[0], lo[1]);
   }
 }
 
@@ -437,8 +439,10 @@ cudaError_t prepare_resid_kernels() {
 
 void launch_lsplit(const float* U, const float* V, const float* sigma, int64_t m, int64_t n, int RP, int r,
                    const float* zscale, void* A, void* B, cudaStream_t st, const int* skip) {
-  const int64_t tot = m + n;
-  k_lsplit<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(U, V, sigma, m, n, RP, r, zscale,
+  const int64_t tot = m + n;   // rows, one warp each, 8 warps a block, at most 4096 blocks
+  int64_t blocks = (tot + 7) / 8;
+  if (blocks > 4096) blocks = 4096;
+  k_lsplit<<<(unsigned)blocks, 256, 0, st>>>(U, V, sigma, m, n, RP, r, zscale,
                                                           reinterpret_cast<__half*>(A), reinterpret_cast<__half*>(B),
                                                           skip);
 }

@@ -609,28 +609,38 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_rank(const double* __restrict
 constexpr int SVD_THREADS = 1024;
 
 __device__ void mm_1024(const float (*A)[LD], const float (*B)[LD], float (*C)[LD], int n, bool a_transposed) {
-  // C = A B (or A^T B); C must not alias A or B.  Thread (ty, tx) of the 32 x 32 grid owns
-  // rows ty, ty + 32 and columns tx, tx + 32: a warp shares its rows (broadcast loads of A)
-  // and reads consecutive columns of B (conflict-free).
-  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-  const int r0 = ty, r1 = ty + 32, c0 = tx, c1 = tx + 32;
-  if (r0 < n) {
-    float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-    const bool h1 = r1 < n;
-#pragma unroll 4
+  // C = A B (or A^T B); C must not alias A or B.  The product is bound by shared-memory
+  // loads, so 256 of the block's threads each own a 4 x 4 block (rows ty + 16 a, columns
+  // tx + 16 b): per K step a warp issues 8 loads for 512 FMAs, against 4 loads for 128 with
+  // a 2 x 2 block per thread.  A warp's rows are two values of ty (near-broadcast loads of
+  // A); its columns are 16 consecutive ones (conflict-free loads of B).
+  const int tid = threadIdx.x;
+  if (tid < 256) {
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 2
     for (int t = 0; t < n; ++t) {
-      const float a0 = a_transposed ? A[t][r0] : A[r0][t];
-      const float a1 = h1 ? (a_transposed ? A[t][r1] : A[r1][t]) : 0.f;
-      const float b0 = B[t][c0], b1 = B[t][c1];
-      s00 = fmaf(a0, b0, s00);
-      s01 = fmaf(a0, b1, s01);
-      s10 = fmaf(a1, b0, s10);
-      s11 = fmaf(a1, b1, s11);
+      float av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = a_transposed ? A[t][ty + 16 * a] : A[ty + 16 * a][t];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = B[t][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
     }
-    if (c0 < n) C[r0][c0] = s00;
-    if (c1 < n) C[r0][c1] = s01;
-    if (h1 && c0 < n) C[r1][c0] = s10;
-    if (h1 && c1 < n) C[r1][c1] = s11;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (i < n && j < n) C[i][j] = acc[a][b];
+      }
   }
   __syncthreads();
 }
