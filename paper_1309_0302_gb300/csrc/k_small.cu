@@ -622,7 +622,7 @@ __device__ void mm_1024(const float (*A)[LD], const float (*B)[LD], float (*C)[L
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll 2
+#pragma unroll 4
     for (int t = 0; t < n; ++t) {
       float av[4], bv[4];
 #pragma unroll
@@ -678,6 +678,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
   __shared__ int order[kMaxRP];
   __shared__ int rotated;
   __shared__ unsigned s_dmax;        // largest |cos| between a rotated pair in this sweep (float bits)
+  __shared__ int s_anyrot;           // some pair was rotated in this call
   __shared__ float s_scale;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = a.r, RP = a.RP;
@@ -742,7 +743,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
     if (lane == 0 && cmax > 0.f) atomicMax(&s_dmax, __float_as_uint(cmax));
   }
   __syncthreads();
-  const bool warm_done = __uint_as_float(s_dmax) < 2e-6f;
+  // the same bound as the sweep's rotation test (a pair below it would not be rotated)
+  const bool warm_done = __uint_as_float(s_dmax) < 4e-6f;
+  if (tid == 0) s_anyrot = 0;
   __syncthreads();
 
   const int np = (r + 1) & ~1;
@@ -791,6 +794,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
             }
             if (lane == 0) {
               rotated = 1;
+              s_anyrot = 1;
               atomicMax(&s_dmax, __float_as_uint(fabsf(ga) / (sqrtf(al) * sqrtf(be))));
             }
           }
@@ -807,14 +811,21 @@ __global__ void __launch_bounds__(SVD_THREADS) k_svd(SvdArgs2 a) {
       break;
     }
   }
-  // Newton-Schulz: V := V (3I - V^T V) / 2 restores orthonormality lost to rounding
-  mm_1024(V, V, X1, r, true);                       // X1 = V^T V
-  for (int e = tid; e < r * r; e += SVD_THREADS) {
-    const int i = e / r, j = e % r;
-    X1[i][j] = ((i == j) ? 1.5f : 0.f) - 0.5f * X1[i][j];
-  }
+  // Newton-Schulz: V := V (3I - V^T V) / 2 restores orthonormality lost to rounding in
+  // the rotations; without any rotation V is the previous call's V, already restored
   __syncthreads();
-  mm_1024(V, X1, X2, r, false);                     // X2 = reorthonormalised V
+  if (s_anyrot) {
+    mm_1024(V, V, X1, r, true);                     // X1 = V^T V
+    for (int e = tid; e < r * r; e += SVD_THREADS) {
+      const int i = e / r, j = e % r;
+      X1[i][j] = ((i == j) ? 1.5f : 0.f) - 0.5f * X1[i][j];
+    }
+    __syncthreads();
+    mm_1024(V, X1, X2, r, false);                   // X2 = reorthonormalised V
+  } else {
+    for (int e = tid; e < r * r; e += SVD_THREADS) X2[e / r][e % r] = V[e / r][e % r];
+    __syncthreads();
+  }
   if (tid < RP) {
     float v = 0.f;
     if (tid < r)
