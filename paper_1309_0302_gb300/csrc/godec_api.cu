@@ -277,7 +277,6 @@ void prod(godec_ctx* c, int i, float* out, bool want_bt2, const float* T0, const
   l.pend = c->pend;
   l.ctl = c->ctl;
   l.pdl = 1;
-  l.defer = 1;   // ignored by the 16-bit kernel of the precision form
   PROF(c, 0, c->st, launch_prod_tc(l, c->st));
 }
 
@@ -402,9 +401,7 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
   for (int i = 0; i < nprod; ++i) {
     const bool even = (i % 2) == 0;
     const int64_t rows = even ? m : n;
-    // Gram partials of a chain product: one per tile, or tc_finish_split() per tile when
-    // the float32 kernel leaves the completion to its second kernel
-    const int64_t tiles = prod_tiles(rows) * (c->Z16 ? 1 : tc_finish_split());
+    const int64_t tiles = prod_tiles(rows);
     void* nextB = bt2(c, i & 1);
     SlotLaunch sl;
     sl.R_next[0] = sR(0, i);
@@ -1101,7 +1098,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
       return bail(GODEC_ERR_CUDA);
     }
   }
-  c->gpart_stride = ((size_t)tiles * tc_finish_split() * rr * sizeof(double) + 255) & ~size_t(255);
+  c->gpart_stride = ((size_t)tiles * rr * sizeof(double) + 255) & ~size_t(255);
   CKI(dalloc(&c->gparts, c->gpart_stride * np));
   CKI(dalloc(&c->g64, (size_t)(np + 2) * rr));
   CKI(dalloc(&c->gscr, (size_t)apply_blocks(mx) * rr));

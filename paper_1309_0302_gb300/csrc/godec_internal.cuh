@@ -185,11 +185,8 @@ struct TcLaunch {
   int* pend;               // G x geom.maxpend ints of scratch
   Ctl* ctl;
   int pdl = 0;             // programmatic dependent launch on the preceding kernel of the stream
-  int defer = 0;           // float32 kernel only: tiles completed by a second kernel, with
-                           // tc_finish_split() Gram partials per tile (gram_part room for them)
 };
 void launch_prod_tc(const TcLaunch& l, cudaStream_t st);
-int tc_finish_split();
 int64_t apply_blocks(int64_t rows);
 
 // r x r kernels (k_small.cu).

@@ -105,7 +105,6 @@ struct TcArgs {
   int* pend;                // G x maxpend: tiles each CTA completes, deferred to its end
   int maxpend;
   Ctl* ctl;
-  int defer;                // completion left to k_prod_finish (slots only, no counters)
 };
 
 __device__ __forceinline__ int64_t cta_of(int64_t g, int64_t S, int G) { return ((g + 1) * (int64_t)G - 1) / S; }
@@ -336,216 +335,6 @@ __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nth
     }
   }
   named_sync(bar, nthr);   // Ps and Ts free again
-}
-
-// ---- tile completion as a kernel of its own -------------------------------------------
-// With TcArgs::defer the product kernel only writes its partial slots and exits; this
-// kernel, launched right after it (programmatic dependent launch), completes the tiles:
-// kFinSplit blocks per 128-row tile, each on FR rows, so the completion work that the
-// product kernel would leave to one CTA per tile at its very end (slot sum, normaliser,
-// outputs, Gram partial) is spread over all SMs.  The Gram partials are per block: the
-// Gram sum runs over tiles * kFinSplit of them.
-constexpr int kFinSplit = 2, FR = BM / kFinSplit, kFinThreads = 256;
-
-template <int RPp>
-__global__ void __launch_bounds__(kFinThreads) k_prod_finish(TcArgs a) {
-  __shared__ __align__(16) float Ps[FR * EPI_LD];
-  __shared__ __align__(16) float Ts[RPp * RPp];
-  __shared__ float csc[kMaxRP];
-  pdl_wait();                  // every slot of the product is written
-  pdl_launch_dependents();     // the next product may begin its prologue (it waits for us)
-  if (block_skip(a.ctl ? &a.ctl->abort : nullptr)) return;
-  const int tid = threadIdx.x, lane = tid & 31, nthr = kFinThreads;
-  const int RP = a.RP, RP4 = RP / 4;
-  const int64_t t = blockIdx.x / kFinSplit;
-  const int h = (int)(blockIdx.x % kFinSplit);
-  const int64_t c_first = cta_of(t * a.ks, a.S, a.G);
-  const int nseg = (int)(cta_of((t + 1) * a.ks - 1, a.S, a.G) - c_first + 1);
-  const int64_t o0 = t * BM + (int64_t)h * FR;
-  const int nrow = (int)(a.rows - o0 < 0 ? 0 : (a.rows - o0 < FR ? a.rows - o0 : FR));
-  const float zi = a.zscale ? a.zscale[1] : 1.f;
-  if (tid < kMaxRP) csc[tid] = (tid < RP && a.cscale) ? a.cscale[tid] : 1.f;
-  const float* Tn = (a.ctl && a.ctl->slot_parity) ? a.Tn1 : a.Tn0;
-  if (Tn)
-    for (int e = tid; e < RP * RP4; e += nthr)
-      *reinterpret_cast<float4*>(Ts + (e / RP4) * RPp + (e % RP4) * 4) = __ldg(reinterpret_cast<const float4*>(Tn) + e);
-  __syncthreads();
-  // (1) this block's rows: sum of the slots in slot order (deterministic), unscaled
-  const float4* part = reinterpret_cast<const float4*>(a.part + (t * a.maxseg * (int64_t)BM + (int64_t)h * FR) * RP);
-  const int64_t slot4 = (int64_t)BM * RP4;
-  const int nitem = FR * RP4;
-  for (int it0 = tid; it0 < nitem; it0 += 2 * nthr) {
-    float4 acc[2];
-    acc[0] = acc[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s0 = 0; s0 < nseg; s0 += 4) {
-      float4 v[2][4];
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int it = it0 + q * nthr;
-          v[q][k] = (s0 + k < nseg && it < nitem) ? __ldcg(part + (s0 + k) * slot4 + it) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          acc[q].x += v[q][k].x;
-          acc[q].y += v[q][k].y;
-          acc[q].z += v[q][k].z;
-          acc[q].w += v[q][k].w;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int it = it0 + q * nthr;
-      if (it < nitem) {
-        const int row = it / RP4, c = (it % RP4) * 4;
-        float* pr = Ps + row * EPI_LD + c;
-        const bool live = row < nrow;
-        pr[0] = live ? acc[q].x * (csc[c] * zi) : 0.f;
-        pr[1] = live ? acc[q].y * (csc[c + 1] * zi) : 0.f;
-        pr[2] = live ? acc[q].z * (csc[c + 2] * zi) : 0.f;
-        pr[3] = live ? acc[q].w * (csc[c + 3] * zi) : 0.f;
-      }
-    }
-  }
-  __syncthreads();
-  // (2) Y <- Y T: a warp takes an 8-column group for 32 rows (lane = row), T read at
-  // warp-uniform addresses, only rows c <= the group's last column when T is upper
-  // triangular; at most two items a warp (RP <= 64: 8 groups x 2 row blocks)
-  if (Tn) {
-    const int nw = nthr >> 5, CB = RP / 8, nit = CB * (FR / 32);
-    float acc[2][8];
-    int item[2] = {-1, -1};
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int itm = (tid >> 5) + k * nw;
-      if (itm < nit) {
-        item[k] = itm;
-        const int cg = itm % CB, r0 = (itm / CB) * 32 + lane, l0 = cg * 8;
-        const int cend = a.t_upper ? l0 + 8 : RP;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[k][j] = 0.f;
-#pragma unroll 4
-        for (int c = 0; c < cend; ++c) {
-          const float y = Ps[r0 * EPI_LD + c];
-          const float4 t0 = *reinterpret_cast<const float4*>(Ts + c * RPp + l0);
-          const float4 t1 = *reinterpret_cast<const float4*>(Ts + c * RPp + l0 + 4);
-          const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[k][j] = fmaf(y, tv[j], acc[k][j]);
-        }
-      }
-    }
-    __syncthreads();   // every read of Y done before it is overwritten
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (item[k] >= 0) {
-        const int cg = item[k] % CB, r0 = (item[k] / CB) * 32 + lane, l0 = cg * 8;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) Ps[r0 * EPI_LD + l0 + j] = acc[k][j];
-      }
-    __syncthreads();
-  }
-  // (3) outputs: rows (float4 per thread) and the split transposed operand
-  if (a.out)
-    for (int it = tid; it < nrow * RP4; it += nthr) {
-      const int row = it / RP4, c = (it % RP4) * 4;
-      const float* pr = Ps + row * EPI_LD + c;
-      *reinterpret_cast<float4*>(a.out + (o0 + row) * (int64_t)RP + c) = make_float4(pr[0], pr[1], pr[2], pr[3]);
-    }
-  if (a.bt2)
-    for (int it = tid; it < RP * FR; it += nthr) {
-      const int l = it / FR, row = it % FR;
-      if (row < nrow) {
-        const float v = Ps[row * EPI_LD + l] * kSkinnyScale;
-        const __half c1 = __float2half_rn(v);
-        a.bt2[(int64_t)l * a.ldb + o0 + row] = c1;
-        a.bt2[(int64_t)(RP + l) * a.ldb + o0 + row] = __float2half_rn((v - __half2float(c1)) * kLoScale);
-      }
-    }
-  // (4) Gram partial of the block's rows (rows past nrow are zero), as in tile_finish
-  if (a.gram_mode) {
-    const int nb = RP / 4, nblk = nb * (nb + 1) / 2, npair = RP * RP, nit = nblk * 4;
-    const int64_t gidx = t * kFinSplit + h;
-    for (int base = tid - lane; base < nit; base += nthr) {
-      const int it = base + lane;
-      const bool act = it < nit;
-      const int blk = act ? it >> 2 : 0, sp = it & 3;
-      int bi = 0, rem = blk;
-      while (rem >= nb - bi) {
-        rem -= nb - bi;
-        ++bi;
-      }
-      const int bj = bi + rem;
-      const float* pi = Ps + 4 * bi;
-      const float* pj = Ps + 4 * bj;
-      const bool wr = act && sp == 0;
-      if (a.gram_mode == 1) {
-        float acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-        if (act)
-#pragma unroll 4
-          for (int r = sp; r < FR; r += 4) {
-            const float* pr = pi + r * EPI_LD;
-            const float* qr = pj + r * EPI_LD;
-            const float uu[4] = {pr[0], pr[1], pr[2], pr[3]}, vv[4] = {qr[0], qr[1], qr[2], qr[3]};
-#pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4)
-#pragma unroll
-              for (int j4 = 0; j4 < 4; ++j4) acc[i4 * 4 + j4] = fmaf(uu[i4], vv[j4], acc[i4 * 4 + j4]);
-          }
-        float* gp = reinterpret_cast<float*>(a.gram_part) + gidx * npair;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          float v = acc[e];
-          v += __shfl_xor_sync(0xffffffffu, v, 1);
-          v += __shfl_xor_sync(0xffffffffu, v, 2);
-          if (wr) {
-            const int i = 4 * bi + e / 4, j = 4 * bj + e % 4;
-            gp[i * RP + j] = v;
-            gp[j * RP + i] = v;
-          }
-        }
-      } else {
-        float hi[16], lo[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
-        if (act)
-#pragma unroll 1
-          for (int r = sp; r < FR; r += 4) {
-            const float* pr = pi + r * EPI_LD;
-            const float* qr = pj + r * EPI_LD;
-            const float uu[4] = {pr[0], pr[1], pr[2], pr[3]}, vv[4] = {qr[0], qr[1], qr[2], qr[3]};
-#pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4)
-#pragma unroll
-              for (int j4 = 0; j4 < 4; ++j4) {
-                const int e = i4 * 4 + j4;
-                const float x = uu[i4], z = vv[j4];
-                const float pp = x * z, pe = fmaf(x, z, -pp);
-                const float sum = hi[e] + pp, bb = sum - hi[e];
-                lo[e] += ((hi[e] - (sum - bb)) + (pp - bb)) + pe;
-                hi[e] = sum;
-              }
-          }
-        double* gp = reinterpret_cast<double*>(a.gram_part) + gidx * npair;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          double d = (double)hi[e] + (double)lo[e];
-          d += __shfl_xor_sync(0xffffffffu, d, 1);
-          d += __shfl_xor_sync(0xffffffffu, d, 2);
-          if (wr) {
-            const int i = 4 * bi + e / 4, j = 4 * bj + e % 4;
-            gp[i * RP + j] = d;
-            gp[j * RP + i] = d;
-          }
-        }
-      }
-    }
-  }
 }
 
 // One TMA producer loop over this CTA's stages [g0, g1).  Zsrc stages are two
@@ -831,7 +620,6 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 #pragma unroll
       for (int l = 0; l < RPp; l += 4)
         if (l < a.RP) *reinterpret_cast<float4*>(p + l) = make_float4(y[l], y[l + 1], y[l + 2], y[l + 3]);
-      if (a.defer) continue;   // k_prod_finish completes every tile after this kernel
       __threadfence();
       named_sync(1, BM);
       if (et == 0) s_last = (atomicAdd(&a.counters[t], 1u) == (unsigned)(nseg - 1));
@@ -1064,7 +852,6 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 #pragma unroll
       for (int l = 0; l < RPp; l += 4)
         if (l < a.RP) *reinterpret_cast<float4*>(p + l) = make_float4(y[l], y[l + 1], y[l + 2], y[l + 3]);
-      if (a.defer) continue;   // k_prod_finish completes every tile after this kernel
       __threadfence();
       named_sync(1, BM);
       if (et == 0) s_last = (atomicAdd(&a.counters[t], 1u) == (unsigned)(nseg - 1));
@@ -1245,24 +1032,6 @@ static void launch_tc(Kern kern, unsigned grid, unsigned block, size_t smem, cud
   cudaLaunchKernelEx(&cfg, kern, A, B, a);
 }
 
-// The completion kernel, always a programmatic dependent of the product just launched.
-template <typename Kern>
-static void launch_fin(Kern kern, unsigned grid, cudaStream_t st, const TcArgs& a) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kFinThreads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-int tc_finish_split() { return kFinSplit; }
-
 void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   TcArgs a;
   a.rows = l.rows;
@@ -1286,7 +1055,6 @@ void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   a.t_upper = l.t_upper;
   a.pend = l.pend;
   a.maxpend = l.geom.maxpend;
-  a.defer = (l.defer && !l.half_a && l.prescaled) ? 1 : 0;
   a.ctl = l.ctl;
   const CUtensorMap& A = *reinterpret_cast<const CUtensorMap*>(l.mapA);
   const CUtensorMap& B = *reinterpret_cast<const CUtensorMap*>(l.mapB);
@@ -1306,15 +1074,6 @@ void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
       case 32: launch_tc(k_prod_tc<32, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
       case 48: launch_tc(k_prod_tc<48, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
       default: launch_tc(k_prod_tc<64, true>, G, kThreads, kTcSmem, st, pdl, A, B, a); break;
-    }
-    if (a.defer) {
-      const unsigned nb = (unsigned)(l.geom.tiles * kFinSplit);
-      switch (rpp) {
-        case 16: launch_fin(k_prod_finish<16>, nb, st, a); break;
-        case 32: launch_fin(k_prod_finish<32>, nb, st, a); break;
-        case 48: launch_fin(k_prod_finish<48>, nb, st, a); break;
-        default: launch_fin(k_prod_finish<64>, nb, st, a); break;
-      }
     }
   } else {
     switch (rpp) {
