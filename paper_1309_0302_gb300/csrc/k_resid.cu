@@ -151,6 +151,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
       int nband = 0, sx = 0, sb = 0;
       uint32_t phx = 0, phb = 0;
       int64_t nx = 0, nbb = 0;
+      const uint64_t pol = policy_evict_first();
       for (int64_t g = g0; g < g1 && !s_err; ++g) {
         if (ib != band) {
           if (nband > 0 && !mbar_wait(&aempty, (uint32_t)((nband - 1) & 1), kRWait)) { rtimeout(ctl, &s_err); break; }
@@ -169,8 +170,9 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
         // both boxes always: columns past n (and rows past m) are zero-filled, and so are
         // the rows of A and B past m and n, which makes R exactly 0 there
         mbar_expect_tx(&xfull[sx], (uint32_t)(2 * kXBox));
-        tma_load_2d(sX + sx * kXSlot, &mapX, &xfull[sx], (int)(jb * RNC), (int)(ib * RM));
-        tma_load_2d(sX + sx * kXSlot + kXBox, &mapX, &xfull[sx], (int)(jb * RNC + 32), (int)(ib * RM));
+        // X is streamed once per pass and is larger than L2: evict its lines first
+        tma_load_2d_hint(sX + sx * kXSlot, &mapX, &xfull[sx], (int)(jb * RNC), (int)(ib * RM), pol);
+        tma_load_2d_hint(sX + sx * kXSlot + kXBox, &mapX, &xfull[sx], (int)(jb * RNC + 32), (int)(ib * RM), pol);
         ++nx;
         if (++sb == NBS) { sb = 0; phb ^= 1u; }
         if (++sx == NXS) { sx = 0; phx ^= 1u; }

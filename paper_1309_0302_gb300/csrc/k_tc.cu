@@ -348,14 +348,17 @@ __device__ void produce(const CUtensorMap* map, unsigned char* ring, int nslot, 
   int s = 0;
   uint32_t ph = 0;
   int64_t issued = 0;
+  // Zsrc is streamed once per product and is larger than L2: its lines go first, which
+  // leaves L2 to the skinny operand (read by every CTA) and the partial slots
+  const uint64_t pol = policy_evict_first();
   for (int64_t g = g0; g < g1 && !*s_err; ++g) {
     if (!mbar_wait(&emptyb[s], ph ^ 1u, kWaitLimit)) { note_timeout(ctl, s_err); break; }
     unsigned char* dst = ring + (size_t)s * slot_bytes;
     if (IS_A) {
       // both boxes always: columns at and past K are zero-filled
       mbar_expect_tx(&fullb[s], 2 * box_bytes);
-      tma_load_2d(dst, map, &fullb[s], (int)(kst * BK), (int)(t * BM));
-      tma_load_2d(dst + box_bytes, map, &fullb[s], (int)(kst * BK + 32), (int)(t * BM));
+      tma_load_2d_hint(dst, map, &fullb[s], (int)(kst * BK), (int)(t * BM), pol);
+      tma_load_2d_hint(dst + box_bytes, map, &fullb[s], (int)(kst * BK + 32), (int)(t * BM), pol);
     } else {
       mbar_expect_tx(&fullb[s], box_bytes);
       tma_load_2d(dst, map, &fullb[s], (int)(kst * BK), 0);
@@ -738,11 +741,12 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       int64_t t = g0 / ks, kst = g0 % ks, issued = 0;
       int s = 0;
       uint32_t ph = 0;
+      const uint64_t pol = policy_evict_first();   // Z16 streamed once per product
       for (int64_t g = g0; g < g1 && !s_err; ++g) {
         if (!mbar_wait(&emptyb[s], ph ^ 1u, kWaitLimit)) { note_timeout(ctl, &s_err); break; }
         if (isA) {
           mbar_expect_tx(&fullb[s], (uint32_t)kStageA16);
-          tma_load_2d(sA + (size_t)s * kStageA16, &mapA, &fullb[s], (int)(kst * BK), (int)(t * BM));
+          tma_load_2d_hint(sA + (size_t)s * kStageA16, &mapA, &fullb[s], (int)(kst * BK), (int)(t * BM), pol);
         } else {
           mbar_expect_tx(&fullb[s], bbytes);
           tma_load_2d(sB + (size_t)s * kStageB16, &mapB, &fullb[s], (int)(kst * BK), 0);
