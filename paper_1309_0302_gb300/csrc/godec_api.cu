@@ -46,6 +46,8 @@ struct godec_ctx {
   cudaStream_t st = nullptr;
   cudaStream_t cap_st = nullptr;    // private stream used while capturing
   cudaStream_t side_st = nullptr;   // off-critical-path work of the power chain
+  cudaStream_t rank_st = nullptr;   // the rank test, joined before the S-step commits
+  bool rank_forked = false;
   cudaEvent_t ev[kEvents] = {};
   int ev_used = 0;
   int dev = 0, nsm = 0;   // nsm: the SMs this problem's grids are sized for (its budget)
@@ -151,7 +153,7 @@ static void prof_mark(godec_ctx* c, int cls, cudaStream_t s) {
   cudaEventRecord(c->ev_pool[c->prof_used++], s);
   if (cls >= 0) {
     c->prof_cls.push_back(cls);
-    c->prof_side.push_back(s == c->side_st ? 1 : 0);
+    c->prof_side.push_back(s == c->side_st ? 1 : (s == c->rank_st ? 2 : 0));
   }
 }
 
@@ -234,6 +236,24 @@ void join_side(godec_ctx* c) {
   cudaStreamWaitEvent(c->st, e, 0);
 }
 
+// The rank test runs on a stream of its own: its verdict (a rank drop abandons the
+// iteration) is needed only before the S-step commits, so it overlaps the rest of the
+// chain instead of delaying the lagged-normaliser updates queued behind it.
+void fork_rank(godec_ctx* c) {
+  cudaEvent_t e = c->ev[c->ev_used++ % kEvents];
+  cudaEventRecord(e, c->st);
+  cudaStreamWaitEvent(c->rank_st, e, 0);
+  c->rank_forked = true;
+}
+
+void join_rank(godec_ctx* c) {
+  if (!c->rank_forked) return;
+  cudaEvent_t e = c->ev[c->ev_used++ % kEvents];
+  cudaEventRecord(e, c->rank_st);
+  cudaStreamWaitEvent(c->st, e, 0);
+  c->rank_forked = false;
+}
+
 char* gpart(godec_ctx* c, int i) { return c->gparts + (size_t)i * c->gpart_stride; }
 void* bt2(godec_ctx* c, int b) { return static_cast<char*>(c->bt2) + (size_t)b * 2 * c->RP * c->ldb * 2; }
 
@@ -277,7 +297,14 @@ void prod(godec_ctx* c, int i, float* out, bool want_bt2, const float* T0, const
   l.pend = c->pend;
   l.ctl = c->ctl;
   l.pdl = 1;
+  l.z_prefetch = i > 0;   // within the chain no kernel writes Z (the S-step comes before product 0)
   PROF(c, 0, c->st, launch_prod_tc(l, c->st));
+}
+
+cudaEvent_t record(godec_ctx* c, cudaStream_t s) {
+  cudaEvent_t e = c->ev[c->ev_used++ % kEvents];
+  cudaEventRecord(e, s);
+  return e;
 }
 
 void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out, cudaStream_t s) {
@@ -398,11 +425,18 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
   auto sT = [&](int h, int i) { return c->Tslot + ((size_t)h * nprod + i) * rr; };
   const float* rapp_last[2] = {nullptr, nullptr};
   bool have_pi = false;
+  cudaEvent_t rank_gram = nullptr;                // the rank test's Gram of P (fast path)
+  cudaEvent_t side_core = nullptr;                // side work the core SVD needs (all but the last slot)
   for (int i = 0; i < nprod; ++i) {
     const bool even = (i % 2) == 0;
     const int64_t rows = even ? m : n;
     const int64_t tiles = prod_tiles(rows);
     void* nextB = bt2(c, i & 1);
+    // the rank test's Gram reads P until `last` rewrites it
+    if (i == last && rank_gram) {
+      cudaStreamWaitEvent(c->st, rank_gram, 0);
+      rank_gram = nullptr;
+    }
     SlotLaunch sl;
     sl.R_next[0] = sR(0, i);
     sl.R_next[1] = sR(1, i);
@@ -412,18 +446,29 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
     const int pi_mode = (i == i_rank) ? 2 : ((i > i_rank && i < last) ? 1 : 0);
     sl.pi_mode = pi_mode;
     if (i == i_rank) {
-      // P = Z Q2 unnormalised, with an exactly accumulated Gram for the rank test
-      prod(c, i, c->P, false, nullptr, nullptr, 2);
-      gram_sum(c, gpart(c, i), 1, tiles, g64(c, i), c->st);
-      fork_side(c);
-      PROF(c, 5, c->side_st,
-           launch_rank(g64(c, i), c->r, RP, c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4, c->ctl, c->side_st));
+      // P = Z Q2 unnormalised, with an exactly accumulated Gram for the rank test.  On the
+      // fast path nothing on the critical path needs that Gram: it is formed on the rank
+      // test's stream from P instead of in the product's tile completion.
+      const bool aside = fast && i != last;
+      prod(c, i, c->P, false, nullptr, nullptr, aside ? 0 : 2);
+      if (aside) {
+        fork_rank(c);
+        PROF(c, 1, c->rank_st, launch_gram_tiles(c->P, rows, RP, 2, gpart(c, i), c->ctl, c->rank_st));
+        gram_sum(c, gpart(c, i), 1, tiles, g64(c, i), c->rank_st);
+        rank_gram = record(c, c->rank_st);
+      } else {
+        gram_sum(c, gpart(c, i), 1, tiles, g64(c, i), c->st);
+        fork_rank(c);
+      }
+      PROF(c, 5, c->rank_st,
+           launch_rank(g64(c, i), c->r, RP, c->p.rank_tol > 0 ? c->p.rank_tol : 1e-4, c->ctl, c->rank_st));
       if (i == last) {   // q = 0: this product is also the last one
         final_cqr2(c, rows, g64(c, i), c->Rfin + 4 * rr, c->Rfin + 6 * rr, nullptr, g64(c, nprod + 1), nullptr);
         continue;
       }
       if (fast) {
         apply(c, c->P, rows, sT(0, i), sT(1, i), nullptr, nullptr, nextB);
+        cudaStreamWaitEvent(c->side_st, rank_gram, 0);   // the slot update reads that Gram
         sl.fast = 1;
         sl.g64 = g64(c, i);
         sl.g_is_p = 1;
@@ -458,6 +503,9 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
         final_cqr2(c, rows, g64(c, i), Ra, Rb, fin, g64(c, nprod + (i == i_q2 ? 0 : 1)),
                    i == i_q2 ? nextB : nullptr);
       }
+      // the last slot update prepares the next iteration only: the core SVD waits for the
+      // side work queued before it, not for it
+      if (i == last) side_core = record(c, c->side_st);
       fork_side(c);
       sl.fast = 0;
       if (fast) {
@@ -474,6 +522,8 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       slot(c, sl);
     } else {
       if (fast) {
+        // (the lagged normaliser's Gram stays in the tile completion: the side stream runs
+        // on the few SMs the product leaves free and has no room for it)
         prod(c, i, nullptr, true, sT(0, i), sT(1, i), 1);
         fork_side(c);
         gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->side_st);
@@ -495,22 +545,25 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       if (pi_mode) have_pi = true;
     }
   }
-  join_side(c);
+  if (side_core) cudaStreamWaitEvent(c->st, side_core, 0);
+  else join_side(c);
   // r x r core, SVD and singular-value root, then L = (Q1 Um) diag(sigma) (Q2 Vm)^T with
   // Q1 Um = P (Rl^{-1} Um), Rl the last factor applied to P (Ra after one CholeskyQR pass,
-  // Rb after two): the SVD kernel returns Rl^{-1} Um; V is formed on the side stream
+  // Rb after two): the SVD kernel returns Rl^{-1} Um; V is formed on the rank test's
+  // stream (long idle by then; the side stream may still run the last slot update)
   const float* Rb_last = (fast && last != i_rank) ? nullptr : c->Rfin + 6 * rr;
   const float* Tl = inv_of(c, Rb_last ? Rb_last : c->Rfin + 4 * rr);
   PROF(c, 6, c->st,
        launch_svd(c->Rfin + 4 * rr, Rb_last, rapp_last[0], rapp_last[1], have_pi ? c->Pi : nullptr,
                   c->Vprev, c->r, RP, q, c->Um, c->Vm, c->sigma, c->ctl, c->st, Tl));
-  fork_side(c);
-  PROF(c, 3, c->side_st, launch_apply(c->Q2, n, RP, c->Vm, c->Vm, c->V, nullptr, c->ctl, c->side_st));
+  fork_rank(c);
+  PROF(c, 3, c->rank_st, launch_apply(c->Q2, n, RP, c->Vm, c->Vm, c->V, nullptr, c->ctl, c->rank_st));
   apply(c, c->P, m, c->Um, c->Um, c->U, nullptr);
-  join_side(c);
+  join_rank(c);
   if (c->Z16 && !(c->p.flags & GODEC_FLAG_NO_REFINE)) refine(c);
   // operands of the tensor-core residual pass
   PROF(c, 3, c->st, launch_lsplit(c->U, c->V, c->sigma, m, n, RP, c->r, c->ctl->zscale, c->LA, c->LB, c->st));
+  join_side(c);
 }
 
 // S-step of one iteration (Algorithm 1, eq. raw_lss) on the current L factors; r = 0 means L = 0.
@@ -962,6 +1015,7 @@ void godec_destroy(godec_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->side_st) cudaStreamDestroy(c->side_st);
+  if (c->rank_st) cudaStreamDestroy(c->rank_st);
   delete c;
 }
 
@@ -1006,6 +1060,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
   CKI(prepare_resid_kernels());
   CKI(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
   CKI(cudaStreamCreateWithFlags(&c->side_st, cudaStreamNonBlocking));
+  CKI(cudaStreamCreateWithFlags(&c->rank_st, cudaStreamNonBlocking));
   for (int k = 0; k < kEvents; ++k) CKI(cudaEventCreateWithFlags(&c->ev[k], cudaEventDisableTiming));
   const int64_t m = p->m, n = p->n, mx = std::max(m, n);
   const int RP = c->RP, np = c->nprod;
@@ -1220,6 +1275,7 @@ godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* la
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
     CK(cudaStreamSynchronize(c->side_st));
+    CK(cudaStreamSynchronize(c->rank_st));
     for (size_t i = 0; i < c->prof_cls.size(); ++i) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));

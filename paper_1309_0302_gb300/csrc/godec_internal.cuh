@@ -185,11 +185,17 @@ struct TcLaunch {
   int* pend;               // G x geom.maxpend ints of scratch
   Ctl* ctl;
   int pdl = 0;             // programmatic dependent launch on the preceding kernel of the stream
+  int z_prefetch = 0;      // the preceding kernels leave Zsrc unchanged: its first stages may be
+                           // loaded before the wait on them (with pdl)
 };
 void launch_prod_tc(const TcLaunch& l, cudaStream_t st);
 int64_t apply_blocks(int64_t rows);
 
 // r x r kernels (k_small.cu).
+// Gram partials of the 128-row tiles of the rows x RP float32 matrix Y (row stride RP;
+// k_gram.cu): mode 1 float, mode 2 exactly accumulated double; layout as the product's
+// gram_part.
+void launch_gram_tiles(const float* Y, int64_t rows, int RP, int mode, void* part, const Ctl* ctl, cudaStream_t st);
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
                      cudaStream_t st);
 // R (upper, Rᵀ R = Gram) and T = R^{-1}, both RP x RP.

@@ -58,6 +58,8 @@ k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restri
 // ---- block helpers on 64 x 64 (padded RP x RP) matrices in shared memory -----------
 // Thread (ty, tx) owns rows ty + 16a and columns tx + 16b, a, b in 0..3.
 
+constexpr int CB = 8;   // block size of the triangular inverse
+
 // Inverse of the 8 x 8 upper-triangular block at (k0, k0) of R into Ui (lane c < 8
 // back-substitutes column c; rd[i] = 1 / R[k0+i][k0+i]).
 __device__ __forceinline__ void block_inverse8(const float (*R)[LD], int k0, const float* rd, float (*Ui)[LD],
@@ -74,80 +76,6 @@ __device__ __forceinline__ void block_inverse8(const float (*R)[LD], int k0, con
 #pragma unroll
     for (int i = 0; i < 8; ++i) Ui[ui0 + i][ui0 + lane] = x[i];
   }
-}
-
-// Upper Cholesky G = R^T R in place of R (R must start as a copy of G; n a multiple
-// of 8).  Right-looking in 8 x 8 blocks: warp 0 factors the diagonal block (and inverts
-// its factor), all threads solve the block row and update the trailing upper triangle;
-// four barriers per block step instead of one per column.  Pivots j < nchk below thr
-// are raised to thr and reported through *bad.
-constexpr int CB = 8;
-__device__ void chol_upper(float (*R)[LD], int n, int nchk, float thr, int* bad) {
-  __shared__ float Ui[CB][LD];   // inverse of the current diagonal factor
-  __shared__ float rs[CB];       // 1 / diagonal of the current factor
-  const int tid = threadIdx.x, lane = tid & 31;
-  for (int k0 = 0; k0 < n; k0 += CB) {
-    if (tid < 32) {
-      // (1) diagonal block: column-by-column Cholesky inside one warp (two entries a lane)
-      for (int j = 0; j < CB; ++j) {
-        float d = R[k0 + j][k0 + j];
-        if (k0 + j < nchk && !(d > thr)) {
-          if (lane == 0) *bad = 1;
-          d = thr > 0.f ? thr : 1e-30f;
-        }
-        const float rsq = rsqrtf(d), sq = d * rsq, invd = rsq * rsq;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int e = lane + 32 * h, a = e / CB, c = e % CB;
-          if (a > j && c >= a) R[k0 + a][k0 + c] -= R[k0 + j][k0 + a] * R[k0 + j][k0 + c] * invd;
-        }
-        __syncwarp();
-        if (lane >= j && lane < CB) R[k0 + j][k0 + lane] = (lane == j) ? sq : R[k0 + j][k0 + lane] * rsq;
-        if (lane == 0) rs[j] = rsq;
-        __syncwarp();
-      }
-      block_inverse8(R, k0, rs, Ui, 0, lane);
-    }
-    __syncthreads();
-    // (2) block row: R[k0+i][j] = sum_{t <= i} Ui[t][i] A[k0+t][j] for j beyond the block
-    const int j0 = k0 + CB, w = n - j0;
-    float pv[2] = {0.f, 0.f};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = tid + SMALL_THREADS * h;
-      if (e < CB * w) {
-        const int i = e / w, j = j0 + e % w;
-        float sacc = 0.f;
-#pragma unroll
-        for (int t = 0; t < CB; ++t)
-          if (t <= i) sacc = fmaf(Ui[t][i], R[k0 + t][j], sacc);
-        pv[h] = sacc;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = tid + SMALL_THREADS * h;
-      if (e < CB * w) R[k0 + e / w][j0 + e % w] = pv[h];
-    }
-    __syncthreads();
-    // (3) trailing upper triangle: A[a][c] -= sum_t R[k0+t][a] R[k0+t][c], c >= a
-    for (int e = tid; e < w * w; e += SMALL_THREADS) {
-      const int a = j0 + e / w, c = j0 + e % w;
-      if (c >= a) {
-        float sacc = R[a][c];
-#pragma unroll
-        for (int t = 0; t < CB; ++t) sacc = fmaf(-R[k0 + t][a], R[k0 + t][c], sacc);
-        R[a][c] = sacc;
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < n * n; e += SMALL_THREADS) {
-    const int i = e / n, c = e % n;
-    if (c < i) R[i][c] = 0.f;
-  }
-  __syncthreads();
 }
 
 // Inverse Ri of an upper-triangular R (n a multiple of 8), in 8 x 8 blocks: warps
@@ -288,10 +216,46 @@ __device__ float block_absmax(const float (*M)[LD], int n) {
   return r;
 }
 
+// Upper Cholesky factor and its inverse together, by symmetric Gaussian elimination of the
+// augmented matrix [G | I] with one barrier per column.  With G = L D L^T (L unit lower),
+// the elimination leaves U = D L^T in the left block and E = L^{-1} in the right one, so
+// R = D^{-1/2} U and R^{-1} = E^T D^{-1/2}.  The trailing block is updated in full (both
+// triangles), so column j holds the multipliers of step j.  Thread (rw, cc) owns column
+// index cc and every fourth row: while cc > j it addresses the left block, once cc <= j
+// the right one (E's columns beyond j are still those of I and need no update, and the
+// left columns up to j are no longer read).  A (n rows) is overwritten with U in its upper
+// triangle; E must hold I on entry.  Pivots j < nchk at or below thr are raised to thr and
+// reported through *bad; dv receives the pivots used.
+__device__ void chol_elim(float (*A)[LD], float (*E)[LD], int n, int nchk, float thr, int* bad, float* dv) {
+  const int tid = threadIdx.x, cc = tid & 63, rw = tid >> 6;
+  for (int j = 0; j < n; ++j) {
+    float d = A[j][j];
+    if (j < nchk && !(d > thr)) {
+      d = thr > 0.f ? thr : 1e-30f;
+      if (tid == 0) *bad = 1;
+    }
+    if (tid == 0) dv[j] = d;
+    const float invd = 1.f / d;
+    if (cc < n) {
+      float* col = (cc > j) ? &A[0][cc] : &E[0][cc];
+      const float pj = col[j * LD];
+#pragma unroll 4
+      for (int a = j + 1 + rw; a < n; a += 4) {
+        const float mult = A[a][j] * invd;
+        col[a * LD] = fmaf(-mult, pj, col[a * LD]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
 // numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
-// factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.
-__device__ void robust_chol(float (*G)[LD], float (*R)[LD], int r, int RP, Ctl* ctl) {
+// factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.  G is kept;
+// R receives the factor (upper, zero below), E (64 x LD) L^{-1} and dv the pivots, so that
+// R^{-1}[i][c] = E[c][i] / sqrt(dv[c]) for c >= i.
+__device__ void robust_chol(const float (*G)[LD], float (*R)[LD], float (*E)[LD], float* dv, int r, int RP,
+                            Ctl* ctl) {
   __shared__ float s_gmax;
   __shared__ int s_bad;
   if (threadIdx.x == 0) {
@@ -304,12 +268,23 @@ __device__ void robust_chol(float (*G)[LD], float (*R)[LD], int r, int RP, Ctl* 
     for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
       const int i = e / kMaxRP, j = e % kMaxRP;
       R[i][j] = G[i][j] + ((attempt == 1 && i == j && i < r) ? 1e-5f * s_gmax : 0.f);
+      E[i][j] = (i == j) ? 1.f : 0.f;
     }
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    chol_upper(R, RP, r, 1e-6f * s_gmax, &s_bad);
+    chol_elim(R, E, RP, r, 1e-6f * s_gmax, &s_bad, dv);
     if (!s_bad) break;
     if (threadIdx.x == 0) ctl->chol_shifts += 1;
+  }
+  // R = D^{-1/2} U, the lower triangle cleared
+  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
+    const int i = e / kMaxRP, c = e % kMaxRP;
+    float v = 0.f;
+    if (i < RP && c < RP && c >= i) {
+      const float si = rsqrtf(dv[i]);
+      v = (c == i) ? dv[i] * si : R[i][c] * si;
+    }
+    R[i][c] = v;
   }
   __syncthreads();
 }
@@ -380,13 +355,15 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
   extern __shared__ __align__(16) float smf[];
   float (*R)[LD] = reinterpret_cast<float (*)[LD]>(smf) + 2 * kMaxRP;
   float (*Ri)[LD] = R + kMaxRP;
+  __shared__ float dv[kMaxRP];
   if (!F64) {
     float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
+    float (*E)[LD] = G + kMaxRP;
     if (!load_gram(G, g64, r, RP)) {
       if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
       return;
     }
-    robust_chol(G, R, r, RP, ctl);
+    robust_chol(G, R, E, dv, r, RP, ctl);
   } else {
   double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);            // 2 float blocks
   __shared__ double s_gmax;
@@ -444,8 +421,17 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
     if (threadIdx.x == 0 && !(hi <= alarm_ratio * lo)) { ctl->alarm = 1; ctl->abort = 1; }
   }
   store_mat(Rout, R, RP);
-  tri_inverse(R, Ri, RP, nullptr);
-  store_mat(Tout, Ri, RP);
+  if (!F64) {
+    // T = E^T D^{-1/2} from the elimination
+    const float (*E)[LD] = reinterpret_cast<const float (*)[LD]>(smf) + kMaxRP;
+    for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) {
+      const int i = e / RP, c = e % RP;
+      Tout[e] = (c >= i) ? E[c][i] * rsqrtf(dv[c]) : 0.f;
+    }
+  } else {
+    tri_inverse(R, Ri, RP, nullptr);
+    store_mat(Tout, Ri, RP);
+  }
 }
 
 // ---- off the critical path: lagged normaliser of a chain slot ---------------------------
@@ -515,7 +501,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
       }
       __syncthreads();
     }
-    robust_chol(A, C, r, RP, ctl);                   // C = R~
+    __shared__ float dv[kMaxRP];
+    robust_chol(A, C, D, dv, r, RP, ctl);            // C = R~ (D: scratch)
     if (threadIdx.x == 0) {
       float lo = 3.4e38f, hi = 0.f;
       for (int j = 0; j < r; ++j) { lo = fminf(lo, C[j][j]); hi = fmaxf(hi, C[j][j]); }

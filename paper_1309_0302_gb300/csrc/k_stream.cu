@@ -306,10 +306,39 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * RB;
   const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
-  for (int e = tid; e < RP * RP; e += AP_THREADS) Ts[e / RP][e % RP] = __ldg(T + e);
-  for (int e = tid; e < RB * RP; e += AP_THREADS) {
-    const int i = e / RP, c = e % RP;
-    Ps[i][c] = (i < nrow) ? P[(r0 + i) * RP + c] : 0.f;
+  // Every load is issued before the first store (T and the block's rows as float4s: RP is
+  // a multiple of 8), so the block waits for one memory round trip, not one per element.
+  constexpr int kT4 = kMaxRP * kMaxRP / 4 / AP_THREADS, kP4 = RB * kMaxRP / 4 / AP_THREADS;
+  const int RP4 = RP / 4, nT4 = RP * RP4, nP4 = nrow * RP4;
+  const float4* T4 = reinterpret_cast<const float4*>(T);
+  const float4* P4 = reinterpret_cast<const float4*>(P + r0 * RP);
+  float4 tv[kT4], pv[kP4];
+#pragma unroll
+  for (int k = 0; k < kT4; ++k) {
+    const int e = tid + k * AP_THREADS;
+    tv[k] = e < nT4 ? __ldg(T4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < kP4; ++k) {
+    const int e = tid + k * AP_THREADS;
+    pv[k] = e < nP4 ? __ldcg(P4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < kT4; ++k) {
+    const int e = tid + k * AP_THREADS;
+    if (e < nT4) *reinterpret_cast<float4*>(&Ts[e / RP4][(e % RP4) * 4]) = tv[k];
+  }
+#pragma unroll
+  for (int k = 0; k < kP4; ++k) {
+    const int e = tid + k * AP_THREADS;
+    if (e < RB * RP4) {
+      const int i = e / RP4, c = (e % RP4) * 4;
+      const float4 v = pv[k];   // rows past nrow load as zero
+      Ps[i][c] = v.x;
+      Ps[i][c + 1] = v.y;
+      Ps[i][c + 2] = v.z;
+      Ps[i][c + 3] = v.w;
+    }
   }
   __syncthreads();
   const int row = tid >> 3, cg = (tid & 7) * 8;   // this thread: row, columns cg .. cg+7

@@ -50,6 +50,7 @@
 #include <cudaTypedefs.h>
 
 #include "godec_internal.cuh"
+#include "gram_tile.cuh"
 #include "tc_util.cuh"
 
 namespace godec {
@@ -104,6 +105,7 @@ struct TcArgs {
   int t_upper;              // the normaliser is upper triangular
   int* pend;                // G x maxpend: tiles each CTA completes, deferred to its end
   int maxpend;
+  int z_prefetch;           // Zsrc's first stages may be loaded before the programmatic wait
   Ctl* ctl;
 };
 
@@ -132,13 +134,22 @@ __device__ __forceinline__ uint32_t pack_h2(float even, float odd) {
 // RPp) a copy of T; csc = per-column output factors 1 / s_B, zi = 1 / s_Z.
 template <int RPp>
 __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nthr, int bar, float* Ps, float* Ts,
-                            const float* csc, float zi) {
+                            const float* csc, float zi, const float* Tn) {
   const int RP = a.RP, RP4 = RP / 4;
   const int64_t o0 = t * BM;
   const int nrow = (int)(a.rows - o0 < BM ? a.rows - o0 : BM);
   __threadfence();   // the other segments' slots: written before their counter increments
   if (u == 0) a.counters[t] = 0u;
-  const float* Tn = (a.ctl && a.ctl->slot_parity) ? a.Tn1 : a.Tn0;
+  // T (chosen at the kernel's start) is loaded together with the slots: one memory round
+  // trip for the whole phase
+  constexpr int kTq = kMaxRP * kMaxRP / 4 / 256;   // float4s of T per thread for nthr >= 256
+  const int nT4 = Tn ? RP * RP4 : 0;
+  float4 tq[kTq];
+#pragma unroll
+  for (int k = 0; k < kTq; ++k) {
+    const int e = u + k * nthr;
+    tq[k] = e < nT4 ? __ldg(reinterpret_cast<const float4*>(Tn) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   // (1) rows of the tile into Ps: sum of the slots, unscaled.  Consecutive threads take
   // consecutive float4s of a slot (coalesced); four items per thread and up to four slots
   // each are in flight at once.
@@ -182,9 +193,11 @@ __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nth
       }
     }
   }
-  if (Tn)
-    for (int e = u; e < RP * RP4; e += nthr)
-      *reinterpret_cast<float4*>(Ts + (e / RP4) * RPp + (e % RP4) * 4) = __ldg(reinterpret_cast<const float4*>(Tn) + e);
+#pragma unroll
+  for (int k = 0; k < kTq; ++k) {
+    const int e = u + k * nthr;
+    if (e < nT4) *reinterpret_cast<float4*>(Ts + (e / RP4) * RPp + (e % RP4) * 4) = tq[k];
+  }
   named_sync(bar, nthr);
   // (2) Y <- Y T.  A warp takes an 8-column group of the output for one half of the rows
   // (lane: rows lane and lane + 32 of the half), so T is read at warp-uniform addresses;
@@ -250,89 +263,10 @@ __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nth
         a.bt2[(int64_t)(RP + l) * a.ldb + o0 + row] = __float2half_rn((v - __half2float(c1)) * kLoScale);
       }
     }
-  // (4) Gram partial Y^T Y (rows past nrow are zero): the upper triangle in 4 x 4 blocks,
-  // each block's rows split over four adjacent lanes (row r to lane r mod 4), reduced by
-  // shuffles and mirrored on writing
+  // (4) Gram partial Y^T Y of the tile (rows past nrow are zero)
   if (a.gram_mode) {
-    const int nb = RP / 4, nblk = nb * (nb + 1) / 2, npair = RP * RP, nit = nblk * 4;
-    const int lane = u & 31;
-    for (int base = u - lane; base < nit; base += nthr) {
-      const int it = base + lane;
-      const bool act = it < nit;
-      const int blk = act ? it >> 2 : 0, sp = it & 3;
-      int bi = 0, rem = blk;
-      while (rem >= nb - bi) {
-        rem -= nb - bi;
-        ++bi;
-      }
-      const int bj = bi + rem;
-      const float* pi = Ps + 4 * bi;
-      const float* pj = Ps + 4 * bj;
-      const bool wr = act && sp == 0;
-      if (a.gram_mode == 1) {
-        float acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-        if (act)
-#pragma unroll 4
-          for (int r = sp; r < BM; r += 4) {
-            const float* pr = pi + r * EPI_LD;
-            const float* qr = pj + r * EPI_LD;
-            const float uu[4] = {pr[0], pr[1], pr[2], pr[3]}, vv[4] = {qr[0], qr[1], qr[2], qr[3]};
-#pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4)
-#pragma unroll
-              for (int j4 = 0; j4 < 4; ++j4) acc[i4 * 4 + j4] = fmaf(uu[i4], vv[j4], acc[i4 * 4 + j4]);
-          }
-        float* gp = reinterpret_cast<float*>(a.gram_part) + t * npair;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          float v = acc[e];
-          v += __shfl_xor_sync(0xffffffffu, v, 1);
-          v += __shfl_xor_sync(0xffffffffu, v, 2);
-          if (wr) {
-            const int i = 4 * bi + e / 4, j = 4 * bj + e % 4;
-            gp[i * RP + j] = v;
-            gp[j * RP + i] = v;
-          }
-        }
-      } else {
-        // double-float accumulation: exact products (fma residual), two-sum of the running total
-        float hi[16], lo[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) hi[e] = lo[e] = 0.f;
-        if (act)
-#pragma unroll 1
-          for (int r = sp; r < BM; r += 4) {
-            const float* pr = pi + r * EPI_LD;
-            const float* qr = pj + r * EPI_LD;
-            const float uu[4] = {pr[0], pr[1], pr[2], pr[3]}, vv[4] = {qr[0], qr[1], qr[2], qr[3]};
-#pragma unroll
-            for (int i4 = 0; i4 < 4; ++i4)
-#pragma unroll
-              for (int j4 = 0; j4 < 4; ++j4) {
-                const int e = i4 * 4 + j4;
-                const float x = uu[i4], z = vv[j4];
-                const float p = x * z, pe = fmaf(x, z, -p);
-                const float sum = hi[e] + p, bb = sum - hi[e];
-                lo[e] += ((hi[e] - (sum - bb)) + (p - bb)) + pe;
-                hi[e] = sum;
-              }
-          }
-        double* gp = reinterpret_cast<double*>(a.gram_part) + t * npair;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          double d = (double)hi[e] + (double)lo[e];
-          d += __shfl_xor_sync(0xffffffffu, d, 1);
-          d += __shfl_xor_sync(0xffffffffu, d, 2);
-          if (wr) {
-            const int i = 4 * bi + e / 4, j = 4 * bj + e % 4;
-            gp[i * RP + j] = d;
-            gp[j * RP + i] = d;
-          }
-        }
-      }
-    }
+    const size_t esz = a.gram_mode == 2 ? sizeof(double) : sizeof(float);
+    gram_tile(Ps, EPI_LD, RP, a.gram_mode, static_cast<char*>(a.gram_part) + (size_t)t * RP * RP * esz, u, nthr);
   }
   named_sync(bar, nthr);   // Ps and Ts free again
 }
@@ -343,11 +277,13 @@ __device__ void tile_finish(const TcArgs& a, int64_t t, int nseg, int u, int nth
 template <bool IS_A>
 __device__ void produce(const CUtensorMap* map, unsigned char* ring, int nslot, size_t slot_bytes, uint32_t box_bytes,
                         uint64_t* fullb, uint64_t* emptyb, int64_t g0, int64_t g1, int64_t ks, int64_t K, Ctl* ctl,
-                        volatile int* s_err) {
-  int64_t t = g0 / ks, kst = g0 % ks;
-  int s = 0;
-  uint32_t ph = 0;
-  int64_t issued = 0;
+                        volatile int* s_err, int64_t npre = 0) {
+  // npre stages were issued already (prefetch_a): continue after them
+  int64_t t = (g0 + npre) / ks, kst = (g0 + npre) % ks;
+  int s = (int)(npre % nslot);
+  uint32_t ph = (uint32_t)((npre / nslot) & 1);
+  int64_t issued = npre;
+  g0 += npre;
   // Zsrc is streamed once per product and is larger than L2: its lines go first, which
   // leaves L2 to the skinny operand (read by every CTA) and the partial slots
   const uint64_t pol = policy_evict_first();
@@ -370,6 +306,26 @@ __device__ void produce(const CUtensorMap* map, unsigned char* ring, int nslot, 
   // Every copy issued has landed before the CTA may exit (immediate in the normal case).
   for (int64_t j = (issued > nslot ? issued - nslot : 0); j < issued; ++j)
     if (!mbar_wait(&fullb[(int)(j % nslot)], (uint32_t)((j / nslot) & 1), kWaitLimit)) note_timeout(ctl, s_err);
+}
+
+// The first stages of this CTA's Zsrc range into the empty ring (every slot is free at the
+// start), issued before the programmatic wait on the preceding kernel when that kernel
+// leaves Zsrc unchanged: the stream then starts as soon as the skinny operand lands.
+// Returns the number of stages issued; produce() continues after them and drains them on
+// an abort like its own.
+__device__ int64_t prefetch_a(const CUtensorMap* map, unsigned char* ring, uint64_t* fullb, int64_t g0, int64_t g1,
+                              int64_t ks) {
+  const uint64_t pol = policy_evict_first();
+  const int64_t n = (g1 - g0 < NA) ? g1 - g0 : NA;
+  int64_t t = g0 / ks, kst = g0 % ks;
+  for (int64_t s = 0; s < n; ++s) {
+    unsigned char* dst = ring + (size_t)s * kStageA;
+    mbar_expect_tx(&fullb[s], 2 * (uint32_t)kBoxA);
+    tma_load_2d_hint(dst, map, &fullb[s], (int)(kst * BK), (int)(t * BM), pol);
+    tma_load_2d_hint(dst + kBoxA, map, &fullb[s], (int)(kst * BK + 32), (int)(t * BM), pol);
+    if (++kst == ks) { kst = 0; ++t; }
+  }
+  return n > 0 ? n : 0;
 }
 
 // Warp-uniform bounded wait: lane 0 polls, the warp follows (__syncwarp orders the
@@ -400,11 +356,13 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   __shared__ int s_npend;   // tiles this CTA completes (listed in a.pend), done at its end
   __shared__ float s_csc[kMaxRP];
   __shared__ float s_zi;
+  __shared__ const float* s_tn;   // the normaliser of this launch (by slot parity)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x;
   const int64_t S = a.S, ks = a.ks, K = a.K;
   const int G = a.G;
   const int64_t g0 = (int64_t)c * S / G, g1 = (int64_t)(c + 1) * S / G;
+  int64_t npre = 0;   // Zsrc stages issued before the programmatic wait (thread 0, the producer)
   if (tid == 0) {
     for (int s = 0; s < NA; ++s) {
       mbar_init(&afull[s], 1);
@@ -422,10 +380,12 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     }
     mbar_init(&mma_done, 1);
     fence_barrier_init();
+    if (a.z_prefetch) npre = prefetch_a(&mapA, sA, afull, g0, g1, ks);
   }
   if (warp == 1) tmem_alloc(&tmem_base, kTmemCols);
   // Launched as a programmatic dependent of the previous product: everything above ran
-  // while that product completed its tiles; no global memory is touched before this.
+  // while that product completed its tiles; apart from the prefetch of Zsrc (which the
+  // preceding kernels do not write), no global memory is touched before this.
   pdl_wait();
   if (tid == 0) {
     // Iteration already abandoned, or Z outgrew its scale in the last S-step (the caller
@@ -434,6 +394,7 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     if (ctl && ctl->range_err) ctl->abort = 1;
     s_npend = 0;
     s_zi = a.zscale ? a.zscale[1] : 1.f;
+    s_tn = (ctl && ctl->slot_parity) ? a.Tn1 : a.Tn0;
   }
   if (tid < kMaxRP) s_csc[tid] = (tid < a.RP && a.cscale) ? a.cscale[tid] : 1.f;
   __syncthreads();
@@ -443,7 +404,7 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
   if (warp == 0) {
     // ---------------- TMA producer: Zsrc tiles ----------------
     if (lane == 0)
-      produce<true>(&mapA, sA, NA, kStageA, (uint32_t)kBoxA, afull, aempty, g0, g1, ks, K, ctl, &s_err);
+      produce<true>(&mapA, sA, NA, kStageA, (uint32_t)kBoxA, afull, aempty, g0, g1, ks, K, ctl, &s_err, npre);
   } else if (warp == 14) {
     // ---------------- TMA producer: skinny-operand tiles ----------------
     if (lane == 0)
@@ -651,7 +612,7 @@ k_prod_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
     const int64_t t = a.pend[(int64_t)c * a.maxpend + k];
     const int64_t c_first = cta_of(t * ks, S, G);
     const int nseg = (int)(cta_of((t + 1) * ks - 1, S, G) - c_first + 1);
-    tile_finish<RPp>(a, t, nseg, tid, kThreads, 0, Ps, Ts, s_csc, s_zi);
+    tile_finish<RPp>(a, t, nseg, tid, kThreads, 0, Ps, Ts, s_csc, s_zi, s_tn);
   }
 }
 
@@ -695,6 +656,7 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   __shared__ int s_stop, s_last, s_npend;
   __shared__ float s_csc[kMaxRP];
   __shared__ float s_zi;
+  __shared__ const float* s_tn;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x;
   const int64_t S = a.S, ks = a.ks;
@@ -725,6 +687,7 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     if (ctl && ctl->range_err) ctl->abort = 1;
     s_npend = 0;
     s_zi = a.zscale ? a.zscale[1] : 1.f;
+    s_tn = (ctl && ctl->slot_parity) ? a.Tn1 : a.Tn0;
   }
   if (tid < kMaxRP) s_csc[tid] = (tid < a.RP && a.cscale) ? a.cscale[tid] : 1.f;
   __syncthreads();
@@ -883,7 +846,7 @@ k_prod_h16(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     const int64_t t = a.pend[(int64_t)c * a.maxpend + k];
     const int64_t c_first = cta_of(t * ks, S, G);
     const int nseg = (int)(cta_of((t + 1) * ks - 1, S, G) - c_first + 1);
-    tile_finish<RPp>(a, t, nseg, tid, kThreads16, 0, Ps, Ts, s_csc, s_zi);
+    tile_finish<RPp>(a, t, nseg, tid, kThreads16, 0, Ps, Ts, s_csc, s_zi, s_tn);
   }
 }
 
@@ -1056,6 +1019,7 @@ void launch_prod_tc(const TcLaunch& l, cudaStream_t st) {
   a.zscale = l.zscale;
   a.gram_part = l.gram_part;
   a.gram_mode = l.gram_mode;
+  a.z_prefetch = l.z_prefetch;
   a.t_upper = l.t_upper;
   a.pend = l.pend;
   a.maxpend = l.geom.maxpend;
