@@ -95,6 +95,7 @@ struct godec_ctx {
   char* gparts = nullptr;              // per product: tiles x RP x RP Gram partials (double room)
   size_t gpart_stride = 0;
   double* g64 = nullptr;               // per product reduced Gram, + 2 for the CholeskyQR2 rounds
+  float* g32 = nullptr;                // the same in float (read by the float32 factorisations)
   float* gscr = nullptr;               // Gram partials of the second CholeskyQR2 round
   float* Rtmp = nullptr;               // exact path: factor of each product and its inverse (2 rr each)
   float* Rslot = nullptr;              // [2][nprod] lagged factors
@@ -264,6 +265,11 @@ void refresh_z16(godec_ctx* c) {
   launch_to_half(c->Zt, c->p.n, c->p.m, c->ldzt, c->Zt16, c->ldzt, c->nsm, c->st);
 }
 double* g64(godec_ctx* c, int i) { return c->g64 + (size_t)i * c->RP * c->RP; }
+// The float copy of a Gram in c->g64 (written by the same Gram sum), else null.
+float* g32_of(godec_ctx* c, const double* g) {
+  const size_t n = (size_t)(c->nprod + 2) * c->RP * c->RP;
+  return (c->g32 && g >= c->g64 && g < c->g64 + n) ? c->g32 + (g - c->g64) : nullptr;
+}
 
 // Product i of the chain: even i streams Z (rows m, K n), odd i streams Z^T (rows n, K m).
 // Its skinny operand is the split transposed output of product i-1 (A1 for i = 0); the
@@ -308,13 +314,13 @@ cudaEvent_t record(godec_ctx* c, cudaStream_t s) {
 }
 
 void gram_sum(godec_ctx* c, const void* part, int dbl, int64_t nblk, double* out, cudaStream_t s) {
-  PROF(c, 1, s, launch_gram_sum(part, dbl, nblk, c->RP, out, c->ctl, s));
+  PROF(c, 1, s, launch_gram_sum(part, dbl, nblk, c->RP, out, c->ctl, s, g32_of(c, out)));
 }
 
 // R with Rᵀ R = Gram, and T = R^{-1} stored right after R.
 void chol(godec_ctx* c, const double* g, float* R, float alarm_ratio = 0.f) {
   PROF(c, 2, c->st, launch_chol(g, c->r, c->RP, R, R + (size_t)c->RP * c->RP, c->ctl, c->st, alarm_ratio,
-                                (c->p.flags & GODEC_FLAG_FP64_FACTOR) != 0));
+                                (c->p.flags & GODEC_FLAG_FP64_FACTOR) != 0, g32_of(c, g)));
 }
 const float* inv_of(godec_ctx* c, const float* R) { return R + (size_t)c->RP * c->RP; }
 
@@ -337,6 +343,7 @@ void final_cqr2(godec_ctx* c, int64_t rows, const double* g1, float* Ra, float* 
 }
 
 void slot(godec_ctx* c, SlotLaunch& sl) {
+  sl.g32 = g32_of(c, sl.g64);
   sl.r = c->r;
   sl.RP = c->RP;
   sl.ctl = c->ctl;
@@ -1006,7 +1013,7 @@ void godec_destroy(godec_ctx* c) {
   free_graphs(c);
   void* ptrs[] = {c->Z, c->Zt, c->Z16, c->Zt16, c->A1, c->A1_orig, c->P, c->bt2, c->cs, c->rescale_tmp, c->LA, c->LB, c->Q1, c->Q2,
                   c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->pend, c->gparts, c->RA, c->RB, c->Wa, c->Wb, c->Qa, c->Qb, c->Qtmp, c->Rf,
-                  c->cs_ref, c->rf_part, c->rf_g, c->rf_C, c->rf_core, c->rf_U, c->rf_V, c->g64, c->gscr,
+                  c->cs_ref, c->rf_part, c->rf_g, c->rf_C, c->rf_core, c->rf_U, c->rf_V, c->g64, c->g32, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
                   c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1], c->sbits};
   for (void* p : ptrs) cudaFree(p);
@@ -1156,6 +1163,7 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
   c->gpart_stride = ((size_t)tiles * rr * sizeof(double) + 255) & ~size_t(255);
   CKI(dalloc(&c->gparts, c->gpart_stride * np));
   CKI(dalloc(&c->g64, (size_t)(np + 2) * rr));
+  CKI(dalloc(&c->g32, (size_t)(np + 2) * rr));
   CKI(dalloc(&c->gscr, (size_t)apply_blocks(mx) * rr));
   CKI(dalloc(&c->Rtmp, (size_t)np * 2 * rr));
   CKI(dalloc(&c->Rslot, (size_t)2 * np * rr));

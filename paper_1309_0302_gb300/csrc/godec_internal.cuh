@@ -197,12 +197,13 @@ int64_t apply_blocks(int64_t rows);
 // gram_part.
 void launch_gram_tiles(const float* Y, int64_t rows, int RP, int mode, void* part, const Ctl* ctl, cudaStream_t st);
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
-                     cudaStream_t st);
+                     cudaStream_t st, float* out32 = nullptr);
 // R (upper, Rᵀ R = Gram) and T = R^{-1}, both RP x RP.
 void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
-                 float alarm_ratio = 0.f, bool fp64 = false);
+                 float alarm_ratio = 0.f, bool fp64 = false, const float* g32 = nullptr);
 struct SlotLaunch {
   const double* g64 = nullptr;
+  const float* g32 = nullptr;   // float copy of g64 (nullable)
   int g_is_p = 0;
   const float* R_app[2] = {nullptr, nullptr};
   const float* T_app[2] = {nullptr, nullptr};

@@ -19,8 +19,10 @@
 // per warp in shared memory (the histogram's space) and written out with one global
 // atomic per full buffer, so no tile waits on a contended atomic.
 //
-// Warps: 0 TMA producer (X, B and A tiles), 1 MMA issuer and TMEM owner, 2-9
-// epilogue (two per TMEM lane quarter, one per 32-column half of the tile).  Tiles
+// Warps: 0 TMA producer (X, B and A tiles), 1 MMA issuer and TMEM owner, 2-17
+// epilogue (four per TMEM lane quarter, one per 16-column quarter of the tile: with
+// four epilogue warps per scheduler the per-element chains overlap, where two left the
+// pass bound by their latency at about half the memory rate).  Tiles
 // are taken in row-band order in one contiguous range per CTA, so A changes at most
 // a few times per CTA.  Every wait is bounded; a timeout sets ctl->timeout.
 #include <cuda.h>
@@ -37,7 +39,8 @@ using namespace tc;
 
 constexpr int RM = 128, RNC = 64;           // tile rows and columns
 constexpr int NXS = 4, NBS = 2;             // X slots, B slots (B tiles come from L2)
-constexpr int kEpiW = 8;
+constexpr int kEpiW = 16;
+constexpr int kECols = RNC / (kEpiW / 4);   // columns of a tile per epilogue thread
 constexpr int kRThreads = 32 * (2 + kEpiW);
 constexpr size_t kXBox = (size_t)RM * 32 * 4;     // 32 float32 columns x 128 rows = 16 KB
 constexpr size_t kXSlot = 2 * kXBox;
@@ -51,7 +54,7 @@ constexpr size_t kOffH = kOffA + 2 * kAHalf;
 constexpr size_t kRSmem = kOffH + (size_t)kHistBins * 4 + 1024;
 constexpr uint32_t kRWait = 1u << 20;
 constexpr float kLoInv = 1.f / 2048.f;
-constexpr int kStage = 128;                       // staged candidates per epilogue warp
+constexpr int kStage = 64;                        // staged candidates per epilogue warp
 static_assert(kEpiW * kStage * 16 <= kHistBins * 4, "candidate staging fits the histogram space");
 static_assert(kRSmem <= 232448 - 1024, "shared memory of the residual pass");
 
@@ -229,8 +232,9 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
     // Each thread owns one row and 32 columns of the tile: R = X - (D_h + 2^-11 D_l) / s_Z,
     // formed with two FMAs (1 / s_Z is a power of two, so the scaled terms are exact).
     const int w = warp - 2;
-    const int q4 = warp & 3, half = w >> 2;
+    const int q4 = warp & 3, cq = w >> 2;   // TMEM lane quarter; column quarter of the tile
     const int row = q4 * 32 + lane, sw = row & 7;
+    const int f4b = (cq & 1) * 4;           // this quarter's first float4 in its 128-byte box row
     const uint32_t tlane = (uint32_t)(q4 * 32) << 16;
     const float zinv = a.zscale[1], zlo = zinv * kLoInv;
     // candidate iff key >= max(guess, 1); for a non-NaN value that is |R| >= gf (a NaN
@@ -270,20 +274,20 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
         break;
       }
       tc_fence_after();
-      const uint32_t taddr = tbase + (uint32_t)(b * 128) + tlane + (uint32_t)(half * 32);
-      float vh[32], vl[32];
-      tmem_ld32x2(taddr, taddr + 64, vh, vl);
+      const uint32_t taddr = tbase + (uint32_t)(b * 128) + tlane + (uint32_t)(cq * kECols);
+      float vh[kECols], vl[kECols];
+      tmem_ld16x2(taddr, taddr + 64, vh, vl);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&accempty[b]);
-      float4* xs = reinterpret_cast<float4*>(sX + sx * kXSlot + half * kXBox + row * 128);
+      float4* xs = reinterpret_cast<float4*>(sX + sx * kXSlot + (cq >> 1) * kXBox + row * 128);
       float f0 = 0.f, f1 = 0.f;
       if (mode == PASS_CAND) {
         // pass 1: R back into this thread's own X row segment, candidate columns as a mask
         unsigned cm = 0u;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 x = xs[u ^ sw];
+        for (int u = 0; u < kECols / 4; ++u) {
+          const float4 x = xs[(f4b + u) ^ sw];
           float r[4];
           const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -294,11 +298,11 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
             else if (e & 1) f1 = fmaf(r[e], r[e], f1);
             else f0 = fmaf(r[e], r[e], f0);
           }
-          xs[u ^ sw] = make_float4(r[0], r[1], r[2], r[3]);
+          xs[(f4b + u) ^ sw] = make_float4(r[0], r[1], r[2], r[3]);
         }
         const float* xf = reinterpret_cast<const float*>(xs);
         if (!isfinite(f0 + f1))   // rare: tell a NaN or an infinity from an overflowing sum
-          for (int t = 0; t < 32; ++t) bad |= rkey(xf[t]) >= 0x7f800000u;
+          for (int t = 0; t < kECols; ++t) bad |= rkey(xf[(((f4b + (t >> 2)) ^ sw) << 2) | (t & 3)]) >= 0x7f800000u;
         // pass 2: the candidates, one per lane and round, in lane order
         const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(cm));
         if (tot) {
@@ -316,7 +320,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
             dv = a.cand_val + base;
             lim = a.cand_cap > base ? a.cand_cap - base : 0ull;
           }
-          const long long rb = (long long)((ib * RM + row) * n + jb * RNC + half * 32);
+          const long long rb = (long long)((ib * RM + row) * n + jb * RNC + cq * kECols);
           unsigned pos = 0u, mm = cm;
           unsigned bal = __ballot_sync(0xffffffffu, mm != 0u);
           while (bal) {
@@ -324,7 +328,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
               const int q = __ffs(mm) - 1;
               mm &= mm - 1u;
               const unsigned p = pos + __popc(bal & lt_mask);
-              const float v = xf[(((q >> 2) ^ sw) << 2) | (q & 3)];
+              const float v = xf[(((f4b + (q >> 2)) ^ sw) << 2) | (q & 3)];
               const unsigned key = rkey(v);
               bad |= key >= 0x7f800000u;
               if (p < lim) {
@@ -341,8 +345,8 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
         fence_proxy_async();   // the in-place writes precede the slot's next TMA fill
       } else if (mode == PASS_FULL) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 x = xs[u ^ sw];
+        for (int u = 0; u < kECols / 4; ++u) {
+          const float4 x = xs[(f4b + u) ^ sw];
           const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -356,10 +360,10 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
           }
         }
       } else {   // dump
-        const int64_t i = ib * RM + row, j0 = jb * RNC + half * 32;
+        const int64_t i = ib * RM + row, j0 = jb * RNC + cq * kECols;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 x = xs[u ^ sw];
+        for (int u = 0; u < kECols / 4; ++u) {
+          const float4 x = xs[(f4b + u) ^ sw];
           const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {

@@ -31,7 +31,8 @@ constexpr int LD = kMaxRP + 1;
 constexpr int GS_ENT = 32, GS_SPLIT = 8;
 template <typename T>
 __global__ void __launch_bounds__(GS_ENT * GS_SPLIT)
-k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out, const Ctl* ctl) {
+k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out, float* __restrict__ out32,
+           const Ctl* ctl) {
   if (ctl && ctl->abort) return;
   __shared__ double red[GS_SPLIT][GS_ENT];
   const int lane = threadIdx.x % GS_ENT, sp = threadIdx.x / GS_ENT;
@@ -52,6 +53,7 @@ k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restri
 #pragma unroll
     for (int k = 0; k < GS_SPLIT; ++k) t += red[k][lane];
     out[e] = t;
+    if (out32) out32[e] = (float)t;   // the float copy: its reader then needs no float64 work
   }
 }
 
@@ -189,16 +191,28 @@ __device__ void load_gram_nb(float (*G)[LD], const double* g64, int r, int RP, i
   if (bad) *nf = 1;
 }
 
-__device__ void store_mat(float* dst, const float (*S)[LD], int RP) {
-  for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) dst[e] = S[e / RP][e % RP];
+// The same from the float copy of the Gram (written beside the float64 one by k_gram_sum):
+// no float64 instruction, whose rate on GB300 would make these 4096 conversions and checks
+// take microseconds on the one SM.
+__device__ void load_gram32_nb(float (*G)[LD], const float* g32, int r, int RP, int* nf) {
+  float v[kPerThread];
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int e = threadIdx.x + k * SMALL_THREADS, i = e / kMaxRP, j = e % kMaxRP;
+    v[k] = (i < r && j < r) ? __ldcg(g32 + i * RP + j) : (i == j ? 1.f : 0.f);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int e = threadIdx.x + k * SMALL_THREADS;
+    bad |= !isfinite(v[k]);
+    G[e / kMaxRP][e % kMaxRP] = v[k];
+  }
+  if (bad) *nf = 1;
 }
 
-// Gram (double, RP x RP) into float G, padded block set to the identity.  False if
-// the Gram holds NaN/Inf.
-__device__ bool load_gram(float (*G)[LD], const double* g64, int r, int RP) {
-  int nf = 0;
-  load_gram_nb(G, g64, r, RP, &nf);
-  return __syncthreads_or(nf) == 0;
+__device__ void store_mat(float* dst, const float (*S)[LD], int RP) {
+  for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) dst[e] = S[e / RP][e % RP];
 }
 
 // Largest |M[i][j]| over the n x n block (all threads get it).
@@ -220,73 +234,113 @@ __device__ float block_absmax(const float (*M)[LD], int n) {
 // augmented matrix [G | I] with one barrier per column.  With G = L D L^T (L unit lower),
 // the elimination leaves U = D L^T in the left block and E = L^{-1} in the right one, so
 // R = D^{-1/2} U and R^{-1} = E^T D^{-1/2}.  The trailing block is updated in full (both
-// triangles), so column j holds the multipliers of step j.  Thread (rw, cc) owns column
-// index cc and every fourth row: while cc > j it addresses the left block, once cc <= j
-// the right one (E's columns beyond j are still those of I and need no update, and the
-// left columns up to j are no longer read).  A (n rows) is overwritten with U in its upper
-// triangle; E must hold I on entry.  Pivots j < nchk at or below thr are raised to thr and
-// reported through *bad; dv receives the pivots used.
-__device__ void chol_elim(float (*A)[LD], float (*E)[LD], int n, int nchk, float thr, int* bad, float* dv) {
+// triangles), so column j holds the multipliers of step j.
+// Thread (rw, cc) = (tid / 64, tid % 64) holds one column index cc and the rows of class rw
+// (a = rw mod 4) not yet final, row rw + 4 (k + m) in register slot k (m rows of the class
+// are final already): column cc of the left block until step cc, where the left column is
+// done (its entries below the pivot are the multipliers, used in that step only) and the
+// same registers take column cc of E over (I's column, zero in the rows kept).  Step j:
+// the owners of row j (slot 0 of class j mod 4, final since step j-1) publish it as the
+// pivot row, store it to Us / Es and shift it out of their registers (so every register
+// index stays static); the pivot's owner publishes 1 / pivot; the owners of column j
+// publish the multipliers' numerators, zero for the rows not updated.  After the barrier a
+// step is one fma per register.  Only those rows and columns pass through shared memory
+// (double-buffered, so one barrier a step), and no lane branches on its entries.  On return
+// Us / Es (64 x LD) hold U and E by rows (columns < n).
+constexpr int kRowsPT = kMaxRP / 4;
+
+__device__ __forceinline__ void chol_reg_core(float (&V)[kRowsPT], int n, int nchk, float thr, int* bad, float* dv,
+                                              float (*Us)[LD], float (*Es)[LD]) {
+  __shared__ __align__(16) float prow[2][kMaxRP];   // row j: left entries (cc > j), E entries (cc <= j)
+  __shared__ __align__(16) float pcol[2][kMaxRP];   // column j, slot k of class rw at rw * 16 + k
+  __shared__ float pinv[2];
   const int tid = threadIdx.x, cc = tid & 63, rw = tid >> 6;
   for (int j = 0; j < n; ++j) {
-    float d = A[j][j];
-    if (j < nchk && !(d > thr)) {
-      d = thr > 0.f ? thr : 1e-30f;
-      if (tid == 0) *bad = 1;
-    }
-    if (tid == 0) dv[j] = d;
-    const float invd = 1.f / d;
-    if (cc < n) {
-      float* col = (cc > j) ? &A[0][cc] : &E[0][cc];
-      const float pj = col[j * LD];
-#pragma unroll 4
-      for (int a = j + 1 + rw; a < n; a += 4) {
-        const float mult = A[a][j] * invd;
-        col[a * LD] = fmaf(-mult, pj, col[a * LD]);
+    const int b = j & 1;
+    const bool owner = rw == (j & 3);
+    const int m = (j + 3 - rw) >> 2;   // rows of this class before row j, already shifted out
+    if (owner && cc < n) {
+      const float v0 = V[0];
+      prow[b][cc] = (cc == j) ? 1.f : v0;
+      Us[j][cc] = (cc >= j) ? v0 : 0.f;
+      Es[j][cc] = (cc < j) ? v0 : ((cc == j) ? 1.f : 0.f);
+      if (cc == j) {
+        float d = v0;
+        if (j < nchk && !(d > thr)) {
+          d = thr > 0.f ? thr : 1e-30f;
+          *bad = 1;
+        }
+        dv[j] = d;
+        pinv[b] = 1.f / d;
       }
     }
+    if (cc == j) {
+#pragma unroll
+      for (int k = 0; k < kRowsPT; k += 4) {
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = rw + 4 * (k + u + m);
+          w[u] = (a > j && a < n) ? V[k + u] : 0.f;
+        }
+        *reinterpret_cast<float4*>(&pcol[b][rw * 16 + k]) = make_float4(w[0], w[1], w[2], w[3]);
+      }
+#pragma unroll
+      for (int k = 0; k < kRowsPT; ++k) V[k] = 0.f;   // column j of E from here on
+    }
     __syncthreads();
+    if (cc < n) {
+      const float pj = prow[b][cc] * pinv[b];
+#pragma unroll
+      for (int k = 0; k < kRowsPT; k += 4) {
+        const float4 m4 = *reinterpret_cast<const float4*>(&pcol[b][rw * 16 + k]);
+        V[k] = fmaf(-m4.x, pj, V[k]);
+        V[k + 1] = fmaf(-m4.y, pj, V[k + 1]);
+        V[k + 2] = fmaf(-m4.z, pj, V[k + 2]);
+        V[k + 3] = fmaf(-m4.w, pj, V[k + 3]);
+      }
+    }
+    if (owner) {   // row j is out: the next row of this class moves to slot 0
+#pragma unroll
+      for (int k = 0; k + 1 < kRowsPT; ++k) V[k] = V[k + 1];
+      V[kRowsPT - 1] = 0.f;
+    }
   }
+  __syncthreads();
 }
 
 // Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
 // numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
-// factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.  G is kept;
-// R receives the factor (upper, zero below), E (64 x LD) L^{-1} and dv the pivots, so that
-// R^{-1}[i][c] = E[c][i] / sqrt(dv[c]) for c >= i.
-__device__ void robust_chol(const float (*G)[LD], float (*R)[LD], float (*E)[LD], float* dv, int r, int RP,
-                            Ctl* ctl) {
+// factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.  G (64 x 64,
+// padded block the identity) is kept; on return Us / Es hold U and E (chol_reg_core) and
+// dv the pivots used: R[a][c] = Us[a][c] / sqrt(dv[a]) (c > a), R[a][a] = sqrt(dv[a]),
+// R^{-1}[i][c] = Es[c][i] / sqrt(dv[c]) (c >= i).
+__device__ __forceinline__ void robust_chol(const float (*G)[LD], float (*Us)[LD], float (*Es)[LD], float* dv, int r,
+                                            int RP, Ctl* ctl) {
   __shared__ float s_gmax;
   __shared__ int s_bad;
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.x, cc = tid & 63, rw = tid >> 6;
+  if (tid < 32) {
     float gm = 0.f;
-    for (int j = 0; j < r; ++j) gm = fmaxf(gm, G[j][j]);
-    s_gmax = gm;
+    for (int j = tid; j < r; j += 32) gm = fmaxf(gm, G[j][j]);
+    for (int o = 16; o; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if (tid == 0) s_gmax = gm;
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
     __syncthreads();
-    for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
-      const int i = e / kMaxRP, j = e % kMaxRP;
-      R[i][j] = G[i][j] + ((attempt == 1 && i == j && i < r) ? 1e-5f * s_gmax : 0.f);
-      E[i][j] = (i == j) ? 1.f : 0.f;
+    const float shift = attempt == 1 ? 1e-5f * s_gmax : 0.f;
+    float V[kRowsPT];
+#pragma unroll
+    for (int k = 0; k < kRowsPT; ++k) {
+      const int a = rw + 4 * k;
+      V[k] = G[a][cc] + ((a == cc && a < r) ? shift : 0.f);
     }
-    if (threadIdx.x == 0) s_bad = 0;
+    if (tid == 0) s_bad = 0;
     __syncthreads();
-    chol_elim(R, E, RP, r, 1e-6f * s_gmax, &s_bad, dv);
+    chol_reg_core(V, RP, r, 1e-6f * s_gmax, &s_bad, dv, Us, Es);
     if (!s_bad) break;
-    if (threadIdx.x == 0) ctl->chol_shifts += 1;
+    if (tid == 0) ctl->chol_shifts += 1;
   }
-  // R = D^{-1/2} U, the lower triangle cleared
-  for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {
-    const int i = e / kMaxRP, c = e % kMaxRP;
-    float v = 0.f;
-    if (i < RP && c < RP && c >= i) {
-      const float si = rsqrtf(dv[i]);
-      v = (c == i) ? dv[i] * si : R[i][c] * si;
-    }
-    R[i][c] = v;
-  }
-  __syncthreads();
 }
 
 // dst = M / max|M|, ctl->m_logscale (+)= log(max|M|).
@@ -348,7 +402,8 @@ __device__ void chol64(double (*Gd)[LD], float (*R)[LD], int r, int RP, double t
 // F64: the factorisation runs in float64 (chol64) instead of the blocked float32 Cholesky;
 // either way R and T = R^{-1} are stored in float32 and T is formed in float32.
 template <bool F64>
-__global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict__ g64, int r, int RP,
+__global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict__ g64, const float* __restrict__ g32,
+                                                        int r, int RP,
                                                         float* __restrict__ Rout, float* __restrict__ Tout,
                                                         float alarm_ratio, Ctl* ctl) {
   if (ctl->abort) return;
@@ -359,11 +414,15 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
   if (!F64) {
     float (*G)[LD] = reinterpret_cast<float (*)[LD]>(smf);
     float (*E)[LD] = G + kMaxRP;
-    if (!load_gram(G, g64, r, RP)) {
+    int nf = 0;
+    if (g32) load_gram32_nb(G, g32, r, RP, &nf);
+    else load_gram_nb(G, g64, r, RP, &nf);
+    if (__syncthreads_or(nf)) {
       if (threadIdx.x == 0) { ctl->nonfinite = 1; ctl->abort = 1; }
       return;
     }
-    robust_chol(G, R, E, dv, r, RP, ctl);
+    (void)E;
+    robust_chol(G, R, Ri, dv, r, RP, ctl);   // U into R's block, E into Ri's
   } else {
   double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);            // 2 float blocks
   __shared__ double s_gmax;
@@ -413,22 +472,27 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
   }
   if (alarm_ratio > 0.f && threadIdx.x < 32) {
     float lo = 3.4e38f, hi = 0.f;
-    for (int j = threadIdx.x; j < r; j += 32) { lo = fminf(lo, R[j][j]); hi = fmaxf(hi, R[j][j]); }
+    for (int j = threadIdx.x; j < r; j += 32) {
+      const float dj = F64 ? R[j][j] : sqrtf(dv[j]);
+      lo = fminf(lo, dj);
+      hi = fmaxf(hi, dj);
+    }
     for (int o = 16; o; o >>= 1) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if (threadIdx.x == 0 && !(hi <= alarm_ratio * lo)) { ctl->alarm = 1; ctl->abort = 1; }
   }
-  store_mat(Rout, R, RP);
   if (!F64) {
-    // T = E^T D^{-1/2} from the elimination
-    const float (*E)[LD] = reinterpret_cast<const float (*)[LD]>(smf) + kMaxRP;
+    // R = D^{-1/2} U and T = E^T D^{-1/2} (U in R's block, E in Ri's)
     for (int e = threadIdx.x; e < RP * RP; e += SMALL_THREADS) {
       const int i = e / RP, c = e % RP;
-      Tout[e] = (c >= i) ? E[c][i] * rsqrtf(dv[c]) : 0.f;
+      const float si = rsqrtf(dv[i]);
+      Rout[e] = (c > i) ? R[i][c] * si : ((c == i) ? dv[i] * si : 0.f);
+      Tout[e] = (c >= i) ? Ri[c][i] * rsqrtf(dv[c]) : 0.f;
     }
   } else {
+    store_mat(Rout, R, RP);
     tri_inverse(R, Ri, RP, nullptr);
     store_mat(Tout, Ri, RP);
   }
@@ -441,6 +505,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
 // the applied factor also enters Pi := R_app Pi (the core of eq. mlr_app).
 struct SlotArgs {
   const double* g64;       // Gram of Q~ (fast path), or of P when g_is_p (then Q~ = P T_app)
+  const float* g32;        // its float copy (nullable)
   int g_is_p;
   const float* R_app[2];   // applied factor, by slot parity (both null: identity)
   const float* T_app[2];   // its inverse (needed when g_is_p)
@@ -478,7 +543,10 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
   if (a.L2) load_mat_nb(E2, a.L2, RP);
   if (a.fast && a.g_is_p) load_mat_nb(TA, a.T_app[cur], RP);
   if (a.pi_mode == 1) load_mat_nb(PI, a.Pi, RP);
-  if (a.fast) load_gram_nb(A, a.g64, r, RP, &nf);
+  if (a.fast) {
+    if (a.g32) load_gram32_nb(A, a.g32, r, RP, &nf);
+    else load_gram_nb(A, a.g64, r, RP, &nf);
+  }
   const int any_nf = __syncthreads_or(nf);
   if (a.L1) mat_mul(E1, B, B, RP, true);             // B = L1 R_app
   if (a.L2) mat_mul(E2, B, B, RP, true);             // B = L2 L1 R_app
@@ -502,7 +570,17 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
       __syncthreads();
     }
     __shared__ float dv[kMaxRP];
-    robust_chol(A, C, D, dv, r, RP, ctl);            // C = R~ (D: scratch)
+    robust_chol(A, C, D, dv, r, RP, ctl);            // U into C, E into D (scratch)
+    for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {   // C = R~, in place
+      const int i = e / kMaxRP, c = e % kMaxRP;
+      float v = 0.f;
+      if (i < RP && c < RP && c >= i) {
+        const float si = rsqrtf(dv[i]);
+        v = (c == i) ? dv[i] * si : C[i][c] * si;
+      }
+      C[i][c] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       float lo = 3.4e38f, hi = 0.f;
       for (int j = 0; j < r; ++j) { lo = fminf(lo, C[j][j]); hi = fmaxf(hi, C[j][j]); }
@@ -893,26 +971,27 @@ cudaError_t prepare_small_kernels() {
 }
 
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
-                     cudaStream_t st) {
+                     cudaStream_t st, float* out32) {
   const int npair = RP * RP;
   const unsigned grid = (unsigned)((npair + GS_ENT - 1) / GS_ENT);
   if (gram_double)
     k_gram_sum<double><<<grid, GS_ENT * GS_SPLIT, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out,
-                                                            ctl);
+                                                            out32, ctl);
   else
     k_gram_sum<float><<<grid, GS_ENT * GS_SPLIT, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out,
-                                                           ctl);
+                                                           out32, ctl);
 }
 
 void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
-                 float alarm_ratio, bool fp64) {
-  if (fp64) k_chol<true><<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, T, alarm_ratio, ctl);
-  else k_chol<false><<<1, SMALL_THREADS, kSmall4, st>>>(g64, r, RP, R, T, alarm_ratio, ctl);
+                 float alarm_ratio, bool fp64, const float* g32) {
+  if (fp64) k_chol<true><<<1, SMALL_THREADS, kSmall4, st>>>(g64, nullptr, r, RP, R, T, alarm_ratio, ctl);
+  else k_chol<false><<<1, SMALL_THREADS, kSmall4, st>>>(g64, g32, r, RP, R, T, alarm_ratio, ctl);
 }
 
 void launch_slot(const SlotLaunch& l, cudaStream_t st) {
   SlotArgs a;
   a.g64 = l.g64;
+  a.g32 = l.g32;
   a.g_is_p = l.g_is_p;
   for (int h = 0; h < 2; ++h) {
     a.R_app[h] = l.R_app[h];

@@ -286,23 +286,26 @@ cudaError_t prepare_prod_t() {
 
 // ----------------------------------------------------------------------------------
 // Q = P T (T dense RP x RP; a triangular inverse is passed as a dense matrix), for
-// rows x RP row-major P.  32 rows per block, eight threads per row (8 output columns
-// each, RP a multiple of 8), two blocks per SM at the chain's sizes; the block's rows
-// are staged in shared memory before any output is written, so P and Q may alias.
-// Optional outputs: Q itself, the float16 split transposed copy for the tensor-core
-// product, and the block's float Gram partial QᵀQ.
+// rows x RP row-major P.  64 rows per block; thread (g, c) keeps column c of T in registers
+// and forms Q[i][c] for the rows i = g mod 4 of the block, reading each row of P as float4
+// broadcasts (one shared-memory wavefront per four fmas of the warp; staging T per thread
+// row instead re-reads it for every row and leaves the kernel bound by shared memory).
+// The block's rows are staged in shared memory before any output is written, so P and Q
+// may alias.  Optional outputs: Q itself, the float16 split transposed copy for the
+// tensor-core product, and the block's float Gram partial QᵀQ.
 // ----------------------------------------------------------------------------------
-constexpr int RB = 32;              // rows per block
+constexpr int RB = 64;              // rows per block
 constexpr int AP_THREADS = 256;
-constexpr int AP_LD = kMaxRP + 1;   // odd stride: rows of a warp fall in different banks
+constexpr int AP_PLD = kMaxRP + 4;  // P rows: float4-aligned (read as broadcasts)
+constexpr int AP_OLD = kMaxRP + 1;  // T, then the output rows: odd stride, column reads conflict-free
 
 __global__ void __launch_bounds__(AP_THREADS)
 k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, const float* __restrict__ T1, float* Q,
         float* __restrict__ gram_part, const Ctl* ctl, void* __restrict__ bt2, int64_t ldb) {
   if (ctl && ctl->abort) return;
   const float* T = (ctl && ctl->slot_parity) ? T1 : T0;
-  __shared__ __align__(16) float Ts[kMaxRP][kMaxRP];
-  __shared__ float Ps[RB][AP_LD];
+  __shared__ float Ts[kMaxRP * AP_OLD];   // T, then the output rows
+  __shared__ __align__(16) float Ps[RB * AP_PLD];
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * RB;
   const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
@@ -323,90 +326,95 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
     const int e = tid + k * AP_THREADS;
     pv[k] = e < nP4 ? __ldcg(P4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  // T rows and P rows into shared memory; P's columns RP .. kMaxRP-1 and rows past nrow zero
 #pragma unroll
   for (int k = 0; k < kT4; ++k) {
     const int e = tid + k * AP_THREADS;
-    if (e < nT4) *reinterpret_cast<float4*>(&Ts[e / RP4][(e % RP4) * 4]) = tv[k];
+    if (e < nT4) {
+      float* t = Ts + (e / RP4) * AP_OLD + (e % RP4) * 4;
+      t[0] = tv[k].x;
+      t[1] = tv[k].y;
+      t[2] = tv[k].z;
+      t[3] = tv[k].w;
+    }
   }
 #pragma unroll
   for (int k = 0; k < kP4; ++k) {
-    const int e = tid + k * AP_THREADS;
-    if (e < RB * RP4) {
-      const int i = e / RP4, c = (e % RP4) * 4;
-      const float4 v = pv[k];   // rows past nrow load as zero
-      Ps[i][c] = v.x;
-      Ps[i][c + 1] = v.y;
-      Ps[i][c + 2] = v.z;
-      Ps[i][c + 3] = v.w;
-    }
+    const int e = tid + k * AP_THREADS;   // float4 e of the block's rows (row e / RP4)
+    if (e < RB * RP4) *reinterpret_cast<float4*>(Ps + (e / RP4) * AP_PLD + (e % RP4) * 4) = pv[k];
   }
+  const int pad4 = kMaxRP / 4 - RP4;
+  for (int e = tid; e < RB * pad4; e += AP_THREADS)
+    *reinterpret_cast<float4*>(Ps + (e / pad4) * AP_PLD + (RP4 + e % pad4) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
-  const int row = tid >> 3, cg = (tid & 7) * 8;   // this thread: row, columns cg .. cg+7
-  float q[8];
+  const int c = tid & 63, g = tid >> 6;
+  float tcol[kMaxRP];
 #pragma unroll
-  for (int l = 0; l < 8; ++l) q[l] = 0.f;
-  if (cg < RP) {
-#pragma unroll 4
-    for (int a = 0; a < RP; ++a) {
-      const float pa = Ps[row][a];
-      const float4 t0 = *reinterpret_cast<const float4*>(&Ts[a][cg]);
-      const float4 t1 = *reinterpret_cast<const float4*>(&Ts[a][cg + 4]);
-      q[0] = fmaf(pa, t0.x, q[0]);
-      q[1] = fmaf(pa, t0.y, q[1]);
-      q[2] = fmaf(pa, t0.z, q[2]);
-      q[3] = fmaf(pa, t0.w, q[3]);
-      q[4] = fmaf(pa, t1.x, q[4]);
-      q[5] = fmaf(pa, t1.y, q[5]);
-      q[6] = fmaf(pa, t1.z, q[6]);
-      q[7] = fmaf(pa, t1.w, q[7]);
+  for (int a = 0; a < kMaxRP; ++a) tcol[a] = (a < RP && c < RP) ? Ts[a * AP_OLD + c] : 0.f;
+  float acc[RB / 4];
+#pragma unroll
+  for (int k = 0; k < RB / 4; ++k) acc[k] = 0.f;
+#pragma unroll
+  for (int a = 0; a < kMaxRP; a += 4) {
+#pragma unroll
+    for (int k = 0; k < RB / 4; ++k) {
+      const float4 p = *reinterpret_cast<const float4*>(Ps + (g + 4 * k) * AP_PLD + a);
+      acc[k] = fmaf(p.x, tcol[a], acc[k]);
+      acc[k] = fmaf(p.y, tcol[a + 1], acc[k]);
+      acc[k] = fmaf(p.z, tcol[a + 2], acc[k]);
+      acc[k] = fmaf(p.w, tcol[a + 3], acc[k]);
     }
   }
-  __syncthreads();   // every thread has read its P row: Ps now holds Q
-  if (cg < RP)
+  __syncthreads();   // every thread has read T: Ts takes the output rows
+  float* Os = Ts;
+  if (c < RP)
 #pragma unroll
-    for (int l = 0; l < 8; ++l) Ps[row][cg + l] = (row < nrow) ? q[l] : 0.f;
+    for (int k = 0; k < RB / 4; ++k) Os[(g + 4 * k) * AP_OLD + c] = acc[k];
   __syncthreads();
   if (Q)
-    for (int e = tid; e < nrow * RP; e += AP_THREADS) Q[(r0 + e / RP) * RP + e % RP] = Ps[e / RP][e % RP];
+    for (int e = tid; e < nrow * RP; e += AP_THREADS) {
+      const int i = e / RP, cc = e % RP;
+      Q[(r0 + i) * RP + cc] = Os[i * AP_OLD + cc];
+    }
   if (bt2) {
     __half* b2 = reinterpret_cast<__half*>(bt2);
     for (int e = tid; e < RP * RB; e += AP_THREADS) {
-      const int c = e / RB, i = e % RB;   // consecutive threads: consecutive rows of one column
+      const int cc = e / RB, i = e % RB;   // consecutive threads: consecutive rows of one column
       if (i < nrow) {
-        const float v = Ps[i][c] * kSkinnyScale;
+        const float v = Os[i * AP_OLD + cc] * kSkinnyScale;
         const __half c1 = __float2half_rn(v);
-        b2[(int64_t)c * ldb + r0 + i] = c1;
-        b2[(int64_t)(RP + c) * ldb + r0 + i] = __float2half_rn((v - __half2float(c1)) * 2048.f);
+        b2[(int64_t)cc * ldb + r0 + i] = c1;
+        b2[(int64_t)(RP + cc) * ldb + r0 + i] = __float2half_rn((v - __half2float(c1)) * 2048.f);
       }
     }
   }
   if (!gram_part) return;
   // Gram partial: thread (bi, bj) accumulates the 4 x 4 block rows 4bi.., columns 4bj..
   const int bi = tid >> 4, bj = tid & 15;
-  float g[4][4];
+  float gg[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) g[u][v] = 0.f;
+    for (int v = 0; v < 4; ++v) gg[u][v] = 0.f;
   if (4 * bi < RP && 4 * bj < RP) {
 #pragma unroll 4
     for (int i = 0; i < nrow; ++i) {
       float x[4], y[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        x[u] = Ps[i][4 * bi + u];
-        y[u] = Ps[i][4 * bj + u];
+        x[u] = Os[i * AP_OLD + 4 * bi + u];
+        y[u] = Os[i * AP_OLD + 4 * bj + u];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) g[u][v] = fmaf(x[u], y[v], g[u][v]);
+        for (int v = 0; v < 4; ++v) gg[u][v] = fmaf(x[u], y[v], gg[u][v]);
     }
     float* out = gram_part + (int64_t)blockIdx.x * RP * RP;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) out[(4 * bi + u) * RP + 4 * bj + v] = g[u][v];
+      for (int v = 0; v < 4; ++v) out[(4 * bi + u) * RP + 4 * bj + v] = gg[u][v];
   }
 }
 
