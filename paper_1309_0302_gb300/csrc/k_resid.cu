@@ -19,10 +19,13 @@
 // per warp in shared memory (the histogram's space) and written out with one global
 // atomic per full buffer, so no tile waits on a contended atomic.
 //
-// Warps: 0 TMA producer (X, B and A tiles), 1 MMA issuer and TMEM owner, 2-17
-// epilogue (four per TMEM lane quarter, one per 16-column quarter of the tile: with
-// four epilogue warps per scheduler the per-element chains overlap, where two left the
-// pass bound by their latency at about half the memory rate).  Tiles
+// Warps: 0 TMA producer of the X tiles, 18 TMA producer of the B and A tiles (the MMA's
+// operands), 1 MMA issuer and TMEM owner, 2-17 epilogue (four per TMEM lane quarter, one
+// per 16-column quarter of the tile).  With one producer for everything, B(t) (from L2,
+// ~2 us under the stream) was issued only once X(t-1) had a free slot, and the chain
+// epilogue(t-4) -> B(t) -> MMA(t) -> epilogue(t) set the pace at about half the memory
+// rate; with B and A on their own producer and three B slots, the MMAs run ahead and
+// the X ring alone paces the pass.  Tiles
 // are taken in row-band order in one contiguous range per CTA, so A changes at most
 // a few times per CTA.  Every wait is bounded; a timeout sets ctl->timeout.
 #include <cuda.h>
@@ -38,10 +41,12 @@ namespace {
 using namespace tc;
 
 constexpr int RM = 128, RNC = 64;           // tile rows and columns
-constexpr int NXS = 4, NBS = 2;             // X slots, B slots (B tiles come from L2)
+constexpr int NXS = 4, NBS = 3;             // X slots, B slots (B tiles come from L2)
+constexpr int kAcc = 4;                     // accumulators in TMEM (128 columns each)
 constexpr int kEpiW = 16;
 constexpr int kECols = RNC / (kEpiW / 4);   // columns of a tile per epilogue thread
-constexpr int kRThreads = 32 * (2 + kEpiW);
+constexpr int kRThreads = 32 * (3 + kEpiW);
+constexpr int kBWarp = 2 + kEpiW;           // the B / A producer
 constexpr size_t kXBox = (size_t)RM * 32 * 4;     // 32 float32 columns x 128 rows = 16 KB
 constexpr size_t kXSlot = 2 * kXBox;
 constexpr size_t kBBox = (size_t)RNC * 128;       // 64 halves x 64 rows = 8 KB
@@ -72,6 +77,19 @@ struct RTArgs {
 };
 
 __device__ __forceinline__ unsigned rkey(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+
+// r[q] for a run-time q < 16 by a select tree on q's bits: the values stay in registers
+// (an indexed access would put the array in local memory)
+__device__ __forceinline__ float pick16(const float (&r)[16], int q) {
+  float a8[8], a4[4], a2[2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a8[i] = (q & 8) ? r[i + 8] : r[i];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a4[i] = (q & 4) ? a8[i + 4] : a8[i];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) a2[i] = (q & 2) ? a4[i + 2] : a4[i];
+  return (q & 1) ? a2[1] : a2[0];
+}
 
 __device__ __forceinline__ bool wwait(uint64_t* bar, uint32_t parity, int lane) {
   int ok = 1;
@@ -111,8 +129,8 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
   unsigned char* sB = sm + kOffB;
   unsigned char* sA = sm + kOffA;
   unsigned* hist = reinterpret_cast<unsigned*>(sm + kOffH);
-  __shared__ uint64_t xfull[NXS], xempty[NXS], bfull[NBS], bempty[NBS], afull, aempty, accfull[2], accempty[2],
-      mma_done;
+  __shared__ uint64_t xfull[NXS], xempty[NXS], bfull[NBS], bempty[NBS], afull, aempty, accfull[kAcc],
+      accempty[kAcc], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_err;
   __shared__ double s_red[kEpiW];
@@ -132,7 +150,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
     }
     mbar_init(&afull, 1);
     mbar_init(&aempty, 1);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kAcc; ++b) {
       mbar_init(&accfull[b], 1);
       mbar_init(&accempty[b], kEpiW);
     }
@@ -142,19 +160,42 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
   }
   if (mode == PASS_FULL)
     for (int b = tid; b < kHistBins; b += kRThreads) hist[b] = 0u;
-  if (warp == 1) tmem_alloc(&tmem_base, 256);
+  if (warp == 1) tmem_alloc(&tmem_base, 128 * kAcc);
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer: X tiles ----------------
+    if (lane == 0) {
+      int64_t ib = g0 / nbj, jb = g0 % nbj;
+      int sx = 0;
+      uint32_t phx = 0;
+      int64_t nx = 0;
+      const uint64_t pol = policy_evict_first();
+      for (int64_t g = g0; g < g1 && !s_err; ++g) {
+        if (!mbar_wait(&xempty[sx], phx ^ 1u, kRWait)) { rtimeout(ctl, &s_err); break; }
+        // both boxes always: columns past n (and rows past m) are zero-filled, and so are
+        // the rows of A and B past m and n, which makes R exactly 0 there
+        mbar_expect_tx(&xfull[sx], (uint32_t)(2 * kXBox));
+        // X is streamed once per pass and is larger than L2: evict its lines first
+        tma_load_2d_hint(sX + sx * kXSlot, &mapX, &xfull[sx], (int)(jb * RNC), (int)(ib * RM), pol);
+        tma_load_2d_hint(sX + sx * kXSlot + kXBox, &mapX, &xfull[sx], (int)(jb * RNC + 32), (int)(ib * RM), pol);
+        ++nx;
+        if (++sx == NXS) { sx = 0; phx ^= 1u; }
+        if (++jb == nbj) { jb = 0; ++ib; }
+      }
+      // every copy issued has landed before the CTA may exit
+      for (int64_t j = (nx > NXS ? nx - NXS : 0); j < nx; ++j)
+        if (!mbar_wait(&xfull[(int)(j % NXS)], (uint32_t)((j / NXS) & 1), kRWait)) rtimeout(ctl, &s_err);
+    }
+  } else if (warp == kBWarp) {
+    // ---------------- TMA producer: B tiles and the A band ----------------
     if (lane == 0) {
       int64_t band = -1, ib = g0 / nbj, jb = g0 % nbj;
-      int nband = 0, sx = 0, sb = 0;
-      uint32_t phx = 0, phb = 0;
-      int64_t nx = 0, nbb = 0;
-      const uint64_t pol = policy_evict_first();
+      int nband = 0, sb = 0;
+      uint32_t phb = 0;
+      int64_t nbb = 0;
       for (int64_t g = g0; g < g1 && !s_err; ++g) {
         if (ib != band) {
           if (nband > 0 && !mbar_wait(&aempty, (uint32_t)((nband - 1) & 1), kRWait)) { rtimeout(ctl, &s_err); break; }
@@ -169,21 +210,9 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
         tma_load_2d(sB + sb * kBSlot, &mapB, &bfull[sb], 0, (int)(jb * RNC));
         tma_load_2d(sB + sb * kBSlot + kBBox, &mapB, &bfull[sb], 64, (int)(jb * RNC));
         ++nbb;
-        if (!mbar_wait(&xempty[sx], phx ^ 1u, kRWait)) { rtimeout(ctl, &s_err); break; }
-        // both boxes always: columns past n (and rows past m) are zero-filled, and so are
-        // the rows of A and B past m and n, which makes R exactly 0 there
-        mbar_expect_tx(&xfull[sx], (uint32_t)(2 * kXBox));
-        // X is streamed once per pass and is larger than L2: evict its lines first
-        tma_load_2d_hint(sX + sx * kXSlot, &mapX, &xfull[sx], (int)(jb * RNC), (int)(ib * RM), pol);
-        tma_load_2d_hint(sX + sx * kXSlot + kXBox, &mapX, &xfull[sx], (int)(jb * RNC + 32), (int)(ib * RM), pol);
-        ++nx;
         if (++sb == NBS) { sb = 0; phb ^= 1u; }
-        if (++sx == NXS) { sx = 0; phx ^= 1u; }
         if (++jb == nbj) { jb = 0; ++ib; }
       }
-      // every copy issued has landed before the CTA may exit
-      for (int64_t j = (nx > NXS ? nx - NXS : 0); j < nx; ++j)
-        if (!mbar_wait(&xfull[(int)(j % NXS)], (uint32_t)((j / NXS) & 1), kRWait)) rtimeout(ctl, &s_err);
       for (int64_t j = (nbb > NBS ? nbb - NBS : 0); j < nbb; ++j)
         if (!mbar_wait(&bfull[(int)(j % NBS)], (uint32_t)((j / NBS) & 1), kRWait)) rtimeout(ctl, &s_err);
       if (nband > 0 && !mbar_wait(&afull, (uint32_t)((nband - 1) & 1), kRWait)) rtimeout(ctl, &s_err);
@@ -201,9 +230,9 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
           if (!mbar_wait(&afull, (uint32_t)(nb & 1), kRWait)) { rtimeout(ctl, &s_err); break; }
           ++nb;
         }
-        const int b = ai & 1;
+        const int b = ai % kAcc;
         if (!mbar_wait(&bfull[sb], phb, kRWait) ||
-            !mbar_wait(&accempty[b], (uint32_t)(((ai >> 1) & 1) ^ 1), kRWait)) {
+            !mbar_wait(&accempty[b], (uint32_t)(((ai / kAcc) & 1) ^ 1), kRWait)) {
           rtimeout(ctl, &s_err);
           break;
         }
@@ -240,11 +269,13 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
     // candidate iff key >= max(guess, 1); for a non-NaN value that is |R| >= gf (a NaN
     // fails the compare, lands in the sum and is caught there)
     const float gf = __uint_as_float(guess > 1u ? guess : 1u);
-    const unsigned lt_mask = (1u << lane) - 1u;
     int64_t ib = g0 / nbj, jb = g0 % nbj;
     int sx = 0, ai = 0;
     uint32_t phx = 0;
-    double dsum = 0.0;
+    // sum of R^2 over the non-candidates: float per tile, compensated (Kahan) across tiles,
+    // float64 once at the end (a float64 add per tile and thread kept GB300's slow
+    // float64 pipe busy and stalled the epilogue)
+    float ssum = 0.f, scmp = 0.f;
     bool bad = false;
     // this warp's candidate staging area (candidate mode uses the histogram's space)
     unsigned* st_key = reinterpret_cast<unsigned*>(hist) + w * kStage;
@@ -268,8 +299,8 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
     };
     for (int64_t g = g0; g < g1; ++g) {
       if (__any_sync(0xffffffffu, s_err != 0)) break;
-      const int b = ai & 1;
-      if (!wwait(&accfull[b], (uint32_t)((ai >> 1) & 1), lane) || !wwait(&xfull[sx], phx, lane)) {
+      const int b = ai % kAcc;
+      if (!wwait(&accfull[b], (uint32_t)((ai / kAcc) & 1), lane) || !wwait(&xfull[sx], phx, lane)) {
         if (lane == 0) rtimeout(ctl, &s_err);
         break;
       }
@@ -283,27 +314,31 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
       float4* xs = reinterpret_cast<float4*>(sX + sx * kXSlot + (cq >> 1) * kXBox + row * 128);
       float f0 = 0.f, f1 = 0.f;
       if (mode == PASS_CAND) {
-        // pass 1: R back into this thread's own X row segment, candidate columns as a mask
+        // R in registers, the candidate columns as a mask; branch-free: the candidate bit
+        // by select, the non-candidate square by a selected factor (a NaN fails the
+        // compare and reaches the sum)
+        static_assert(kECols == 16, "pick16");
+        float rr[kECols];
         unsigned cm = 0u;
 #pragma unroll
         for (int u = 0; u < kECols / 4; ++u) {
           const float4 x = xs[(f4b + u) ^ sw];
-          float r[4];
           const float xv[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int q = 4 * u + e;
-            r[e] = fmaf(-vl[q], zlo, fmaf(-vh[q], zinv, xv[e]));
-            if (fabsf(r[e]) >= gf) cm |= 1u << q;
-            else if (e & 1) f1 = fmaf(r[e], r[e], f1);
-            else f0 = fmaf(r[e], r[e], f0);
+            rr[q] = fmaf(-vl[q], zlo, fmaf(-vh[q], zinv, xv[e]));
+            const bool cand = fabsf(rr[q]) >= gf;
+            cm |= cand ? (1u << q) : 0u;
+            const float w2 = cand ? 0.f : rr[q];
+            if (e & 1) f1 = fmaf(w2, rr[q], f1);
+            else f0 = fmaf(w2, rr[q], f0);
           }
-          xs[(f4b + u) ^ sw] = make_float4(r[0], r[1], r[2], r[3]);
         }
-        const float* xf = reinterpret_cast<const float*>(xs);
         if (!isfinite(f0 + f1))   // rare: tell a NaN or an infinity from an overflowing sum
-          for (int t = 0; t < kECols; ++t) bad |= rkey(xf[(((f4b + (t >> 2)) ^ sw) << 2) | (t & 3)]) >= 0x7f800000u;
-        // pass 2: the candidates, one per lane and round, in lane order
+#pragma unroll
+          for (int q = 0; q < kECols; ++q) bad |= rkey(rr[q]) >= 0x7f800000u;
+        // the candidates, one per lane and round, in lane order
         const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)__popc(cm));
         if (tot) {
           if (staged + tot > kStage) flush();
@@ -321,6 +356,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
             lim = a.cand_cap > base ? a.cand_cap - base : 0ull;
           }
           const long long rb = (long long)((ib * RM + row) * n + jb * RNC + cq * kECols);
+          const unsigned lt_mask = (1u << lane) - 1u;
           unsigned pos = 0u, mm = cm;
           unsigned bal = __ballot_sync(0xffffffffu, mm != 0u);
           while (bal) {
@@ -328,7 +364,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
               const int q = __ffs(mm) - 1;
               mm &= mm - 1u;
               const unsigned p = pos + __popc(bal & lt_mask);
-              const float v = xf[(((f4b + (q >> 2)) ^ sw) << 2) | (q & 3)];
+              const float v = pick16(rr, q);
               const unsigned key = rkey(v);
               bad |= key >= 0x7f800000u;
               if (p < lim) {
@@ -340,9 +376,9 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
             pos += (unsigned)__popc(bal);
             bal = __ballot_sync(0xffffffffu, mm != 0u);
           }
+          __syncwarp();
           if (tot <= kStage) staged += tot;
         }
-        fence_proxy_async();   // the in-place writes precede the slot's next TMA fill
       } else if (mode == PASS_FULL) {
 #pragma unroll
         for (int u = 0; u < kECols / 4; ++u) {
@@ -377,8 +413,11 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
       if (++sx == NXS) { sx = 0; phx ^= 1u; }
       ++ai;
       if (++jb == nbj) { jb = 0; ++ib; }
-      dsum += (double)(f0 + f1);
+      const float y = (f0 + f1) - scmp, t = ssum + y;
+      scmp = (t - ssum) - y;
+      ssum = t;
     }
+    double dsum = (double)ssum - (double)scmp;
     if (mode == PASS_CAND) flush();
     // sums over the epilogue warps, then one atomic per CTA
 #pragma unroll
@@ -400,7 +439,7 @@ k_resid_tc(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUt
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tbase, 256);
+    tmem_dealloc(tbase, 128 * kAcc);
   }
 }
 
