@@ -255,6 +255,19 @@ godec_status godec_profile(godec_ctx* ctx, int32_t n_iter, double* ms, int64_t* 
                            double* bytes_product);
 
 /*
+ * Self-test of the timeout path.  Every wait of the device pipelines (TMA, tensor-core
+ * and epilogue hand-offs, see GODEC_ERR_TIMEOUT) is bounded: a wait that gives up flags
+ * the context, the kernel drains what it has in flight and returns, and the host call
+ * reports GODEC_ERR_TIMEOUT with the context still usable.  This call runs one such
+ * wait that nothing completes, with `polls` polls of at most ~2 us each (1 .. 1 << 20),
+ * on the context's stream, and reports it through the same path: it returns
+ * GODEC_ERR_TIMEOUT (godec_last_error says which wait), the iteration count and the
+ * factors are unchanged, and the next godec_iterate runs normally.  GODEC_ERR_ARG for
+ * polls out of range.
+ */
+godec_status godec_check_timeout(godec_ctx* ctx, uint32_t polls);
+
+/*
  * The launches of the last iteration that godec_profile ran, in enqueue order:
  * for each (up to cap) its class, whether it ran on the side stream, and its
  * start and end events in milliseconds after the iteration's first event

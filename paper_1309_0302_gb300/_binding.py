@@ -69,6 +69,7 @@ def _declare(lib):
                             C.c_int64, i64p, i32p, f64p], C.c_int),
         "godec_profile": ([_P, C.c_int32, f64p, i64p, f64p], C.c_int),
         "godec_profile_trace": ([_P, C.c_int32, i32p, i32p, f32p, f32p, i32p], C.c_int),
+        "godec_check_timeout": ([_P, C.c_uint32], C.c_int),
         "godec_hard_threshold": ([_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P, _P, C.c_int64, i64p, _P],
                                  C.c_int),
         "godec_mul_ZB": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
@@ -197,6 +198,11 @@ class GoDec:
         it, e = C.c_int32(0), C.c_double(0.0)
         _check(library().godec_solve(self._h, C.byref(it), C.byref(e)), "godec_solve", self._h)
         return it.value, e.value
+
+    def check_timeout(self, polls: int = 1000) -> None:
+        """Run the timeout self-test (godec_check_timeout): raises GodecError with
+        status 5 (GODEC_ERR_TIMEOUT) when the bounded wait gives up, as it must."""
+        _check(library().godec_check_timeout(self._h, C.c_uint32(polls)), "godec_check_timeout", self._h)
 
     def info(self) -> dict:
         inf = GodecInfo()

@@ -876,8 +876,7 @@ godec_status handle_abort(godec_ctx* c, const Ctl& h) {
   if (c->sbits) CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
   if (h.timeout) {
     launch_reset_iter(c->ctl, c->st);
-    return fail(c, GODEC_ERR_TIMEOUT, "a device-side wait of the tensor-core product timed out (iteration %d)",
-                h.iter + 1);
+    return fail(c, GODEC_ERR_TIMEOUT, "a bounded device-side wait gave up (iteration %d)", h.iter + 1);
   }
   if (h.range_err && !h.nonfinite) {
     // Z outgrew its scale in the last S-step; the iteration after it was skipped.
@@ -1254,6 +1253,18 @@ godec_status godec_solve(godec_ctx* c, int32_t* iters, double* rel_err) {
   if (iters) *iters = h.iter;
   if (rel_err) *rel_err = h.rel_err;
   return GODEC_OK;
+}
+
+godec_status godec_check_timeout(godec_ctx* c, uint32_t polls) {
+  if (!c) return GODEC_ERR_ARG;
+  if (polls < 1 || polls > (1u << 20)) return fail(c, GODEC_ERR_ARG, "polls must be in 1 .. 2^20");
+  launch_wait_check(c->ctl, polls, c->st);
+  CK(cudaGetLastError());
+  Ctl h;
+  godec_status s = read_ctl(c, &h);
+  if (s) return s;
+  if (h.abort) return handle_abort(c, h);
+  return fail(c, GODEC_ERR_STATE, "the self-test wait completed, which nothing should make it do");
 }
 
 godec_status godec_profile(godec_ctx* c, int32_t n_iter, double* ms, int64_t* launches,

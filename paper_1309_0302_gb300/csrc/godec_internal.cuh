@@ -298,6 +298,8 @@ void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st);
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);
 // Reset the per-iteration S-step state (after an aborted iteration or at start).
 void launch_reset_iter(Ctl* ctl, cudaStream_t st);
+// One bounded wait that nothing completes; flags ctl->timeout / abort when it gives up.
+void launch_wait_check(Ctl* ctl, uint32_t polls, cudaStream_t st);
 
 // Error text returned by godec_last_error(NULL) for calls without a context.
 void set_static_error(const char* fmt, ...);

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "godec_internal.cuh"
+#include "tc_util.cuh"
 
 namespace godec {
 
@@ -197,7 +198,24 @@ __global__ void k_sort_scatter(const long long* kin, const float* vin, long long
   }
 }
 
+// Self-test of the timeout path: thread 0 waits, with the pipelines' bounded polling
+// helper, on a fresh mbarrier that nothing arrives on, and gives up after `polls` polls
+// (each at most tc::kPollNs) as a pipeline wait does: it flags the context (timeout,
+// abort) and returns.  Nothing is left in flight.
+__global__ void k_wait_check(Ctl* ctl, uint32_t polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  tc::mbar_init(&bar, 1);
+  tc::fence_barrier_init();
+  if (!tc::mbar_wait(&bar, 0u, polls)) {
+    ctl->timeout = 1;
+    ctl->abort = 1;
+  }
+}
+
 }  // namespace
+
+void launch_wait_check(Ctl* ctl, uint32_t polls, cudaStream_t st) { k_wait_check<<<1, 32, 0, st>>>(ctl, polls); }
 
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t st) {
   // bytes must be a multiple of 16 and p 16-byte aligned
