@@ -189,6 +189,8 @@ typedef struct godec_info {
                                  path) power chain; the others used lagged normalisers */
   int32_t svd_sweeps;         /* Jacobi sweeps of the last core SVD */
   int32_t chol_shifts;        /* Cholesky factorisations that needed a diagonal shift */
+  int32_t alarms;             /* fast-path iterations abandoned because a lagged normaliser no
+                                 longer conditioned the chain (each redone on the exact path) */
 } godec_info;
 godec_status godec_get_info(godec_ctx* ctx, godec_info* info);
 

@@ -31,7 +31,7 @@ class GodecInfo(C.Structure):
                 ("obj", C.c_double), ("normX2", C.c_double), ("nnz", C.c_int64),
                 ("select_passes", C.c_int32), ("rank_drops", C.c_int32),
                 ("launches_per_iter", C.c_int32), ("exact_iters", C.c_int32),
-                ("svd_sweeps", C.c_int32), ("chol_shifts", C.c_int32)]
+                ("svd_sweeps", C.c_int32), ("chol_shifts", C.c_int32), ("alarms", C.c_int32)]
 
 
 class GrebsmoParams(C.Structure):

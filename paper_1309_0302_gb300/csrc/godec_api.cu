@@ -122,6 +122,7 @@ struct godec_ctx {
   int backoff = 1;      // exact iterations owed at the next alarm (doubles while alarms repeat)
   int rank_drops = 0;
   int exact_iters = 0;
+  int alarms = 0;          // fast iterations abandoned by a conditioning alarm
   int rescales = 0;
   // kernel-level profiling (eager launches bracketed by events)
   bool prof = false;
@@ -794,6 +795,7 @@ godec_status reset_state(godec_ctx* c) {
   c->exact_left = 0;
   c->backoff = 1;
   c->exact_iters = 0;
+  c->alarms = 0;
   CK(cudaMemcpyAsync(c->A1, c->A1_orig, (size_t)c->p.n * c->RP * sizeof(float), cudaMemcpyDeviceToDevice,
                      c->st));
   launch_split_t(c->A1, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
@@ -897,6 +899,7 @@ godec_status handle_abort(godec_ctx* c, const Ctl& h) {
     if (c->r <= 0) return fail(c, GODEC_ERR_UNSUPPORTED, "rank test found rank 0 (X - S is zero)");
     if ((s = drop_columns(c))) return s;
   } else if (h.alarm) {
+    ++c->alarms;
     // the lagged normalisers no longer condition the chain (its subspaces moved): stay on
     // the exact path for `backoff` iterations, twice as many at each repeated alarm
     c->need_exact = true;
@@ -1350,6 +1353,7 @@ godec_status godec_get_info(godec_ctx* c, godec_info* info) {
   info->exact_iters = c->exact_iters;
   info->svd_sweeps = h.svd_sweeps;
   info->chol_shifts = h.chol_shifts;
+  info->alarms = c->alarms;
   return GODEC_OK;
 }
 
