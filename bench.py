@@ -443,6 +443,7 @@ def form_c4():
     ms_b, ck_b = _timed(st, lambda: b.iterate(20), 10)
     ms_b /= 20
     tun = b.tuning()
+    paths = [b.problem(j).info() for j in range(len(ds))]
     b.close()
     single = 0.0
     cks = []
@@ -459,7 +460,9 @@ def form_c4():
     return {"workload": "64 problems, m, n log-uniform in [256, 4096], r in 2..32, 2-5 % sparse, q = 1",
             "batch": {"ms_per_batch_iter": ms_b, "problem_iterations_per_s": 64e3 / ms_b,
                       "algorithmic_GBps": nbytes / ms_b / 1e6, "policy": tun["policy"],
-                      "policy_ms": tun["policy_ms"], "init_s_with_tuning": t_init, "clocks": ck_b},
+                      "policy_ms": tun["policy_ms"], "init_s_with_tuning": t_init, "clocks": ck_b,
+                      "exact_path_iterations": sum(p_["exact_iters"] for p_ in paths),
+                      "iterations": sum(p_["iter"] for p_ in paths), "alarms": sum(p_["alarms"] for p_ in paths)},
             "one_by_one": {"ms_per_round_of_64": single, "problem_iterations_per_s": 64e3 / single,
                            "clocks": ck_single},
             "speedup_batch_over_one_by_one": single / ms_b}
