@@ -92,6 +92,15 @@ typedef struct godec_params {
    3.5 times slower (about 110 us against 31 us at r = 50); the factor is applied in
    float32 either way. */
 #define GODEC_FLAG_FP64_FACTOR 4
+/* The chain's first projection (X - S) A1 (Algorithm 1's L-step; A1 is fixed for the run)
+   is formed either by streaming X - S like the other products, or as X A1 - S A1 with
+   X A1 computed once per godec_init / godec_reset and S A1 summed over the k entries of
+   S.  The second reads S at random positions, and on GB300 it is the faster one only
+   for sparse S: by default it is used when k <= m n / 256.  These flags force one or the
+   other (both set: GODEC_ERR_ARG).  Plain form only: the precision form, GreBsmo, naive
+   GoDec, LinGoDec and MSE training always stream. */
+#define GODEC_FLAG_SPARSE_FIRST 8
+#define GODEC_FLAG_DENSE_FIRST 16
 
 typedef struct godec_ctx godec_ctx;
 
@@ -248,11 +257,13 @@ godec_status godec_mul_ZtC(const float* Z, int64_t m, int64_t n, int64_t ldz,
  * stream), 6 core SVD and root, 7 residual pass (S-step), 8 selection control,
  * radix-select rounds and S emit, 9 sparse update of X - S and its transpose,
  * 10 the precision form's float32 correction apart from its two streaming
- * products (which count in class 0).
+ * products (which count in class 0), 11 the chain's first projection from the
+ * cached X A1 (X A1 - S A1 over the support of S, in place of the first
+ * streaming product).
  * bytes_product (host, nullable) receives the algorithmic bytes of one
  * streaming product at the current rank: 4*m*n (X - S) + 4*(m + n)*r.
  */
-#define GODEC_PROF_CLASSES 11
+#define GODEC_PROF_CLASSES 12
 godec_status godec_profile(godec_ctx* ctx, int32_t n_iter, double* ms, int64_t* launches,
                            double* bytes_product);
 

@@ -16,6 +16,8 @@ PREC_FP32 = 0
 PREC_BF16_REFINE = 1
 FLAG_NO_REFINE = 2
 FLAG_FP64_FACTOR = 4
+FLAG_SPARSE_FIRST = 8
+FLAG_DENSE_FIRST = 16
 MAX_RANK = 64
 
 
@@ -210,7 +212,7 @@ class GoDec:
         return {f: getattr(inf, f) for f, _ in GodecInfo._fields_}
 
     PROF_CLASSES = ["product", "gram_sum", "chol", "tall_small", "slot_update", "rank_test",
-                    "svd_root", "residual", "select_emit", "z_update", "refine"]
+                    "svd_root", "residual", "select_emit", "z_update", "refine", "sparse_proj"]
 
     def profile(self, n_iter: int):
         """Run n_iter iterations with per-kernel CUDA events; returns per-class totals."""

@@ -108,8 +108,11 @@ struct godec_ctx {
   long long* cand_idx = nullptr;
   float* cand_val = nullptr;
   unsigned long long cap = 0;
-  unsigned* sbits = nullptr;           // m n bits: the support of the S-step in flight (clear between S-steps)
+  unsigned* sbits = nullptr;           // two bitmaps of m n bits: the support of the committed S (bitmap
+  long long sbits_words = 0;           // ctl->cur) and a clear one the next S-step marks its support in
   size_t sbits_bytes = 0;
+  float* XA1 = nullptr;                // m x RP: X A1, the cached part of the first projection (null: the
+                                       // first product streams Z)
   long long* S_idx[2] = {nullptr, nullptr};
   float* S_val[2] = {nullptr, nullptr};
   int idx_bits = 1;
@@ -529,7 +532,21 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
       sl.pi_mode = 0;
       slot(c, sl);
     } else {
-      if (fast) {
+      // the first projection (X - S) A1 = X A1 - S A1 from the cached X A1
+      const bool sp = i == 0 && c->XA1;
+      if (sp)
+        PROF(c, 11, c->st,
+             launch_sproj(c->XA1, c->A1, RP, c->X, c->p.ldx, c->Z, c->ldz, m, n, c->sbits, c->sbits_words, c->ctl,
+                          c->P, c->st));
+      if (fast && sp) {
+        apply(c, c->P, rows, sT(0, i), sT(1, i), nullptr, c->gscr, nextB);
+        fork_side(c);
+        gram_sum(c, c->gscr, 0, apply_blocks(rows), g64(c, i), c->side_st);
+        sl.fast = 1;
+        sl.g64 = g64(c, i);
+        sl.R_app[0] = sR(0, i);
+        sl.R_app[1] = sR(1, i);
+      } else if (fast) {
         // (the lagged normaliser's Gram stays in the tile completion: the side stream runs
         // on the few SMs the product leaves free and has no room for it)
         prod(c, i, nullptr, true, sT(0, i), sT(1, i), 1);
@@ -541,7 +558,8 @@ void enqueue_lstep(godec_ctx* c, bool fast) {
         sl.R_app[1] = sR(1, i);
       } else {
         float* Rt = c->Rtmp + (size_t)i * 2 * rr;
-        prod(c, i, c->P, false, nullptr, nullptr, 1);
+        if (sp) PROF(c, 1, c->st, launch_gram_tiles(c->P, rows, RP, 1, gpart(c, i), c->ctl, c->st));
+        else prod(c, i, c->P, false, nullptr, nullptr, 1);
         gram_sum(c, gpart(c, i), 0, tiles, g64(c, i), c->st);
         chol(c, g64(c, i), Rt);
         apply(c, c->P, rows, inv_of(c, Rt), inv_of(c, Rt), nullptr, nullptr, nextB);
@@ -643,6 +661,7 @@ void enqueue_sstep(godec_ctx* c, int r) {
   ea.zscale = c->ctl->zscale;
   ea.max_nnz = c->p.k;
   ea.sbits = c->sbits;
+  ea.sbits_words = c->sbits_words;
   PROF(c, 8, st, launch_emit(ea, c->nsm, st));
   if (c->Z) PROF(c, 9, st, launch_z_update(ea, c->nsm, st));
 }
@@ -778,7 +797,43 @@ godec_status drop_columns(godec_ctx* c) {
     CK(cudaMemset2DAsync(c->A1 + c->r, c->RP * sizeof(float), 0, (c->RP - c->r) * sizeof(float), c->p.n,
                          c->st));
   launch_split_t(c->A1, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
+  // X A1 loses the same columns (the others keep their split scales, so this is exactly
+  // the product over the new A1)
+  if (c->XA1 && c->r < c->RP)
+    CK(cudaMemset2DAsync(c->XA1 + c->r, c->RP * sizeof(float), 0, (c->RP - c->r) * sizeof(float), c->p.m,
+                         c->st));
   return GODEC_OK;
+}
+
+// Both support bitmaps cleared, then the committed S's support marked again in bitmap
+// ctl->cur (an S-step cut short may have marked entries in the other one).
+godec_status rebuild_sbits(godec_ctx* c) {
+  if (!c->sbits) return GODEC_OK;
+  CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
+  launch_sbits_rebuild(c->sbits, c->sbits_words, c->S_idx, c->ctl, c->p.k, c->st);
+  CK(cudaGetLastError());
+  return GODEC_OK;
+}
+
+// X A1 for the chain's first projection (k_sproj.cu): the tensor-core product over X
+// itself, split at Z's scale s_Z (set from max |X|, so X s_Z stays in the split's range).
+void form_xa1(godec_ctx* c) {
+  TcLaunch l{};
+  l.mapA = c->tmap[5];
+  l.mapB = c->tmap[4];
+  l.rows = c->p.m;
+  l.K = c->p.n;
+  l.RP = c->RP;
+  l.geom = c->tg[0];
+  l.part = c->part;
+  l.counters = c->counters;
+  l.out = c->XA1;
+  l.cscale = c->cs;
+  l.zscale = c->ctl->zscale;
+  l.prescaled = 0;
+  l.pend = c->pend;
+  l.ctl = c->ctl;
+  launch_prod_tc(l, c->st);
 }
 
 // A product that saw the abort flag part-way leaves tile counters behind.
@@ -800,7 +855,6 @@ godec_status reset_state(godec_ctx* c) {
                      c->st));
   launch_split_t(c->A1, c->p.n, c->RP, bt2(c, 2), c->ldb, c->cs, c->st);
   if (godec_status s = clear_counters(c)) return s;
-  if (c->sbits) CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
   std::vector<float> eye((size_t)c->RP * c->RP, 0.f);
   for (int i = 0; i < c->RP; ++i) eye[(size_t)i * c->RP + i] = 1.f;
   CK(cudaMemcpyAsync(c->Vprev, eye.data(), eye.size() * sizeof(float), cudaMemcpyHostToDevice, c->st));
@@ -811,6 +865,7 @@ godec_status reset_state(godec_ctx* c) {
   h.r_eff = c->p.r;
   h.tol = -1.0;
   CK(cudaMemcpyAsync(c->ctl, &h, offsetof(Ctl, hist), cudaMemcpyHostToDevice, c->st));
+  if (godec_status s = rebuild_sbits(c)) return s;   // S = 0: both bitmaps empty
   launch_sumsq(c->X, c->p.m, c->p.n, c->p.ldx,
                reinterpret_cast<double*>(reinterpret_cast<char*>(c->ctl) + offsetof(Ctl, normX2)), c->nsm, c->st);
   // working copies Z = X s_Z and Z^T, with s_Z from max |X|
@@ -818,6 +873,7 @@ godec_status reset_state(godec_ctx* c) {
   launch_scale_copy(c->X, c->p.m, c->p.n, c->p.ldx, c->Z, c->ldz, c->ctl->zscale, c->nsm, c->st);
   launch_transpose(c->X, c->p.m, c->p.n, c->p.ldx, c->Zt, c->ldzt, c->st, c->ctl->zscale);
   refresh_z16(c);
+  if (c->XA1) form_xa1(c);
   launch_reset_iter(c->ctl, c->st);
   if (c->lingo) {
     // the features' basis Qf = orth(F) (F was copied into A1) and its split operand, fixed
@@ -875,7 +931,7 @@ godec_status handle_abort(godec_ctx* c, const Ctl& h) {
   godec_status s;
   if ((s = clear_counters(c))) return s;
   // an S-step cut short may leave support bits behind
-  if (c->sbits) CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
+  if ((s = rebuild_sbits(c))) return s;
   if (h.timeout) {
     launch_reset_iter(c->ctl, c->st);
     return fail(c, GODEC_ERR_TIMEOUT, "a bounded device-side wait gave up (iteration %d)", h.iter + 1);
@@ -988,6 +1044,9 @@ bool bad_params(const godec_params* p, char* why, size_t nwhy) {
   }
   // the S-step's radix histograms count entries in 32 bits
   if ((double)p->m * (double)p->n >= 4294967296.0) { snprintf(why, nwhy, "m*n must be below 2^32"); return true; }
+  if ((p->flags & GODEC_FLAG_SPARSE_FIRST) && (p->flags & GODEC_FLAG_DENSE_FIRST)) {
+    snprintf(why, nwhy, "GODEC_FLAG_SPARSE_FIRST and GODEC_FLAG_DENSE_FIRST exclude each other"); return true;
+  }
   return false;
 }
 
@@ -1017,7 +1076,7 @@ void godec_destroy(godec_ctx* c) {
                   c->U, c->V, c->sigma, c->Um, c->Vm, c->part, c->counters, c->pend, c->gparts, c->RA, c->RB, c->Wa, c->Wb, c->Qa, c->Qb, c->Qtmp, c->Rf,
                   c->cs_ref, c->rf_part, c->rf_g, c->rf_C, c->rf_core, c->rf_U, c->rf_V, c->g64, c->g32, c->gscr,
                   c->Rtmp, c->Rslot, c->Tslot, c->Rfin, c->Pi, c->Vprev, c->ctl, c->cand_key, c->cand_idx,
-                  c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1], c->sbits};
+                  c->cand_val, c->S_idx[0], c->S_idx[1], c->S_val[0], c->S_val[1], c->sbits, c->XA1};
   for (void* p : ptrs) cudaFree(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev)
@@ -1106,6 +1165,14 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
   }
   CKI(dalloc(&c->A1, (size_t)n * RP));
   CKI(dalloc(&c->A1_orig, (size_t)n * RP));
+  // plain GoDec with a given test matrix: its first projection subtracts S A1 from a cached
+  // X A1 when S is sparse enough for that to beat streaming Z (the other forms change A1 or
+  // X between L-steps, or stream a float16 copy of Z).  The cost of S A1 grows with k at
+  // about the rate of random reads from HBM; at m = n = 10^4 it matches the 94 us product
+  // near k = m n / 200 and saves 40 us at k = m n / 1000.
+  const bool sparse_first = (p->flags & GODEC_FLAG_SPARSE_FIRST) ||
+                            (!(p->flags & GODEC_FLAG_DENSE_FIRST) && (double)p->k * 256.0 <= (double)m * (double)n);
+  if (A1 && !greb && !c->naive && !c->lingo && !c->Z16 && sparse_first) CKI(dalloc(&c->XA1, (size_t)m * RP));
   CKI(dalloc(&c->P, (size_t)mx * RP));
   CKI(dalloc(&c->Q1, (size_t)m * RP));
   CKI(dalloc(&c->Q2, (size_t)n * RP));
@@ -1183,7 +1250,8 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
     CKI(dalloc(&c->S_idx[b], (size_t)p->k));
     CKI(dalloc(&c->S_val[b], (size_t)p->k));
   }
-  c->sbits_bytes = (size_t)((mn + 31) / 32) * sizeof(unsigned);
+  c->sbits_words = ((long long)((mn + 31) / 32) + 31) / 32 * 32;   // each bitmap 128-byte aligned
+  c->sbits_bytes = 2 * (size_t)c->sbits_words * sizeof(unsigned);
   CKI(dalloc(reinterpret_cast<char**>(&c->sbits), c->sbits_bytes));
   c->idx_bits = 1;
   while ((1ull << c->idx_bits) < mn) ++c->idx_bits;
@@ -1764,6 +1832,7 @@ static void greb_sstep(godec_ctx* c, int ri, unsigned guess, const float* U, flo
     se.S_val[b] = c->S_val[b];
   }
   se.sbits = c->sbits;
+  se.sbits_words = c->sbits_words;
   se.lambda = lambda;
   launch_emit_soft(se, c->nsm, st);
   EmitArgs ea{};
@@ -1782,6 +1851,7 @@ static void greb_sstep(godec_ctx* c, int ri, unsigned guess, const float* U, flo
   ea.zscale = c->ctl->zscale;
   ea.max_nnz = c->p.k;
   ea.sbits = c->sbits;
+  ea.sbits_words = c->sbits_words;
   launch_z_update(ea, c->nsm, st);
 }
 
@@ -1943,7 +2013,7 @@ godec_status godec_lingodec_iterate(godec_ctx* c, int32_t n_iter, double* rel_er
       if (h.nonfinite) return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - W F^T");
       if (h.abort && h.need_bigger_cand && attempt < 8) {
         if ((s = clear_counters(c))) return s;
-        CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, c->st));
+        if ((s = rebuild_sbits(c))) return s;
         if ((s = greb_grow(c, h, h.cand_count))) return s;
         continue;
       }
@@ -2203,7 +2273,7 @@ godec_status godec_grebsmo_run(godec_ctx* c, int32_t* r_out, double* stage_err, 
         if (h.nonfinite) return fail(c, GODEC_ERR_NONFINITE, "non-finite values in X - U V");
         if (h.abort && h.need_bigger_cand && attempt < 8) {
           if ((s = clear_counters(c))) return s;
-          CK(cudaMemsetAsync(c->sbits, 0, c->sbits_bytes, st));
+          if ((s = rebuild_sbits(c))) return s;
           if ((s = greb_grow(c, h, h.cand_count))) return s;
           continue;
         }

@@ -138,6 +138,14 @@ cudaError_t prepare_stream_kernels();
 void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, float* Q,
                   float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2 = nullptr, int64_t ldb = 0);
 
+// First projection of the chain from the cached X A1 (k_sproj.cu): P = X A1 - S A1 (m x RP,
+// row stride RP; XA1 and A1 likewise), S read on its support (bitmap ctl->cur of sbits,
+// `words` words per bitmap) as X - Z / s_Z; each row's entries are subtracted in column
+// order.  Like the product, it abandons the iteration when Z is flagged out of range.
+void launch_sproj(const float* XA1, const float* A1, int RP, const float* X, int64_t ldx, const float* Z, int64_t ldz,
+                  int64_t m, int64_t n, const unsigned* sbits, long long words, Ctl* ctl, float* P,
+                  cudaStream_t st);
+
 // Tensor-core streaming product (k_tc.cu).
 struct TcGeom {
   int64_t tiles = 0, ks = 0, S = 0;
@@ -291,10 +299,16 @@ struct EmitArgs {
   void* Zt16;
   const float* zscale;     // Z and Zt are stored scaled by zscale[0]
   long long max_nnz;       // bound on the support of S (k): the z-update grid
-  unsigned* sbits;         // m n bits, all clear between S-steps: the emit marks Omega_t so the
-                           // restore of Omega_{t-1} skips entries the scatter rewrites anyway
+  unsigned* sbits;         // two bitmaps of m n bits (nullable), sbits_words words apart: bitmap
+  long long sbits_words;   // `cur` holds the support of the committed S, the other one is clear.
+                           // The emit marks Omega_t in the clear one, the restore of Omega_{t-1}
+                           // skips the entries marked there and clears the old bitmap.
 };
 void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st);
+// The support bitmap of the committed S (bitmap ctl->cur) from its index list, after both
+// bitmaps were cleared (an S-step cut short may leave bits behind).
+void launch_sbits_rebuild(unsigned* sbits, long long words, long long* const S_idx[2], const Ctl* ctl,
+                          long long max_nnz, cudaStream_t st);
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st);
 // Reset the per-iteration S-step state (after an aborted iteration or at start).
 void launch_reset_iter(Ctl* ctl, cudaStream_t st);
@@ -348,7 +362,8 @@ struct SoftEmitArgs {
   long long s_cap;         // entries the S buffers hold
   long long* S_idx[2];
   float* S_val[2];
-  unsigned* sbits;
+  unsigned* sbits;         // as in EmitArgs
+  long long sbits_words;
   float lambda;
 };
 void launch_soft_plan(Ctl* ctl, unsigned guess, cudaStream_t st);

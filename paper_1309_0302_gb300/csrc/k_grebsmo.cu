@@ -40,13 +40,14 @@ __global__ void __launch_bounds__(SOFT_THREADS) k_emit_soft(SoftEmitArgs a) {
   const int nb = ctl->cur ^ 1;
   long long* Sidx = a.S_idx[nb];
   float* Sval = a.S_val[nb];
+  unsigned* bits = a.sbits ? a.sbits + (size_t)nb * (size_t)a.sbits_words : nullptr;   // clear until now
   for (unsigned long long e = (unsigned long long)blockIdx.x * SOFT_THREADS + threadIdx.x; e < cnt;
        e += (unsigned long long)gridDim.x * SOFT_THREADS) {
     const long long idx = a.cand_idx[e];
     const float v = a.cand_val[e];
     Sidx[e] = idx;
     Sval[e] = v - copysignf(a.lambda, v);   // sgn(R) (|R| - lambda), |R| > lambda
-    if (a.sbits) atomicOr(&a.sbits[idx >> 5], 1u << (idx & 31));
+    if (bits) atomicOr(&bits[idx >> 5], 1u << (idx & 31));
   }
   __threadfence();
   __shared__ unsigned s_last;

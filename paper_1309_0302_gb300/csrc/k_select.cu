@@ -435,6 +435,7 @@ k_emit(EmitArgs a) {
   const unsigned long long cut = ctl->idx_cut;
   long long* Sidx = a.S_idx[nb];
   float* Sval = a.S_val[nb];
+  unsigned* bits = a.sbits ? a.sbits + (size_t)nb * (size_t)a.sbits_words : nullptr;   // clear until now
   double dsum = 0.0;
   const unsigned long long tile = (unsigned long long)EMIT_THREADS * EMIT_ITEMS;
   __shared__ unsigned long long s_base;
@@ -465,7 +466,7 @@ k_emit(EmitArgs a) {
           const long long idx = a.cand_idx[c];
           Sidx[pos] = idx;
           Sval[pos] = a.cand_val[c];
-          if (a.sbits) atomicOr(&a.sbits[idx >> 5], 1u << (idx & 31));
+          if (bits) atomicOr(&bits[idx >> 5], 1u << (idx & 31));
         }
         ++pos;
       }
@@ -577,27 +578,31 @@ __device__ __forceinline__ void split_idx(long long idx, long long n, float ninv
 __device__ __forceinline__ bool z_skip(const Ctl* ctl) { return ctl->abort && !ctl->converged; }
 
 // Entries of Omega_{t-1} that left the support get Z = X back; those still in Omega_t
-// (their bit set by the emit) are left to the scatter, which writes them anyway.
+// (their bit set by the emit) are left to the scatter, which writes them anyway.  The
+// bitmap of Omega_{t-1} is cleared on the way (every set bit of it belongs to an entry
+// of Omega_{t-1}, so each such entry simply zeroes its word).
 __global__ void k_z_restore(EmitArgs a) {
   Ctl* ctl = a.ctl;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (z_skip(ctl) || (long long)blockIdx.x * blockDim.x >= ctl->nnz_prev) return;
   const long long nnz = ctl->nnz_prev;
   const float zs = a.zscale ? a.zscale[0] : 1.f;
+  const int cb = ctl->cur;
   bool bad = false;
   if (e < nnz) {
-    const long long idx = a.S_idx[ctl->cur ^ 1][e];
-    if (!a.sbits || !((__ldcg(&a.sbits[idx >> 5]) >> (idx & 31)) & 1u)) {
+    const long long idx = a.S_idx[cb ^ 1][e];
+    const unsigned* now = a.sbits ? a.sbits + (size_t)cb * (size_t)a.sbits_words : nullptr;
+    if (!now || !((__ldcg(&now[idx >> 5]) >> (idx & 31)) & 1u)) {
       long long i, j;
       split_idx(idx, a.n, 1.f / (float)a.n, i, j);
       z_write(a, i, j, a.X[i * a.ldx + j], zs, bad);
     }
+    if (a.sbits) a.sbits[(size_t)(cb ^ 1) * (size_t)a.sbits_words + (size_t)(idx >> 5)] = 0u;
   }
   z_flag(ctl, bad);
 }
 
-// Z = X - S_t on Omega_t; clears the support bits again (every set bit of a word belongs
-// to Omega_t, so the word is simply zeroed).
+// Z = X - S_t on Omega_t.
 __global__ void k_z_scatter(EmitArgs a) {
   Ctl* ctl = a.ctl;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -611,9 +616,16 @@ __global__ void k_z_scatter(EmitArgs a) {
     long long i, j;
     split_idx(idx, a.n, 1.f / (float)a.n, i, j);
     z_write(a, i, j, a.X[i * a.ldx + j] - a.S_val[cb][e], zs, bad);
-    if (a.sbits) a.sbits[idx >> 5] = 0u;
   }
   z_flag(ctl, bad);
+}
+
+__global__ void k_sbits_rebuild(unsigned* sbits, long long words, long long* S0, long long* S1, const Ctl* ctl) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cb = ctl->cur;
+  if (e >= ctl->nnz_cur) return;
+  const long long idx = (cb ? S1 : S0)[e];
+  atomicOr(&sbits[(size_t)cb * (size_t)words + (size_t)(idx >> 5)], 1u << (idx & 31));
 }
 
 // Per-iteration S-step state back to "start of an iteration" (one thread).
@@ -675,6 +687,12 @@ void launch_select_round(const SelectArgs& a, int nsm, cudaStream_t st) {
 
 void launch_emit(const EmitArgs& a, int nsm, cudaStream_t st) {
   k_emit<<<(unsigned)(2 * nsm), EMIT_THREADS, 0, st>>>(a);
+}
+
+void launch_sbits_rebuild(unsigned* sbits, long long words, long long* const S_idx[2], const Ctl* ctl,
+                          long long max_nnz, cudaStream_t st) {
+  const long long nb = (max_nnz + 255) / 256;
+  k_sbits_rebuild<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, st>>>(sbits, words, S_idx[0], S_idx[1], ctl);
 }
 
 void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st) {

@@ -25,6 +25,11 @@ def test_status_strings_and_bad_args_without_gpu():
     p = g._binding.GodecParams(m=10, n=10, ldx=10, r=2, q=0, k=5, tol=1e-7, max_iter=5)
     assert lib.godec_init(ctypes.byref(h), ctypes.byref(p), None, None, None) == 1   # ldx*4 % 16
     assert h.value is None
+    # the two first-projection flags exclude each other
+    p = g._binding.GodecParams(m=10, n=12, ldx=12, r=2, q=0, k=5, tol=1e-7, max_iter=5,
+                               flags=g.FLAG_SPARSE_FIRST | g.FLAG_DENSE_FIRST)
+    assert lib.godec_init(ctypes.byref(h), ctypes.byref(p), None, None, None) == 1
+    assert b"exclude each other" in lib.godec_last_error(None)
 
 
 def _header_arity():
