@@ -577,44 +577,36 @@ __device__ __forceinline__ void split_idx(long long idx, long long n, float ninv
 // stop the iterations after it), so Z always matches the committed S.
 __device__ __forceinline__ bool z_skip(const Ctl* ctl) { return ctl->abort && !ctl->converged; }
 
-// Entries of Omega_{t-1} that left the support get Z = X back; those still in Omega_t
-// (their bit set by the emit) are left to the scatter, which writes them anyway.  The
-// bitmap of Omega_{t-1} is cleared on the way (every set bit of it belongs to an entry
-// of Omega_{t-1}, so each such entry simply zeroes its word).
-__global__ void k_z_restore(EmitArgs a) {
+// The update of Z (and its copies) from S_{t-1} to S_t, one launch: entries of Omega_{t-1}
+// that left the support get Z = X back, and Z = X - S_t on Omega_t.  The two sets are
+// disjoint (the restore skips every entry the emit marked in the bitmap of Omega_t), so
+// thread e does entry e of both lists.  The bitmap of Omega_{t-1} is cleared on the way
+// (every set bit of it belongs to an entry of Omega_{t-1}, so each such entry simply
+// zeroes its word).
+__global__ void k_z_update(EmitArgs a) {
   Ctl* ctl = a.ctl;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (z_skip(ctl) || (long long)blockIdx.x * blockDim.x >= ctl->nnz_prev) return;
-  const long long nnz = ctl->nnz_prev;
+  if (z_skip(ctl)) return;
+  const long long np = ctl->nnz_prev, nc = ctl->nnz_cur;
+  if ((long long)blockIdx.x * blockDim.x >= (np > nc ? np : nc)) return;
   const float zs = a.zscale ? a.zscale[0] : 1.f;
+  const float ninv = 1.f / (float)a.n;
   const int cb = ctl->cur;
   bool bad = false;
-  if (e < nnz) {
+  if (e < np) {
     const long long idx = a.S_idx[cb ^ 1][e];
     const unsigned* now = a.sbits ? a.sbits + (size_t)cb * (size_t)a.sbits_words : nullptr;
     if (!now || !((__ldcg(&now[idx >> 5]) >> (idx & 31)) & 1u)) {
       long long i, j;
-      split_idx(idx, a.n, 1.f / (float)a.n, i, j);
+      split_idx(idx, a.n, ninv, i, j);
       z_write(a, i, j, a.X[i * a.ldx + j], zs, bad);
     }
     if (a.sbits) a.sbits[(size_t)(cb ^ 1) * (size_t)a.sbits_words + (size_t)(idx >> 5)] = 0u;
   }
-  z_flag(ctl, bad);
-}
-
-// Z = X - S_t on Omega_t.
-__global__ void k_z_scatter(EmitArgs a) {
-  Ctl* ctl = a.ctl;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (z_skip(ctl) || (long long)blockIdx.x * blockDim.x >= ctl->nnz_cur) return;
-  const int cb = ctl->cur;
-  const long long nnz = ctl->nnz_cur;
-  const float zs = a.zscale ? a.zscale[0] : 1.f;
-  bool bad = false;
-  if (e < nnz) {
+  if (e < nc) {
     const long long idx = a.S_idx[cb][e];
     long long i, j;
-    split_idx(idx, a.n, 1.f / (float)a.n, i, j);
+    split_idx(idx, a.n, ninv, i, j);
     z_write(a, i, j, a.X[i * a.ldx + j] - a.S_val[cb][e], zs, bad);
   }
   z_flag(ctl, bad);
@@ -699,8 +691,7 @@ void launch_z_update(const EmitArgs& a, int nsm, cudaStream_t st) {
   (void)nsm;
   const long long nb = (a.max_nnz + 255) / 256;
   const unsigned grid = (unsigned)(nb > 0 ? nb : 1);
-  k_z_restore<<<grid, 256, 0, st>>>(a);
-  k_z_scatter<<<grid, 256, 0, st>>>(a);
+  k_z_update<<<grid, 256, 0, st>>>(a);
 }
 
 }  // namespace godec
