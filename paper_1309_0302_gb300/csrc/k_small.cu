@@ -26,32 +26,39 @@ constexpr int SMALL_THREADS = 256;   // 16 x 16 threads, each owning a 4 x 4 blo
 constexpr int LD = kMaxRP + 1;
 
 // ---- Gram sums over row tiles --------------------------------------------------------
-// Block = 32 entries x 8 tile strides: each thread sums every 8th partial of one entry
-// (independent loads in flight), the 8 partial sums are added in a fixed order.
-constexpr int GS_ENT = 32, GS_SPLIT = 8;
-template <typename T>
-__global__ void __launch_bounds__(GS_ENT * GS_SPLIT)
+// Block = E entries x (NT / E) tile strides: each thread sums every (NT / E)-th partial of
+// one entry in four independent chains, and the block adds the strides' sums by a fixed
+// tree, so the order is fixed for given (nblk, E, NT).  Few entries (small r) take a
+// small E and large blocks, so that many threads share the partials of each entry.
+template <typename T, int E, int NT>
+__global__ void __launch_bounds__(NT)
 k_gram_sum(const T* __restrict__ part, int64_t nblk, int npair, double* __restrict__ out, float* __restrict__ out32,
            const Ctl* ctl) {
   if (ctl && ctl->abort) return;
-  __shared__ double red[GS_SPLIT][GS_ENT];
-  const int lane = threadIdx.x % GS_ENT, sp = threadIdx.x / GS_ENT;
-  const int e = blockIdx.x * GS_ENT + lane;
-  double s0 = 0.0, s1 = 0.0;
+  constexpr int SPLIT = NT / E;
+  __shared__ double red[SPLIT][E];
+  const int lane = threadIdx.x % E, sp = threadIdx.x / E;
+  const int e = blockIdx.x * E + lane;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   if (e < npair) {
     int64_t b = sp;
-    for (; b + GS_SPLIT < nblk; b += 2 * GS_SPLIT) {
+    for (; b + 3 * SPLIT < nblk; b += 4 * SPLIT) {
       s0 += (double)part[b * npair + e];
-      s1 += (double)part[(b + GS_SPLIT) * npair + e];
+      s1 += (double)part[(b + SPLIT) * npair + e];
+      s2 += (double)part[(b + 2 * SPLIT) * npair + e];
+      s3 += (double)part[(b + 3 * SPLIT) * npair + e];
     }
-    if (b < nblk) s0 += (double)part[b * npair + e];
+    for (; b < nblk; b += SPLIT) s0 += (double)part[b * npair + e];
   }
-  red[sp][lane] = s0 + s1;
+  red[sp][lane] = (s0 + s1) + (s2 + s3);
   __syncthreads();
-  if (sp == 0 && e < npair) {
-    double t = 0.0;
 #pragma unroll
-    for (int k = 0; k < GS_SPLIT; ++k) t += red[k][lane];
+  for (int h = SPLIT / 2; h >= 1; h >>= 1) {
+    if (sp < h) red[sp][lane] += red[sp + h][lane];
+    __syncthreads();
+  }
+  if (sp == 0 && e < npair) {
+    const double t = red[0][lane];
     out[e] = t;
     if (out32) out32[e] = (float)t;   // the float copy: its reader then needs no float64 work
   }
@@ -973,13 +980,24 @@ cudaError_t prepare_small_kernels() {
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
                      cudaStream_t st, float* out32) {
   const int npair = RP * RP;
-  const unsigned grid = (unsigned)((npair + GS_ENT - 1) / GS_ENT);
-  if (gram_double)
-    k_gram_sum<double><<<grid, GS_ENT * GS_SPLIT, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out,
-                                                            out32, ctl);
-  else
-    k_gram_sum<float><<<grid, GS_ENT * GS_SPLIT, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out,
-                                                           out32, ctl);
+  // many entries (r > 44): 32 per block of 256 threads; few: 8 per block of 1024
+  if (npair >= 2048) {
+    const unsigned grid = (unsigned)((npair + 31) / 32);
+    if (gram_double)
+      k_gram_sum<double, 32, 256><<<grid, 256, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out,
+                                                        out32, ctl);
+    else
+      k_gram_sum<float, 32, 256><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out, out32,
+                                                       ctl);
+  } else {
+    const unsigned grid = (unsigned)((npair + 7) / 8);
+    if (gram_double)
+      k_gram_sum<double, 8, 1024><<<grid, 1024, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out,
+                                                         out32, ctl);
+    else
+      k_gram_sum<float, 8, 1024><<<grid, 1024, 0, st>>>(reinterpret_cast<const float*>(part), nblk, npair, out,
+                                                        out32, ctl);
+  }
 }
 
 void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,

@@ -287,7 +287,8 @@ cudaError_t prepare_prod_t() {
 // ----------------------------------------------------------------------------------
 // Q = P T (T dense RP x RP; a triangular inverse is passed as a dense matrix), for
 // rows x RP row-major P.  64 rows per block; thread (g, c) keeps column c of T in registers
-// and forms Q[i][c] for the rows i = g mod 4 of the block, reading each row of P as float4
+// and forms Q[i][c] for the rows i = g mod (256 / RPc) of the block (RPc = RP rounded up
+// to 16, 32 or 64), reading each row of P as float4
 // broadcasts (one shared-memory wavefront per four fmas of the warp; staging T per thread
 // row instead re-reads it for every row and leaves the kernel bound by shared memory).
 // The block's rows are staged in shared memory before any output is written, so P and Q
@@ -296,22 +297,26 @@ cudaError_t prepare_prod_t() {
 // ----------------------------------------------------------------------------------
 constexpr int RB = 64;              // rows per block
 constexpr int AP_THREADS = 256;
-constexpr int AP_PLD = kMaxRP + 4;  // P rows: float4-aligned (read as broadcasts)
 constexpr int AP_OLD = kMaxRP + 1;  // T, then the output rows: odd stride, column reads conflict-free
 
+// RPc: RP rounded up to 16, 32 or 64 (thread (g, c): column c < RPc of rows g + (256 / RPc) k).
+template <int RPc>
 __global__ void __launch_bounds__(AP_THREADS)
 k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, const float* __restrict__ T1, float* Q,
         float* __restrict__ gram_part, const Ctl* ctl, void* __restrict__ bt2, int64_t ldb) {
+  constexpr int PLD = RPc + 4;                 // P rows: float4-aligned (read as broadcasts)
+  constexpr int NG = AP_THREADS / RPc;         // row groups
+  constexpr int RPT = RB / NG;                 // rows per thread
   if (ctl && ctl->abort) return;
   const float* T = (ctl && ctl->slot_parity) ? T1 : T0;
   __shared__ float Ts[kMaxRP * AP_OLD];   // T, then the output rows
-  __shared__ __align__(16) float Ps[RB * AP_PLD];
+  __shared__ __align__(16) float Ps[RB * PLD];
   const int tid = threadIdx.x;
   const int64_t r0 = (int64_t)blockIdx.x * RB;
   const int nrow = (int)(rows - r0 < RB ? rows - r0 : RB);
   // Every load is issued before the first store (T and the block's rows as float4s: RP is
   // a multiple of 8), so the block waits for one memory round trip, not one per element.
-  constexpr int kT4 = kMaxRP * kMaxRP / 4 / AP_THREADS, kP4 = RB * kMaxRP / 4 / AP_THREADS;
+  constexpr int kT4 = (RPc * RPc / 4 + AP_THREADS - 1) / AP_THREADS, kP4 = RB * RPc / 4 / AP_THREADS;
   const int RP4 = RP / 4, nT4 = RP * RP4, nP4 = nrow * RP4;
   const float4* T4 = reinterpret_cast<const float4*>(T);
   const float4* P4 = reinterpret_cast<const float4*>(P + r0 * RP);
@@ -326,7 +331,7 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
     const int e = tid + k * AP_THREADS;
     pv[k] = e < nP4 ? __ldcg(P4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  // T rows and P rows into shared memory; P's columns RP .. kMaxRP-1 and rows past nrow zero
+  // T rows and P rows into shared memory; P's columns RP .. RPc-1 and rows past nrow zero
 #pragma unroll
   for (int k = 0; k < kT4; ++k) {
     const int e = tid + k * AP_THREADS;
@@ -341,24 +346,24 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
 #pragma unroll
   for (int k = 0; k < kP4; ++k) {
     const int e = tid + k * AP_THREADS;   // float4 e of the block's rows (row e / RP4)
-    if (e < RB * RP4) *reinterpret_cast<float4*>(Ps + (e / RP4) * AP_PLD + (e % RP4) * 4) = pv[k];
+    if (e < RB * RP4) *reinterpret_cast<float4*>(Ps + (e / RP4) * PLD + (e % RP4) * 4) = pv[k];
   }
-  const int pad4 = kMaxRP / 4 - RP4;
+  const int pad4 = RPc / 4 - RP4;
   for (int e = tid; e < RB * pad4; e += AP_THREADS)
-    *reinterpret_cast<float4*>(Ps + (e / pad4) * AP_PLD + (RP4 + e % pad4) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(Ps + (e / pad4) * PLD + (RP4 + e % pad4) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
-  const int c = tid & 63, g = tid >> 6;
-  float tcol[kMaxRP];
+  const int c = tid % RPc, g = tid / RPc;
+  float tcol[RPc];
 #pragma unroll
-  for (int a = 0; a < kMaxRP; ++a) tcol[a] = (a < RP && c < RP) ? Ts[a * AP_OLD + c] : 0.f;
-  float acc[RB / 4];
+  for (int a = 0; a < RPc; ++a) tcol[a] = (a < RP && c < RP) ? Ts[a * AP_OLD + c] : 0.f;
+  float acc[RPT];
 #pragma unroll
-  for (int k = 0; k < RB / 4; ++k) acc[k] = 0.f;
+  for (int k = 0; k < RPT; ++k) acc[k] = 0.f;
 #pragma unroll
-  for (int a = 0; a < kMaxRP; a += 4) {
+  for (int a = 0; a < RPc; a += 4) {
 #pragma unroll
-    for (int k = 0; k < RB / 4; ++k) {
-      const float4 p = *reinterpret_cast<const float4*>(Ps + (g + 4 * k) * AP_PLD + a);
+    for (int k = 0; k < RPT; ++k) {
+      const float4 p = *reinterpret_cast<const float4*>(Ps + (g + NG * k) * PLD + a);
       acc[k] = fmaf(p.x, tcol[a], acc[k]);
       acc[k] = fmaf(p.y, tcol[a + 1], acc[k]);
       acc[k] = fmaf(p.z, tcol[a + 2], acc[k]);
@@ -369,7 +374,7 @@ k_apply(const float* P, int64_t rows, int RP, const float* __restrict__ T0, cons
   float* Os = Ts;
   if (c < RP)
 #pragma unroll
-    for (int k = 0; k < RB / 4; ++k) Os[(g + 4 * k) * AP_OLD + c] = acc[k];
+    for (int k = 0; k < RPT; ++k) Os[(g + NG * k) * AP_OLD + c] = acc[k];
   __syncthreads();
   if (Q)
     for (int e = tid; e < nrow * RP; e += AP_THREADS) {
@@ -452,7 +457,10 @@ int64_t apply_blocks(int64_t rows) { return (rows + RB - 1) / RB; }
 
 void launch_apply(const float* P, int64_t rows, int RP, const float* T0, const float* T1, float* Q,
                   float* gram_part, const Ctl* ctl, cudaStream_t st, void* bt2, int64_t ldb) {
-  k_apply<<<(unsigned)apply_blocks(rows), AP_THREADS, 0, st>>>(P, rows, RP, T0, T1, Q, gram_part, ctl, bt2, ldb);
+  const unsigned grid = (unsigned)apply_blocks(rows);
+  if (RP <= 16) k_apply<16><<<grid, AP_THREADS, 0, st>>>(P, rows, RP, T0, T1, Q, gram_part, ctl, bt2, ldb);
+  else if (RP <= 32) k_apply<32><<<grid, AP_THREADS, 0, st>>>(P, rows, RP, T0, T1, Q, gram_part, ctl, bt2, ldb);
+  else k_apply<64><<<grid, AP_THREADS, 0, st>>>(P, rows, RP, T0, T1, Q, gram_part, ctl, bt2, ldb);
 }
 
 }  // namespace godec
