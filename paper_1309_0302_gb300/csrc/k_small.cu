@@ -316,12 +316,86 @@ __device__ __forceinline__ void chol_reg_core(float (&V)[kRowsPT], int n, int nc
   __syncthreads();
 }
 
+// The same elimination of [G | I] by one warp, the matrix in registers: lane l holds
+// columns l and l + 32 (all rows, RPc of them), G's column until its step, then E's (the
+// registers of column j become E's column j at step j).  Step j: the pivot d = G[j][j] and
+// the multipliers l_i = G[j][i] / d (row j of the columns i > j; G stays symmetric) are
+// broadcast by shuffles, row j of U and E is stored, and every column takes
+// x_i -= l_i x_j for i > j, column j itself becoming -l_i.  No block barrier: the steps
+// are unrolled (RPc = RP rounded up to 16, 32 or 64; the padded block of G is the
+// identity), so every register index is static.  Pivots j < nchk at or below thr are
+// raised to thr and reported through *bad.
+// Step j of chol_warp_core; the steps are instantiated one by one, so that every register
+// index is a compile-time constant.
+template <int RPc, int NS, int j>
+__device__ __forceinline__ void chol_warp_step(float (&V)[NS][RPc], int lane, int nchk, float thr, int& badl, float* dv,
+                                               float (*Us)[LD], float (*Es)[LD]) {
+  if constexpr (j < RPc) {
+    const unsigned full = 0xffffffffu;
+    float d = __shfl_sync(full, V[j >> 5][j], j & 31);
+    if (j < nchk && !(d > thr)) {
+      d = thr > 0.f ? thr : 1e-30f;
+      badl = 1;
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int c = lane + 32 * s;
+      if (c < RPc) {
+        const float v = V[s][j];
+        Us[j][c] = c >= j ? v : 0.f;
+        Es[j][c] = c < j ? v : (c == j ? 1.f : 0.f);
+      }
+    }
+    if (lane == 0) dv[j] = d;
+    const float inv = 1.f / d;
+    const bool own = lane == (j & 31);   // this lane holds column j (in slot j >> 5)
+#pragma unroll
+    for (int i = j + 1; i < RPc; ++i) {
+      const float li = __shfl_sync(full, V[i >> 5][j], i & 31) * inv;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const float upd = fmaf(-li, V[s][j], V[s][i]);
+        V[s][i] = (s == (j >> 5) && own) ? -li : upd;
+      }
+    }
+    chol_warp_step<RPc, NS, j + 1>(V, lane, nchk, thr, badl, dv, Us, Es);
+  }
+}
+
+// The same elimination of [G | I] by one warp, the matrix in registers: lane l holds
+// columns l and l + 32 (all rows, RPc of them), G's column until its step, then E's (the
+// registers of column j become E's column j at step j).  Step j: the pivot d = G[j][j] and
+// the multipliers l_i = G[j][i] / d (row j of the columns i > j; G stays symmetric) are
+// broadcast by shuffles, row j of U and E is stored, and every column takes
+// x_i -= l_i x_j for i > j, column j itself becoming -l_i.  No block barrier
+// (RPc = RP rounded up to 16, 32 or 64; the padded block of G is the identity).  Pivots
+// j < nchk at or below thr are raised to thr and reported through *bad.
+template <int RPc>
+__device__ __forceinline__ void chol_warp_core(const float (*G)[LD], float shift, int nchk, float thr, int* bad,
+                                               float* dv, float (*Us)[LD], float (*Es)[LD]) {
+  constexpr int NS = RPc > 32 ? 2 : 1;
+  const int lane = threadIdx.x & 31;
+  float V[NS][RPc];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int c = lane + 32 * s;
+#pragma unroll
+    for (int i = 0; i < RPc; ++i) V[s][i] = c < RPc ? G[i][c] + ((i == c && i < nchk) ? shift : 0.f) : 0.f;
+  }
+  int badl = 0;
+  chol_warp_step<RPc, NS, 0>(V, lane, nchk, thr, badl, dv, Us, Es);
+  if (lane == 0 && badl) *bad = 1;
+}
+
 // Cholesky with a shifted fallback: pivots below 1e-6 of the largest diagonal mean a
 // numerically rank-deficient chain (Z of rank < r before the rank test lowers r); the
 // factorisation is then redone on G + 1e-5 max(diag) I, which keeps Q bounded.  G (64 x 64,
 // padded block the identity) is kept; on return Us / Es hold U and E (chol_reg_core) and
 // dv the pivots used: R[a][c] = Us[a][c] / sqrt(dv[a]) (c > a), R[a][a] = sqrt(dv[a]),
 // R^{-1}[i][c] = Es[c][i] / sqrt(dv[c]) (c >= i).
+// WARP: RP <= 32, the one-warp elimination (instantiated apart, so that the kernels for
+// larger RP do not carry its code).
+template <bool WARP>
 __device__ __forceinline__ void robust_chol(const float (*G)[LD], float (*Us)[LD], float (*Es)[LD], float* dv, int r,
                                             int RP, Ctl* ctl) {
   __shared__ float s_gmax;
@@ -334,17 +408,27 @@ __device__ __forceinline__ void robust_chol(const float (*G)[LD], float (*Us)[LD
     if (tid == 0) s_gmax = gm;
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
-    __syncthreads();
-    const float shift = attempt == 1 ? 1e-5f * s_gmax : 0.f;
-    float V[kRowsPT];
-#pragma unroll
-    for (int k = 0; k < kRowsPT; ++k) {
-      const int a = rw + 4 * k;
-      V[k] = G[a][cc] + ((a == cc && a < r) ? shift : 0.f);
-    }
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    chol_reg_core(V, RP, r, 1e-6f * s_gmax, &s_bad, dv, Us, Es);
+    const float shift = attempt == 1 ? 1e-5f * s_gmax : 0.f;
+    const float thr = 1e-6f * s_gmax;
+    if constexpr (WARP) {
+      // one warp, the matrix in registers (a fully unrolled elimination; above 32 columns
+      // its straight-line code outgrows the instruction cache and the block version wins)
+      if (tid < 32) {
+        if (RP <= 16) chol_warp_core<16>(G, shift, r, thr, &s_bad, dv, Us, Es);
+        else chol_warp_core<32>(G, shift, r, thr, &s_bad, dv, Us, Es);
+      }
+      __syncthreads();
+    } else {
+      float V[kRowsPT];
+#pragma unroll
+      for (int k = 0; k < kRowsPT; ++k) {
+        const int a = rw + 4 * k;
+        V[k] = G[a][cc] + ((a == cc && a < r) ? shift : 0.f);
+      }
+      chol_reg_core(V, RP, r, thr, &s_bad, dv, Us, Es);
+    }
     if (!s_bad) break;
     if (tid == 0) ctl->chol_shifts += 1;
   }
@@ -408,7 +492,7 @@ __device__ void chol64(double (*Gd)[LD], float (*R)[LD], int r, int RP, double t
 // sent back to the exact path (alarm).
 // F64: the factorisation runs in float64 (chol64) instead of the blocked float32 Cholesky;
 // either way R and T = R^{-1} are stored in float32 and T is formed in float32.
-template <bool F64>
+template <bool F64, bool WARP>
 __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict__ g64, const float* __restrict__ g32,
                                                         int r, int RP,
                                                         float* __restrict__ Rout, float* __restrict__ Tout,
@@ -429,7 +513,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_chol(const double* __restrict
       return;
     }
     (void)E;
-    robust_chol(G, R, Ri, dv, r, RP, ctl);   // U into R's block, E into Ri's
+    robust_chol<WARP>(G, R, Ri, dv, r, RP, ctl);   // U into R's block, E into Ri's
   } else {
   double (*Gd)[LD] = reinterpret_cast<double (*)[LD]>(smf);            // 2 float blocks
   __shared__ double s_gmax;
@@ -528,6 +612,7 @@ struct SlotArgs {
   Ctl* ctl;
 };
 
+template <bool WARP>
 __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
   Ctl* ctl = a.ctl;
   if (ctl->abort) return;
@@ -577,7 +662,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_slot(SlotArgs a) {
       __syncthreads();
     }
     __shared__ float dv[kMaxRP];
-    robust_chol(A, C, D, dv, r, RP, ctl);            // U into C, E into D (scratch)
+    robust_chol<WARP>(A, C, D, dv, r, RP, ctl);            // U into C, E into D (scratch)
     for (int e = threadIdx.x; e < kMaxRP * kMaxRP; e += SMALL_THREADS) {   // C = R~, in place
       const int i = e / kMaxRP, c = e % kMaxRP;
       float v = 0.f;
@@ -969,9 +1054,13 @@ constexpr size_t kSmall8 = 8 * kMaxRP * LD * sizeof(float);
 }  // namespace
 
 cudaError_t prepare_small_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_chol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall8);
+  cudaError_t e = cudaFuncSetAttribute(k_chol<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_chol<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall8);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slot<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall8);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmall4);
   return e;
@@ -1002,8 +1091,9 @@ void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, do
 
 void launch_chol(const double* g64, int r, int RP, float* R, float* T, Ctl* ctl, cudaStream_t st,
                  float alarm_ratio, bool fp64, const float* g32) {
-  if (fp64) k_chol<true><<<1, SMALL_THREADS, kSmall4, st>>>(g64, nullptr, r, RP, R, T, alarm_ratio, ctl);
-  else k_chol<false><<<1, SMALL_THREADS, kSmall4, st>>>(g64, g32, r, RP, R, T, alarm_ratio, ctl);
+  if (fp64) k_chol<true, false><<<1, SMALL_THREADS, kSmall4, st>>>(g64, nullptr, r, RP, R, T, alarm_ratio, ctl);
+  else if (RP <= 32) k_chol<false, true><<<1, SMALL_THREADS, kSmall4, st>>>(g64, g32, r, RP, R, T, alarm_ratio, ctl);
+  else k_chol<false, false><<<1, SMALL_THREADS, kSmall4, st>>>(g64, g32, r, RP, R, T, alarm_ratio, ctl);
 }
 
 void launch_slot(const SlotLaunch& l, cudaStream_t st) {
@@ -1026,7 +1116,8 @@ void launch_slot(const SlotLaunch& l, cudaStream_t st) {
   a.RP = l.RP;
   a.alarm_ratio = l.alarm_ratio;
   a.ctl = l.ctl;
-  k_slot<<<1, SMALL_THREADS, kSmall8, st>>>(a);
+  if (l.RP <= 32) k_slot<true><<<1, SMALL_THREADS, kSmall8, st>>>(a);
+  else k_slot<false><<<1, SMALL_THREADS, kSmall8, st>>>(a);
 }
 
 void launch_rank(const double* g64, int r, int RP, double rank_tol, Ctl* ctl, cudaStream_t st) {
