@@ -1069,8 +1069,9 @@ cudaError_t prepare_small_kernels() {
 void launch_gram_sum(const void* part, int gram_double, int64_t nblk, int RP, double* out, const Ctl* ctl,
                      cudaStream_t st, float* out32) {
   const int npair = RP * RP;
-  // many entries (r > 44): 32 per block of 256 threads; few: 8 per block of 1024
-  if (npair >= 2048) {
+  // 32 entries per block of 256 threads (8 partials in flight per entry), unless there are
+  // few entries and many partials (small r over a tall matrix): then 8 per block of 1024
+  if (npair >= 2048 || nblk < 256) {
     const unsigned grid = (unsigned)((npair + 31) / 32);
     if (gram_double)
       k_gram_sum<double, 32, 256><<<grid, 256, 0, st>>>(reinterpret_cast<const double*>(part), nblk, npair, out,
