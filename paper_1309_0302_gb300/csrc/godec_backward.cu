@@ -14,8 +14,9 @@
 //
 // The forward sweep recomputes and checkpoints the per-iteration factors (A2, Y2, Y2p,
 // Q, Z Y2p and L_t on Omega_t; Q an orthonormal basis of range(Y2) from CholeskyQR2);
-// the backward sweep rebuilds Z_t from X and the checkpointed
-// values.  Streaming products with Z_t and Z_t^T run on the tensor-core product kernel
+// the backward sweep reuses Z_t and Z_t^T kept from the forward sweep when all T of them
+// fit in a quarter of the free device memory, and otherwise rebuilds them from X and the
+// checkpointed values.  Streaming products with Z_t and Z_t^T run on the tensor-core product kernel
 // (float32 accuracy); the r x r solve is the Cholesky kernel of the L-step.
 #include <algorithm>
 #include <cstdio>
@@ -149,9 +150,18 @@ extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int
   const int RP = (r + 7) / 8 * 8, R3 = 3 * r;
   const int64_t mx = std::max(m, n), ldz = (n + 63) / 64 * 64, ldzt = (m + 63) / 64 * 64;
   Scratch sc{st};
-  // iterates, products' scratch
-  float* Z = sc.get<float>((size_t)m * ldz);
-  float* Zt = sc.get<float>((size_t)n * ldzt);
+  // Iterates Z_t and Z_t^T: one copy each for all t, rebuilt in the backward sweep, or (when
+  // all T of them fit in a quarter of the free device memory) one per t, kept from the
+  // forward sweep, which saves the backward sweep's copy, scatter, transpose and scale.
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+  const bool keep = (double)T * (double)(m * ldz + n * ldzt) * sizeof(float) <= 0.25 * (double)free_b;
+  const int nzb = keep ? T : 1;
+  std::vector<float*> Zb(nzb), Ztb(nzb);
+  for (int b = 0; b < nzb; ++b) {
+    Zb[b] = sc.get<float>((size_t)m * ldz);
+    Ztb[b] = sc.get<float>((size_t)n * ldzt);
+  }
   float* Gt = gL ? sc.get<float>((size_t)n * ldzt) : nullptr;      // dense gradient transposed
   Engine E;
   E.st = st;
@@ -162,9 +172,10 @@ extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int
   E.Bp = sc.get<float>((size_t)mx * RP);
   E.cscale = sc.get<float>(RP);
   E.Yp = sc.get<float>((size_t)mx * RP);
-  float* zsc = sc.get<float>(8);             // {s, 1/s} of Z_t, then of the dense gradient
-  unsigned* zmax = sc.get<unsigned>(4);
-  Source sZ, sZt, sG, sGt;
+  float* zsc = sc.get<float>(2 * (size_t)nzb + 2);     // {s, 1/s} of each Z_t copy, then of the dense gradient
+  unsigned* zmax = sc.get<unsigned>((size_t)nzb + 1);
+  std::vector<Source> sZs(nzb), sZts(nzb);
+  Source sG, sGt;
   // per-iteration checkpoints (forward sweep)
   std::vector<float*> A2(T), Y2(T), Y2p(T), Qk(T), ZY2p(T), Lv(T);
   for (int t = 0; t < T; ++t) {
@@ -190,11 +201,10 @@ extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int
   double* cpart = sc.get<double>((size_t)kCrossParts * GODEC_MAX_RANK * GODEC_MAX_RANK);
   Ctl* ctl = sc.get<Ctl>(1);
   if (sc.ok) {
-    sZ.geom = tc_geometry(m, n, nsm);
-    sZt.geom = tc_geometry(n, m, nsm);
+    const TcGeom gz = tc_geometry(m, n, nsm), gzt = tc_geometry(n, m, nsm);
     size_t npart = 0, npend = 0;
     int64_t tiles = 0;
-    for (const TcGeom& g : {sZ.geom, sZt.geom}) {
+    for (const TcGeom& g : {gz, gzt}) {
       npart = std::max(npart, (size_t)g.tiles * g.maxseg * 128 * RP);
       npend = std::max(npend, (size_t)g.G * g.maxpend);
       tiles = std::max(tiles, g.tiles);
@@ -207,32 +217,38 @@ extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int
     set_static_error("godec_backward: out of device memory");
     return GODEC_ERR_OOM;
   }
-  cudaMemsetAsync(E.cnt, 0, (size_t)std::max(sZ.geom.tiles, sZt.geom.tiles) * sizeof(unsigned), st);
+  cudaMemsetAsync(E.cnt, 0, (size_t)std::max(tc_geometry(m, n, nsm).tiles, tc_geometry(n, m, nsm).tiles) * sizeof(unsigned), st);
   cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
   E.Kb[0] = n;
   E.Kb[1] = m;
-  bool mapped = setup_source(sZ, Z, m, n, ldz, nsm, zsc, zmax) && setup_source(sZt, Zt, n, m, ldzt, nsm, zsc, zmax) &&
-                make_tmap_f16(E.mapB[0], E.Bs, 2 * RP, n, E.ldb, 2 * RP) &&
+  bool mapped = make_tmap_f16(E.mapB[0], E.Bs, 2 * RP, n, E.ldb, 2 * RP) &&
                 make_tmap_f16(E.mapB[1], E.Bs, 2 * RP, m, E.ldb, 2 * RP);
+  for (int b = 0; b < nzb; ++b)
+    mapped = mapped && setup_source(sZs[b], Zb[b], m, n, ldz, nsm, zsc + 2 * b, zmax + b) &&
+             setup_source(sZts[b], Ztb[b], n, m, ldzt, nsm, zsc + 2 * b, zmax + b);
   if (gL) {
-    mapped = mapped && setup_source(sG, gL, m, n, ldg, nsm, zsc + 2, zmax + 1) &&
-             setup_source(sGt, Gt, n, m, ldzt, nsm, zsc + 2, zmax + 1);
+    mapped = mapped && setup_source(sG, gL, m, n, ldg, nsm, zsc + 2 * nzb, zmax + nzb) &&
+             setup_source(sGt, Gt, n, m, ldzt, nsm, zsc + 2 * nzb, zmax + nzb);
   }
   if (!mapped) {
     set_static_error("godec_backward: tensor map encoding failed");
     return GODEC_ERR_CUDA;
   }
   const size_t rowb = sizeof(float);
-  // Z_t = X with L_{t-1} on Omega_{t-1}; Z_t^T; the shared scale of both
+  // Z_t = X with L_{t-1} on Omega_{t-1}; Z_t^T; the shared scale of both (copy slot b)
   auto build_Z = [&](int t) {
+    const int b = keep ? t : 0;
+    float *Z = Zb[b], *Zt = Ztb[b];
     cudaMemcpy2DAsync(Z, ldz * rowb, X, ldx * rowb, n * rowb, m, cudaMemcpyDeviceToDevice, st);
     if (t > 0 && support_nnz[t - 1] > 0) launch_scatter_set(supports[t - 1], Lv[t - 1], support_nnz[t - 1], n, Z, ldz, st);
     launch_transpose(Z, m, n, ldz, Zt, ldzt, st);
-    launch_zscale(Z, m, n, ldz, zmax, zsc, nsm, st);
+    launch_zscale(Z, m, n, ldz, zmax + b, zsc + 2 * b, nsm, st);
   };
   // ---------------- forward sweep: checkpoints ----------------
   for (int t = 0; t < T; ++t) {
     build_Z(t);
+    const Source& sZ = sZs[keep ? t : 0];
+    const Source& sZt = sZts[keep ? t : 0];
     E.mul(sZ, A1, r, A2[t]);                                   // A2 = Z A1
     E.mul(sZt, A2[t], r, Y2[t]);                               // Y2 = Z^T A2
     // Y2 = Q R by CholeskyQR2 (R = R2 R1), so that W = (Y2^T Y2)^{-1} = R^{-1} R^{-T} and
@@ -254,10 +270,12 @@ extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int
   // ---------------- backward sweep ----------------
   if (gL) {
     launch_transpose(gL, m, n, ldg, Gt, ldzt, st);
-    launch_zscale(gL, m, n, ldg, zmax + 1, zsc + 2, nsm, st);
+    launch_zscale(gL, m, n, ldg, zmax + nzb, zsc + 2 * nzb, nsm, st);
   }
   for (int t = T - 1; t >= 0; --t) {
-    build_Z(t);
+    if (!keep) build_Z(t);
+    const Source& sZ = sZs[keep ? t : 0];
+    const Source& sZt = sZts[keep ? t : 0];
     // a = G Y2p and Wn = b = G^T (Z Y2p)
     if (t == T - 1 && gL) {
       E.mul(sG, Y2p[t], r, a);

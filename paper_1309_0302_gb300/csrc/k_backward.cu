@@ -133,52 +133,72 @@ __global__ void k_scatter_set(const int64_t* __restrict__ idx, const float* __re
   Z[row * ldz + col] = vals[e];
 }
 
-// D (m x n) = beta D + U V^T, U m x K (ldu), V n x K (ldv), K <= 192: 64 x 64 output
-// tiles, 256 threads each owning a 4 x 4 block, K in chunks of 32 through shared memory.
+// D (m x n) = beta D + U V^T, U m x K (ldu), V n x K (ldv), K <= 192: 128 x 128 output
+// tiles, 256 threads each owning an 8 x 8 block (rows ty*4 + {0..3} and 64 + ty*4 + {0..3},
+// the same for columns with tx), read from shared memory as float4s (four loads per 64
+// fmas), K in chunks of 32 through shared memory; D read and written as float4s when its
+// rows allow (ldd and the pointer 16-byte aligned), else element by element.
+constexpr int OA_T = 128, OA_KC = 32, OA_LD = OA_T + 4;
 __global__ void __launch_bounds__(BW_THREADS)
 k_outer_acc(const float* __restrict__ U, int64_t ldu, const float* __restrict__ V, int64_t ldv, int K, int64_t m,
             int64_t n, float beta, float* __restrict__ D, int64_t ldd) {
-  constexpr int TM = 64, KC = 32;
-  __shared__ float sU[KC][TM + 1], sV[KC][TM + 1];
+  __shared__ __align__(16) float sU[OA_KC][OA_LD];
+  __shared__ __align__(16) float sV[OA_KC][OA_LD];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  const int64_t i0 = (int64_t)blockIdx.y * TM, j0 = (int64_t)blockIdx.x * TM;
-  float acc[4][4];
+  const int64_t i0 = (int64_t)blockIdx.y * OA_T, j0 = (int64_t)blockIdx.x * OA_T;
+  float acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < 8; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += OA_KC) {
     __syncthreads();
-    for (int e = tid; e < KC * TM; e += BW_THREADS) {
-      const int rr = e / KC, kk = e % KC;   // consecutive threads along k: rows of U / V are contiguous
+    for (int e = tid; e < OA_KC * OA_T; e += BW_THREADS) {
+      const int rr = e / OA_KC, kk = e % OA_KC;   // consecutive threads along k: rows of U / V are contiguous
       const int64_t gi = i0 + rr, gj = j0 + rr;
       sU[kk][rr] = (gi < m && k0 + kk < K) ? U[gi * ldu + k0 + kk] : 0.f;
       sV[kk][rr] = (gj < n && k0 + kk < K) ? V[gj * ldv + k0 + kk] : 0.f;
     }
     __syncthreads();
+    const int kc = (K - k0 < OA_KC) ? K - k0 : OA_KC;
 #pragma unroll 4
-    for (int kk = 0; kk < KC; ++kk) {
-      float u[4], v[4];
+    for (int kk = 0; kk < kc; ++kk) {
+      const float4 u0 = *reinterpret_cast<const float4*>(&sU[kk][ty * 4]);
+      const float4 u1 = *reinterpret_cast<const float4*>(&sU[kk][64 + ty * 4]);
+      const float4 v0 = *reinterpret_cast<const float4*>(&sV[kk][tx * 4]);
+      const float4 v1 = *reinterpret_cast<const float4*>(&sV[kk][64 + tx * 4]);
+      const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-      for (int a = 0; a < 4; ++a) u[a] = sU[kk][ty + 16 * a];
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) v[b] = sV[kk][tx + 16 * b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(u[a], v[b], acc[a][b]);
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(u[a], v[b], acc[a][b]);
     }
   }
+  const bool vec = ((ldd & 3) == 0) && ((reinterpret_cast<uintptr_t>(D) & 15) == 0);
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t gi = i0 + ty + 16 * a;
+  for (int a = 0; a < 8; ++a) {
+    const int64_t gi = i0 + (a < 4 ? ty * 4 + a : 64 + ty * 4 + a - 4);
     if (gi >= m) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int64_t gj = j0 + tx + 16 * b;
-      if (gj < n) {
-        float* d = D + gi * ldd + gj;
-        *d = (beta != 0.f ? beta * *d : 0.f) + acc[a][b];
+    for (int h = 0; h < 2; ++h) {
+      const int64_t gj = j0 + h * 64 + tx * 4;
+      float* d = D + gi * ldd + gj;
+      const float* ac = &acc[a][4 * h];
+      if (vec && gj + 3 < n) {
+        float4 o = make_float4(ac[0], ac[1], ac[2], ac[3]);
+        if (beta != 0.f) {
+          const float4 p = *reinterpret_cast<const float4*>(d);
+          o.x = fmaf(beta, p.x, o.x);
+          o.y = fmaf(beta, p.y, o.y);
+          o.z = fmaf(beta, p.z, o.z);
+          o.w = fmaf(beta, p.w, o.w);
+        }
+        *reinterpret_cast<float4*>(d) = o;
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (gj + b < n) d[b] = (beta != 0.f ? beta * d[b] : 0.f) + ac[b];
       }
     }
   }
@@ -244,7 +264,7 @@ void launch_axpy(const float* x, float* y, int64_t count, float alpha, cudaStrea
 
 void launch_outer_acc(const float* U, int64_t ldu, const float* V, int64_t ldv, int K, int64_t m, int64_t n,
                       float beta, float* D, int64_t ldd, cudaStream_t st) {
-  dim3 grid((unsigned)((n + 63) / 64), (unsigned)((m + 63) / 64));
+  dim3 grid((unsigned)((n + OA_T - 1) / OA_T), (unsigned)((m + OA_T - 1) / OA_T));
   k_outer_acc<<<grid, BW_THREADS, 0, st>>>(U, ldu, V, ldv, K, m, n, beta, D, ldd);
 }
 
