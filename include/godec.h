@@ -305,8 +305,13 @@ godec_status godec_profile_trace(godec_ctx* ctx, int32_t cap, int32_t* cls, int3
  *              meaning gU gV^T; or gL (device, m x ldg float32, ldg*4 a multiple of
  *              16 bytes).  The unused pointers are null.
  *   dX       : device, m x lddx float32, overwritten with the gradient
+ *   flags    : 0 or GODEC_BACKWARD_REBUILD
  * The per-iteration factors are recomputed in a forward sweep (checkpointed for the
- * backward sweep), so only the supports are needed from the forward run.  Scratch is
+ * backward sweep), so only the supports are needed from the forward run.  The iterates
+ * Z_t and Z_t^T of the forward sweep are kept for the backward sweep when all T of them
+ * fit in a quarter of the free device memory (2 T m n floats); with
+ * GODEC_BACKWARD_REBUILD, or when they do not fit, one copy is kept and rebuilt from X
+ * and the checkpoints in the backward sweep (slower, 2 m n floats).  Scratch is
  * allocated and freed on `stream` (stream-ordered); the call does not synchronise.
  * Float32 arithmetic with the float32-accurate tensor-core products; the sparse products
  * accumulate with float atomics (results may differ in the last bits between runs).
@@ -315,7 +320,8 @@ godec_status godec_profile_trace(godec_ctx* ctx, int32_t cap, int32_t* cls, int3
 godec_status godec_backward(const float* X, int64_t m, int64_t n, int64_t ldx, const float* A1, int32_t r,
                             int32_t T, const int64_t* const* supports, const int64_t* support_nnz,
                             const float* gU, const float* gV, int32_t g_rank, const float* gL, int64_t ldg,
-                            float* dX, int64_t lddx, void* stream);
+                            float* dX, int64_t lddx, int32_t flags, void* stream);
+#define GODEC_BACKWARD_REBUILD 1
 
 /*
  * Entry-wise hard threshold of a dense matrix (eq. raw_lss, the S-step of

@@ -76,7 +76,7 @@ def _declare(lib):
                                  C.c_int),
         "godec_mul_ZB": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
         "godec_backward": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, C.c_int32, C.POINTER(_P), i64p,
-                            _P, _P, C.c_int32, _P, C.c_int64, _P, C.c_int64, _P], C.c_int),
+                            _P, _P, C.c_int32, _P, C.c_int64, _P, C.c_int64, C.c_int32, _P], C.c_int),
         "godec_mul_ZtC": ([_P, C.c_int64, C.c_int64, C.c_int64, _P, C.c_int32, _P, _P], C.c_int),
         "godec_batch_init": ([C.POINTER(_P), C.c_int32, C.POINTER(GodecParams), C.POINTER(_P), C.POINTER(_P),
                               C.c_int32, _P], C.c_int),
@@ -497,12 +497,14 @@ def mul_ZtC(Z, Cm, stream=None):
     return _mul("godec_mul_ZtC", Z, Cm, stream)
 
 
-def backward(X, A1, T: int, supports, gU=None, gV=None, gL=None, stream=None):
+def backward(X, A1, T: int, supports, gU=None, gV=None, gL=None, stream=None, rebuild: bool = False):
     """dLoss/dX of T unrolled q = 0 iterations with frozen supports (godec_backward).
 
     X (m, n) and A1 (n, r) CUDA float32; ``supports`` the T-1 int64 CUDA tensors of
     linear indices of Omega_1 .. Omega_{T-1}; dLoss/dL_T as gU (m, g) and gV (n, g)
-    (meaning gU gV^T) or dense gL (m, n).  Returns dX (m, n).
+    (meaning gU gV^T) or dense gL (m, n).  ``rebuild``: recompute the iterates in the
+    backward sweep instead of keeping them (GODEC_BACKWARD_REBUILD: less memory, slower).
+    Returns dX (m, n).
     """
     torch = _torch()
     m, n = X.shape
@@ -527,7 +529,7 @@ def backward(X, A1, T: int, supports, gU=None, gV=None, gL=None, stream=None):
         gU, gV = gU.contiguous(), gV.contiguous()
         args = (_ptr(gU), _ptr(gV), gU.shape[1], None, 0)
     st = library().godec_backward(_ptr(X), m, n, X.stride(0), _ptr(A1), r, int(T), ptrs, nnz, *args,
-                                  _ptr(dXp), dXp.stride(0), _stream_ptr(stream))
+                                  _ptr(dXp), dXp.stride(0), 1 if rebuild else 0, _stream_ptr(stream))
     _check(st, "godec_backward")
     return dXp[:, :n]
 

@@ -126,12 +126,12 @@ bool setup_source(Source& s, const float* p, int64_t rows, int64_t K, int64_t ld
 extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int64_t ldx, const float* A1, int32_t r,
                                        int32_t T, const int64_t* const* supports, const int64_t* support_nnz,
                                        const float* gU, const float* gV, int32_t g_rank, const float* gL, int64_t ldg,
-                                       float* dX, int64_t lddx, void* stream) {
+                                       float* dX, int64_t lddx, int32_t flags, void* stream) {
   const bool lowrank = gU && gV;
   if (!X || !A1 || !dX || m < 1 || n < 1 || ldx < n || lddx < n || r < 1 || r > GODEC_MAX_RANK || r > m ||
       r > n || T < 1 || (T > 1 && (!supports || !support_nnz)) || lowrank == (gL != nullptr) ||
       (lowrank && (g_rank < 1 || g_rank > GODEC_MAX_RANK)) || (gL && ldg < n) || (ldx * 4) % 16 != 0 ||
-      (gL && (ldg * 4) % 16 != 0)) {
+      (gL && (ldg * 4) % 16 != 0) || (flags & ~GODEC_BACKWARD_REBUILD)) {
     set_static_error("godec_backward: invalid argument");
     return GODEC_ERR_ARG;
   }
@@ -155,7 +155,8 @@ extern "C" godec_status godec_backward(const float* X, int64_t m, int64_t n, int
   // forward sweep, which saves the backward sweep's copy, scatter, transpose and scale.
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
-  const bool keep = (double)T * (double)(m * ldz + n * ldzt) * sizeof(float) <= 0.25 * (double)free_b;
+  const bool keep = !(flags & GODEC_BACKWARD_REBUILD) &&
+                    (double)T * (double)(m * ldz + n * ldzt) * sizeof(float) <= 0.25 * (double)free_b;
   const int nzb = keep ? T : 1;
   std::vector<float*> Zb(nzb), Ztb(nzb);
   for (int b = 0; b < nzb; ++b) {

@@ -143,6 +143,32 @@ def test_backward_rejects_bad_arguments():
         G.backward(X, A1, 1, [], gU=gU.double(), gV=gU.double())
 
 
+@pytest.mark.parametrize("dense", [False, True])
+def test_backward_rebuilt_iterates_match_kept(dense):
+    """GODEC_BACKWARD_REBUILD (the iterates rebuilt in the backward sweep from X and the
+    checkpoints) gives the gradient of the default, which keeps them from the forward sweep;
+    only the float atomics of the sparse products may differ in the last bits."""
+    torch = pytest.importorskip("torch")
+    import paper_1309_0302_gb300 as G
+    d, X, A1, Us, Vs = _case(300, 257, 6, 0.02, 6, 4, 5)
+    r, k, T = d["r"], d["k"], 4
+    gpu = G.GoDec(X, A1, r, k, 0, tol=0.0, max_iter=T)
+    sup = []
+    for t in range(T):
+        gpu.iterate(1)
+        if t < T - 1:
+            sup.append(gpu.S()[0].clone())
+    U, s, V = gpu.L()
+    gpu.close()
+    gU = torch.cat([2.0 * U * s, -2.0 * torch.from_numpy(Us).float().cuda()], 1).contiguous()
+    gV = torch.cat([V, torch.from_numpy(Vs).float().cuda()], 1).contiguous()
+    kw = {"gL": (gU @ gV.T).contiguous()} if dense else {"gU": gU, "gV": gV}
+    kept = G.backward(X, A1, T, sup, **kw).cpu().numpy().astype(np.float64)
+    rebuilt = G.backward(X, A1, T, sup, rebuild=True, **kw).cpu().numpy().astype(np.float64)
+    assert np.isfinite(kept).all() and np.abs(kept).max() > 0
+    assert _rel(rebuilt, kept) <= 1e-5
+
+
 @pytest.mark.slow
 def test_backward_c5_full_size():
     """C5 (4096 x 4096, r = 20, k = 2 %, q = 0, T = 10, loss ||L_T - L*||^2 with a rank-20
