@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the C1/C3/C4/C5 timing records")
     ap.add_argument("--kernel", choices=["product", "product_t", "iteration", "backward", "precision", "batched", "c1",
-                                         "grebsmo", "naive", "lingodec", "mse"], default=None,
+                                         "grebsmo", "naive", "lingodec", "mse", "first_projection"], default=None,
                     help="profiling aid: run one kernel family on a small case and exit (no JSON line)")
     ap.add_argument("--size", type=int, default=8192)
     return ap.parse_args()
@@ -286,7 +286,7 @@ def run_gb300(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_forms:
         line["forms"] = {"c1": form_c1(), "c3_precision": form_c3(), "c4_batched": form_c4(),
                          "c5_differentiated": form_c5(), "grebsmo": form_grebsmo(), "naive": form_naive(),
-                         "lingodec": form_lingodec(), "mse": form_mse()}
+                         "lingodec": form_lingodec(), "mse": form_mse(), "first_projection": form_first_projection()}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, times, cores = oracle_steps(d["X"], d["A1"], BASELINE_ITERS, 0)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -560,6 +560,36 @@ def form_naive():
             "rel_err_after_16_iterations": rel, "clocks": ck}
 
 
+def form_first_projection():
+    """The chain's first projection (X - S) A1 both ways on the 10000 x 10000, r = 50, q = 2
+    shape with a sparser S (k = 10^5, 0.1 %): streamed over Z like the other products
+    (GODEC_FLAG_DENSE_FIRST), or X A1 - S A1 from the cached X A1 (GODEC_FLAG_SPARSE_FIRST,
+    the default at this density).  Whole iterations, CUDA events, same input; the counts of
+    alarms and exact-path iterations say how many of the timed iterations were redone."""
+    import torch
+
+    import paper_1309_0302_gb300 as G
+    import synth
+    k = 100000
+    d = synth.lowrank_sparse(M, N, R, k, -20.0, 20.0, 1e-2, replica_seed(0), "c2_sparse")
+    X, A1 = torch.from_numpy(d["X"]).cuda(), torch.from_numpy(d["A1"]).cuda()
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, flags in (("sparse", G.FLAG_SPARSE_FIRST), ("dense", G.FLAG_DENSE_FIRST)):
+        g = G.GoDec(X, A1, R, k, Q, tol=-1.0, max_iter=1 << 30, flags=flags)
+        g.iterate(6)
+        ms, ck = _timed(st, lambda: g.iterate(10), 3)
+        ms /= 10
+        info = g.info()
+        out[name] = {"ms_per_iter": ms, "iterations_per_s": 1e3 / ms, "rel_err": info["rel_err"],
+                     "alarms": info["alarms"], "exact_path_iterations": info["exact_iters"],
+                     "iterations": info["iter"], "clocks": ck}
+        g.close()
+    return {"workload": "10000 x 10000, rank 50, k = 1e5 (0.1 %) U[-20, 20], noise 1e-2; r = 50, q = 2",
+            "sparse_first": out["sparse"], "dense_first": out["dense"],
+            "speedup_sparse_over_dense": out["dense"]["ms_per_iter"] / out["sparse"]["ms_per_iter"]}
+
+
 def form_lingodec():
     """LinGoDec (Sec. 4.3) on the paper's synthetic recipe at 20000 users x 5000 items,
     d = 50 item features, rank 10, 5 % +-1 outliers: iterations/s."""
@@ -638,9 +668,11 @@ def run_kernel_case(args):
         f = G.mul_ZB if args.kernel == "product" else G.mul_ZtC
         for _ in range(3):
             f(Z, B)
-    elif args.kernel in ("backward", "precision", "batched", "c1", "grebsmo", "naive", "lingodec", "mse"):
+    elif args.kernel in ("backward", "precision", "batched", "c1", "grebsmo", "naive", "lingodec", "mse",
+                         "first_projection"):
         f = {"backward": form_c5, "precision": form_c3, "batched": form_c4, "c1": form_c1, "grebsmo": form_grebsmo,
-             "naive": form_naive, "lingodec": form_lingodec, "mse": form_mse}[args.kernel]
+             "naive": form_naive, "lingodec": form_lingodec, "mse": form_mse,
+             "first_projection": form_first_projection}[args.kernel]
         print(json.dumps(f(), indent=1))
     else:
         d = synth.small_case(n, n, R, 0.01, R, Q, tag="kernel_case")
