@@ -612,6 +612,8 @@ __global__ void k_z_update(EmitArgs a) {
   z_flag(ctl, bad);
 }
 
+// The support bitmap of the committed S (bitmap ctl->cur) from its index list, one entry
+// per thread; both bitmaps were cleared before (after an S-step cut short).
 __global__ void k_sbits_rebuild(unsigned* sbits, long long words, long long* S0, long long* S1, const Ctl* ctl) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int cb = ctl->cur;
