@@ -563,8 +563,8 @@ def form_naive():
 def form_first_projection():
     """The chain's first projection (X - S) A1 both ways on the 10000 x 10000, r = 50, q = 2
     shape with a sparser S (k = 10^5, 0.1 %): streamed over Z like the other products
-    (GODEC_FLAG_DENSE_FIRST), or X A1 - S A1 from the cached X A1 (GODEC_FLAG_SPARSE_FIRST,
-    the default at this density).  Whole iterations, CUDA events, same input; the counts of
+    (GODEC_FLAG_DENSE_FIRST, the default), or X A1 - S A1 from the cached X A1
+    (GODEC_FLAG_SPARSE_FIRST).  Whole iterations, CUDA events, same input; the counts of
     alarms and exact-path iterations say how many of the timed iterations were redone."""
     import torch
 

@@ -93,12 +93,14 @@ typedef struct godec_params {
    float32 either way. */
 #define GODEC_FLAG_FP64_FACTOR 4
 /* The chain's first projection (X - S) A1 (Algorithm 1's L-step; A1 is fixed for the run)
-   is formed either by streaming X - S like the other products, or as X A1 - S A1 with
-   X A1 computed once per godec_init / godec_reset and S A1 summed over the k entries of
-   S.  The second reads S at random positions, and on GB300 it is the faster one only
-   for sparse S: by default it is used when k <= m n / 256.  These flags force one or the
-   other (both set: GODEC_ERR_ARG).  Plain form only: the precision form, GreBsmo, naive
-   GoDec, LinGoDec and MSE training always stream. */
+   is formed either by streaming X - S like the other products (the default,
+   GODEC_FLAG_DENSE_FIRST), or, with GODEC_FLAG_SPARSE_FIRST, as X A1 - S A1 with X A1
+   computed once per godec_init / godec_reset and S A1 summed over the k entries of S.
+   The second reads S at random positions: on GB300 its kernel is faster only for sparse
+   S (k below about m n / 200), and over whole iterations its rounding made the lagged
+   normalisers' alarm trip more often on the inputs measured.  Both flags set:
+   GODEC_ERR_ARG.  Plain form only: the precision form, GreBsmo, naive GoDec, LinGoDec and
+   MSE training always stream. */
 #define GODEC_FLAG_SPARSE_FIRST 8
 #define GODEC_FLAG_DENSE_FIRST 16
 

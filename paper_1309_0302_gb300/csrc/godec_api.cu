@@ -1165,13 +1165,14 @@ static godec_status init_ctx(godec_ctx** out, const godec_params* p, const float
   }
   CKI(dalloc(&c->A1, (size_t)n * RP));
   CKI(dalloc(&c->A1_orig, (size_t)n * RP));
-  // plain GoDec with a given test matrix: its first projection subtracts S A1 from a cached
-  // X A1 when S is sparse enough for that to beat streaming Z (the other forms change A1 or
-  // X between L-steps, or stream a float16 copy of Z).  The cost of S A1 grows with k at
-  // about the rate of random reads from HBM; at m = n = 10^4 it matches the 94 us product
-  // near k = m n / 200 and saves 40 us at k = m n / 1000.
-  const bool sparse_first = (p->flags & GODEC_FLAG_SPARSE_FIRST) ||
-                            (!(p->flags & GODEC_FLAG_DENSE_FIRST) && (double)p->k * 256.0 <= (double)m * (double)n);
+  // plain GoDec with a given test matrix, on request: its first projection subtracts S A1
+  // from a cached X A1 (the other forms change A1 or X between L-steps, or stream a float16
+  // copy of Z).  The cost of S A1 grows with k at about the rate of random reads from HBM;
+  // at m = n = 10^4 it matches the 94 us product near k = m n / 200 and saves 40 us at
+  // k = m n / 1000, but over whole iterations at k = m n / 1000 the lagged normalisers'
+  // alarm trips more often with it (8 against 2 in 36 iterations), which costs more than
+  // it saves, so streaming stays the default.
+  const bool sparse_first = (p->flags & GODEC_FLAG_SPARSE_FIRST) != 0;
   if (A1 && !greb && !c->naive && !c->lingo && !c->Z16 && sparse_first) CKI(dalloc(&c->XA1, (size_t)m * RP));
   CKI(dalloc(&c->P, (size_t)mx * RP));
   CKI(dalloc(&c->Q1, (size_t)m * RP));

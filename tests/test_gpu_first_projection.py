@@ -104,13 +104,13 @@ def test_sparse_first_bitwise_deterministic():
         assert np.array_equal(a, b)
 
 
-def test_default_way_follows_density():
-    """Without a flag the cached X A1 is used for k <= m n / 256 and Z is streamed above:
-    the default run is bitwise the forced run of the same way."""
-    for dens, way in [(0.002, "sparse"), (0.02, "dense")]:
+def test_default_way_is_streamed():
+    """Without a flag the first projection streams Z at any density: the default run is
+    bitwise the run with GODEC_FLAG_DENSE_FIRST."""
+    for dens in (0.002, 0.02):
         d = synth.small_case(500, 400, 5, dens, 5, 1, tag=f"fp_def_{dens}")
         outs = []
-        for flags in (0, _flags()[way]):
+        for flags in (0, _flags()["dense"]):
             run = GpuRun(d, flags=flags)
             run.g.iterate(3)
             outs.append(run.factors32() + run.sparse())
